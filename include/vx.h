@@ -1,0 +1,212 @@
+/*
+ * vx.h - C ABI of the GB300 voxel lattice soft-body simulator.
+ *
+ * The simulator is the heterogeneous voxel lattice of Hiller & Lipson,
+ * "Dynamic Simulation of Soft Heterogeneous Objects" (arXiv 1212.2845):
+ * adjacent voxels are joined by Euler-Bernoulli beam bonds with composite
+ * material properties (Sec 2.1.1-2.1.2); each step computes every bond force
+ * and then updates every voxel synchronously with "double Euler" integration
+ * (Sec 2.1.3), with bond and ground damping (Sec 2.1.5), gravity, floor
+ * contact with Coulomb friction (Sec 2.2.1), surface-voxel collisions behind a
+ * collision horizon (Sec 2.2.2) and volumetric (thermal) actuation (Sec 2.3).
+ * The object model follows the paper's App. B (CVX_Object / CVX_Environment /
+ * CVX_Sim); here one opaque vx_sim plays all three roles.
+ *
+ * Conventions for every entry point:
+ *   - Return value: VX_OK (0) on success, a negative VX_ERR_* code otherwise;
+ *     vx_last_error() then gives a message (thread-local, valid until the
+ *     next failing call on the same thread).  No C++ exception crosses the ABI.
+ *   - All voxel arrays are in CANONICAL ORDER: bodies in order, then occupied
+ *     sites x-fastest, then y, then z (index x + nx*(y + ny*z), empty sites
+ *     skipped).  Vectors are interleaved: [N][3] or [N][4].
+ *   - The caller owns every pointer it passes; the library copies what it
+ *     needs before returning and keeps no caller pointer.  The library owns
+ *     its device memory (allocated in vx_create, released in vx_destroy).
+ *   - Host pointers are plain (pageable or pinned) host memory unless an
+ *     argument says "device".  Streams are cudaStream_t passed as void*
+ *     (NULL = legacy default stream).
+ *   - Units: SI (m, kg, s, Pa, N, K).
+ *   - A vx_sim must not be used from two host threads at once.
+ */
+#ifndef VX_H
+#define VX_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define VX_API __attribute__((visibility("default")))
+#else
+#define VX_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define VX_OK 0
+#define VX_ERR_ARG (-1)       /* invalid argument (paper: SetMat returns false)   */
+#define VX_ERR_CUDA (-2)      /* a CUDA runtime call failed                        */
+#define VX_ERR_OOM (-3)       /* device or host allocation failed                  */
+#define VX_ERR_UNSTABLE (-4)  /* non-finite state (paper: TimeStep returns false)  */
+#define VX_ERR_TIMEOUT (-5)   /* a bounded device wait ran out                     */
+#define VX_ERR_STATE (-6)     /* call not valid in the current state               */
+#define VX_ERR_CAPACITY (-7)  /* a fixed-size buffer (collision pairs) overflowed  */
+
+typedef struct vx_sim vx_sim;
+
+/* Material of a palette entry (paper App. B, CVX_Object::AddMat: elastic
+ * modulus and Poisson ratio; density, thermal expansion and friction are the
+ * "other physical properties"). E > 0, -1 < nu < 0.5, rho > 0, mu >= 0. */
+typedef struct {
+  float E;    /* elastic modulus [Pa]                          */
+  float nu;   /* Poisson ratio                                 */
+  float rho;  /* density [kg/m^3]                              */
+  float cte;  /* coefficient of thermal expansion [1/K] (Sec 2.3) */
+  float mu_s; /* static friction coefficient with the floor (Sec 2.2.1) */
+  float mu_k; /* dynamic friction coefficient with the floor        */
+} vx_material;
+
+/* Lattice description (paper App. B, CVX_Object::InitializeMatter + SetMat).
+ * Each body is its own workspace nx*ny*nz of cubic voxels of edge voxel_size;
+ * grid holds one byte per site, bodies concatenated, x fastest:
+ * 0 = empty, k > 0 = palette[k-1].  Bodies never interact (independent
+ * worlds stepped together). origin: [n_bodies][3] position of each
+ * workspace's corner, or NULL for zeros.
+ * Limits: 1 <= nx, ny <= 2048, 1 <= nz <= 1024 per body, n_materials <= 255,
+ * total voxels < 2^31. */
+typedef struct {
+  int32_t n_bodies;
+  const int32_t* dims;
+  const uint8_t* grid;
+  float voxel_size;
+  const vx_material* palette;
+  int32_t n_materials;
+  const float* origin;
+} vx_desc;
+
+/* State of every voxel in canonical order.  Positions are stored as FP32
+ * offsets from each voxel's lattice anchor (its rest centre,
+ * origin + (i+1/2, j+1/2, k+1/2) l), so that small strains keep full FP32
+ * precision; vx_get_anchors gives the anchors.  Any field may be NULL
+ * (skipped).  flags: bit 0 = fixed (immobile), bit 1 = static friction. */
+typedef struct {
+  float* offset;   /* [N][3] position minus anchor [m]          */
+  float* quat;     /* [N][4] orientation (w, x, y, z), unit     */
+  float* vel;      /* [N][3] linear velocity [m/s]              */
+  float* angvel;   /* [N][3] angular velocity, world frame [rad/s] */
+  uint8_t* flags;  /* [N]                                       */
+} vx_state_view;
+
+#define VX_FLAG_FIXED 1u
+#define VX_FLAG_STATIC 2u
+
+/* ---- version / errors --------------------------------------------------- */
+VX_API const char* vx_version(void);
+/* Message of the last failing call on this thread ("" if none). */
+VX_API const char* vx_last_error(void);
+
+/* ---- host-only planning (no GPU needed) --------------------------------- */
+/* Counts of the lattice a description would create: occupied voxels, bonds
+ * (adjacent occupied sites of one body, Sec 2.1.2) and surface voxels (fewer
+ * than 6 occupied face neighbours, Sec 2.2.2).  Any output may be NULL. */
+VX_API int vx_plan_counts(const vx_desc* desc, int64_t* n_voxels, int64_t* n_bonds, int64_t* n_surface);
+
+/* Stable timestep of every body (Sec 2.1.4): dt = dt_factor / (2 pi w_max),
+ * w_max the largest sqrt(k/m) over the body's bonds (k = E_c l, m the smaller
+ * mass) and over its voxels' own contact springs (k = E l).  log_E: per-voxel
+ * natural-log modulus overriding the palette, or NULL.  dt_out: [n_bodies]. */
+VX_API int vx_plan_dt(const vx_desc* desc, const float* log_E, float dt_factor, double* dt_out);
+
+/* Voxels of `body` touching a region given as fractions of its workspace
+ * (paper App. B, AddFixedRegion/AddForcedRegion: "all voxels touching this
+ * region"): the closed voxel cube [i/nx,(i+1)/nx] x ... intersects the closed
+ * box [loc, loc+size].  mask: [N] canonical order (set to 1 or 0);
+ * n_out: number selected. */
+VX_API int vx_region_mask(const vx_desc* desc, int32_t body, const float loc[3], const float size[3],
+                   uint8_t* mask, int64_t* n_out);
+
+/* ---- lifetime ------------------------------------------------------------ */
+/* Build the lattice (Sec 2.1: voxelised geometry, composite bonds,
+ * precomputed surface list) on the current CUDA device and reset the state
+ * to rest.  Defaults: zeta_bond 1, zeta_ground 0, zeta_collision 1, no
+ * gravity, floor or collisions, no actuation, dt_factor 0.9. */
+VX_API int vx_create(const vx_desc* desc, vx_sim** out);
+VX_API void vx_destroy(vx_sim* sim);
+VX_API int vx_get_counts(vx_sim* sim, int64_t* n_voxels, int64_t* n_bonds, int64_t* n_surface);
+/* Lattice anchors (rest centres) [N][3] in double precision, host memory. */
+VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
+
+/* ---- configuration (host inputs, copied) -------------------------------- */
+/* Replace the palette (same count); recomputes bonds' composites and dt. */
+VX_API int vx_set_materials(vx_sim* sim, const vx_material* palette, int32_t n_materials);
+/* Per-voxel natural-log elastic modulus (overrides the palette's E) and
+ * actuation phase [rad]; NULL leaves that field unchanged.  log_E recomputes dt. */
+VX_API int vx_set_voxel_params(vx_sim* sim, const float* log_E, const float* phase);
+/* Per-voxel fixed flags (1 = immobile). */
+VX_API int vx_set_fixed_mask(vx_sim* sim, const uint8_t* mask);
+/* Paper App. B AddFixedRegion: fix every voxel of `body` touching the region.
+ * n_out (nullable): voxels selected. */
+VX_API int vx_add_fixed_region(vx_sim* sim, int32_t body, const float loc[3], const float size[3], int64_t* n_out);
+/* Paper App. B AddForcedRegion: F [N] split equally among the voxels of
+ * `body` touching the region (added to any force already there). */
+VX_API int vx_add_forced_region(vx_sim* sim, int32_t body, const float loc[3], const float size[3],
+                         const float F[3], int64_t* n_out);
+/* Per-voxel external force [N][3] (replaces all forces), or NULL to clear. */
+VX_API int vx_set_forces(vx_sim* sim, const float* F);
+/* Damping ratios (paper App. B SetBondDampZ, SetSlowDampZ, SetCollisionDampZ);
+ * each in [0, 1]; larger values may be unstable (the paper says the same). */
+VX_API int vx_set_damping(vx_sim* sim, float zeta_bond, float zeta_ground, float zeta_collision);
+/* Gravity along z [m/s^2] (e.g. -9.81), floor plane z = 0 on/off,
+ * voxel self-collision on/off (Sec 2.2). */
+VX_API int vx_set_environment(vx_sim* sim, float gravity_z, int32_t floor_on, int32_t collide_on);
+/* Volumetric actuation (Sec 2.3): the temperature offset of voxel v at step n
+ * is offset + amplitude * sin(2 pi n / period + phase_v) (period 0: offset
+ * only).  Bond rest length l (1 + (cte1 dT1 + cte2 dT2) / 2). */
+VX_API int vx_set_actuation(vx_sim* sim, float amplitude_K, int64_t period_steps, float offset_K);
+/* Stable-timestep safety factor f in (0, 1]; recomputes dt. */
+VX_API int vx_set_dt_factor(vx_sim* sim, float f);
+/* dt of every body [n_bodies] (double on the host; the device steps in FP32). */
+VX_API int vx_get_dt(vx_sim* sim, double* dt_per_body);
+/* Override dt of every body (frozen until the next recompute). */
+VX_API int vx_set_dt(vx_sim* sim, const double* dt_per_body);
+
+/* ---- state -------------------------------------------------------------- */
+/* Rest state: zero offsets, identity orientations, velocity v0 (or zero if
+ * NULL) for non-fixed voxels, zero angular velocity, static flags clear, step
+ * counter 0, collision candidates rebuilt.  Synchronous. */
+VX_API int vx_reset(vx_sim* sim, const float v0[3]);
+/* Copy the state to caller buffers (dst_on_device = 1: device pointers, else
+ * host).  Synchronous with respect to work already queued on `stream`. */
+VX_API int vx_read_state(vx_sim* sim, const vx_state_view* out, int32_t dst_on_device, void* stream);
+/* Overwrite the state from caller buffers (NULL fields unchanged). */
+VX_API int vx_write_state(vx_sim* sim, const vx_state_view* in, int32_t src_on_device, void* stream);
+/* Step counter n (number of steps taken since the last reset). */
+VX_API int vx_get_step(vx_sim* sim, int64_t* step);
+VX_API int vx_set_step(vx_sim* sim, int64_t step);
+
+/* ---- stepping ----------------------------------------------------------- */
+/* Advance n_steps explicit steps (paper App. B CVX_Sim::TimeStep, repeated),
+ * enqueued on `stream`; then waits for them and returns VX_ERR_UNSTABLE if any
+ * voxel state became non-finite (the first bad step/voxel is kept, see
+ * vx_get_status).  */
+VX_API int vx_step(vx_sim* sim, int64_t n_steps, void* stream);
+/* Same, without waiting: the status is checked by a later vx_get_status. */
+VX_API int vx_step_async(vx_sim* sim, int64_t n_steps, void* stream);
+/* Wait for `stream`, then report: status (VX_OK / VX_ERR_UNSTABLE /
+ * VX_ERR_CAPACITY), first bad step and voxel (canonical index) or -1. */
+VX_API int vx_get_status(vx_sim* sim, void* stream, int32_t* status, int64_t* bad_step, int64_t* bad_voxel);
+
+/* ---- collisions (Sec 2.2.2) ---------------------------------------------- */
+/* Rebuild the surface-voxel candidate list from the current positions now. */
+VX_API int vx_rebuild_collisions(vx_sim* sim, void* stream);
+/* Current candidate pairs (i < j, canonical indices, sorted by i then j) into
+ * host memory pairs [cap][2]; n_out = total count (may exceed cap). */
+VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int64_t* n_out);
+/* Number of candidate-list rebuilds since create, and the horizon
+ * accumulator of body 0 [m]. */
+VX_API int vx_collision_stats(vx_sim* sim, int64_t* n_rebuilds, double* accumulator);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VX_H */

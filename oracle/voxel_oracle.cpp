@@ -821,7 +821,6 @@ long orc_partners_of(orc_sim* o, const double* off, int i, int32_t* out, long ca
     int c[3] = {T.vi[v], T.vj[v], T.vk[v]};
     return (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(off[3 * v + a], S.qK));
   };
-  std::vector<std::array<int64_t, 3>> xq(T.N);
   long n = 0;
   for (int j = 0; j < T.N; ++j) {
     if (j == i || !T.surface[j] || T.body[j] != T.body[i]) continue;

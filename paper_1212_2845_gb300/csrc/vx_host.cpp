@@ -1,0 +1,139 @@
+// Host lattice build: compaction of the material grid into voxels, bond
+// neighbours, surface voxels, per-body stable timestep and region selection.
+#include "vx_host.h"
+
+#include <algorithm>
+#include <cmath>
+
+namespace vx {
+
+int build_lattice(const vx_desc* d, Lattice& L, std::string& err) {
+  if (!d) { err = "desc is NULL"; return VX_ERR_ARG; }
+  if (d->n_bodies < 1 || !d->dims || !d->grid || !d->palette) { err = "desc: missing bodies, dims, grid or palette"; return VX_ERR_ARG; }
+  if (d->n_materials < 1 || d->n_materials > 255) { err = "desc: n_materials must be in [1, 255]"; return VX_ERR_ARG; }
+  if (!(d->voxel_size > 0.f) || !std::isfinite(d->voxel_size)) { err = "desc: voxel_size must be positive"; return VX_ERR_ARG; }
+  for (int m = 0; m < d->n_materials; ++m) {
+    const vx_material& p = d->palette[m];
+    if (!(p.E > 0.f) || !(p.rho > 0.f) || !(p.nu > -1.f && p.nu < 0.5f) || !(p.mu_s >= 0.f) || !(p.mu_k >= 0.f) ||
+        !std::isfinite(p.cte) || !std::isfinite(p.E) || !std::isfinite(p.rho)) {
+      err = "desc: material " + std::to_string(m) + " out of range (E>0, rho>0, -1<nu<0.5, mu>=0)";
+      return VX_ERR_ARG;
+    }
+  }
+  L = Lattice();
+  L.n_bodies = d->n_bodies;
+  L.l = d->voxel_size;
+  L.palette.assign(d->palette, d->palette + d->n_materials);
+  L.dims.assign(d->dims, d->dims + 3 * d->n_bodies);
+  L.origin.assign(3 * (size_t)d->n_bodies, 0.f);
+  if (d->origin) L.origin.assign(d->origin, d->origin + 3 * d->n_bodies);
+  std::vector<size_t> site_off(d->n_bodies + 1, 0);
+  for (int b = 0; b < d->n_bodies; ++b) {
+    int nx = L.dims[3 * b], ny = L.dims[3 * b + 1], nz = L.dims[3 * b + 2];
+    if (nx < 1 || ny < 1 || nz < 1 || nx > 2048 || ny > 2048 || nz > 1024) {
+      err = "desc: body " + std::to_string(b) + " dims out of range (1..2048, 1..2048, 1..1024)";
+      return VX_ERR_ARG;
+    }
+    site_off[b + 1] = site_off[b] + (size_t)nx * ny * nz;
+  }
+  // count and validate
+  int64_t N = 0;
+  for (size_t s = 0; s < site_off[d->n_bodies]; ++s) {
+    uint8_t m = d->grid[s];
+    if (m == 0) continue;
+    if (m > d->n_materials) { err = "desc: grid references material " + std::to_string(m) + " beyond the palette"; return VX_ERR_ARG; }
+    ++N;
+  }
+  if (N == 0) { err = "desc: lattice has no occupied site"; return VX_ERR_ARG; }
+  if (N >= (int64_t)1 << 31) { err = "desc: too many voxels"; return VX_ERR_ARG; }
+  L.N = N;
+  L.body.resize(N); L.lat.resize(N); L.mat.resize(N);
+  L.body_first.assign(d->n_bodies + 1, 0);
+  // site -> voxel index, per body, built on the fly (one body at a time)
+  int64_t v = 0;
+  L.nbr.assign(6 * (size_t)N, -1);
+  std::vector<int32_t> s2v;
+  for (int b = 0; b < d->n_bodies; ++b) {
+    int nx = L.dims[3 * b], ny = L.dims[3 * b + 1], nz = L.dims[3 * b + 2];
+    const uint8_t* g = d->grid + site_off[b];
+    s2v.assign((size_t)nx * ny * nz, -1);
+    L.body_first[b] = (int32_t)v;
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          size_t s = (size_t)i + (size_t)nx * ((size_t)j + (size_t)ny * k);
+          if (!g[s]) continue;
+          s2v[s] = (int32_t)v;
+          L.body[v] = b; L.lat[v] = pack_ijk(i, j, k); L.mat[v] = (uint8_t)(g[s] - 1);
+          ++v;
+        }
+    for (int64_t u = L.body_first[b]; u < v; ++u) {
+      int c[3] = {lat_i(L.lat[u]), lat_j(L.lat[u]), lat_k(L.lat[u])};
+      int n[3] = {nx, ny, nz};
+      int occ = 0;
+      for (int a = 0; a < 3; ++a)
+        for (int sgn = 0; sgn < 2; ++sgn) {
+          int cc[3] = {c[0], c[1], c[2]};
+          cc[a] += sgn ? 1 : -1;
+          int32_t w = -1;
+          if (cc[a] >= 0 && cc[a] < n[a]) w = s2v[(size_t)cc[0] + (size_t)nx * ((size_t)cc[1] + (size_t)ny * cc[2])];
+          L.nbr[(size_t)(2 * a + sgn) * N + u] = w;
+          if (w >= 0) ++occ;
+          if (w >= 0 && sgn) ++L.n_bonds;
+        }
+      if (occ < 6) L.surf_list.push_back((int32_t)u);
+    }
+  }
+  L.body_first[d->n_bodies] = (int32_t)v;
+  L.n_surface = (int64_t)L.surf_list.size();
+  return VX_OK;
+}
+
+void stable_dt(const Lattice& L, const float* logE, float dt_factor, std::vector<double>& dt) {
+  std::vector<double> wmax(L.n_bodies, 0.0);
+  const double l = L.l;
+  auto E_of = [&](int64_t v) { return logE ? std::exp((double)logE[v]) : (double)L.palette[L.mat[v]].E; };
+  auto m_of = [&](int64_t v) { return (double)L.palette[L.mat[v]].rho * l * l * l; };
+  for (int64_t v = 0; v < L.N; ++v) {
+    int b = L.body[v];
+    double Ev = E_of(v), mv = m_of(v);
+    wmax[b] = std::max(wmax[b], std::sqrt(Ev * l / mv));   // voxel's own contact spring
+    for (int a = 0; a < 3; ++a) {
+      int32_t u = L.nbr[(size_t)(2 * a + 1) * L.N + v];
+      if (u < 0) continue;
+      double Eu = E_of(u);
+      double Ec = 2.0 * Ev * Eu / (Ev + Eu);
+      double k = Ec * l;  // a1 = E_c A / l with A = l^2
+      wmax[b] = std::max(wmax[b], std::sqrt(k / std::min(mv, m_of(u))));
+    }
+  }
+  dt.assign(L.n_bodies, 0.0);
+  for (int b = 0; b < L.n_bodies; ++b)
+    dt[b] = wmax[b] > 0.0 ? (double)dt_factor / (2.0 * M_PI * wmax[b]) : 0.0;
+}
+
+int64_t region_mask(const Lattice& L, int body, const float loc[3], const float size[3], uint8_t* mask) {
+  int64_t cnt = 0;
+  const int32_t* n = &L.dims[3 * body];
+  for (int64_t v = 0; v < L.N; ++v) {
+    bool in = L.body[v] == body;
+    int c[3] = {lat_i(L.lat[v]), lat_j(L.lat[v]), lat_k(L.lat[v])};
+    for (int a = 0; a < 3 && in; ++a) {
+      double lo = (double)c[a] / n[a], hi = (double)(c[a] + 1) / n[a];
+      double r0 = loc[a], r1 = (double)loc[a] + (double)size[a];
+      if (hi < r0 || lo > r1) in = false;
+    }
+    mask[v] = in ? 1 : 0;
+    cnt += in ? 1 : 0;
+  }
+  return cnt;
+}
+
+void quant_params(float l, int* K, int64_t* Q) {
+  int e = 0;
+  std::frexp(65536.0 / (double)l, &e);
+  *K = e - 1;
+  *Q = (int64_t)std::nearbyint(std::ldexp((double)l, *K));
+}
+
+}  // namespace vx

@@ -1,0 +1,47 @@
+// Host-side lattice description shared by the library's translation units.
+// Pure C++ (no CUDA): the lattice build, timestep and region selection run on
+// the host once per create / parameter change.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "vx.h"
+
+namespace vx {
+
+// Packed lattice coordinate of a voxel: i | j << 11 | k << 22.
+inline uint32_t pack_ijk(int i, int j, int k) { return (uint32_t)i | ((uint32_t)j << 11) | ((uint32_t)k << 22); }
+inline int lat_i(uint32_t p) { return (int)(p & 2047u); }
+inline int lat_j(uint32_t p) { return (int)((p >> 11) & 2047u); }
+inline int lat_k(uint32_t p) { return (int)(p >> 22); }
+
+struct Lattice {
+  int n_bodies = 0;
+  std::vector<int32_t> dims;        // 3 per body
+  float l = 0.f;
+  std::vector<vx_material> palette;
+  std::vector<float> origin;        // 3 per body
+  int64_t N = 0, n_bonds = 0, n_surface = 0;
+  std::vector<int32_t> body;        // per voxel
+  std::vector<uint32_t> lat;        // per voxel, packed (i, j, k) within its body
+  std::vector<uint8_t> mat;         // per voxel, 0-based palette index
+  std::vector<int32_t> nbr;         // 6 planes of N: -x,+x,-y,+y,-z,+z neighbour or -1
+  std::vector<int32_t> surf_list;   // canonical indices of surface voxels, ascending
+  std::vector<int32_t> body_first;  // n_bodies + 1
+};
+
+// Validates the description and fills the lattice.  Returns VX_OK or an
+// error code with a message in err.
+int build_lattice(const vx_desc* d, Lattice& L, std::string& err);
+
+// Per-body stable timestep (paper Sec 2.1.4) in double.
+void stable_dt(const Lattice& L, const float* logE, float dt_factor, std::vector<double>& dt);
+
+// Voxels touching a region given in workspace fractions (paper App. B).
+int64_t region_mask(const Lattice& L, int body, const float loc[3], const float size[3], uint8_t* mask);
+
+// Collision quantisation: 2^K <= 65536 / l < 2^(K+1), Q = rint(l 2^K).
+void quant_params(float l, int* K, int64_t* Q);
+
+}  // namespace vx

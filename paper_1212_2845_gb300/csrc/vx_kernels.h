@@ -1,0 +1,55 @@
+// Launch wrappers of the library's kernels (host-callable).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "vx_dev.cuh"
+
+namespace vx {
+
+struct CollideArgs {
+  int S;                  // surface voxels
+  int n_bodies;
+  int H;                  // hash buckets (power of two)
+  int K;                  // quantisation: offset * 2^K
+  int64_t Q;              // quantisation: lattice step rint(l 2^K)
+  int64_t pitch;
+  float threshold;        // horizon accumulator threshold [m]
+  const float* st;        // state planes (offsets used)
+  const int32_t* surf;    // surface voxel list (canonical, ascending)
+  const uint32_t* lat;
+  const int32_t* body;    // or nullptr
+  const float* dt_body;
+  int64_t* xq;            // 3 planes of S
+  uint32_t* bucket;       // S
+  uint32_t* hcount;       // H
+  uint32_t* hcursor;      // H
+  uint32_t* hstart;       // H + 1
+  uint32_t* bsum;         // ceil(H / 1024)
+  int32_t* sorted;        // S
+  int32_t* ccount;        // S
+  int32_t* cand;          // S x kCandCap
+  float* acc;             // per body
+  unsigned* vmax_bits;    // per body
+  int* flag;              // per body rebuild flag
+  int* any;               // any body flagged
+  long long* n_rebuilds;
+  int* status;
+};
+
+void launch_step(const StepArgs& A, cudaStream_t s);
+void launch_horizon(const CollideArgs& C, cudaStream_t s);
+void launch_rebuild(const CollideArgs& C, cudaStream_t s);
+void launch_flag_all(const CollideArgs& C, cudaStream_t s);
+
+// state <-> interleaved staging (offset[N][3], quat[N][4], vel[N][3],
+// angvel[N][3], flags[N]); any destination/source pointer may be null
+void launch_pack_state(const float* st, int64_t pitch, int N, const uint8_t* flags, float* off, float* quat,
+                       float* vel, float* angvel, uint8_t* fl, cudaStream_t s);
+void launch_unpack_state(float* st, int64_t pitch, int N, uint8_t* flags, const float* off, const float* quat,
+                         const float* vel, const float* angvel, const uint8_t* fl, cudaStream_t s);
+// rest state: zero offsets, identity quaternions, v0 for non-fixed voxels
+void launch_reset_state(float* st, int64_t pitch, int N, uint8_t* flags, float v0x, float v0y, float v0z,
+                        cudaStream_t s);
+
+}  // namespace vx

@@ -26,14 +26,20 @@ def material(E, nu=0.35, rho=1000.0, cte=0.0, mu_s=1.0, mu_k=0.5):
     return (float(E), float(nu), float(rho), float(cte), float(mu_s), float(mu_k))
 
 
+def f32(x):
+    """Round to the nearest float32 value, kept as float64: the CUDA library
+    takes FP32 inputs, so scenes carry values both sides read identically."""
+    return np.asarray(x, dtype=np.float32).astype(np.float64)
+
+
 def _base(dims, grid, l, palette, **kw):
     """Assemble a scene dict with the defaults used when a setting is not stated."""
     dims = np.asarray(dims, dtype=np.int32).reshape(-1, 3)
     sc = dict(
         dims=dims,
         grid=np.ascontiguousarray(grid, dtype=np.uint8).ravel(),
-        voxel_size=float(l),
-        palette=np.asarray(palette, dtype=np.float64).reshape(-1, 6),
+        voxel_size=float(f32(l)),
+        palette=f32(np.asarray(palette, dtype=np.float64).reshape(-1, 6)),
         origin=np.zeros((dims.shape[0], 3), dtype=np.float64),
         phase=None,           # per-voxel actuation phase (canonical order) or None
         log_E=None,           # per-voxel log stiffness override or None
@@ -46,6 +52,22 @@ def _base(dims, grid, l, palette, **kw):
         name="scene",
     )
     sc.update(kw)
+    return normalize(sc)
+
+
+FLOAT_KEYS = ("zeta_bond", "zeta_ground", "zeta_collision", "gravity_z", "act_amplitude", "act_offset",
+              "dt_factor")
+
+
+def normalize(sc):
+    """Round every floating-point setting to a float32 value (see f32)."""
+    for k in FLOAT_KEYS:
+        sc[k] = float(f32(sc[k]))
+    sc["v0"] = tuple(float(x) for x in f32(sc["v0"]))
+    sc["origin"] = f32(sc["origin"])
+    for k in ("phase", "log_E", "force"):
+        if sc.get(k) is not None:
+            sc[k] = f32(sc[k])
     return sc
 
 
@@ -101,7 +123,7 @@ def hetero_block(dims=(64, 64, 32), seed=2, steps=10000):
     sc = _base([dims], grid, 1e-3, pal, gravity_z=-9.81, floor=True,
                act_amplitude=20.0, act_period=2000, steps=steps,
                name=f"hetero_block_{nx}x{ny}x{nz}")
-    sc["phase"] = rng.uniform(0.0, 2.0 * math.pi, size=n_occupied(sc))
+    sc["phase"] = f32(rng.uniform(0.0, 2.0 * math.pi, size=n_occupied(sc)))
     return sc
 
 
@@ -118,7 +140,7 @@ def hollow_ball(R=100, t=8, drop=5, l=1e-3, v0=-2.0, steps=20000):
     sc = _base([(n, n, n)], grid, l, [material(0.5e6, 0.45, 1100.0)],
                gravity_z=-9.81, floor=True, collide=True, v0=(0.0, 0.0, v0),
                steps=steps, name=f"hollow_ball_R{R}_t{t}")
-    sc["origin"][0] = (0.0, 0.0, (drop - kmin) * l)
+    sc["origin"][0] = f32((0.0, 0.0, (drop - kmin) * l))
     return sc
 
 
@@ -139,7 +161,7 @@ def population(n_bodies=4096, seed=4, lo=4, hi=24, steps=20000):
     sc = _base(dims, np.concatenate(grids), 1e-3, pal, gravity_z=-9.81, floor=True,
                act_amplitude=20.0, act_period=2000, steps=steps,
                name=f"population_{n_bodies}")
-    sc["phase"] = rng.uniform(0.0, 2.0 * math.pi, size=n_occupied(sc))
+    sc["phase"] = f32(rng.uniform(0.0, 2.0 * math.pi, size=n_occupied(sc)))
     return sc
 
 
@@ -153,10 +175,10 @@ def design_population(n_bodies=1024, n=12, seed=5, steps=2000):
                floor=True, act_amplitude=20.0, act_period=2000, steps=steps,
                name=f"design_{n_bodies}x{n}^3")
     nv = n_bodies * n ** 3
-    sc["log_E"] = rng.uniform(math.log(1e5), math.log(1e8), size=nv)
-    sc["phase"] = rng.uniform(0.0, 2.0 * math.pi, size=nv)
+    sc["log_E"] = f32(rng.uniform(math.log(1e5), math.log(1e8), size=nv))
+    sc["phase"] = f32(rng.uniform(0.0, 2.0 * math.pi, size=nv))
     # bodies side by side along x, 2 voxels apart (independent worlds anyway)
-    sc["origin"][:, 0] = np.arange(n_bodies) * (n + 2) * 1e-3
+    sc["origin"][:, 0] = f32(np.arange(n_bodies) * (n + 2) * 1e-3)
     return sc
 
 
@@ -170,7 +192,7 @@ def random_blob(dims=(6, 5, 4), seed=0, fill=0.8, n_mat=3):
     pal = [material(1e6 * 10 ** (k % 3), 0.3 + 0.05 * k, 1000.0 + 100 * k, 0.01 * (k % 2),
                     0.8, 0.4) for k in range(n_mat)]
     sc = _base([dims], grid, 1e-3, pal, name=f"blob_{nx}x{ny}x{nz}_s{seed}")
-    sc["phase"] = rng.uniform(0.0, 2.0 * math.pi, size=n_occupied(sc))
+    sc["phase"] = f32(rng.uniform(0.0, 2.0 * math.pi, size=n_occupied(sc)))
     return sc
 
 

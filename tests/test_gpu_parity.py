@@ -1,0 +1,321 @@
+"""GPU (sm_103a kernels through the C ABI) against the FP64 oracle.
+
+Every test builds the same seeded scene on both sides, steps both, and
+compares element by element.  Tolerances (FP32 kernel vs FP64 oracle):
+positions within 1e-5 of the body's bounding-box diagonal after 1,000 steps
+without contact, 1e-3 with contact and friction; one-step force responses
+within 1e-4 of the largest response; collision candidate sets bit-exact.
+"""
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1212_2845_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def vx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1212_2845_gb300 import build, vx as _vx
+    build.build()
+    return _vx
+
+
+def f32_dt(ora):
+    """The oracle's own timestep of every body, rounded to FP32 as the kernels step."""
+    return np.array([np.float32(ora.dt(b)) for b in range(ora.n_bodies)], dtype=np.float64)
+
+
+def pair(vx, sc):
+    sim = vx.Sim(sc)
+    ora = Oracle(sc)
+    ora.set_dt(f32_dt(ora))
+    return sim, ora
+
+
+def body_diag(sc, pos):
+    ijk = scenes.canonical_coords(sc)
+    d = np.zeros(len(pos))
+    for b in np.unique(ijk[:, 0]):
+        m = ijk[:, 0] == b
+        d[m] = np.linalg.norm(np.ptp(pos[m], axis=0)) if m.sum() > 1 else sc["voxel_size"]
+    return d
+
+
+def pos_error(sc, g, o):
+    return np.max(np.linalg.norm(g["pos"] - o["pos"], axis=1) / body_diag(sc, o["pos"]))
+
+
+def quat_error(g, o):
+    d1 = np.abs(g["quat"] - o["quat"]).max(axis=1)
+    d2 = np.abs(g["quat"] + o["quat"]).max(axis=1)
+    return np.minimum(d1, d2).max()
+
+
+# ---------------------------------------------------------------------------
+# single step, every force term on, random perturbed state
+# ---------------------------------------------------------------------------
+
+def perturbed_scene(dims, seed, **kw):
+    sc = scenes.random_blob(dims, seed=seed, fill=0.75)
+    sc.update(gravity_z=-9.81, floor=True, zeta_bond=0.7, zeta_ground=0.05, zeta_collision=0.8,
+              act_amplitude=15.0, act_period=37, act_offset=2.0)
+    sc.update(kw)
+    scenes.normalize(sc)
+    rng = np.random.default_rng(seed)
+    n = scenes.n_occupied(sc)
+    sc["fixed"] = (rng.random(n) < 0.05).astype(np.uint8)
+    sc["force"] = scenes.f32(rng.normal(size=(n, 3)) * 1e-4)
+    return sc
+
+
+def random_state(n, seed, l, amp=0.05):
+    rng = np.random.default_rng(seed + 100)
+    off = (rng.normal(size=(n, 3)) * amp * l).astype(np.float32)
+    ax = rng.normal(size=(n, 3))
+    ang = rng.normal(size=n) * 0.05
+    ax /= np.linalg.norm(ax, axis=1, keepdims=True)
+    q = np.concatenate([np.cos(ang / 2)[:, None], np.sin(ang / 2)[:, None] * ax], axis=1)
+    q = (q / np.linalg.norm(q, axis=1, keepdims=True)).astype(np.float32)
+    vel = (rng.normal(size=(n, 3)) * 0.01).astype(np.float32)
+    w = (rng.normal(size=(n, 3)) * 5.0).astype(np.float32)
+    return off, q, vel, w
+
+
+def set_both(sim, ora, anchors, off, q, vel, w, flags=None):
+    sim.write_state(offset=off, quat=q, vel=vel, angvel=w, flags=flags)
+    st = None if flags is None else (flags >> 1) & 1
+    ora.set_state(pos=anchors + off.astype(np.float64), quat=q.astype(np.float64), vel=vel.astype(np.float64),
+                  angvel=w.astype(np.float64), static=st)
+
+
+@pytest.mark.parametrize("dims,seed", [((7, 5, 4), 0), ((9, 6, 5), 1), ((33, 3, 2), 2), ((1, 1, 13), 3)])
+def test_one_step_force_response(vx, dims, seed):
+    sc = perturbed_scene(dims, seed)
+    sim, ora = pair(vx, sc)
+    anchors = ora.anchors(sc)
+    assert np.allclose(sim.anchors(), anchors, rtol=0, atol=1e-15)
+    off, q, vel, w = random_state(sim.N, seed, sc["voxel_size"])
+    off[:, 2] -= 0.01 * sc["voxel_size"]  # some voxels pressed into the floor
+    free = sc["fixed"] == 0
+    vel[~free] = 0
+    w[~free] = 0
+    for n0 in (0, 11):  # two actuation phases
+        sim.set_step(n0)
+        ora.set_step_counter(n0)
+        set_both(sim, ora, anchors, off, q, vel, w)
+        sim.step(1)
+        ora.step(1)
+        g, o = sim.state(), ora.state()
+        dv_g, dv_o = g["vel"] - vel, o["vel"] - vel
+        dw_g, dw_o = g["angvel"] - w, o["angvel"] - w
+        assert np.abs(dv_g - dv_o).max() <= 1e-4 * np.abs(dv_o).max() + 1e-9
+        assert np.abs(dw_g - dw_o).max() <= 1e-4 * np.abs(dw_o).max() + 1e-6
+        assert np.array_equal(g["static"], o["static"])
+        assert np.abs(g["pos"] - o["pos"]).max() < 1e-10
+        assert quat_error(g, o) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# rollouts
+# ---------------------------------------------------------------------------
+
+def test_cantilever_1000_steps(vx):
+    """Config 1: 10x10x10 cantilever under gravity, 1,000 steps, 1e-5 of the diagonal."""
+    sc = scenes.cantilever()
+    sim, ora = pair(vx, sc)
+    sim.step(1000)
+    ora.step(1000)
+    g, o = sim.state(), ora.state()
+    err = pos_error(sc, g, o)
+    disp = np.abs(o["pos"] - ora.anchors(sc)).max()
+    rel_disp = np.abs(g["pos"] - o["pos"]).max() / disp
+    print(f"cantilever: pos err/diag {err:.2e}, err/max displacement {rel_disp:.2e}")
+    assert err < 1e-5
+    assert rel_disp < 1e-3
+    assert quat_error(g, o) < 1e-5
+
+
+def test_hetero_block_reduced(vx):
+    """Config 2 mix (soft/stiff, actuation, floor + friction) on a 16x16x8 block, 2,000 steps."""
+    sc = scenes.hetero_block(dims=(16, 16, 8), seed=2)
+    sim, ora = pair(vx, sc)
+    sim.step(2000)
+    ora.step(2000)
+    g, o = sim.state(), ora.state()
+    err = pos_error(sc, g, o)
+    flips = int(np.sum(g["static"] != o["static"]))
+    print(f"hetero block: pos err/diag {err:.2e}, static flag mismatches {flips}/{sim.N}")
+    assert err < 1e-3
+
+
+def test_population_reduced(vx):
+    """Config 4 mix on 12 bodies of uneven size (per-body timestep), 600 steps."""
+    sc = scenes.population(n_bodies=12, seed=4, lo=2, hi=9)
+    sim, ora = pair(vx, sc)
+    assert np.allclose(sim.dt(), [ora.dt(b) for b in range(12)], rtol=1e-7)
+    sim.step(600)
+    ora.step(600)
+    g, o = sim.state(), ora.state()
+    assert pos_error(sc, g, o) < 1e-3
+
+
+def test_design_population_reduced(vx):
+    """Config 5 inputs (per-voxel log-stiffness and phase) on 3 bodies of 6^3, 400 steps."""
+    sc = scenes.design_population(n_bodies=3, n=6, seed=5)
+    sim, ora = pair(vx, sc)
+    sim.step(400)
+    ora.step(400)
+    assert pos_error(sc, sim.state(), ora.state()) < 1e-3
+
+
+def test_appendix_a_program(vx):
+    """App. A: 5x10x5 beam, 10 MPa, -Y face fixed, 1 kN on +Y face, slow damping 0.013, 400 steps."""
+    sc = scenes._base([(5, 10, 5)], np.ones(250, np.uint8), 1e-3, [scenes.material(1e7, 0.3)],
+                      zeta_ground=0.013)
+    sim = vx.Sim(sc)
+    ora = Oracle(sc)
+    assert sim.add_fixed_region(0, (0, 0, 0), (1, 0.01, 1)) == 50
+    assert sim.add_forced_region(0, (0, 0.99, 0), (1, 0.01, 1), (0, 0, -1000.0)) == 50
+    ora.set_fixed(ora.region_mask(0, (0, 0, 0), (1, 0.01, 1)))
+    m = ora.region_mask(0, scenes.f32((0, 0.99, 0)), scenes.f32((1, 0.01, 1)))
+    F = np.zeros((ora.N, 3))
+    F[m.astype(bool), 2] = float(np.float32(-1000.0 / 50))
+    ora.set_force(F)
+    ora.reset()
+    ora.set_dt(f32_dt(ora))
+    sim.step(400)
+    ora.step(400)
+    g, o = sim.state(), ora.state()
+    assert np.array_equal(g["flags"] & 1, ora.region_mask(0, (0, 0, 0), (1, 0.01, 1)))
+    assert pos_error(sc, g, o) < 1e-5
+
+
+def test_deterministic_bitwise(vx):
+    sc = scenes.hetero_block(dims=(12, 9, 7), seed=6)
+    outs = []
+    for _ in range(2):
+        sim = vx.Sim(sc)
+        sim.step(300)
+        s = sim.read_state()
+        outs.append(np.concatenate([s["offset"].ravel(), s["quat"].ravel(), s["vel"].ravel(), s["angvel"].ravel()]))
+        sim.close()
+    assert np.array_equal(outs[0].view(np.uint32), outs[1].view(np.uint32))
+
+
+def test_state_roundtrip_and_reset(vx):
+    sc = scenes.random_blob((5, 4, 3), seed=9)
+    sim = vx.Sim(sc)
+    off, q, vel, w = random_state(sim.N, 9, sc["voxel_size"])
+    flags = np.zeros(sim.N, np.uint8)
+    sim.write_state(offset=off, quat=q, vel=vel, angvel=w, flags=flags)
+    s = sim.read_state()
+    for k, a in (("offset", off), ("quat", q), ("vel", vel), ("angvel", w)):
+        assert np.array_equal(s[k], a)
+    sim.reset()
+    s = sim.read_state()
+    assert not s["offset"].any() and not s["vel"].any()
+    assert np.array_equal(s["quat"], np.tile([1, 0, 0, 0], (sim.N, 1)).astype(np.float32))
+    assert sim.step_count == 0
+
+
+def test_unstable_is_reported_not_trapped(vx):
+    sc = scenes.random_blob((4, 4, 4), seed=1)
+    sc.update(zeta_bond=0.0)
+    sim = vx.Sim(sc)
+    off, q, vel, w = random_state(sim.N, 1, sc["voxel_size"])
+    sim.write_state(offset=off, quat=q, vel=vel, angvel=w)
+    sim.set_dt(sim.dt() * 40)
+    with pytest.raises(vx.VxError) as e:
+        sim.step(3000)
+    assert e.value.code == -4
+    st, bad_step, bad_voxel = sim.status()
+    assert st == -4 and 0 <= bad_step < 3000 and 0 <= bad_voxel < sim.N
+    sim.reset()
+    sim.set_dt_factor(0.9)
+    sim.step(10)
+
+
+# ---------------------------------------------------------------------------
+# collision candidates (bit-exact sets)
+# ---------------------------------------------------------------------------
+
+def scrambled_offsets(n, l, seed, amp=0.45):
+    rng = np.random.default_rng(seed)
+    return (rng.uniform(-amp, amp, size=(n, 3)) * l).astype(np.float32)
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_collision_set_bit_exact_small(vx, seed):
+    sc = scenes.hollow_ball(R=10, t=3)
+    sc["collide"] = True
+    sim, ora = pair(vx, sc)
+    off = scrambled_offsets(sim.N, sc["voxel_size"], seed)
+    sim.write_state(offset=off)
+    sim.rebuild_collisions()
+    gp = {tuple(p) for p in sim.collision_pairs()}
+    op = {tuple(p) for p in ora.pairs_from_offsets(off.astype(np.float64))}
+    print(f"pairs: gpu {len(gp)}, oracle {len(op)}")
+    assert len(op) > 100
+    assert gp == op
+
+
+def test_collision_threshold_exact(vx):
+    """Pairs placed exactly on, one unit inside and one unit outside the
+    quantised 2-voxel horizon."""
+    l = float(scenes.f32(1e-3))
+    K, Q = Oracle.quant_params(l)
+    grid = np.zeros(9, np.uint8)
+    grid[[0, 4, 8]] = 1
+    sc = scenes._base([(9, 1, 1)], grid, l, [scenes.material(1e6)], collide=True)
+    sim, ora = pair(vx, sc)
+    for dq, expect in [(0, False), (1, True), (-1, False)]:
+        off = np.zeros((3, 3), np.float32)
+        off[1, 0] = np.float32((-2 * Q - dq) / 2.0 ** K)   # voxel 4 moved to 2 Q - dq from voxel 0
+        off[2, 0] = np.float32(10 * l)                       # voxel 8 far away
+        sim.write_state(offset=off)
+        sim.rebuild_collisions()
+        gp = {tuple(p) for p in sim.collision_pairs()}
+        op = {tuple(p) for p in ora.pairs_from_offsets(off.astype(np.float64))}
+        assert gp == op
+        assert ((0, 1) in gp) == expect
+
+
+def test_collision_sets_full_ball_sampled(vx):
+    """Config 3 size: full 200^3 shell, scrambled state; sampled surface voxels'
+    partner lists against the oracle's brute force."""
+    sc = scenes.hollow_ball()
+    sim = vx.Sim(sc, apply_scene=False)
+    sim.set_environment(0.0, False, True)
+    ora = Oracle(sc, apply_scene=False)
+    off = scrambled_offsets(sim.N, sc["voxel_size"], 5, amp=0.4)
+    sim.write_state(offset=off)
+    sim.rebuild_collisions()
+    pairs = sim.collision_pairs()
+    _, _, surf = ora.topology()
+    rng = np.random.default_rng(6)
+    sample = rng.choice(np.nonzero(surf)[0], size=150, replace=False)
+    off64 = off.astype(np.float64)
+    for i in sample:
+        mine = np.sort(np.concatenate([pairs[pairs[:, 0] == i, 1], pairs[pairs[:, 1] == i, 0]]))
+        assert np.array_equal(mine, ora.partners_of(off64, i)), i
+
+
+def test_ball_drop_with_self_collision(vx):
+    """Config 3 physics on a scaled shell (R=12, t=3): floor impact, horizon
+    rebuilds and voxel contacts, 900 steps."""
+    sc = scenes.hollow_ball(R=12, t=3)
+    sim, ora = pair(vx, sc)
+    sim.step(900)
+    ora.step(900)
+    g, o = sim.state(), ora.state()
+    err = pos_error(sc, g, o)
+    nr_g, _ = sim.collision_stats()
+    nr_o = ora.n_rebuilds()
+    print(f"ball: pos err/diag {err:.2e}, rebuilds gpu {nr_g} oracle {nr_o}")
+    assert err < 1e-3
+    assert abs(nr_g - nr_o) <= max(2, nr_o // 10)

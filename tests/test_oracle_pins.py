@@ -173,7 +173,8 @@ def test_thin_cantilever_matches_paper_and_closed_form():
     g = GOLD["thin_cantilever"]
     sc, tip = beam_scene(tuple(g["voxels"]), -g["tip_force_N"], 0.0025)
     o = Oracle(sc)
-    E, l = g["E_Pa"], g["voxel_size_m"]
+    E, l = g["E_Pa"], sc["voxel_size"]   # l: the paper's 1 mm as the scene's FP32 value
+    assert l == pytest.approx(g["voxel_size_m"], rel=1e-7)
     L = (g["voxels"][0] - 1) * l  # fixed-voxel centre to tip-voxel centre
     closed = g["tip_force_N"] * L ** 3 / (3 * E * l ** 4 / 12)
     assert closed * 1e3 == pytest.approx(g["analytical_mm"], abs=5e-4)
@@ -191,7 +192,8 @@ def test_thin_cantilever_small_load_is_linear():
     g = GOLD["thin_cantilever"]
     sc, tip = beam_scene(tuple(g["voxels"]), -g["tip_force_N"] / 10, 0.0025)
     o = Oracle(sc)
-    closed = g["tip_force_N"] / 10 * (19e-3) ** 3 / (3 * g["E_Pa"] * 1e-12 / 12)
+    l = sc["voxel_size"]
+    closed = g["tip_force_N"] / 10 * (19 * l) ** 3 / (3 * g["E_Pa"] * l ** 4 / 12)
     z0 = o.state()["pos"][tip, 2][0]
     dz = -relax(o, lambda: o.state()["pos"][tip, 2][0] - z0, tol=1e-10, chunk=5000)
     assert dz == pytest.approx(closed, rel=1e-3)
@@ -221,7 +223,8 @@ def test_free_expansion_zero_stress_state():
     o = Oracle(sc)
     ext = lambda: np.ptp(o.state()["pos"][:, 0])
     e = relax(o, ext, tol=1e-13)
-    assert e == pytest.approx((n - 1) * 1e-3 * (1 + a * dT), rel=1e-9)
+    l, a, dT = sc["voxel_size"], sc["palette"][0, 3], sc["act_offset"]
+    assert e == pytest.approx((n - 1) * l * (1 + a * dT), rel=1e-9)
     s = o.state()
     assert np.abs(s["vel"]).max() < 1e-9
 
@@ -330,12 +333,12 @@ def test_free_fall_symplectic_euler():
     """One voxel under gravity: v_n = n g dt, z_n = z_0 + g dt^2 n (n + 1) / 2."""
     sc = scenes._base([(1, 1, 1)], np.ones(1, np.uint8), 1e-3, [scenes.material(1e6)], gravity_z=-9.81)
     o = Oracle(sc)
-    dt = o.dt()
+    dt, g = o.dt(), sc["gravity_z"]
     z0 = o.state()["pos"][0, 2]
     o.step(100)
     s = o.state()
-    assert s["vel"][0, 2] == pytest.approx(-9.81 * 100 * dt, rel=1e-12)
-    assert s["pos"][0, 2] - z0 == pytest.approx(-9.81 * dt * dt * 100 * 101 / 2, rel=1e-10)
+    assert s["vel"][0, 2] == pytest.approx(g * 100 * dt, rel=1e-12)
+    assert s["pos"][0, 2] - z0 == pytest.approx(g * dt * dt * 100 * 101 / 2, rel=1e-10)
 
 
 def test_floor_rest_penetration():
@@ -344,20 +347,23 @@ def test_floor_rest_penetration():
                       gravity_z=-9.81, floor=True, zeta_collision=1.0)
     o = Oracle(sc)
     z = relax(o, lambda: o.state()["pos"][0, 2], tol=1e-13)
-    pen = 0.5e-3 - z
-    assert pen == pytest.approx(1000 * 1e-9 * 9.81 / (1e6 * 1e-3), rel=1e-9)
+    l = sc["voxel_size"]
+    pen = 0.5 * l - z
+    assert pen == pytest.approx(1000 * l ** 3 * -sc["gravity_z"] / (1e6 * l), rel=1e-9)
 
 
 def test_static_friction_threshold_and_sliding_deceleration():
     """Coulomb model of Sec 2.2.1: no motion while |F_l| <= mu_s F_n; once it
     slides with the push removed, it decelerates at mu_d g and halts."""
-    mu_s, mu_k, m, g = 0.8, 0.4, 1e-6, 9.81
     def scene(Fx):
         sc = scenes._base([(1, 1, 1)], np.ones(1, np.uint8), 1e-3,
-                          [scenes.material(1e6, mu_s=mu_s, mu_k=mu_k)],
-                          gravity_z=-g, floor=True, zeta_collision=1.0)
+                          [scenes.material(1e6, mu_s=0.8, mu_k=0.4)],
+                          gravity_z=-9.81, floor=True, zeta_collision=1.0)
         sc["force"] = np.array([[Fx, 0.0, 0.0]])
         return sc
+    sc0 = scene(0.0)
+    mu_s, mu_k = sc0["palette"][0, 4], sc0["palette"][0, 5]
+    m, g = 1000.0 * sc0["voxel_size"] ** 3, -sc0["gravity_z"]
     # settle first without lateral load, then push
     for frac, moves in [(0.98, False), (1.02, True)]:
         o = Oracle(scene(0.0))
