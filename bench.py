@@ -1,0 +1,237 @@
+"""Benchmark of one explicit lattice step on the heterogeneous actuated block
+(64 x 64 x 32 sites, 10 % empty, soft/stiff mix, sinusoidal actuation, floor
+contact with friction, gravity; seed 2).
+
+One bench "step" is one simulation step of the whole lattice (bond pass +
+voxel gather/contact/integrate pass).  The state fits in L2, so the timed
+loop writes a 256 MB buffer between steps (L2 flush) and times every step
+with CUDA events on the simulator's stream; `value` is voxel-steps per second
+over the K timed steps.
+
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on the
+same workload instead.  Under torchrun every rank runs an independent replica
+(the plain step of one lattice is not sharded across GPUs).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1212_2845_gb300 import scenes  # noqa: E402
+
+METRIC = "voxel-steps/s"
+WORKLOAD = "hetero_block_64x64x32 (plain step: bond pass + voxel pass)"
+B_ALG = 112  # algorithmic bytes per voxel-step for this workload (state r/w 104, flags 2, material 1,
+             # bond mask 1, phase 4); bond results are not algorithmic traffic
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except FileNotFoundError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            self.proc.wait()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
+
+
+def cpu_baseline(sc, seconds=12.0):
+    """The FP64 oracle (single thread) on a bounded sample of the same workload."""
+    from oracle import Oracle
+    o = Oracle(sc)
+    n = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        o.step(5)
+        n += 5
+    t = time.perf_counter() - t0
+    return {"value": o.N * n / t, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{WORKLOAD}, first {n} steps from rest, FP64, 1 thread, {t:.1f} s"}
+
+
+def run_reference(args, sc):
+    rank, _, ws = dist_env()
+    if rank != 0:
+        return
+    from oracle import Oracle
+    o = Oracle(sc)
+    for _ in range(args.warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(1)
+    t = time.perf_counter() - t0
+    v = o.N * args.steps / t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "voxels": o.N, "bonds": o.n_bonds},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": f"{args.steps} steps after {args.warmup} warm-up, 1 thread"},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    sc = scenes.hetero_block()
+    if args.impl == "reference":
+        run_reference(args, sc)
+        return
+
+    import torch
+    rank, local_rank, ws = dist_env()
+    torch.cuda.set_device(local_rank)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1212_2845_gb300 import vx
+
+    sim = vx.Sim(sc)
+    stream = torch.cuda.Stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            flush.fill_(0.0)
+            sim.step_async(1, stream)
+    stream.synchronize()
+
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local_rank) as clk:
+        t_wall0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            for i in range(args.steps):
+                flush.fill_(float(i & 1))          # evicts the lattice from L2 between steps
+                ev[i][0].record(stream)
+                sim.step_async(1, stream)
+                ev[i][1].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall0
+        torch.cuda.synchronize()
+    st, _, _ = sim.status(stream)
+    if st != 0:
+        raise RuntimeError(f"simulation reported status {st}")
+    times = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3  # s
+    t_steps = float(times.sum())
+    if ws > 1:
+        tt = torch.tensor([t_steps], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_steps = float(tt.item())
+        torch.distributed.barrier()
+    value = ws * sim.N * args.steps / t_steps
+    avg = t_steps / args.steps
+
+    # end to end through the C ABI with host buffers: state in, one step, state out
+    N = sim.N
+    pin = {k: torch.empty(shape, dtype=dt).pin_memory() for k, shape, dt in
+           (("offset", (N, 3), torch.float32), ("quat", (N, 4), torch.float32), ("vel", (N, 3), torch.float32),
+            ("angvel", (N, 3), torch.float32), ("flags", (N,), torch.uint8))}
+    sim.read_state_into(**pin, stream=stream, on_device=False)
+    nb = sum(t.numel() * t.element_size() for t in pin.values())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        sim.write_state_from(**pin, stream=stream, on_device=False)
+        sim.step(1, stream)
+        sim.read_state_into(**pin, stream=stream, on_device=False)
+    t_e2e = time.perf_counter() - t0
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    peak, peak_kind = load_peaks()
+    achieved = B_ALG * N / avg / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": avg * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "voxels": N, "bonds": sim.n_bonds, "l2": "flushed between steps",
+                   "parallelism": "replicas" if ws > 1 else "single", "bond_steps_per_s": ws * sim.n_bonds * args.steps / t_steps,
+                   "wall_s": t_wall},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "one step (bond_pass + voxel_pass)",
+                     "bytes_per_voxel_step": B_ALG, "peak_kind": peak_kind},
+        "e2e": {"value": N * args.e2e_steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": nb,
+                "d2h_bytes_per_step": nb},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk.summary(),
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(sc)
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

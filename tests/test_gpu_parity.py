@@ -174,24 +174,28 @@ def test_design_population_reduced(vx):
 
 
 def test_appendix_a_program(vx):
-    """App. A: 5x10x5 beam, 10 MPa, -Y face fixed, 1 kN on +Y face, slow damping 0.013, 400 steps."""
+    """App. A: 5x10x5 beam of 10 MPa voxels, -Y face fixed, force on the +Y face,
+    slow damping 0.013, 400 steps.  The printed 1 kN (40 MPa on a 5 mm x 5 mm
+    section, strain ~4) is far outside the small-angle beam model and diverges
+    on both sides; 1 N keeps the same program in the elastic range."""
     sc = scenes._base([(5, 10, 5)], np.ones(250, np.uint8), 1e-3, [scenes.material(1e7, 0.3)],
                       zeta_ground=0.013)
     sim = vx.Sim(sc)
     ora = Oracle(sc)
-    assert sim.add_fixed_region(0, (0, 0, 0), (1, 0.01, 1)) == 50
-    assert sim.add_forced_region(0, (0, 0.99, 0), (1, 0.01, 1), (0, 0, -1000.0)) == 50
-    ora.set_fixed(ora.region_mask(0, (0, 0, 0), (1, 0.01, 1)))
+    assert sim.add_fixed_region(0, (0, 0, 0), (1, 0.01, 1)) == 25      # the y = 0 layer, 5 x 5
+    assert sim.add_forced_region(0, (0, 0.99, 0), (1, 0.01, 1), (0, 0, -1.0)) == 25
+    fixed = ora.region_mask(0, (0, 0, 0), (1, 0.01, 1))
+    ora.set_fixed(fixed)
     m = ora.region_mask(0, scenes.f32((0, 0.99, 0)), scenes.f32((1, 0.01, 1)))
     F = np.zeros((ora.N, 3))
-    F[m.astype(bool), 2] = float(np.float32(-1000.0 / 50))
+    F[m.astype(bool), 2] = float(np.float32(-1.0 / 25))
     ora.set_force(F)
     ora.reset()
     ora.set_dt(f32_dt(ora))
     sim.step(400)
     ora.step(400)
     g, o = sim.state(), ora.state()
-    assert np.array_equal(g["flags"] & 1, ora.region_mask(0, (0, 0, 0), (1, 0.01, 1)))
+    assert np.array_equal(g["flags"] & 1, fixed)
     assert pos_error(sc, g, o) < 1e-5
 
 
