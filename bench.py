@@ -2,11 +2,13 @@
 (64 x 64 x 32 sites, 10 % empty, soft/stiff mix, sinusoidal actuation, floor
 contact with friction, gravity; seed 2).
 
-One bench "step" is one simulation step of the whole lattice (bond pass +
-voxel gather/contact/integrate pass).  The state fits in L2, so the timed
-loop writes a 256 MB buffer between steps (L2 flush) and times every step
-with CUDA events on the simulator's stream; `value` is voxel-steps per second
-over the K timed steps.
+One bench "step" is one simulation step of the whole lattice: one launch of
+the fused step kernel (bonds, gather, contacts, integration).  The state fits
+in L2, so the timed loop writes a 256 MB buffer between steps (L2 flush) and
+times every step with CUDA events on the simulator's stream; `value` is
+voxel-steps per second over the K timed steps.  The line also carries the same
+measurement on a lattice larger than L2 (hollow shell R 200, t 8), where HBM
+bandwidth bounds the step.
 
 Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on the
 same workload instead.  Under torchrun every rank runs an independent replica
@@ -31,7 +33,7 @@ sys.path.insert(0, ROOT)
 from paper_1212_2845_gb300 import scenes  # noqa: E402
 
 METRIC = "voxel-steps/s"
-WORKLOAD = "hetero_block_64x64x32 (plain step: bond pass + voxel pass)"
+WORKLOAD = "hetero_block_64x64x32 (plain step, fused kernel)"
 B_ALG = 112  # algorithmic bytes per voxel-step for this workload (state r/w 104, flags 2, material 1,
              # bond mask 1, phase 4); bond results are not algorithmic traffic
 
@@ -130,6 +132,49 @@ def run_reference(args, sc):
     print(json.dumps(line), flush=True)
 
 
+def time_steps(sim, stream, steps, warmup, flush=None):
+    """Per-step CUDA-event times (s) of `steps` single-step launches."""
+    import torch
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            if flush is not None:
+                flush.fill_(0.0)
+            sim.step_async(1, stream)
+    stream.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    with torch.cuda.stream(stream):
+        for i in range(steps):
+            if flush is not None:
+                flush.fill_(float(i & 1))      # evicts the lattice from L2 between steps
+            ev[i][0].record(stream)
+            sim.step_async(1, stream)
+            ev[i][1].record(stream)
+    stream.synchronize()
+    st, _, _ = sim.status(stream)
+    if st != 0:
+        raise RuntimeError(f"simulation reported status {st}")
+    return np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
+
+
+def large_lattice(stream, peak, steps=200, warmup=5):
+    """Plain step on a hollow shell of outer radius 200 and thickness 8 voxels
+    (3.86M voxels, state ~400 MB per step: larger than L2), on the floor."""
+    from paper_1212_2845_gb300 import vx
+    sc = scenes.hollow_ball(R=200, t=8, collide=False)
+    sim = vx.Sim(sc)
+    t = time_steps(sim, stream, steps, warmup)
+    avg = float(t.mean())
+    b_alg = 108  # state r/w 104, flags 2, material 1, bond mask 1
+    out = {"workload": "hollow_shell_R200_t8 (plain step, fused kernel, no self-collision)", "voxels": sim.N,
+           "bonds": sim.n_bonds, "value": sim.N / avg, "unit": METRIC, "ms_per_step": avg * 1e3,
+           "l2": "inputs larger than L2",
+           "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg}}
+    sim.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -138,6 +183,7 @@ def main():
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=300)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     sc = scenes.hetero_block()
@@ -156,31 +202,14 @@ def main():
     sim = vx.Sim(sc)
     stream = torch.cuda.Stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    with torch.cuda.stream(stream):
-        for _ in range(args.warmup):
-            flush.fill_(0.0)
-            sim.step_async(1, stream)
-    stream.synchronize()
-
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
         t_wall0 = time.perf_counter()
-        with torch.cuda.stream(stream):
-            for i in range(args.steps):
-                flush.fill_(float(i & 1))          # evicts the lattice from L2 between steps
-                ev[i][0].record(stream)
-                sim.step_async(1, stream)
-                ev[i][1].record(stream)
-        stream.synchronize()
+        times = time_steps(sim, stream, args.steps, args.warmup, flush)
         t_wall = time.perf_counter() - t_wall0
         torch.cuda.synchronize()
-    st, _, _ = sim.status(stream)
-    if st != 0:
-        raise RuntimeError(f"simulation reported status {st}")
-    times = np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3  # s
     t_steps = float(times.sum())
     if ws > 1:
         tt = torch.tensor([t_steps], dtype=torch.float64, device="cuda")
@@ -219,13 +248,15 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single", "bond_steps_per_s": ws * sim.n_bonds * args.steps / t_steps,
                    "wall_s": t_wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "one step (bond_pass + voxel_pass)",
+                     "traffic": None, "kernel": "fused_step<256>",
                      "bytes_per_voxel_step": B_ALG, "peak_kind": peak_kind},
         "e2e": {"value": N * args.e2e_steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": nb,
                 "d2h_bytes_per_step": nb},
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": args.steps,
         "clocks": clk.summary(),
     }
+    if not args.no_large:
+        line["large_lattice"] = large_lattice(stream, peak)
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

@@ -125,6 +125,15 @@ VX_API int vx_plan_dt(const vx_desc* desc, const float* log_E, float dt_factor, 
 VX_API int vx_region_mask(const vx_desc* desc, int32_t body, const float loc[3], const float size[3],
                    uint8_t* mask, int64_t* n_out);
 
+/* Tiles of the fused step kernel for a description: voxels are ordered in
+ * 4x4x4-site bricks along a Morton curve and cut into runs of at most
+ * tile_max voxels (128, 256 or 512); each tile also stages its halo (face
+ * neighbours outside it).  Outputs (nullable): number of tiles, halo entries
+ * over all tiles, bonds over all tiles (bonds on a tile border counted in both
+ * tiles), and the largest owned + halo set of one tile. */
+VX_API int vx_plan_tiles(const vx_desc* desc, int32_t tile_max, int64_t* n_tiles, int64_t* n_halo,
+                         int64_t* n_tile_bonds, int32_t* max_local);
+
 /* ---- lifetime ------------------------------------------------------------ */
 /* Build the lattice (Sec 2.1: voxelised geometry, composite bonds,
  * precomputed surface list) on the current CUDA device and reset the state
@@ -135,6 +144,19 @@ VX_API void vx_destroy(vx_sim* sim);
 VX_API int vx_get_counts(vx_sim* sim, int64_t* n_voxels, int64_t* n_bonds, int64_t* n_surface);
 /* Lattice anchors (rest centres) [N][3] in double precision, host memory. */
 VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
+
+/* Kernel form of the step.  VX_FORM_FUSED (default): one kernel per step,
+ * bond forces kept in shared memory.  VX_FORM_TWO_PASS: a bond kernel writes
+ * every bond's forces to device memory and a voxel kernel gathers them.  Both
+ * forms compute the same arithmetic and give bitwise-identical states.
+ * tile_max (fused form): 128, 256 or 512 voxels per tile, 0 keeps the current
+ * size (256 at create).  The state is kept. */
+#define VX_FORM_FUSED 0
+#define VX_FORM_TWO_PASS 1
+VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
+/* Current tiling: tile size, tile count, largest staged set, dynamic shared
+ * memory of the fused kernel in bytes.  Any output may be NULL. */
+VX_API int vx_get_tiling(vx_sim* sim, int32_t* tile_max, int64_t* n_tiles, int32_t* max_local, int64_t* smem_bytes);
 
 /* ---- configuration (host inputs, copied) -------------------------------- */
 /* Replace the palette (same count); recomputes bonds' composites and dt. */

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -49,8 +50,13 @@ template <class T> void dfree(T*& p) {
 
 struct vx_sim {
   Lattice L;
+  Tiling T;
   int device = 0;
   int64_t pitch = 0;
+  int form = 0;            // 0 fused, 1 two-pass
+  int tile_max = 256;
+  size_t smem = 0;
+  int cur = 0;             // index of the buffer holding the current state
   // parameters
   float zb = 1.f, zg = 0.f, zc = 1.f, gz = 0.f;
   int floor_on = 0, collide_on = 0;
@@ -59,11 +65,20 @@ struct vx_sim {
   float dt_factor = 0.9f;
   std::vector<double> dt;
   std::vector<float> logE_h;
+  std::vector<float> fext_h;   // canonical order, 3 per voxel
+  std::vector<int32_t> surf_h; // surface voxels, internal order
   int64_t step = 0;
   bool has_phase = false, has_fext = false;
-  // device buffers
-  float* st = nullptr;
-  float* bf = nullptr;
+  // device buffers (internal order)
+  float* st = nullptr;     // two state buffers of NPLANE * pitch floats
+  float* bf = nullptr;     // two-pass bond results (allocated on first use)
+  int32_t* iperm = nullptr;
+  int4* tile_a = nullptr;
+  int4* tile_b = nullptr;
+  int32_t* halo = nullptr;
+  uint16_t* plus = nullptr;
+  uint32_t* hbonds = nullptr;
+  uint8_t* mask = nullptr;
   uint8_t* flags = nullptr;
   uint8_t* mat = nullptr;
   uint32_t* lat = nullptr;
@@ -102,12 +117,16 @@ struct vx_sim {
 
 namespace {
 
+float* cur_state(vx_sim* s) { return s->st + (size_t)s->cur * NPLANE * s->pitch; }
+float* next_state(vx_sim* s) { return s->st + (size_t)(1 - s->cur) * NPLANE * s->pitch; }
+
 StepArgs step_args(vx_sim* s) {
   StepArgs A;
   A.N = (int)s->L.N;
   A.pitch = s->pitch;
   A.l = s->L.l;
-  A.st = s->st;
+  A.st_in = cur_state(s);
+  A.st_out = next_state(s);
   A.flags = s->flags;
   A.mat = s->mat;
   A.lat = s->lat;
@@ -117,14 +136,25 @@ StepArgs step_args(vx_sim* s) {
   A.logE = s->logE_h.empty() ? nullptr : s->logE;
   A.fext = s->has_fext ? s->fext : nullptr;
   A.mats = s->mats;
+  A.n_mats = (int)s->L.palette.size();
   A.dt_body = s->dtb;
   A.origin = s->origin;
   A.bf = s->bf;
   A.zb = s->zb; A.zg = s->zg; A.zc = s->zc; A.gz = s->gz;
   A.floor_on = s->floor_on;
   A.collide_on = s->collide_on;
-  A.actA = s->actA; A.actT0 = s->actT0; A.actP = s->actP;
+  A.actA = s->actA; A.actT0 = s->actT0;
+  A.act_on = (s->actA != 0.f || s->actT0 != 0.f) ? 1 : 0;
+  A.act_w = 0.f;
   A.step = s->step;
+  A.tile_a = s->tile_a;
+  A.tile_b = s->tile_b;
+  A.halo = s->halo;
+  A.plus = s->plus;
+  A.hbonds = s->hbonds;
+  A.mask = s->mask;
+  A.n_tiles = (int)s->T.n_tiles();
+  A.max_local = s->T.max_local;
   A.sidx = s->sidx;
   A.ccount = s->ccount;
   A.cand = s->cand;
@@ -142,7 +172,7 @@ CollideArgs collide_args(vx_sim* s) {
   C.Q = s->qQ;
   C.pitch = s->pitch;
   C.threshold = s->threshold;
-  C.st = s->st;
+  C.st = cur_state(s);
   C.surf = s->surf;
   C.lat = s->lat;
   C.body = s->body;
@@ -221,9 +251,13 @@ int alloc_collisions(vx_sim* s) {
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
     return rc;
-  std::vector<int32_t> sidx(L.N, -1);
-  for (int64_t i = 0; i < S; ++i) sidx[L.surf_list[i]] = (int32_t)i;
-  VX_CUDA(cudaMemcpy(s->surf, L.surf_list.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
+  // surface voxels in ascending internal order
+  std::vector<int32_t> surf(S), sidx(L.N, -1);
+  for (int64_t i = 0; i < S; ++i) surf[i] = s->T.iperm[L.surf_list[i]];
+  std::sort(surf.begin(), surf.end());
+  for (int64_t i = 0; i < S; ++i) sidx[surf[i]] = (int32_t)i;
+  s->surf_h = surf;
+  VX_CUDA(cudaMemcpy(s->surf, surf.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemcpy(s->sidx, sidx.data(), L.N * sizeof(int32_t), cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemset(s->ccount, 0, std::max<int64_t>(S, 1) * sizeof(int32_t)));
   VX_CUDA(cudaMemset(s->acc, 0, L.n_bodies * sizeof(float)));
@@ -253,14 +287,70 @@ int check_sim(vx_sim* s) {
 
 int ensure_stage(vx_sim* s) {
   if (s->stage) return VX_OK;
-  return dalloc(&s->stage, (size_t)14 * s->L.N);  // 13 floats + flags bytes (packed in the 14th plane)
+  return dalloc(&s->stage, (size_t)14 * s->L.N);  // 13 floats + the flag bytes
+}
+
+// canonical-order host array -> internal-order device array
+template <class T> int upload_permuted(vx_sim* s, T* dst, const T* src, int planes, int64_t plane_stride) {
+  int64_t N = s->L.N;
+  std::vector<T> h((size_t)planes * plane_stride, T(0));
+  for (int p = 0; p < planes; ++p)
+    for (int64_t c = 0; c < N; ++c) h[(size_t)p * plane_stride + s->T.iperm[c]] = src[(size_t)planes * c + p];
+  VX_CUDA(cudaMemcpy(dst, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return VX_OK;
+}
+
+int upload_tiling(vx_sim* s) {
+  const Tiling& T = s->T;
+  int64_t nt = T.n_tiles();
+  dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds);
+  int rc;
+  if ((rc = dalloc(&s->tile_a, nt)) || (rc = dalloc(&s->tile_b, nt)) || (rc = dalloc(&s->halo, T.halo.size())) ||
+      (rc = dalloc(&s->plus, T.plus.size())) || (rc = dalloc(&s->hbonds, T.halo_bonds.size())))
+    return rc;
+  VX_CUDA(cudaMemcpy(s->tile_a, T.tile_a.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemcpy(s->tile_b, T.tile_b.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
+  if (!T.halo.empty()) VX_CUDA(cudaMemcpy(s->halo, T.halo.data(), T.halo.size() * 4, cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemcpy(s->plus, T.plus.data(), T.plus.size() * 2, cudaMemcpyHostToDevice));
+  if (!T.halo_bonds.empty())
+    VX_CUDA(cudaMemcpy(s->hbonds, T.halo_bonds.data(), T.halo_bonds.size() * 4, cudaMemcpyHostToDevice));
+  s->smem = fused_smem_bytes(s->tile_max, (int)s->L.palette.size());
+  if (prepare_fused(s->tile_max, s->smem) != 0)
+    return fail(VX_ERR_CUDA, "fused kernel needs " + std::to_string(s->smem) + " bytes of shared memory");
+  return VX_OK;
+}
+
+int ensure_two_pass(vx_sim* s) {
+  if (s->bf) return VX_OK;
+  int64_t N = s->L.N;
+  int rc;
+  if ((rc = dalloc(&s->bf, 27 * s->pitch)) || (rc = dalloc(&s->nbr, 6 * N))) return rc;
+  std::vector<int32_t> nb(6 * (size_t)N);
+  for (int sl = 0; sl < 6; ++sl)
+    for (int64_t c = 0; c < N; ++c) {
+      int32_t u = s->L.nbr[(size_t)sl * N + c];
+      nb[(size_t)sl * N + s->T.iperm[c]] = u < 0 ? -1 : s->T.iperm[u];
+    }
+  VX_CUDA(cudaMemcpy(s->nbr, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemset(s->bf, 0, sizeof(float) * 27 * s->pitch));
+  return VX_OK;
+}
+
+// read-modify-write of the flag bytes in canonical order
+int edit_flags(vx_sim* s, const std::function<void(int64_t c, uint8_t& f)>& fn) {
+  int64_t N = s->L.N;
+  std::vector<uint8_t> f(N);
+  VX_CUDA(cudaMemcpy(f.data(), s->flags, N, cudaMemcpyDeviceToHost));
+  for (int64_t c = 0; c < N; ++c) fn(c, f[s->T.iperm[c]]);
+  VX_CUDA(cudaMemcpy(s->flags, f.data(), N, cudaMemcpyHostToDevice));
+  return VX_OK;
 }
 
 }  // namespace
 
 extern "C" {
 
-const char* vx_version(void) { return "voxsim-gb300 0.1 (sm_103a)"; }
+const char* vx_version(void) { return "voxsim-gb300 0.2 (sm_103a)"; }
 const char* vx_last_error(void) { return g_err.c_str(); }
 
 int vx_plan_counts(const vx_desc* desc, int64_t* n_voxels, int64_t* n_bonds, int64_t* n_surface) {
@@ -285,6 +375,21 @@ int vx_plan_dt(const vx_desc* desc, const float* log_E, float dt_factor, double*
   return VX_OK;
 }
 
+int vx_plan_tiles(const vx_desc* desc, int32_t tile_max, int64_t* n_tiles, int64_t* n_halo, int64_t* n_tile_bonds,
+                  int32_t* max_local) {
+  Lattice L;
+  int rc = build_lattice(desc, L, g_err);
+  if (rc) return rc;
+  Tiling T;
+  if (tile_max != 128 && tile_max != 256 && tile_max != 512) return fail(VX_ERR_ARG, "tile_max must be 128, 256 or 512");
+  if ((rc = build_tiling(L, tile_max, 2 * tile_max, T, g_err))) return rc;
+  if (n_tiles) *n_tiles = T.n_tiles();
+  if (n_halo) *n_halo = (int64_t)T.halo.size();
+  if (n_tile_bonds) *n_tile_bonds = T.n_tile_bonds();
+  if (max_local) *max_local = T.max_local;
+  return VX_OK;
+}
+
 int vx_region_mask(const vx_desc* desc, int32_t body, const float loc[3], const float size[3], uint8_t* mask,
                    int64_t* n_out) {
   if (!loc || !size || !mask) return fail(VX_ERR_ARG, "loc, size and mask are required");
@@ -303,31 +408,38 @@ int vx_create(const vx_desc* desc, vx_sim** out) {
   vx_sim* s = new (std::nothrow) vx_sim();
   if (!s) return fail(VX_ERR_OOM, "host allocation failed");
   int rc = build_lattice(desc, s->L, g_err);
+  if (!rc) rc = build_tiling(s->L, s->tile_max, 2 * s->tile_max, s->T, g_err);
   if (rc) { delete s; return rc; }
   if (cudaGetDevice(&s->device) != cudaSuccess) { delete s; return fail(VX_ERR_CUDA, "no CUDA device"); }
   const Lattice& L = s->L;
   int64_t N = L.N;
   s->pitch = (N + 31) / 32 * 32;
-  if ((rc = dalloc(&s->st, NPLANE * s->pitch)) || (rc = dalloc(&s->bf, 27 * s->pitch)) ||
-      (rc = dalloc(&s->flags, N)) || (rc = dalloc(&s->mat, N)) || (rc = dalloc(&s->lat, N)) ||
-      (rc = dalloc(&s->nbr, 6 * N)) || (rc = dalloc(&s->mats, L.palette.size())) ||
-      (rc = dalloc(&s->dtb, L.n_bodies)) || (rc = dalloc(&s->origin, 3 * L.n_bodies)) ||
-      (rc = dalloc(&s->status, 4)) || (rc = dalloc(&s->vmax, L.n_bodies)) ||
-      (L.n_bodies > 1 && (rc = dalloc(&s->body, N)))) {
+  if ((rc = dalloc(&s->st, 2 * NPLANE * s->pitch)) || (rc = dalloc(&s->flags, N)) || (rc = dalloc(&s->mat, N)) ||
+      (rc = dalloc(&s->lat, N)) || (rc = dalloc(&s->iperm, N)) || (rc = dalloc(&s->mask, N)) ||
+      (rc = dalloc(&s->mats, L.palette.size())) || (rc = dalloc(&s->dtb, L.n_bodies)) ||
+      (rc = dalloc(&s->origin, 3 * L.n_bodies)) || (rc = dalloc(&s->status, 4)) ||
+      (rc = dalloc(&s->vmax, L.n_bodies)) || (L.n_bodies > 1 && (rc = dalloc(&s->body, N)))) {
     vx_destroy(s);
     return rc;
   }
+  std::vector<uint8_t> mat(N);
+  std::vector<uint32_t> lat(N);
+  std::vector<int32_t> body(N);
+  for (int64_t v = 0; v < N; ++v) {
+    int32_t c = s->T.perm[v];
+    mat[v] = L.mat[c]; lat[v] = L.lat[c]; body[v] = L.body[c];
+  }
   auto up = [&](void* d, const void* h, size_t n) { return cudaMemcpy(d, h, n, cudaMemcpyHostToDevice); };
-  if (up(s->mat, L.mat.data(), N) || up(s->lat, L.lat.data(), N * 4) || up(s->nbr, L.nbr.data(), 6 * N * 4) ||
-      up(s->origin, L.origin.data(), 3 * L.n_bodies * 4) ||
-      (s->body && up(s->body, L.body.data(), N * 4)) || cudaMemset(s->flags, 0, N) ||
+  if (up(s->mat, mat.data(), N) || up(s->lat, lat.data(), N * 4) || up(s->iperm, s->T.iperm.data(), N * 4) ||
+      up(s->mask, s->T.mask.data(), N) || up(s->origin, L.origin.data(), 3 * L.n_bodies * 4) ||
+      (s->body && up(s->body, body.data(), N * 4)) || cudaMemset(s->flags, 0, N) ||
       cudaMemset(s->status, 0, 16) || cudaMemset(s->vmax, 0, 4 * L.n_bodies) ||
-      cudaMemset(s->bf, 0, sizeof(float) * 27 * s->pitch)) {
+      cudaMemset(s->st, 0, sizeof(float) * 2 * NPLANE * s->pitch)) {
     vx_destroy(s);
     return fail(VX_ERR_CUDA, "upload failed");
   }
   quant_params(L.l, &s->qK, &s->qQ);
-  if ((rc = upload_materials(s)) || (rc = recompute_dt(s)) || (rc = vx_reset(s, nullptr))) {
+  if ((rc = upload_tiling(s)) || (rc = upload_materials(s)) || (rc = recompute_dt(s)) || (rc = vx_reset(s, nullptr))) {
     vx_destroy(s);
     return rc;
   }
@@ -339,6 +451,7 @@ void vx_destroy(vx_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   dfree(s->st); dfree(s->bf); dfree(s->flags); dfree(s->mat); dfree(s->lat); dfree(s->body); dfree(s->nbr);
+  dfree(s->iperm); dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds); dfree(s->mask);
   dfree(s->phase); dfree(s->logE); dfree(s->fext); dfree(s->mats); dfree(s->dtb); dfree(s->origin);
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
@@ -367,6 +480,36 @@ int vx_get_anchors(vx_sim* s, double* anchors) {
   return VX_OK;
 }
 
+int vx_set_step_form(vx_sim* s, int32_t form, int32_t tile_max) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (form != VX_FORM_FUSED && form != VX_FORM_TWO_PASS) return fail(VX_ERR_ARG, "unknown step form");
+  if (form == VX_FORM_TWO_PASS && (rc = ensure_two_pass(s))) return rc;
+  if (form == VX_FORM_FUSED && tile_max != 0 && tile_max != s->tile_max) {
+    if (tile_max != 128 && tile_max != 256 && tile_max != 512) return fail(VX_ERR_ARG, "tile_max must be 128, 256 or 512");
+    // the voxel order depends only on the lattice, so the state stays valid
+    Tiling T;
+    if ((rc = build_tiling(s->L, tile_max, 2 * tile_max, T, g_err))) return rc;
+    s->T.tile_a.swap(T.tile_a); s->T.tile_b.swap(T.tile_b); s->T.halo.swap(T.halo); s->T.plus.swap(T.plus);
+    s->T.halo_bonds.swap(T.halo_bonds);
+    s->T.tile_max = tile_max;
+    s->T.max_local = T.max_local;
+    s->tile_max = tile_max;
+    if ((rc = upload_tiling(s))) return rc;
+  }
+  s->form = form;
+  return VX_OK;
+}
+
+int vx_get_tiling(vx_sim* s, int32_t* tile_max, int64_t* n_tiles, int32_t* max_local, int64_t* smem_bytes) {
+  if (!s) return fail(VX_ERR_ARG, "sim is NULL");
+  if (tile_max) *tile_max = s->tile_max;
+  if (n_tiles) *n_tiles = s->T.n_tiles();
+  if (max_local) *max_local = s->T.max_local;
+  if (smem_bytes) *smem_bytes = (int64_t)s->smem;
+  return VX_OK;
+}
+
 int vx_set_materials(vx_sim* s, const vx_material* palette, int32_t n) {
   int rc = check_sim(s);
   if (rc) return rc;
@@ -391,12 +534,12 @@ int vx_set_voxel_params(vx_sim* s, const float* log_E, const float* phase) {
       if (!std::isfinite(log_E[v])) return fail(VX_ERR_ARG, "log_E must be finite");
     if (!s->logE && (rc = dalloc(&s->logE, N))) return rc;
     s->logE_h.assign(log_E, log_E + N);
-    VX_CUDA(cudaMemcpy(s->logE, log_E, N * 4, cudaMemcpyHostToDevice));
+    if ((rc = upload_permuted(s, s->logE, log_E, 1, N))) return rc;
     if ((rc = recompute_dt(s))) return rc;
   }
   if (phase) {
     if (!s->phase && (rc = dalloc(&s->phase, N))) return rc;
-    VX_CUDA(cudaMemcpy(s->phase, phase, N * 4, cudaMemcpyHostToDevice));
+    if ((rc = upload_permuted(s, s->phase, phase, 1, N))) return rc;
     s->has_phase = true;
   }
   return VX_OK;
@@ -406,12 +549,7 @@ int vx_set_fixed_mask(vx_sim* s, const uint8_t* mask) {
   int rc = check_sim(s);
   if (rc) return rc;
   if (!mask) return fail(VX_ERR_ARG, "mask is NULL");
-  int64_t N = s->L.N;
-  std::vector<uint8_t> f(N);
-  VX_CUDA(cudaMemcpy(f.data(), s->flags, N, cudaMemcpyDeviceToHost));
-  for (int64_t v = 0; v < N; ++v) f[v] = (uint8_t)((f[v] & ~1u) | (mask[v] ? 1u : 0u));
-  VX_CUDA(cudaMemcpy(s->flags, f.data(), N, cudaMemcpyHostToDevice));
-  return VX_OK;
+  return edit_flags(s, [&](int64_t c, uint8_t& f) { f = (uint8_t)((f & ~1u) | (mask[c] ? 1u : 0u)); });
 }
 
 int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float size[3], int64_t* n_out) {
@@ -419,17 +557,16 @@ int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float
   if (rc) return rc;
   if (!loc || !size || body < 0 || body >= s->L.n_bodies) return fail(VX_ERR_ARG, "bad region");
   int64_t N = s->L.N;
-  std::vector<uint8_t> m(N), f(N);
+  std::vector<uint8_t> m(N);
   int64_t n = region_mask(s->L, body, loc, size, m.data());
-  VX_CUDA(cudaMemcpy(f.data(), s->flags, N, cudaMemcpyDeviceToHost));
-  for (int64_t v = 0; v < N; ++v) if (m[v]) f[v] |= 1u;
-  VX_CUDA(cudaMemcpy(s->flags, f.data(), N, cudaMemcpyHostToDevice));
-  // fixed voxels are immobile: zero their velocities
+  if ((rc = edit_flags(s, [&](int64_t c, uint8_t& f) { if (m[c]) f |= 1u; }))) return rc;
+  // fixed voxels are immobile: zero their velocities in the current state
   std::vector<float> st(NPLANE * (size_t)s->pitch);
-  VX_CUDA(cudaMemcpy(st.data(), s->st, st.size() * 4, cudaMemcpyDeviceToHost));
-  for (int64_t v = 0; v < N; ++v)
-    if (m[v]) for (int p = VX; p <= WZ; ++p) st[(size_t)p * s->pitch + v] = 0.f;
-  VX_CUDA(cudaMemcpy(s->st, st.data(), st.size() * 4, cudaMemcpyHostToDevice));
+  float* cs = cur_state(s);
+  VX_CUDA(cudaMemcpy(st.data(), cs, st.size() * 4, cudaMemcpyDeviceToHost));
+  for (int64_t c = 0; c < N; ++c)
+    if (m[c]) for (int p = VX; p <= WZ; ++p) st[(size_t)p * s->pitch + s->T.iperm[c]] = 0.f;
+  VX_CUDA(cudaMemcpy(cs, st.data(), st.size() * 4, cudaMemcpyHostToDevice));
   if (n_out) *n_out = n;
   return VX_OK;
 }
@@ -444,28 +581,20 @@ int vx_add_forced_region(vx_sim* s, int32_t body, const float loc[3], const floa
   int64_t n = region_mask(s->L, body, loc, size, m.data());
   if (n_out) *n_out = n;
   if (n == 0) return VX_OK;
-  if (!s->fext) {
-    if ((rc = dalloc(&s->fext, 3 * s->pitch))) return rc;
-    VX_CUDA(cudaMemset(s->fext, 0, 12 * s->pitch));
-  }
-  std::vector<float> f(3 * (size_t)s->pitch);
-  VX_CUDA(cudaMemcpy(f.data(), s->fext, f.size() * 4, cudaMemcpyDeviceToHost));
-  for (int64_t v = 0; v < N; ++v)
-    if (m[v]) for (int a = 0; a < 3; ++a) f[(size_t)a * s->pitch + v] += (float)((double)F[a] / (double)n);
-  VX_CUDA(cudaMemcpy(s->fext, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
-  s->has_fext = true;
-  return VX_OK;
+  if (s->fext_h.empty()) s->fext_h.assign(3 * (size_t)N, 0.f);
+  for (int64_t c = 0; c < N; ++c)
+    if (m[c]) for (int a = 0; a < 3; ++a) s->fext_h[3 * c + a] += (float)((double)F[a] / (double)n);
+  return vx_set_forces(s, s->fext_h.data());
 }
 
 int vx_set_forces(vx_sim* s, const float* F) {
   int rc = check_sim(s);
   if (rc) return rc;
-  if (!F) { s->has_fext = false; return VX_OK; }
+  if (!F) { s->has_fext = false; s->fext_h.clear(); return VX_OK; }
   int64_t N = s->L.N;
+  if (F != s->fext_h.data()) s->fext_h.assign(F, F + 3 * N);
   if (!s->fext && (rc = dalloc(&s->fext, 3 * s->pitch))) return rc;
-  std::vector<float> f(3 * (size_t)s->pitch, 0.f);
-  for (int64_t v = 0; v < N; ++v) for (int a = 0; a < 3; ++a) f[(size_t)a * s->pitch + v] = F[3 * v + a];
-  VX_CUDA(cudaMemcpy(s->fext, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+  if ((rc = upload_permuted(s, s->fext, F, 3, s->pitch))) return rc;
   s->has_fext = true;
   return VX_OK;
 }
@@ -495,6 +624,7 @@ int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t col
 int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
   if (!s) return fail(VX_ERR_ARG, "sim is NULL");
   if (period < 0 || !std::isfinite(amplitude) || !std::isfinite(offset)) return fail(VX_ERR_ARG, "bad actuation");
+  if (period == 0) amplitude = 0.f;
   s->actA = amplitude; s->actP = period; s->actT0 = offset;
   update_threshold(s);
   return VX_OK;
@@ -527,7 +657,7 @@ int vx_set_dt(vx_sim* s, const double* dt) {
 int vx_reset(vx_sim* s, const float v0[3]) {
   int rc = check_sim(s);
   if (rc) return rc;
-  launch_reset_state(s->st, s->pitch, (int)s->L.N, s->flags, v0 ? v0[0] : 0.f, v0 ? v0[1] : 0.f,
+  launch_reset_state(cur_state(s), s->pitch, (int)s->L.N, s->flags, v0 ? v0[0] : 0.f, v0 ? v0[1] : 0.f,
                      v0 ? v0[2] : 0.f, 0);
   VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaMemset(s->status, 0, 16));
@@ -545,7 +675,8 @@ int vx_read_state(vx_sim* s, const vx_state_view* out, int32_t dst_on_device, vo
   cudaStream_t st = (cudaStream_t)stream;
   int N = (int)s->L.N;
   if (dst_on_device) {
-    launch_pack_state(s->st, s->pitch, N, s->flags, out->offset, out->quat, out->vel, out->angvel, out->flags, st);
+    launch_pack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, out->offset, out->quat, out->vel, out->angvel,
+                      out->flags, st);
     VX_CUDA(cudaGetLastError());
     VX_CUDA(cudaStreamSynchronize(st));
     return VX_OK;
@@ -556,8 +687,9 @@ int vx_read_state(vx_sim* s, const vx_state_view* out, int32_t dst_on_device, vo
   float* vel = quat + 4 * (size_t)N;
   float* w = vel + 3 * (size_t)N;
   uint8_t* fl = (uint8_t*)(w + 3 * (size_t)N);
-  launch_pack_state(s->st, s->pitch, N, s->flags, out->offset ? off : nullptr, out->quat ? quat : nullptr,
-                    out->vel ? vel : nullptr, out->angvel ? w : nullptr, out->flags ? fl : nullptr, st);
+  launch_pack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, out->offset ? off : nullptr,
+                    out->quat ? quat : nullptr, out->vel ? vel : nullptr, out->angvel ? w : nullptr,
+                    out->flags ? fl : nullptr, st);
   VX_CUDA(cudaGetLastError());
   if (out->offset) VX_CUDA(cudaMemcpyAsync(out->offset, off, 12 * (size_t)N, cudaMemcpyDeviceToHost, st));
   if (out->quat) VX_CUDA(cudaMemcpyAsync(out->quat, quat, 16 * (size_t)N, cudaMemcpyDeviceToHost, st));
@@ -575,7 +707,8 @@ int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, vo
   cudaStream_t st = (cudaStream_t)stream;
   int N = (int)s->L.N;
   if (src_on_device) {
-    launch_unpack_state(s->st, s->pitch, N, s->flags, in->offset, in->quat, in->vel, in->angvel, in->flags, st);
+    launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset, in->quat, in->vel, in->angvel,
+                        in->flags, st);
     VX_CUDA(cudaGetLastError());
     VX_CUDA(cudaStreamSynchronize(st));
     return VX_OK;
@@ -591,8 +724,9 @@ int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, vo
   if (in->vel) VX_CUDA(cudaMemcpyAsync(vel, in->vel, 12 * (size_t)N, cudaMemcpyHostToDevice, st));
   if (in->angvel) VX_CUDA(cudaMemcpyAsync(w, in->angvel, 12 * (size_t)N, cudaMemcpyHostToDevice, st));
   if (in->flags) VX_CUDA(cudaMemcpyAsync(fl, in->flags, (size_t)N, cudaMemcpyHostToDevice, st));
-  launch_unpack_state(s->st, s->pitch, N, s->flags, in->offset ? off : nullptr, in->quat ? quat : nullptr,
-                      in->vel ? vel : nullptr, in->angvel ? w : nullptr, in->flags ? fl : nullptr, st);
+  launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset ? off : nullptr,
+                      in->quat ? quat : nullptr, in->vel ? vel : nullptr, in->angvel ? w : nullptr,
+                      in->flags ? fl : nullptr, st);
   VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaStreamSynchronize(st));
   return VX_OK;
@@ -615,18 +749,18 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   if (rc) return rc;
   if (n < 0) return fail(VX_ERR_ARG, "n_steps must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
-  StepArgs A = step_args(s);
-  CollideArgs C;
-  if (s->collide_on) C = collide_args(s);
   for (int64_t i = 0; i < n; ++i) {
-    A.step = s->step + i;
-    launch_step(A, st);
+    StepArgs A = step_args(s);
+    if (s->actP > 0) A.act_w = (float)(2.0 * M_PI * (double)(s->step % s->actP) / (double)s->actP);
+    launch_step(A, s->form, s->tile_max, s->smem, st);
+    s->cur = 1 - s->cur;
+    s->step += 1;
     if (s->collide_on) {
+      CollideArgs C = collide_args(s);
       launch_horizon(C, st);
       launch_rebuild(C, st);
     }
   }
-  s->step += n;
   VX_CUDA(cudaGetLastError());
   return VX_OK;
 }
@@ -644,7 +778,7 @@ int vx_get_status(vx_sim* s, void* stream, int32_t* status, int64_t* bad_step, i
   std::memcpy(&bs, &h[2], 8);
   if (status) *status = code;
   if (bad_step) *bad_step = (h[0] & kStatusUnstable) ? bs : -1;
-  if (bad_voxel) *bad_voxel = (h[0] & kStatusUnstable) ? h[1] : -1;
+  if (bad_voxel) *bad_voxel = (h[0] & kStatusUnstable) ? s->T.perm[h[1]] : -1;
   return VX_OK;
 }
 
@@ -679,16 +813,17 @@ int vx_get_collision_pairs(vx_sim* s, int32_t* pairs, int64_t cap, int64_t* n_ou
   std::vector<int32_t> cnt(S), cand(S * kCandCap);
   VX_CUDA(cudaMemcpy(cnt.data(), s->ccount, S * 4, cudaMemcpyDeviceToHost));
   VX_CUDA(cudaMemcpy(cand.data(), s->cand, S * kCandCap * 4, cudaMemcpyDeviceToHost));
-  int64_t n = 0;
+  std::vector<std::pair<int32_t, int32_t>> pr;
   for (int64_t i = 0; i < S; ++i) {
-    int32_t v = s->L.surf_list[i];
+    int32_t a = s->T.perm[s->surf_h[i]];
     for (int c = 0; c < cnt[i]; ++c) {
-      int32_t j = cand[i * kCandCap + c];
-      if (j <= v) continue;
-      if (n < cap) { pairs[2 * n] = v; pairs[2 * n + 1] = j; }
-      ++n;
+      int32_t b = s->T.perm[cand[i * kCandCap + c]];
+      if (a < b) pr.emplace_back(a, b);
     }
   }
+  std::sort(pr.begin(), pr.end());
+  int64_t n = (int64_t)pr.size();
+  for (int64_t k = 0; k < n && k < cap; ++k) { pairs[2 * k] = pr[k].first; pairs[2 * k + 1] = pr[k].second; }
   if (n_out) *n_out = n;
   return VX_OK;
 }

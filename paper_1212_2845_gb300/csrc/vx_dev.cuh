@@ -1,9 +1,10 @@
 // Device data layout and FP32 math of one explicit lattice step.
 //
-// State is structure-of-arrays: 13 float planes of `pitch` floats each
-// (offset x,y,z from the lattice anchor, quaternion w,x,y,z, velocity x,y,z,
-// angular velocity x,y,z), so every warp load or store of one component is
-// one coalesced 128-byte transaction.
+// All per-voxel arrays are in the internal order (bricks along a Morton
+// curve, see vx_host.h).  State is structure-of-arrays: 13 float planes of
+// `pitch` floats (offset x,y,z from the lattice anchor, quaternion w,x,y,z,
+// velocity x,y,z, angular velocity x,y,z), double-buffered: a step reads
+// st_in and writes st_out, so neighbours always see the state at step n.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -12,8 +13,7 @@ namespace vx {
 
 enum Plane { OX = 0, OY, OZ, QW, QX, QY, QZ, VX, VY, VZ, WX, WY, WZ, NPLANE };
 
-// Per-material constants precomputed on the host (mass and inertia depend on
-// the lattice dimension l).
+// Per-material constants precomputed on the host in double precision.
 struct DevMat {
   float E;        // elastic modulus [Pa]
   float g_ratio;  // G / E = 1 / (2 (1 + nu))
@@ -21,147 +21,171 @@ struct DevMat {
   float mu_s, mu_k;
   float m, inv_m; // rho l^3 and its inverse
   float I, inv_I; // m l^2 / 6 (solid cube) and its inverse
+  float pad[3];
 };
 
-// Collision candidate capacity per surface voxel.
-constexpr int kCandCap = 48;
-
-// Status word bits.
-constexpr int kStatusUnstable = 1;
+constexpr int kCandCap = 48;        // collision candidates per surface voxel
+constexpr int kStatusUnstable = 1;  // status word bits
 constexpr int kStatusCapacity = 2;
 
 struct StepArgs {
   int N;
   int64_t pitch;
   float l;
-  float* st;               // NPLANE planes
-  uint8_t* flags;          // bit 0 fixed, bit 1 static friction
+  const float* st_in;      // NPLANE planes, state at step n
+  float* st_out;           // NPLANE planes, state at step n + 1
+  uint8_t* flags;          // bit 0 fixed, bit 1 static friction (updated in place by the owner)
   const uint8_t* mat;
   const uint32_t* lat;     // packed i | j << 11 | k << 22
-  const int32_t* body;     // per voxel body index, or nullptr when single body
-  const int32_t* nbr;      // 6 planes (-x,+x,-y,+y,-z,+z)
+  const int32_t* body;     // per voxel body, or nullptr for a single body
   const float* phase;      // per voxel or nullptr
   const float* logE;       // per voxel or nullptr
   const float* fext;       // 3 planes or nullptr
   const DevMat* mats;
+  int n_mats;
   const float* dt_body;    // per body
   const float* origin;     // 3 per body
-  float* bf;               // bond results: 9 components x 3 axes planes
   float zb, zg, zc, gz;
   int floor_on, collide_on;
-  float actA, actT0;
-  int64_t actP;
+  int act_on;              // temperature offset is non-zero somewhere
+  float actA, actT0, act_w;  // dT = T0 + A sin(act_w + phase), act_w = 2 pi (n mod P) / P
   int64_t step;
+  // two-pass form
+  const int32_t* nbr;      // 6 planes (-x,+x,-y,+y,-z,+z), internal indices
+  float* bf;               // bond results: 9 components x 3 axes planes
+  // fused form
+  const int4* tile_a;      // v0, n_owned, halo start, n_halo
+  const int4* tile_b;      // halo-bond list start, end
+  const int32_t* halo;
+  const uint16_t* plus;    // 3 planes: staging slot of the +a neighbour or 0xFFFF
+  const uint32_t* hbonds;  // halo bonds: slot 1 | slot 2 << 12 | axis << 24
+  const uint8_t* mask;     // per voxel 6-bit bond existence
+  int n_tiles, max_local;
   // collisions
   const int32_t* sidx;     // per voxel: surface index or -1
   const int32_t* ccount;   // per surface voxel
-  const int32_t* cand;     // per surface voxel, kCandCap slots
+  const int32_t* cand;     // per surface voxel, kCandCap slots (internal indices, ascending)
   unsigned* vmax_bits;     // per body, float bits of max |v|
-  int* status;             // [0] bits, [1] first bad voxel, [2..3] step (int64)
+  int* status;             // [0] bits, [1] first bad voxel (internal), [2..3] step
 };
 
 // ---------------------------------------------------------------------------
 // small vector / quaternion helpers (FP32)
+//
+// Every operation is an explicit round-to-nearest intrinsic, so the compiler
+// cannot fuse multiply-adds differently at different call sites: a bond or a
+// voxel update gives the same bits wherever it is evaluated (own bond or halo
+// bond, any tile size, fused or two-pass form).
 // ---------------------------------------------------------------------------
 struct V3f { float x, y, z; };
 struct Qf { float w, x, y, z; };
 
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+
 __device__ __forceinline__ V3f v3(float a, float b, float c) { V3f r; r.x = a; r.y = b; r.z = c; return r; }
-__device__ __forceinline__ V3f add(V3f a, V3f b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
-__device__ __forceinline__ V3f sub(V3f a, V3f b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
-__device__ __forceinline__ V3f scl(V3f a, float s) { return v3(a.x * s, a.y * s, a.z * s); }
-__device__ __forceinline__ float dot3(V3f a, V3f b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3f add(V3f a, V3f b) { return v3(add_(a.x, b.x), add_(a.y, b.y), add_(a.z, b.z)); }
+__device__ __forceinline__ V3f sub(V3f a, V3f b) { return v3(sub_(a.x, b.x), sub_(a.y, b.y), sub_(a.z, b.z)); }
+__device__ __forceinline__ V3f scl(V3f a, float s) { return v3(mul_(a.x, s), mul_(a.y, s), mul_(a.z, s)); }
+// a + s b
+__device__ __forceinline__ V3f axpy(V3f a, float s, V3f b) { return v3(fma_(s, b.x, a.x), fma_(s, b.y, a.y), fma_(s, b.z, a.z)); }
+__device__ __forceinline__ float dot3(V3f a, V3f b) { return fma_(a.x, b.x, fma_(a.y, b.y, mul_(a.z, b.z))); }
 __device__ __forceinline__ V3f cross3(V3f a, V3f b) {
-  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+  return v3(fma_(a.y, b.z, -mul_(a.z, b.y)), fma_(a.z, b.x, -mul_(a.x, b.z)), fma_(a.x, b.y, -mul_(a.y, b.x)));
 }
-__device__ __forceinline__ float comp(V3f a, int i) { return i == 0 ? a.x : (i == 1 ? a.y : a.z); }
 // cyclic permutation taking lattice axis a to local x: local[i] = v[(i + a) % 3]
-__device__ __forceinline__ V3f to_axis(V3f v, int a) {
+template <int a> __device__ __forceinline__ V3f to_axis(V3f v) {
   return a == 0 ? v : (a == 1 ? v3(v.y, v.z, v.x) : v3(v.z, v.x, v.y));
 }
-__device__ __forceinline__ V3f from_axis(V3f u, int a) {
+template <int a> __device__ __forceinline__ V3f from_axis(V3f u) {
   return a == 0 ? u : (a == 1 ? v3(u.z, u.x, u.y) : v3(u.y, u.z, u.x));
 }
+// sqrt(x) for x > 0 from the hardware reciprocal square root (2 ulp)
+__device__ __forceinline__ float fsqrt(float x) { return mul_(x, rsqrtf(x)); }
 
 // Rotation matrix rows of unit quaternion q (body -> world).
 struct M3f { V3f r0, r1, r2; };
 __device__ __forceinline__ M3f qmat(Qf q) {
-  float xx = q.x * q.x, yy = q.y * q.y, zz = q.z * q.z;
-  float xy = q.x * q.y, xz = q.x * q.z, yz = q.y * q.z;
-  float wx = q.w * q.x, wy = q.w * q.y, wz = q.w * q.z;
+  float x2 = add_(q.x, q.x), y2 = add_(q.y, q.y), z2 = add_(q.z, q.z);
+  float xx = mul_(q.x, x2), yy = mul_(q.y, y2), zz = mul_(q.z, z2);
+  float xy = mul_(q.x, y2), xz = mul_(q.x, z2), yz = mul_(q.y, z2);
+  float wx = mul_(q.w, x2), wy = mul_(q.w, y2), wz = mul_(q.w, z2);
   M3f m;
-  m.r0 = v3(1.f - 2.f * (yy + zz), 2.f * (xy - wz), 2.f * (xz + wy));
-  m.r1 = v3(2.f * (xy + wz), 1.f - 2.f * (xx + zz), 2.f * (yz - wx));
-  m.r2 = v3(2.f * (xz - wy), 2.f * (yz + wx), 1.f - 2.f * (xx + yy));
+  m.r0 = v3(sub_(1.f, add_(yy, zz)), sub_(xy, wz), add_(xz, wy));
+  m.r1 = v3(add_(xy, wz), sub_(1.f, add_(xx, zz)), sub_(yz, wx));
+  m.r2 = v3(sub_(xz, wy), add_(yz, wx), sub_(1.f, add_(xx, yy)));
   return m;
 }
-// R v
 __device__ __forceinline__ V3f mul(const M3f& m, V3f v) { return v3(dot3(m.r0, v), dot3(m.r1, v), dot3(m.r2, v)); }
-// R^T v
 __device__ __forceinline__ V3f mulT(const M3f& m, V3f v) {
-  return v3(m.r0.x * v.x + m.r1.x * v.y + m.r2.x * v.z,
-            m.r0.y * v.x + m.r1.y * v.y + m.r2.y * v.z,
-            m.r0.z * v.x + m.r1.z * v.y + m.r2.z * v.z);
+  return v3(fma_(m.r0.x, v.x, fma_(m.r1.x, v.y, mul_(m.r2.x, v.z))),
+            fma_(m.r0.y, v.x, fma_(m.r1.y, v.y, mul_(m.r2.y, v.z))),
+            fma_(m.r0.z, v.x, fma_(m.r1.z, v.y, mul_(m.r2.z, v.z))));
 }
-// (R^T e_a) - e_a: row a of R minus the unit vector, with the diagonal entry
-// formed as -2 (sum of the other two squares) so no cancellation occurs.
-__device__ __forceinline__ V3f row_dev(Qf q, int a) {
-  if (a == 0) return v3(-2.f * (q.y * q.y + q.z * q.z), 2.f * (q.x * q.y - q.w * q.z), 2.f * (q.x * q.z + q.w * q.y));
-  if (a == 1) return v3(2.f * (q.x * q.y + q.w * q.z), -2.f * (q.x * q.x + q.z * q.z), 2.f * (q.y * q.z - q.w * q.x));
-  return v3(2.f * (q.x * q.z - q.w * q.y), 2.f * (q.y * q.z + q.w * q.x), -2.f * (q.x * q.x + q.y * q.y));
+// (R^T e_a) - e_a: row a of R(q) minus the unit vector, diagonal entry formed
+// as -2 (sum of the other two squares) so that no cancellation occurs.
+template <int a> __device__ __forceinline__ V3f row_dev(const M3f& R, Qf q) {
+  if (a == 0) return v3(mul_(-2.f, fma_(q.y, q.y, mul_(q.z, q.z))), R.r0.y, R.r0.z);
+  if (a == 1) return v3(R.r1.x, mul_(-2.f, fma_(q.x, q.x, mul_(q.z, q.z))), R.r1.z);
+  return v3(R.r2.x, R.r2.y, mul_(-2.f, fma_(q.x, q.x, mul_(q.y, q.y))));
 }
 
 // Rotation vector of conj(q1) * q2 (shortest arc).
 __device__ __forceinline__ V3f rel_rotvec(Qf a, Qf b) {
-  float w = a.w * b.w + a.x * b.x + a.y * b.y + a.z * b.z;
-  float x = a.w * b.x - a.x * b.w - a.y * b.z + a.z * b.y;
-  float y = a.w * b.y + a.x * b.z - a.y * b.w - a.z * b.x;
-  float z = a.w * b.z - a.x * b.y + a.y * b.x - a.z * b.w;
-  if (w < 0.f) { w = -w; x = -x; y = -y; z = -z; }
-  float s2 = x * x + y * y + z * z;
+  float w = fma_(a.w, b.w, fma_(a.x, b.x, fma_(a.y, b.y, mul_(a.z, b.z))));
+  float x = fma_(a.w, b.x, fma_(-a.x, b.w, fma_(-a.y, b.z, mul_(a.z, b.y))));
+  float y = fma_(a.w, b.y, fma_(a.x, b.z, fma_(-a.y, b.w, -mul_(a.z, b.x))));
+  float z = fma_(a.w, b.z, fma_(-a.x, b.y, fma_(a.y, b.x, -mul_(a.z, b.w))));
+  float sg = w < 0.f ? -1.f : 1.f;
+  w = mul_(w, sg);
+  float s2 = fma_(x, x, fma_(y, y, mul_(z, z)));
   float f;
-  if (s2 < 1e-6f * w * w) {
-    // 2 atan(t) / (t w) with t = s / w, Taylor series to t^4 (error < 2e-19)
-    float t2 = s2 / (w * w);
-    f = (2.f / w) * (1.f - t2 * (1.f / 3.f) + t2 * t2 * 0.2f);
+  if (s2 < mul_(1e-6f, mul_(w, w))) {
+    // 2 atan(t) / (t w) with t = s / w, series to t^4 (remainder < t^6 / 7 < 2e-19)
+    float iw = __fdividef(1.f, w);
+    float t2 = mul_(s2, mul_(iw, iw));
+    f = mul_(add_(iw, iw), fma_(t2, fma_(t2, 0.2f, -1.f / 3.f), 1.f));
   } else {
     float s = sqrtf(s2);
-    f = 2.f * atan2f(s, w) / s;
+    f = __fdividef(mul_(2.f, atan2f(s, w)), s);
   }
-  return v3(x * f, y * f, z * f);
+  f = mul_(f, sg);
+  return v3(mul_(x, f), mul_(y, f), mul_(z, f));
 }
 
-// q <- normalize(exp(w dt) * q)
+// q <- normalize(exp(w dt) * q), w in the world frame
 __device__ __forceinline__ Qf integrate_rot(Qf q, V3f w, float dt) {
-  float a2 = dot3(w, w) * dt * dt;
-  float h2 = 0.25f * a2;  // (|w| dt / 2)^2
-  float c, k;             // cos(|w|dt/2), sin(|w|dt/2)/|w|
-  if (h2 < 1e-6f) {
-    c = 1.f - 0.5f * h2 + h2 * h2 * (1.f / 24.f);
-    k = 0.5f * dt * (1.f - h2 * (1.f / 6.f) + h2 * h2 * (1.f / 120.f));
+  float a2 = mul_(dot3(w, w), mul_(dt, dt));
+  float h2 = mul_(0.25f, a2);  // (|w| dt / 2)^2
+  float c, k;                  // cos(|w|dt/2), sin(|w|dt/2)/|w|
+  if (h2 < 1e-4f) {
+    // series; remainders below h2^3 / 720 and h2^3 / 5040 relative (< 1.4e-15)
+    c = fma_(h2, fma_(h2, 1.f / 24.f, -0.5f), 1.f);
+    k = mul_(mul_(0.5f, dt), fma_(h2, fma_(h2, 1.f / 120.f, -1.f / 6.f), 1.f));
   } else {
     float a = sqrtf(a2);
     float sn, cs;
-    sincosf(0.5f * a, &sn, &cs);
+    sincosf(mul_(0.5f, a), &sn, &cs);
     c = cs;
-    k = sn * dt / a;
+    k = __fdividef(mul_(sn, dt), a);
   }
   Qf d;
-  d.w = c; d.x = w.x * k; d.y = w.y * k; d.z = w.z * k;
+  d.w = c; d.x = mul_(w.x, k); d.y = mul_(w.y, k); d.z = mul_(w.z, k);
   Qf r;
-  r.w = d.w * q.w - d.x * q.x - d.y * q.y - d.z * q.z;
-  r.x = d.w * q.x + d.x * q.w + d.y * q.z - d.z * q.y;
-  r.y = d.w * q.y - d.x * q.z + d.y * q.w + d.z * q.x;
-  r.z = d.w * q.z + d.x * q.y - d.y * q.x + d.z * q.w;
-  float n = 1.f / sqrtf(r.w * r.w + r.x * r.x + r.y * r.y + r.z * r.z);
-  r.w *= n; r.x *= n; r.y *= n; r.z *= n;
+  r.w = fma_(d.w, q.w, fma_(-d.x, q.x, fma_(-d.y, q.y, -mul_(d.z, q.z))));
+  r.x = fma_(d.w, q.x, fma_(d.x, q.w, fma_(d.y, q.z, -mul_(d.z, q.y))));
+  r.y = fma_(d.w, q.y, fma_(-d.x, q.z, fma_(d.y, q.w, mul_(d.z, q.x))));
+  r.z = fma_(d.w, q.z, fma_(d.x, q.y, fma_(-d.y, q.x, mul_(d.z, q.w))));
+  float n = rsqrtf(fma_(r.w, r.w, fma_(r.x, r.x, fma_(r.y, r.y, mul_(r.z, r.z)))));
+  r.w = mul_(r.w, n); r.x = mul_(r.x, n); r.y = mul_(r.y, n); r.z = mul_(r.z, n);
   return r;
 }
 
-// Voxel state used by the bond computation.
 struct VoxS { V3f o; Qf q; V3f v; V3f w; };
 
-__device__ __forceinline__ VoxS load_vox(const float* __restrict__ st, int64_t pitch, int i) {
+__device__ __forceinline__ VoxS load_vox(const float* __restrict__ st, int64_t pitch, int64_t i) {
   VoxS s;
   s.o = v3(st[OX * pitch + i], st[OY * pitch + i], st[OZ * pitch + i]);
   s.q.w = st[QW * pitch + i]; s.q.x = st[QX * pitch + i]; s.q.y = st[QY * pitch + i]; s.q.z = st[QZ * pitch + i];
@@ -170,63 +194,213 @@ __device__ __forceinline__ VoxS load_vox(const float* __restrict__ st, int64_t p
   return s;
 }
 
-// Temperature offset of a voxel at step n (Sec 2.3).
-__device__ __forceinline__ float delta_T(const StepArgs& A, int v) {
-  if (A.actP <= 0) return A.actT0;
-  float frac = (float)(A.step % A.actP) / (float)A.actP;
-  float ph = A.phase ? A.phase[v] : 0.f;
-  return A.actT0 + A.actA * sinf(6.283185307179586f * frac + ph);
+__device__ __forceinline__ void store_vox(float* __restrict__ st, int64_t pitch, int64_t i, const VoxS& s) {
+  st[OX * pitch + i] = s.o.x; st[OY * pitch + i] = s.o.y; st[OZ * pitch + i] = s.o.z;
+  st[QW * pitch + i] = s.q.w; st[QX * pitch + i] = s.q.x; st[QY * pitch + i] = s.q.y; st[QZ * pitch + i] = s.q.z;
+  st[VX * pitch + i] = s.v.x; st[VY * pitch + i] = s.v.y; st[VZ * pitch + i] = s.v.z;
+  st[WX * pitch + i] = s.w.x; st[WY * pitch + i] = s.w.y; st[WZ * pitch + i] = s.w.z;
 }
 
-__device__ __forceinline__ float voxel_E(const StepArgs& A, int v, int m) {
-  return A.logE ? expf(A.logE[v]) : A.mats[m].E;
+// Thermal strain alpha_v dT_v of a voxel at the current step (Sec 2.3).  The
+// sine argument is reduced to [-pi, pi] for the hardware sine (absolute error
+// below 4e-7); the product is rounded explicitly so that every caller gets the
+// same bits whether it stores the value or uses it at once.
+__device__ __forceinline__ float thermal_strain(const StepArgs& A, int64_t g, float cte) {
+  if (!A.act_on) return 0.f;
+  float x = A.act_w + (A.phase ? A.phase[g] : 0.f);
+  x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
+  return __fmul_rn(cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
+}
+
+__device__ __forceinline__ float voxel_E(const StepArgs& A, int64_t g, int m) {
+  return A.logE ? expf(A.logE[g]) : A.mats[m].E;
 }
 
 // Result of one bond: force on voxel 1 (voxel 2 gets -F1), moments on both.
 struct BondOut { V3f F1, M1, M2; };
 
-// One bond along lattice axis a from voxel 1 (negative side) to voxel 2
-// (Sec 2.1.2 co-rotational beam, Sec 2.1.5 damping, Sec 2.3 actuation).
-__device__ __forceinline__ BondOut bond_eval(int a, const VoxS& s1, const VoxS& s2, float l,
-                                             float E1, float E2, float G1, float G2,
-                                             float mmin, float Imin, float eps, float zb) {
-  float Ec = 2.f * E1 * E2 / (E1 + E2);
-  float Gc = 2.f * G1 * G2 / (G1 + G2);
-  float a1 = Ec * l;                       // E_c A / l
-  float a2 = Gc * (l * l * l) * (1.f / 6.f);  // G_c J / l
-  float b1 = a1;                           // 12 E_c I / l^3
-  float b2 = Ec * (l * l) * 0.5f;          // 6 E_c I / l^2
-  float b3 = Ec * (l * l * l) * (1.f / 6.f);  // 2 E_c I / l
+// One bond along lattice axis a from voxel 1 (negative side) to voxel 2:
+// co-rotational beam (Sec 2.1.2) in voxel 1's frame (R1 = R(q1)), local
+// damping (Sec 2.1.5), rest length scaled by the mean thermal strain (Sec 2.3).
+template <int a>
+__device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, const VoxS& s2, float l, float E1,
+                                             float E2, float G1, float G2, float mmin, float Imin, float eps,
+                                             float zb) {
+  float Ec = __fdividef(mul_(mul_(2.f, E1), E2), add_(E1, E2));
+  float Gc = __fdividef(mul_(mul_(2.f, G1), G2), add_(G1, G2));
+  const float l2 = mul_(l, l), l3 = mul_(l2, l);
+  float a1 = mul_(Ec, l);                      // E_c A / l
+  float a2 = mul_(mul_(Gc, l3), 1.f / 6.f);    // G_c J / l
+  float b1 = a1;                               // 12 E_c I / l^3
+  float b2 = mul_(mul_(Ec, l2), 0.5f);         // 6 E_c I / l^2
+  float b3 = mul_(mul_(Ec, l3), 1.f / 6.f);    // 2 E_c I / l
   // position of voxel 2 in voxel 1's frame minus its rest vector l e_a:
   // R1^T (l e_a + do) - l e_a = R1^T do + l (R1^T e_a - e_a)
-  M3f R1 = qmat(s1.q);
   V3f dO = sub(s2.o, s1.o);
-  V3f p = add(mulT(R1, dO), scl(row_dev(s1.q, a), l));
-  p = to_axis(p, a);
-  float X = p.x - l * eps, Y = p.y, Z = p.z;
-  V3f th = to_axis(rel_rotvec(s1.q, s2.q), a);
-  // bond forces on the voxels (negated rows of [K] u, reduced form)
-  V3f F1 = v3(a1 * X, b1 * Y - b2 * th.z, b1 * Z + b2 * th.y);
-  V3f M1 = v3(a2 * th.x, -b2 * Z - b3 * th.y, b2 * Y - b3 * th.z);
-  V3f M2 = v3(-a2 * th.x, -b2 * Z - 2.f * b3 * th.y, b2 * Y - 2.f * b3 * th.z);
+  V3f p = to_axis<a>(axpy(mulT(R1, dO), l, row_dev<a>(R1, s1.q)));
+  float X = fma_(-l, eps, p.x), Y = p.y, Z = p.z;
+  V3f th = to_axis<a>(rel_rotvec(s1.q, s2.q));
+  // bond forces on the voxels: the negated rows of [K] u (reduced form)
+  V3f F1 = v3(mul_(a1, X), fma_(b1, Y, -mul_(b2, th.z)), fma_(b1, Z, mul_(b2, th.y)));
+  V3f M1 = v3(mul_(a2, th.x), fma_(-b2, Z, -mul_(b3, th.y)), fma_(b2, Y, -mul_(b3, th.z)));
+  const float b3x2 = add_(b3, b3);
+  V3f M2 = v3(-mul_(a2, th.x), fma_(-b2, Z, -mul_(b3x2, th.y)), fma_(b2, Y, -mul_(b3x2, th.z)));
   BondOut o;
-  o.F1 = mul(R1, from_axis(F1, a));
-  o.M1 = mul(R1, from_axis(M1, a));
-  o.M2 = mul(R1, from_axis(M2, a));
+  o.F1 = mul(R1, from_axis<a>(F1));
+  o.M1 = mul(R1, from_axis<a>(M1));
+  o.M2 = mul(R1, from_axis<a>(M2));
   if (zb != 0.f) {
-    // V_{2->1} = (v2 - Va) + (D2 - Da) x wa, with D2 - Da = (l e_a + do) / 2
+    // V_{2->1} = (v2 - Va) + (D2 - Da) x wa with D2 - Da = (l e_a + do) / 2
     V3f wa = scl(add(s1.w, s2.w), 0.5f);
     V3f half = scl(dO, 0.5f);
-    if (a == 0) half.x += 0.5f * l; else if (a == 1) half.y += 0.5f * l; else half.z += 0.5f * l;
+    const float hl = mul_(0.5f, l);
+    if (a == 0) half.x = add_(half.x, hl); else if (a == 1) half.y = add_(half.y, hl); else half.z = add_(half.z, hl);
     V3f V21 = add(scl(sub(s2.v, s1.v), 0.5f), cross3(half, wa));
-    float c = 2.f * zb * sqrtf(mmin * a1);
-    float cr = 2.f * zb * sqrtf(Imin * b3);
-    o.F1 = add(o.F1, scl(V21, c));
-    V3f dw = scl(sub(s2.w, s1.w), 0.5f * cr);   // cr (w2 - wa)
+    float c = mul_(mul_(2.f, zb), fsqrt(mul_(mmin, a1)));
+    float cr = mul_(mul_(2.f, zb), fsqrt(mul_(Imin, b3)));
+    o.F1 = axpy(o.F1, c, V21);
+    V3f dw = scl(sub(s2.w, s1.w), mul_(0.5f, cr));   // cr (w2 - wa)
     o.M1 = add(o.M1, dw);
     o.M2 = sub(o.M2, dw);
   }
   return o;
+}
+
+__device__ __forceinline__ void record_bad(const StepArgs& A, int v) {
+  if (atomicOr(&A.status[0], kStatusUnstable) & kStatusUnstable) return;
+  A.status[1] = v;
+  *reinterpret_cast<long long*>(&A.status[2]) = (long long)A.step;
+}
+
+// Per-voxel inputs of the voxel update, loaded before the bond phase so the
+// update itself issues no dependent global reads.
+struct VoxMeta {
+  uint32_t lat;   // packed lattice coordinate
+  int m;          // material
+  int b;          // body
+  uint8_t fl;     // flags
+  float dt, z0;   // body timestep, anchor height of the voxel centre
+  V3f fext;
+};
+
+__device__ __forceinline__ VoxMeta load_meta(const StepArgs& A, int v) {
+  VoxMeta mt;
+  mt.lat = A.lat[v];
+  mt.m = A.mat[v];
+  mt.b = A.body ? A.body[v] : 0;
+  mt.fl = A.flags[v];
+  mt.dt = A.dt_body[mt.b];
+  mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
+  const int64_t P = A.pitch;
+  mt.fext = A.fext ? v3(A.fext[v], A.fext[P + v], A.fext[2 * P + v]) : v3(0.f, 0.f, 0.f);
+  return mt;
+}
+
+// Everything a voxel does after its bond forces are summed (Sec 2.2.1,
+// Sec 2.2.2, Sec 2.1.3): external force, gravity, ground damping, voxel
+// contacts, floor contact with Coulomb friction, then integration.  Writes
+// the new state to st_out; returns |v| for the collision horizon.
+__device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const VoxMeta& mt, VoxS s, V3f F, V3f M,
+                                              float adT, float Ev, const DevMat* mats) {
+  const int64_t P = A.pitch;
+  uint8_t fl = mt.fl;
+  if (fl & 1u) {  // fixed: immobile, state carried over
+    store_vox(A.st_out, P, v, s);
+    return 0.f;
+  }
+  const DevMat& d = mats[mt.m];
+  const float dt = mt.dt;
+  const float l = A.l;
+  F = add(F, mt.fext);
+  F.z = fma_(d.m, A.gz, F.z);
+  float kv = mul_(Ev, l);
+  if (A.zg != 0.f) {
+    F = axpy(F, -mul_(mul_(2.f, A.zg), fsqrt(mul_(d.m, kv))), s.v);
+    M = axpy(M, -mul_(mul_(2.f, A.zg), fsqrt(mul_(mul_(d.I, kv), mul_(mul_(l, l), 1.f / 6.f)))), s.w);
+  }
+  const float hl = mul_(0.5f, l);
+  float h = fma_(hl, adT, hl);  // current half size l (1 + adT) / 2
+  if (A.collide_on) {
+    int si = A.sidx[v];
+    if (si >= 0) {
+      const uint32_t lp = mt.lat;
+      int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);
+      int nc = A.ccount[si];
+      const int32_t* cl = A.cand + (int64_t)si * kCandCap;
+      for (int c = 0; c < nc; ++c) {
+        int j = cl[c];
+        uint32_t lq = A.lat[j];
+        V3f dd = v3(fma_((float)((int)(lq & 2047u) - vi), l, sub_(A.st_in[OX * P + j], s.o.x)),
+                    fma_((float)((int)((lq >> 11) & 2047u) - vj), l, sub_(A.st_in[OY * P + j], s.o.y)),
+                    fma_((float)((int)(lq >> 22) - vk), l, sub_(A.st_in[OZ * P + j], s.o.z)));
+        float r2 = dot3(dd, dd);
+        int mj = A.mat[j];
+        const DevMat& dj = mats[mj];
+        float hj = fma_(hl, thermal_strain(A, j, dj.cte), hl);
+        float cdist = add_(h, hj);
+        if (!(r2 < mul_(cdist, cdist))) continue;
+        float ir = rsqrtf(r2);
+        float r = mul_(r2, ir);
+        V3f nh = scl(dd, ir);
+        float Ej = voxel_E(A, j, mj);
+        float kc = mul_(__fdividef(mul_(mul_(2.f, Ev), Ej), add_(Ev, Ej)), l);
+        F = axpy(F, -mul_(kc, sub_(cdist, r)), nh);
+        V3f vj = v3(A.st_in[VX * P + j], A.st_in[VY * P + j], A.st_in[VZ * P + j]);
+        float cc = mul_(mul_(2.f, A.zc), fsqrt(mul_(fminf(d.m, dj.m), kc)));
+        F = axpy(F, mul_(cc, dot3(sub(vj, s.v), nh)), nh);
+      }
+    }
+  }
+  if (A.floor_on) {
+    float pen = sub_(h, add_(mt.z0, s.o.z));
+    if (pen > 0.f) {
+      float Fn = mul_(kv, pen);
+      F.z = add_(F.z, fma_(-mul_(mul_(2.f, A.zc), fsqrt(mul_(d.m, kv))), s.v.z, Fn));
+      float Fl2 = fma_(F.x, F.x, mul_(F.y, F.y));
+      float vl2 = fma_(s.v.x, s.v.x, mul_(s.v.y, s.v.y));
+      float mus = mul_(d.mu_s, Fn), mud = mul_(d.mu_k, Fn);
+      float mus2 = mul_(mus, mus);
+      bool zero_l = false;
+      float fx = 0.f, fy = 0.f;  // unit direction of the dynamic friction force
+      if (fl & 2u) {
+        if (Fl2 <= mus2) zero_l = true;             // held by static friction
+        else { fl &= ~2u; float i = rsqrtf(Fl2); fx = mul_(F.x, i); fy = mul_(F.y, i); }
+      } else {
+        float vth = mul_(mul_(mud, dt), d.inv_m);
+        if (vl2 <= mul_(vth, vth) && Fl2 <= mus2) { zero_l = true; fl |= 2u; }  // halt
+        else if (vl2 > 0.f) { float i = rsqrtf(vl2); fx = mul_(s.v.x, i); fy = mul_(s.v.y, i); }
+        else { float i = rsqrtf(Fl2); fx = mul_(F.x, i); fy = mul_(F.y, i); }
+      }
+      if (zero_l) { F.x = 0.f; F.y = 0.f; s.v.x = 0.f; s.v.y = 0.f; }
+      else { F.x = fma_(-mud, fx, F.x); F.y = fma_(-mud, fy, F.y); }
+    } else {
+      fl &= ~2u;
+    }
+  }
+  // Sec 2.1.3: P += F dt, D += P/m dt; phi += M dt, theta += phi/I dt
+  s.v = axpy(s.v, mul_(dt, d.inv_m), F);
+  s.o = axpy(s.o, dt, s.v);
+  s.w = axpy(s.w, mul_(dt, d.inv_I), M);
+  s.q = integrate_rot(s.q, s.w, dt);
+  store_vox(A.st_out, P, v, s);
+  if (fl != mt.fl) A.flags[v] = fl;
+  float chk = s.o.x + s.o.y + s.o.z + s.v.x + s.v.y + s.v.z + s.w.x + s.w.y + s.w.z + s.q.w;
+  if (!isfinite(chk)) record_bad(A, v);
+  return fsqrt(fmaxf(dot3(s.v, s.v), 1e-30f));
+}
+
+// Per-body max |v| for the collision horizon (max is order-independent).
+__device__ __forceinline__ void horizon_max(const StepArgs& A, int b, bool active, float speed) {
+  unsigned mask = __activemask();
+  b = active ? b : 0;
+  int b0 = __shfl_sync(mask, b, __ffs(mask) - 1);
+  if (__all_sync(mask, b == b0 || !active)) {
+    float s = active ? speed : 0.f;
+    for (int o = 16; o > 0; o >>= 1) s = fmaxf(s, __shfl_xor_sync(mask, s, o));
+    if ((threadIdx.x & 31) == __ffs(mask) - 1 && s > 0.f) atomicMax(&A.vmax_bits[b0], __float_as_uint(s));
+  } else if (active && speed > 0.f) {
+    atomicMax(&A.vmax_bits[b], __float_as_uint(speed));
+  }
 }
 
 }  // namespace vx

@@ -136,4 +136,98 @@ void quant_params(float l, int* K, int64_t* Q) {
   *Q = (int64_t)std::nearbyint(std::ldexp((double)l, *K));
 }
 
+static uint64_t spread3(uint32_t x) {
+  uint64_t v = x & 0x1fffffu;
+  v = (v | v << 32) & 0x1f00000000ffffull;
+  v = (v | v << 16) & 0x1f0000ff0000ffull;
+  v = (v | v << 8) & 0x100f00f00f00f00full;
+  v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+  v = (v | v << 2) & 0x1249249249249249ull;
+  return v;
+}
+
+int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err) {
+  if (tile_max < 64 || tile_max > 1024) { err = "tile size must be in [64, 1024]"; return VX_ERR_ARG; }
+  local_max = std::min(local_max, kMaxLocal);
+  if (local_max < 160) { err = "local_max must be at least 160 (one brick and its halo)"; return VX_ERR_ARG; }
+  T = Tiling();
+  T.tile_max = tile_max;
+  const int64_t N = L.N;
+  // --- order: (body, Morton(brick), site in brick)
+  std::vector<std::pair<uint64_t, int32_t>> key(N);
+  for (int64_t v = 0; v < N; ++v) {
+    uint32_t p = L.lat[v];
+    int i = lat_i(p), j = lat_j(p), k = lat_k(p);
+    uint64_t m = spread3((uint32_t)(i >> 2)) | spread3((uint32_t)(j >> 2)) << 1 | spread3((uint32_t)(k >> 2)) << 2;
+    uint64_t site = (uint64_t)((i & 3) | (j & 3) << 2 | (k & 3) << 4);
+    key[v] = {m << 6 | site, (int32_t)v};
+  }
+  // bodies are contiguous in canonical order: sort inside each body
+  for (int b = 0; b < L.n_bodies; ++b)
+    std::sort(key.begin() + L.body_first[b], key.begin() + L.body_first[b + 1]);
+  T.perm.resize(N);
+  T.iperm.resize(N);
+  for (int64_t v = 0; v < N; ++v) { T.perm[v] = key[v].second; T.iperm[key[v].second] = (int32_t)v; }
+  // internal neighbour of internal voxel v in slot s, or -1
+  auto nb = [&](int64_t v, int s) -> int32_t {
+    int32_t c = L.nbr[(size_t)s * N + T.perm[v]];
+    return c < 0 ? -1 : T.iperm[c];
+  };
+  T.mask.assign(N, 0);
+  for (int64_t v = 0; v < N; ++v)
+    for (int s = 0; s < 6; ++s)
+      if (nb(v, s) >= 0) T.mask[v] |= (uint8_t)(1u << s);
+  // --- tiles: runs of tile_max consecutive voxels (shortened while the
+  // staged set, owned + halo, exceeds local_max)
+  T.plus.assign(3 * (size_t)N, 0xFFFFu);
+  std::vector<int32_t> hl;
+  int64_t v0 = 0;
+  while (v0 < N) {
+    int64_t len = std::min<int64_t>(tile_max, N - v0);
+    for (;;) {
+      int64_t v1 = v0 + len;
+      hl.clear();
+      for (int64_t v = v0; v < v1; ++v)
+        for (int s = 0; s < 6; ++s) {
+          int32_t u = nb(v, s);
+          if (u >= 0 && (u < v0 || u >= v1)) hl.push_back(u);
+        }
+      std::sort(hl.begin(), hl.end());
+      hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
+      int64_t nl = len + (int64_t)hl.size();
+      if (nl <= local_max || len <= 32) {
+        if (nl > local_max) { err = "tile staging set too large"; return VX_ERR_ARG; }
+        int32_t T0 = (int32_t)len;
+        T.tile_a.insert(T.tile_a.end(), {(int32_t)v0, T0, (int32_t)T.halo.size(), (int32_t)hl.size()});
+        auto local = [&](int32_t u) -> uint32_t {
+          if (u >= v0 && u < v1) return (uint32_t)(u - v0);
+          return (uint32_t)(T0 + (std::lower_bound(hl.begin(), hl.end(), u) - hl.begin()));
+        };
+        int32_t hb0 = (int32_t)T.halo_bonds.size();
+        for (int64_t v = v0; v < v1; ++v)
+          for (int a = 0; a < 3; ++a) {
+            int32_t up = nb(v, 2 * a + 1);
+            if (up >= 0) T.plus[(size_t)a * N + v] = (uint16_t)local(up);
+            int32_t dn = nb(v, 2 * a);
+            if (dn >= 0 && (dn < v0 || dn >= v1))
+              T.halo_bonds.push_back(local(dn) | (uint32_t)(v - v0) << 12 | (uint32_t)a << 24);
+          }
+        T.tile_b.insert(T.tile_b.end(), {hb0, (int32_t)T.halo_bonds.size(), 0, 0});
+        T.halo.insert(T.halo.end(), hl.begin(), hl.end());
+        T.max_local = std::max<int>(T.max_local, (int)nl);
+        v0 = v1;
+        break;
+      }
+      len -= 32;
+    }
+  }
+  return VX_OK;
+}
+
+int64_t Tiling::n_tile_bonds() const {
+  int64_t n = (int64_t)halo_bonds.size();
+  for (uint16_t p : plus) n += p != 0xFFFFu;
+  return n;
+}
+
 }  // namespace vx

@@ -44,4 +44,36 @@ int64_t region_mask(const Lattice& L, int body, const float loc[3], const float 
 // Collision quantisation: 2^K <= 65536 / l < 2^(K+1), Q = rint(l 2^K).
 void quant_params(float l, int* K, int64_t* Q);
 
+// Internal (device) voxel order and the tiles of the fused step kernel.
+//
+// Voxels are grouped into 4x4x4-site bricks; bricks of a body follow a 3-D
+// Morton curve and voxels inside a brick follow the site order.  The fused
+// kernel stages a tile plus its halo (face neighbours outside the tile) in
+// shared memory.  Tiles are runs of tile_max consecutive voxels in this order
+// (shorter only where owned + halo would exceed the staging limit).  Each
+// owned voxel evaluates its own +x, +y, +z bonds (partner slots in `plus`);
+// bonds whose negative-side voxel lies in the halo form the tile's short
+// `halo_bonds` list.
+struct Tiling {
+  int tile_max = 0;
+  int max_local = 0;             // max over tiles of owned + halo voxels
+  std::vector<int32_t> perm;     // internal -> canonical
+  std::vector<int32_t> iperm;    // canonical -> internal
+  std::vector<int32_t> tile_a;   // 4 per tile: v0, n_owned, halo start, n_halo
+  std::vector<int32_t> tile_b;   // 4 per tile: halo-bond list start, end, 0, 0
+  std::vector<int32_t> halo;     // internal voxel indices
+  std::vector<uint16_t> plus;    // 3 planes of N: staging slot of the +a neighbour, 0xFFFF if none
+  std::vector<uint32_t> halo_bonds;  // slot of voxel 1 | slot of voxel 2 << 12 | axis << 24
+  std::vector<uint8_t> mask;     // per internal voxel: bit 2a (-a) / 2a+1 (+a) bond exists
+  int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
+  int64_t n_tile_bonds() const;  // bonds evaluated over all tiles
+};
+
+// Local slots must stay below 4096 (12-bit packing).
+constexpr int kMaxLocal = 4095;
+
+// local_max: largest owned + halo set a tile may stage (shared memory bound);
+// tiles are shrunk brick by brick until they fit.
+int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err);
+
 }  // namespace vx

@@ -37,17 +37,24 @@ struct CollideArgs {
   int* status;
 };
 
-void launch_step(const StepArgs& A, cudaStream_t s);
+// form 0: fused tile kernel (tile_max threads per CTA, smem bytes of dynamic
+// shared memory); form 1: two-pass bond_pass + voxel_pass.
+void launch_step(const StepArgs& A, int form, int tile_max, size_t smem, cudaStream_t s);
+size_t fused_smem_bytes(int tile_max, int n_mats);
+// Raises the fused kernel's dynamic shared memory limit; 0 on success.
+int prepare_fused(int tile_max, size_t smem);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);
 void launch_rebuild(const CollideArgs& C, cudaStream_t s);
 void launch_flag_all(const CollideArgs& C, cudaStream_t s);
 
-// state <-> interleaved staging (offset[N][3], quat[N][4], vel[N][3],
-// angvel[N][3], flags[N]); any destination/source pointer may be null
-void launch_pack_state(const float* st, int64_t pitch, int N, const uint8_t* flags, float* off, float* quat,
-                       float* vel, float* angvel, uint8_t* fl, cudaStream_t s);
-void launch_unpack_state(float* st, int64_t pitch, int N, uint8_t* flags, const float* off, const float* quat,
-                         const float* vel, const float* angvel, const uint8_t* fl, cudaStream_t s);
+// planar internal-order state <-> interleaved canonical-order caller layout
+// (offset[N][3], quat[N][4], vel[N][3], angvel[N][3], flags[N]); iperm maps
+// canonical to internal indices; any destination/source pointer may be null
+void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* iperm, const uint8_t* flags,
+                       float* off, float* quat, float* vel, float* angvel, uint8_t* fl, cudaStream_t s);
+void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, uint8_t* flags, const float* off,
+                         const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
+                         cudaStream_t s);
 // rest state: zero offsets, identity quaternions, v0 for non-fixed voxels
 void launch_reset_state(float* st, int64_t pitch, int N, uint8_t* flags, float v0x, float v0y, float v0z,
                         cudaStream_t s);

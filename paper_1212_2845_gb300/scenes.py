@@ -127,18 +127,18 @@ def hetero_block(dims=(64, 64, 32), seed=2, steps=10000):
     return sc
 
 
-def hollow_ball(R=100, t=8, drop=5, l=1e-3, v0=-2.0, steps=20000):
+def hollow_ball(R=100, t=8, drop=5, l=1e-3, v0=-2.0, steps=20000, collide=True):
     """Spherical shell: sites whose centre lies at distance r, R-t <= r < R
     (voxel units) from the sphere centre; lowest voxel's bottom face `drop`
     voxels above the floor; initial downward velocity v0."""
     n = 2 * R
-    c = np.arange(n) + 0.5 - R
-    z, y, x = np.meshgrid(c, c, c, indexing="ij")
-    r = np.sqrt(x * x + y * y + z * z)
-    grid = ((r >= R - t) & (r < R)).astype(np.uint8)
+    c2 = (2 * np.arange(n, dtype=np.int64) + 1 - n) ** 2      # (2 x)^2 of the site centres, exact
+    s = c2[:, None, None] + c2[None, :, None] + c2[None, None, :]
+    grid = ((s >= 4 * (R - t) ** 2) & (s < 4 * R * R)).astype(np.uint8)
+    del s
     kmin = int(np.nonzero(grid.any(axis=(1, 2)))[0][0])
     sc = _base([(n, n, n)], grid, l, [material(0.5e6, 0.45, 1100.0)],
-               gravity_z=-9.81, floor=True, collide=True, v0=(0.0, 0.0, v0),
+               gravity_z=-9.81, floor=True, collide=collide, v0=(0.0, 0.0, v0),
                steps=steps, name=f"hollow_ball_R{R}_t{t}")
     sc["origin"][0] = f32((0.0, 0.0, (drop - kmin) * l))
     return sc

@@ -57,6 +57,9 @@ SIGNATURES = {
     "vx_plan_counts": (C.c_int, [_pdesc, _pi64, _pi64, _pi64]),
     "vx_plan_dt": (C.c_int, [_pdesc, _pf, _f32, _pd]),
     "vx_region_mask": (C.c_int, [_pdesc, _i32, _pf, _pf, _pu8, _pi64]),
+    "vx_plan_tiles": (C.c_int, [_pdesc, _i32, _pi64, _pi64, _pi64, _pi32]),
+    "vx_set_step_form": (C.c_int, [_P, _i32, _i32]),
+    "vx_get_tiling": (C.c_int, [_P, _pi32, _pi64, _pi32, _pi64]),
     "vx_create": (C.c_int, [_pdesc, C.POINTER(_P)]),
     "vx_destroy": (None, [_P]),
     "vx_get_counts": (C.c_int, [_P, _pi64, _pi64, _pi64]),
@@ -151,6 +154,18 @@ def plan_dt(sc, log_E=None, dt_factor=None):
     return out
 
 
+def plan_tiles(sc, tile_max=256):
+    h = _DescHolder(sc)
+    n = [C.c_int64() for _ in range(3)]
+    ml = C.c_int32()
+    _check(lib().vx_plan_tiles(C.byref(h.desc), int(tile_max), *[C.byref(x) for x in n], C.byref(ml)))
+    return dict(n_tiles=n[0].value, n_halo=n[1].value, n_tile_bonds=n[2].value, max_local=ml.value)
+
+
+FORM_FUSED = 0
+FORM_TWO_PASS = 1
+
+
 def region_mask(sc, body, loc, size):
     h = _DescHolder(sc)
     n = int(np.count_nonzero(h.grid))
@@ -241,6 +256,15 @@ class Sim:
         _check(self._L.vx_add_forced_region(self.h, int(body), _ptr(lo, C.c_float), _ptr(sz, C.c_float),
                                             _ptr(f, C.c_float), C.byref(n)))
         return n.value
+
+    def set_step_form(self, form, tile_max=0):
+        _check(self._L.vx_set_step_form(self.h, int(form), int(tile_max)))
+
+    def tiling(self):
+        tm, ml = C.c_int32(), C.c_int32()
+        nt, sm = C.c_int64(), C.c_int64()
+        _check(self._L.vx_get_tiling(self.h, C.byref(tm), C.byref(nt), C.byref(ml), C.byref(sm)))
+        return dict(tile_max=tm.value, n_tiles=nt.value, max_local=ml.value, smem_bytes=sm.value)
 
     def set_dt_factor(self, f):
         _check(self._L.vx_set_dt_factor(self.h, float(f)))

@@ -103,3 +103,17 @@ def test_invalid_descriptions_are_rejected(bad):
         vx.plan_counts(sc)
     assert e.value.code == -1
     assert vx.lib().vx_last_error().decode()
+
+
+@pytest.mark.parametrize("mk", SCENES)
+@pytest.mark.parametrize("tile_max", [128, 256, 512])
+def test_tile_plan_invariants(mk, tile_max):
+    sc = mk()
+    n, nb, _ = vx.plan_counts(sc)
+    t = vx.plan_tiles(sc, tile_max)
+    assert t["n_tiles"] >= (n + tile_max - 1) // tile_max
+    # every bond is evaluated by each tile that owns one of its voxels: once
+    # inside a tile, twice when it crosses a tile border; crossing bonds are
+    # bounded by the halo entries
+    assert nb <= t["n_tile_bonds"] <= nb + t["n_halo"] * 6
+    assert 0 < t["max_local"] <= 2 * tile_max

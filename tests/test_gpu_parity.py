@@ -323,3 +323,37 @@ def test_ball_drop_with_self_collision(vx):
     print(f"ball: pos err/diag {err:.2e}, rebuilds gpu {nr_g} oracle {nr_o}")
     assert err < 1e-3
     assert abs(nr_g - nr_o) <= max(2, nr_o // 10)
+
+
+# ---------------------------------------------------------------------------
+# step forms and tile sizes
+# ---------------------------------------------------------------------------
+
+def run_form(vx, sc, steps, form, tile_max=0):
+    sim = vx.Sim(sc)
+    sim.set_step_form(form, tile_max)
+    sim.step(steps)
+    s = sim.read_state()
+    sim.close()
+    return s
+
+
+@pytest.mark.parametrize("which", ["hetero", "ball", "population"])
+def test_fused_tile_sizes_bitwise_and_two_pass_close(vx, which):
+    """Every operation of the step is an explicitly rounded intrinsic, so the
+    fused kernel gives the same bits for every tile size and the two-pass form
+    gives the same bits as the fused one."""
+    if which == "hetero":
+        sc, steps = scenes.hetero_block(dims=(20, 17, 9), seed=3), 300
+    elif which == "ball":
+        sc, steps = scenes.hollow_ball(R=10, t=3), 500
+    else:
+        sc, steps = scenes.population(n_bodies=9, seed=7, lo=2, hi=11), 300
+    ref = run_form(vx, sc, steps, vx.FORM_FUSED, 256)
+    for tm in (128, 512):
+        out = run_form(vx, sc, steps, vx.FORM_FUSED, tm)
+        for k in ("offset", "quat", "vel", "angvel", "flags"):
+            assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), (tm, k)
+    two = run_form(vx, sc, steps, vx.FORM_TWO_PASS)
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(two[k].view(np.uint8), ref[k].view(np.uint8)), ("two-pass", k)
