@@ -228,6 +228,38 @@ VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int6
  * accumulator of body 0 [m]. */
 VX_API int vx_collision_stats(vx_sim* sim, int64_t* n_rebuilds, double* accumulator);
 
+/* ---- collision candidates with no device allocation ----------------------
+ * The paper has no counterpart to this entry point: it exists for callers
+ * that cannot allocate device memory where they need collision candidates
+ * (code inside a memory pool or arena that owns the device heap, a plug-in
+ * handed only pre-sized buffers, a real-time loop that must not hit
+ * cudaMalloc's implicit synchronisation).  It computes the same candidate
+ * lists as a vx_sim's collision rebuild, for surface voxels the caller
+ * describes, and calls no cudaMalloc, cudaFree or allocating library routine.
+ *
+ * Inputs (device memory): lat[n_surface] packed lattice coordinates
+ * i | j << 11 | k << 22 within each voxel's body; offset_planes[3][n_surface]
+ * offsets from the lattice anchors (all x, then all y, then all z) [m];
+ * body[n_surface] body of each voxel (may be NULL when n_bodies == 1).
+ * Outputs (device memory, caller-owned): cand_count[n_surface] and
+ * cand[n_surface][48]: for each surface voxel, its candidates as indices into
+ * the same input arrays, ascending.  Candidates: same body, lattice
+ * Manhattan distance > 3, quantised centre distance below 2 voxel_size.
+ *
+ * Limits: n_surface <= VX_STATIC_MAX_SURFACE, n_bodies <= VX_STATIC_MAX_BODIES
+ * (larger inputs return VX_ERR_ARG); more than 48 candidates for a voxel
+ * returns VX_ERR_CAPACITY.  Scratch comes from one fixed device array of
+ * about 4 MiB that every GPU loading the library holds until exit.  The first
+ * call on a device (with that device current) looks up the array's address;
+ * make it before any stream capture.  Calls share the array: calls whose GPU
+ * work overlaps race and must be serialised by the caller.  Work is enqueued
+ * on `stream`; the call waits for it before returning. */
+#define VX_STATIC_MAX_SURFACE 65536
+#define VX_STATIC_MAX_BODIES 4096
+VX_API int vx_collision_candidates_static(const uint32_t* lat, const float* offset_planes, const int32_t* body,
+                                          int32_t n_surface, int32_t n_bodies, float voxel_size,
+                                          int32_t* cand_count, int32_t* cand, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

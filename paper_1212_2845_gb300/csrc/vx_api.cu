@@ -48,6 +48,8 @@ template <class T> void dfree(T*& p) {
 }
 }  // namespace
 
+int vx::set_error(int code, const std::string& msg) { return fail(code, msg); }
+
 struct vx_sim {
   Lattice L;
   Tiling T;

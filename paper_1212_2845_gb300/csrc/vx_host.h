@@ -41,6 +41,9 @@ void stable_dt(const Lattice& L, const float* logE, float dt_factor, std::vector
 // Voxels touching a region given in workspace fractions (paper App. B).
 int64_t region_mask(const Lattice& L, int body, const float loc[3], const float size[3], uint8_t* mask);
 
+// Records the message vx_last_error() returns on this thread; returns code.
+int set_error(int code, const std::string& msg);
+
 // Collision quantisation: 2^K <= 65536 / l < 2^(K+1), Q = rint(l 2^K).
 void quant_params(float l, int* K, int64_t* Q);
 

@@ -87,7 +87,21 @@ SIGNATURES = {
     "vx_rebuild_collisions": (C.c_int, [_P, _P]),
     "vx_get_collision_pairs": (C.c_int, [_P, _pi32, _i64, _pi64]),
     "vx_collision_stats": (C.c_int, [_P, _pi64, _pd]),
+    "vx_collision_candidates_static": (C.c_int, [_P, _P, _P, _i32, _i32, _f32, _P, _P, _P]),
 }
+STATIC_MAX_SURFACE = 65536
+STATIC_MAX_BODIES = 4096
+CAND_CAP = 48
+
+
+def collision_candidates_static(lat, offset_planes, body, n_surface, n_bodies, voxel_size, cand_count, cand,
+                                stream=None):
+    """vx_collision_candidates_static on caller-owned device buffers (torch
+    CUDA tensors): lat int32 [S], offset_planes float32 [3, S], body int32 [S]
+    or None, cand_count int32 [S], cand int32 [S, 48]."""
+    _check(lib().vx_collision_candidates_static(
+        lat.data_ptr(), offset_planes.data_ptr(), None if body is None else body.data_ptr(), int(n_surface),
+        int(n_bodies), float(voxel_size), cand_count.data_ptr(), cand.data_ptr(), _stream_ptr(stream)))
 
 _lib = None
 
