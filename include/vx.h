@@ -146,13 +146,17 @@ VX_API int vx_get_counts(vx_sim* sim, int64_t* n_voxels, int64_t* n_bonds, int64
 VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
 
 /* Kernel form of the step.  VX_FORM_FUSED (default): one kernel per step,
- * bond forces kept in shared memory.  VX_FORM_TWO_PASS: a bond kernel writes
- * every bond's forces to device memory and a voxel kernel gathers them.  Both
- * forms compute the same arithmetic and give bitwise-identical states.
- * tile_max (fused form): 128, 256 or 512 voxels per tile, 0 keeps the current
- * size (256 at create).  The state is kept. */
+ * one CTA per tile, bond forces kept in shared memory.  VX_FORM_TWO_PASS: a
+ * bond kernel writes every bond's forces to device memory and a voxel kernel
+ * gathers them.  VX_FORM_PIPELINED: the fused step with persistent CTAs that
+ * stream the next tile into shared memory (cp.async) while computing the
+ * current one.  All forms compute the same arithmetic and give
+ * bitwise-identical states.  tile_max (fused forms): 128, 256 or 512 voxels
+ * per tile (pipelined: 128 or 256), 0 keeps the current size (256 at create).
+ * The state is kept. */
 #define VX_FORM_FUSED 0
 #define VX_FORM_TWO_PASS 1
+#define VX_FORM_PIPELINED 2
 VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
 /* Current tiling: tile size, tile count, largest staged set, dynamic shared
  * memory of the fused kernel in bytes.  Any output may be NULL. */

@@ -80,6 +80,12 @@ struct vx_sim {
   int32_t* halo = nullptr;
   uint16_t* plus = nullptr;
   uint32_t* hbonds = nullptr;
+  int32_t* tdesc = nullptr;   // pipelined form
+  int32_t* hfix = nullptr;
+  uint32_t* vw = nullptr;
+  uint2* plus2 = nullptr;
+  size_t pipe_smem = 0;
+  int pipe_grid = 0;
   uint8_t* mask = nullptr;
   uint8_t* flags = nullptr;
   uint8_t* mat = nullptr;
@@ -90,6 +96,7 @@ struct vx_sim {
   float* logE = nullptr;
   float* fext = nullptr;
   DevMat* mats = nullptr;
+  float* lut = nullptr;    // material-pair bond constants (n_mats <= kLutMaxMats)
   float* dtb = nullptr;
   float* origin = nullptr;
   int* status = nullptr;
@@ -139,6 +146,7 @@ StepArgs step_args(vx_sim* s) {
   A.fext = s->has_fext ? s->fext : nullptr;
   A.mats = s->mats;
   A.n_mats = (int)s->L.palette.size();
+  A.lut = (s->lut && s->logE_h.empty()) ? s->lut : nullptr;
   A.dt_body = s->dtb;
   A.origin = s->origin;
   A.bf = s->bf;
@@ -154,6 +162,11 @@ StepArgs step_args(vx_sim* s) {
   A.halo = s->halo;
   A.plus = s->plus;
   A.hbonds = s->hbonds;
+  A.tdesc = s->tdesc;
+  A.hfix = s->hfix;
+  A.hstride = s->T.halo_stride;
+  A.vw = s->vw;
+  A.plus2 = s->plus2;
   A.mask = s->mask;
   A.n_tiles = (int)s->T.n_tiles();
   A.max_local = s->T.max_local;
@@ -172,7 +185,8 @@ CollideArgs collide_args(vx_sim* s) {
   C.H = s->H;
   C.K = s->qK;
   C.Q = s->qQ;
-  C.pitch = s->pitch;
+  C.ostride_v = 4;           // offsets are the x, y, z of state plane A
+  C.ostride_a = 1;
   C.threshold = s->threshold;
   C.st = cur_state(s);
   C.surf = s->surf;
@@ -215,6 +229,40 @@ int upload_materials(vx_sim* s) {
     m[i].inv_I = (float)(1.0 / I);
   }
   VX_CUDA(cudaMemcpy(s->mats, m.data(), m.size() * sizeof(DevMat), cudaMemcpyHostToDevice));
+  return VX_OK;
+}
+
+constexpr int kLutMaxMats = 16;
+
+// Bond constants of every material pair (Sec 2.1.1, 2.1.2, 2.1.5) in double,
+// used when no per-voxel stiffness is set: a1, a2, b2, b3, c/2, c/4, cr/2.
+int upload_lut(vx_sim* s) {
+  int nm = (int)s->L.palette.size();
+  if (nm > kLutMaxMats) return VX_OK;
+  if (!s->lut) {
+    int rc = dalloc(&s->lut, (size_t)8 * nm * nm);
+    if (rc) return rc;
+  }
+  std::vector<float> h((size_t)8 * nm * nm, 0.f);
+  const double l = s->L.l;
+  for (int i = 0; i < nm; ++i)
+    for (int j = 0; j < nm; ++j) {
+      const vx_material& p = s->L.palette[i];
+      const vx_material& q = s->L.palette[j];
+      double E1 = p.E, E2 = q.E;
+      double G1 = E1 / (2.0 * (1.0 + (double)p.nu)), G2 = E2 / (2.0 * (1.0 + (double)q.nu));
+      double Ec = 2.0 * E1 * E2 / (E1 + E2), Gc = 2.0 * G1 * G2 / (G1 + G2);
+      double m1 = (double)p.rho * l * l * l, m2 = (double)q.rho * l * l * l;
+      double mmin = std::min(m1, m2), Imin = mmin * l * l / 6.0;
+      double a1 = Ec * l, a2 = Gc * l * l * l / 6.0, b2 = Ec * l * l / 2.0, b3 = Ec * l * l * l / 6.0;
+      float* e = &h[(size_t)8 * (i * nm + j)];
+      e[0] = (float)a1; e[1] = (float)a2; e[2] = (float)b2; e[3] = (float)b3;
+      double c = 2.0 * s->zb * std::sqrt(mmin * a1), cr = 2.0 * s->zb * std::sqrt(Imin * b3);
+      e[4] = (float)(c / 2.0);
+      e[5] = (float)(c / 4.0);
+      e[6] = (float)(cr / 2.0);
+    }
+  VX_CUDA(cudaMemcpy(s->lut, h.data(), h.size() * sizeof(float), cudaMemcpyHostToDevice));
   return VX_OK;
 }
 
@@ -306,17 +354,35 @@ int upload_tiling(vx_sim* s) {
   const Tiling& T = s->T;
   int64_t nt = T.n_tiles();
   dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds);
+  dfree(s->tdesc); dfree(s->hfix); dfree(s->vw); dfree(s->plus2);
   int rc;
+  const int64_t N = s->L.N;
   if ((rc = dalloc(&s->tile_a, nt)) || (rc = dalloc(&s->tile_b, nt)) || (rc = dalloc(&s->halo, T.halo.size())) ||
-      (rc = dalloc(&s->plus, T.plus.size())) || (rc = dalloc(&s->hbonds, T.halo_bonds.size())))
+      (rc = dalloc(&s->plus, T.plus.size())) || (rc = dalloc(&s->hbonds, T.halo_bonds.size())) ||
+      (rc = dalloc(&s->tdesc, T.tile_desc.size())) || (rc = dalloc(&s->hfix, T.halo_fixed.size())) ||
+      (rc = dalloc(&s->vw, N)) || (rc = dalloc(&s->plus2, N)))
     return rc;
+  {
+    std::vector<uint32_t> vw(N);
+    std::vector<uint2> p2(N);
+    for (int64_t v = 0; v < N; ++v) {
+      vw[v] = (uint32_t)s->L.mat[T.perm[v]] | (uint32_t)T.mask[v] << 8;
+      p2[v].x = (uint32_t)T.plus[v] | (uint32_t)T.plus[(size_t)N + v] << 16;
+      p2[v].y = (uint32_t)T.plus[2 * (size_t)N + v] | 0xFFFF0000u;
+    }
+    VX_CUDA(cudaMemcpy(s->vw, vw.data(), N * 4, cudaMemcpyHostToDevice));
+    VX_CUDA(cudaMemcpy(s->plus2, p2.data(), N * 8, cudaMemcpyHostToDevice));
+    VX_CUDA(cudaMemcpy(s->tdesc, T.tile_desc.data(), T.tile_desc.size() * 4, cudaMemcpyHostToDevice));
+    VX_CUDA(cudaMemcpy(s->hfix, T.halo_fixed.data(), T.halo_fixed.size() * 4, cudaMemcpyHostToDevice));
+  }
   VX_CUDA(cudaMemcpy(s->tile_a, T.tile_a.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemcpy(s->tile_b, T.tile_b.data(), nt * sizeof(int4), cudaMemcpyHostToDevice));
   if (!T.halo.empty()) VX_CUDA(cudaMemcpy(s->halo, T.halo.data(), T.halo.size() * 4, cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemcpy(s->plus, T.plus.data(), T.plus.size() * 2, cudaMemcpyHostToDevice));
   if (!T.halo_bonds.empty())
     VX_CUDA(cudaMemcpy(s->hbonds, T.halo_bonds.data(), T.halo_bonds.size() * 4, cudaMemcpyHostToDevice));
-  s->smem = fused_smem_bytes(s->tile_max, (int)s->L.palette.size());
+  int nm = (int)s->L.palette.size();
+  s->smem = fused_smem_bytes(s->tile_max, nm, nm <= kLutMaxMats);
   if (prepare_fused(s->tile_max, s->smem) != 0)
     return fail(VX_ERR_CUDA, "fused kernel needs " + std::to_string(s->smem) + " bytes of shared memory");
   return VX_OK;
@@ -441,7 +507,8 @@ int vx_create(const vx_desc* desc, vx_sim** out) {
     return fail(VX_ERR_CUDA, "upload failed");
   }
   quant_params(L.l, &s->qK, &s->qQ);
-  if ((rc = upload_tiling(s)) || (rc = upload_materials(s)) || (rc = recompute_dt(s)) || (rc = vx_reset(s, nullptr))) {
+  if ((rc = upload_tiling(s)) || (rc = upload_materials(s)) || (rc = upload_lut(s)) || (rc = recompute_dt(s)) ||
+      (rc = vx_reset(s, nullptr))) {
     vx_destroy(s);
     return rc;
   }
@@ -454,7 +521,8 @@ void vx_destroy(vx_sim* s) {
   cudaSetDevice(s->device);
   dfree(s->st); dfree(s->bf); dfree(s->flags); dfree(s->mat); dfree(s->lat); dfree(s->body); dfree(s->nbr);
   dfree(s->iperm); dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds); dfree(s->mask);
-  dfree(s->phase); dfree(s->logE); dfree(s->fext); dfree(s->mats); dfree(s->dtb); dfree(s->origin);
+  dfree(s->tdesc); dfree(s->hfix); dfree(s->vw); dfree(s->plus2);
+  dfree(s->phase); dfree(s->logE); dfree(s->fext); dfree(s->mats); dfree(s->lut); dfree(s->dtb); dfree(s->origin);
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
@@ -485,15 +553,19 @@ int vx_get_anchors(vx_sim* s, double* anchors) {
 int vx_set_step_form(vx_sim* s, int32_t form, int32_t tile_max) {
   int rc = check_sim(s);
   if (rc) return rc;
-  if (form != VX_FORM_FUSED && form != VX_FORM_TWO_PASS) return fail(VX_ERR_ARG, "unknown step form");
+  if (form != VX_FORM_FUSED && form != VX_FORM_TWO_PASS && form != VX_FORM_PIPELINED)
+    return fail(VX_ERR_ARG, "unknown step form");
   if (form == VX_FORM_TWO_PASS && (rc = ensure_two_pass(s))) return rc;
-  if (form == VX_FORM_FUSED && tile_max != 0 && tile_max != s->tile_max) {
+  if (form == VX_FORM_PIPELINED && (tile_max == 512 || (tile_max == 0 && s->tile_max == 512)))
+    return fail(VX_ERR_ARG, "the pipelined form takes tiles of 128 or 256 voxels");
+  if (form != VX_FORM_TWO_PASS && tile_max != 0 && tile_max != s->tile_max) {
     if (tile_max != 128 && tile_max != 256 && tile_max != 512) return fail(VX_ERR_ARG, "tile_max must be 128, 256 or 512");
     // the voxel order depends only on the lattice, so the state stays valid
     Tiling T;
     if ((rc = build_tiling(s->L, tile_max, 2 * tile_max, T, g_err))) return rc;
     s->T.tile_a.swap(T.tile_a); s->T.tile_b.swap(T.tile_b); s->T.halo.swap(T.halo); s->T.plus.swap(T.plus);
-    s->T.halo_bonds.swap(T.halo_bonds);
+    s->T.halo_bonds.swap(T.halo_bonds); s->T.tile_desc.swap(T.tile_desc); s->T.halo_fixed.swap(T.halo_fixed);
+    s->T.halo_stride = T.halo_stride;
     s->T.tile_max = tile_max;
     s->T.max_local = T.max_local;
     s->tile_max = tile_max;
@@ -522,7 +594,7 @@ int vx_set_materials(vx_sim* s, const vx_material* palette, int32_t n) {
       return fail(VX_ERR_ARG, "material out of range");
   }
   s->L.palette.assign(palette, palette + n);
-  if ((rc = upload_materials(s)) || (rc = recompute_dt(s))) return rc;
+  if ((rc = upload_materials(s)) || (rc = upload_lut(s)) || (rc = recompute_dt(s))) return rc;
   update_threshold(s);
   return VX_OK;
 }
@@ -567,7 +639,7 @@ int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float
   float* cs = cur_state(s);
   VX_CUDA(cudaMemcpy(st.data(), cs, st.size() * 4, cudaMemcpyDeviceToHost));
   for (int64_t c = 0; c < N; ++c)
-    if (m[c]) for (int p = VX; p <= WZ; ++p) st[(size_t)p * s->pitch + s->T.iperm[c]] = 0.f;
+    if (m[c]) for (int p = VX; p <= WZ; ++p) st[state_index(p, s->T.iperm[c], s->pitch)] = 0.f;
   VX_CUDA(cudaMemcpy(cs, st.data(), st.size() * 4, cudaMemcpyHostToDevice));
   if (n_out) *n_out = n;
   return VX_OK;
@@ -605,7 +677,9 @@ int vx_set_damping(vx_sim* s, float zb, float zg, float zc) {
   if (!s) return fail(VX_ERR_ARG, "sim is NULL");
   if (!(zb >= 0.f) || !(zg >= 0.f) || !(zc >= 0.f)) return fail(VX_ERR_ARG, "damping ratios must be >= 0");
   s->zb = zb; s->zg = zg; s->zc = zc;
-  return VX_OK;
+  int rc = check_sim(s);
+  if (rc) return rc;
+  return upload_lut(s);
 }
 
 int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t collide_on) {
@@ -754,7 +828,19 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   for (int64_t i = 0; i < n; ++i) {
     StepArgs A = step_args(s);
     if (s->actP > 0) A.act_w = (float)(2.0 * M_PI * (double)(s->step % s->actP) / (double)s->actP);
-    launch_step(A, s->form, s->tile_max, s->smem, st);
+    if (s->form == VX_FORM_PIPELINED) {
+      int nm = (int)s->L.palette.size();
+      size_t sm = pipe_smem_bytes(s->tile_max, A.phase != nullptr, A.logE != nullptr, A.body != nullptr,
+                                  A.fext != nullptr, nm, nm <= kLutMaxMats);
+      if (sm != s->pipe_smem) {
+        if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0)
+          return fail(VX_ERR_CUDA, "pipelined kernel needs " + std::to_string(sm) + " bytes of shared memory");
+        s->pipe_smem = sm;
+      }
+      launch_pipe(A, s->tile_max, s->pipe_smem, s->pipe_grid, st);
+    } else {
+      launch_step(A, s->form, s->tile_max, s->smem, st);
+    }
     s->cur = 1 - s->cur;
     s->step += 1;
     if (s->collide_on) {

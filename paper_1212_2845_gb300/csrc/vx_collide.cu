@@ -59,7 +59,7 @@ __global__ void quantise(CollideArgs C) {
   int64_t ijk[3] = {(int64_t)(lp & 2047u), (int64_t)((lp >> 11) & 2047u), (int64_t)(lp >> 22)};
   int64_t xq[3];
   for (int a = 0; a < 3; ++a) {
-    float o = C.st[(int64_t)(OX + a) * C.pitch + v];
+    float o = C.st[(int64_t)v * C.ostride_v + a * C.ostride_a];
     xq[a] = ijk[a] * C.Q + llrintf(ldexpf(o, C.K));
     C.xq[(int64_t)a * C.S + s] = xq[a];
   }

@@ -1,17 +1,26 @@
 // Device data layout and FP32 math of one explicit lattice step.
 //
 // All per-voxel arrays are in the internal order (bricks along a Morton
-// curve, see vx_host.h).  State is structure-of-arrays: 13 float planes of
-// `pitch` floats (offset x,y,z from the lattice anchor, quaternion w,x,y,z,
-// velocity x,y,z, angular velocity x,y,z), double-buffered: a step reads
-// st_in and writes st_out, so neighbours always see the state at step n.
+// curve, see vx_host.h).  The state of `pitch` voxels is three float4 planes
+// and one float plane (13 floats, 52 bytes per voxel):
+//   A = (offset x, y, z, quat w)   B = (quat x, y, z, vel x)
+//   C = (vel y, z, angvel x, y)    D = angvel z
+// so a warp moves a voxel's state in four coalesced vector accesses.  The
+// state is double-buffered: a step reads st_in and writes st_out, so
+// neighbours always see the state at step n.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 namespace vx {
 
-enum Plane { OX = 0, OY, OZ, QW, QX, QY, QZ, VX, VY, VZ, WX, WY, WZ, NPLANE };
+// State components in plane order (component c of voxel v lives at
+// state_index(c, v, pitch) floats from the buffer start).
+enum Comp { OX = 0, OY, OZ, QW, QX, QY, QZ, VX, VY, VZ, WX, WY, WZ, NPLANE };
+
+__host__ __device__ __forceinline__ int64_t state_index(int c, int64_t v, int64_t pitch) {
+  return c < 12 ? (int64_t)(c >> 2) * 4 * pitch + 4 * v + (c & 3) : 12 * pitch + v;
+}
 
 // Per-material constants precomputed on the host in double precision.
 struct DevMat {
@@ -43,6 +52,7 @@ struct StepArgs {
   const float* fext;       // 3 planes or nullptr
   const DevMat* mats;
   int n_mats;
+  const float* lut;        // per material pair (a1, a2, b2, b3, c, cr, 0, 0), or nullptr
   const float* dt_body;    // per body
   const float* origin;     // 3 per body
   float zb, zg, zc, gz;
@@ -61,6 +71,12 @@ struct StepArgs {
   const uint32_t* hbonds;  // halo bonds: slot 1 | slot 2 << 12 | axis << 24
   const uint8_t* mask;     // per voxel 6-bit bond existence
   int n_tiles, max_local;
+  // pipelined form
+  const int32_t* tdesc;    // 8 ints per tile: v0, n_owned, n_halo, halo-bond start, n_halo_bonds
+  const int32_t* hfix;     // halo indices at hfix[t * hstride + j]
+  int hstride;
+  const uint32_t* vw;      // per voxel: material | bond mask << 8
+  const uint2* plus2;      // per voxel: +x | +y << 16, +z partner staging slots
   // collisions
   const int32_t* sidx;     // per voxel: surface index or -1
   const int32_t* ccount;   // per surface voxel
@@ -142,14 +158,19 @@ __device__ __forceinline__ V3f rel_rotvec(Qf a, Qf b) {
   w = mul_(w, sg);
   float s2 = fma_(x, x, fma_(y, y, mul_(z, z)));
   float f;
-  if (s2 < mul_(1e-6f, mul_(w, w))) {
-    // 2 atan(t) / (t w) with t = s / w, series to t^4 (remainder < t^6 / 7 < 2e-19)
+  if (s2 < mul_(0.04f, mul_(w, w))) {
+    // 2 atan(t) / (t w), t = s / w < 0.2: alternating series to t^10
+    // (remainder below t^12 / 13 < 4e-10)
     float iw = __fdividef(1.f, w);
     float t2 = mul_(s2, mul_(iw, iw));
-    f = mul_(add_(iw, iw), fma_(t2, fma_(t2, 0.2f, -1.f / 3.f), 1.f));
+    float pz = fma_(t2, 1.f / 11.f, -1.f / 9.f);
+    pz = fma_(t2, pz, 1.f / 7.f);
+    pz = fma_(t2, pz, -0.2f);
+    pz = fma_(t2, pz, 1.f / 3.f);
+    f = mul_(add_(iw, iw), fma_(-t2, pz, 1.f));
   } else {
-    float s = sqrtf(s2);
-    f = __fdividef(mul_(2.f, atan2f(s, w)), s);
+    float sq = sqrtf(s2);
+    f = __fdividef(mul_(2.f, atan2f(sq, w)), sq);
   }
   f = mul_(f, sg);
   return v3(mul_(x, f), mul_(y, f), mul_(z, f));
@@ -185,20 +206,38 @@ __device__ __forceinline__ Qf integrate_rot(Qf q, V3f w, float dt) {
 
 struct VoxS { V3f o; Qf q; V3f v; V3f w; };
 
-__device__ __forceinline__ VoxS load_vox(const float* __restrict__ st, int64_t pitch, int64_t i) {
+__device__ __forceinline__ VoxS unpack_vox(float4 a, float4 b, float4 c, float d) {
   VoxS s;
-  s.o = v3(st[OX * pitch + i], st[OY * pitch + i], st[OZ * pitch + i]);
-  s.q.w = st[QW * pitch + i]; s.q.x = st[QX * pitch + i]; s.q.y = st[QY * pitch + i]; s.q.z = st[QZ * pitch + i];
-  s.v = v3(st[VX * pitch + i], st[VY * pitch + i], st[VZ * pitch + i]);
-  s.w = v3(st[WX * pitch + i], st[WY * pitch + i], st[WZ * pitch + i]);
+  s.o = v3(a.x, a.y, a.z);
+  s.q.w = a.w; s.q.x = b.x; s.q.y = b.y; s.q.z = b.z;
+  s.v = v3(b.w, c.x, c.y);
+  s.w = v3(c.z, c.w, d);
   return s;
 }
 
-__device__ __forceinline__ void store_vox(float* __restrict__ st, int64_t pitch, int64_t i, const VoxS& s) {
-  st[OX * pitch + i] = s.o.x; st[OY * pitch + i] = s.o.y; st[OZ * pitch + i] = s.o.z;
-  st[QW * pitch + i] = s.q.w; st[QX * pitch + i] = s.q.x; st[QY * pitch + i] = s.q.y; st[QZ * pitch + i] = s.q.z;
-  st[VX * pitch + i] = s.v.x; st[VY * pitch + i] = s.v.y; st[VZ * pitch + i] = s.v.z;
-  st[WX * pitch + i] = s.w.x; st[WY * pitch + i] = s.w.y; st[WZ * pitch + i] = s.w.z;
+// State access on a buffer of `pitch` voxels (global or shared memory).
+struct StPtr {
+  float4* A; float4* B; float4* C; float* D;
+  __device__ __forceinline__ StPtr(float* base, int64_t pitch) {
+    A = reinterpret_cast<float4*>(base);
+    B = A + pitch;
+    C = B + pitch;
+    D = reinterpret_cast<float*>(C + pitch);
+  }
+  __device__ __forceinline__ VoxS load(int64_t i) const { return unpack_vox(A[i], B[i], C[i], D[i]); }
+  __device__ __forceinline__ void store(int64_t i, const VoxS& s) const {
+    A[i] = make_float4(s.o.x, s.o.y, s.o.z, s.q.w);
+    B[i] = make_float4(s.q.x, s.q.y, s.q.z, s.v.x);
+    C[i] = make_float4(s.v.y, s.v.z, s.w.x, s.w.y);
+    D[i] = s.w.z;
+  }
+};
+
+__device__ __forceinline__ VoxS load_vox(const float* st, int64_t pitch, int64_t i) {
+  return StPtr(const_cast<float*>(st), pitch).load(i);
+}
+__device__ __forceinline__ void store_vox(float* st, int64_t pitch, int64_t i, const VoxS& s) {
+  StPtr(st, pitch).store(i, s);
 }
 
 // Thermal strain alpha_v dT_v of a voxel at the current step (Sec 2.3).  The
@@ -219,21 +258,43 @@ __device__ __forceinline__ float voxel_E(const StepArgs& A, int64_t g, int m) {
 // Result of one bond: force on voxel 1 (voxel 2 gets -F1), moments on both.
 struct BondOut { V3f F1, M1, M2; };
 
-// One bond along lattice axis a from voxel 1 (negative side) to voxel 2:
-// co-rotational beam (Sec 2.1.2) in voxel 1's frame (R1 = R(q1)), local
-// damping (Sec 2.1.5), rest length scaled by the mean thermal strain (Sec 2.3).
-template <int a>
-__device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, const VoxS& s2, float l, float E1,
-                                             float E2, float G1, float G2, float mmin, float Imin, float eps,
+// Beam constants of a bond (Sec 2.1.2) and its damping coefficients (Sec 2.1.5).
+// c2 = c / 2, c4 = c / 4, cr2 = cr / 2 with c = 2 zeta sqrt(m_min a1) and
+// cr = 2 zeta sqrt(I_min b3) the translational and rotational damping coefficients.
+struct BondK { float a1, a2, b2, b3, c2, c4, cr2; };  // b1 = a1 for cubic voxels
+
+__device__ __forceinline__ BondK bond_consts(float l, float E1, float E2, float G1, float G2, float mmin, float Imin,
                                              float zb) {
   float Ec = __fdividef(mul_(mul_(2.f, E1), E2), add_(E1, E2));
   float Gc = __fdividef(mul_(mul_(2.f, G1), G2), add_(G1, G2));
   const float l2 = mul_(l, l), l3 = mul_(l2, l);
-  float a1 = mul_(Ec, l);                      // E_c A / l
-  float a2 = mul_(mul_(Gc, l3), 1.f / 6.f);    // G_c J / l
-  float b1 = a1;                               // 12 E_c I / l^3
-  float b2 = mul_(mul_(Ec, l2), 0.5f);         // 6 E_c I / l^2
-  float b3 = mul_(mul_(Ec, l3), 1.f / 6.f);    // 2 E_c I / l
+  BondK k;
+  k.a1 = mul_(Ec, l);                      // E_c A / l
+  k.a2 = mul_(mul_(Gc, l3), 1.f / 6.f);    // G_c J / l
+  k.b2 = mul_(mul_(Ec, l2), 0.5f);         // 6 E_c I / l^2
+  k.b3 = mul_(mul_(Ec, l3), 1.f / 6.f);    // 2 E_c I / l
+  const float c = mul_(mul_(2.f, zb), fsqrt(mul_(mmin, k.a1)));
+  k.c2 = mul_(c, 0.5f);
+  k.c4 = mul_(c, 0.25f);
+  k.cr2 = mul_(zb, fsqrt(mul_(Imin, k.b3)));
+  return k;
+}
+
+__device__ __forceinline__ BondK lut_consts(const float* lut, int n_mats, int m1, int m2) {
+  const float4* e = reinterpret_cast<const float4*>(lut) + 2 * (m1 * n_mats + m2);
+  float4 u = e[0], w = e[1];
+  BondK k;
+  k.a1 = u.x; k.a2 = u.y; k.b2 = u.z; k.b3 = u.w; k.c2 = w.x; k.c4 = w.y; k.cr2 = w.z;
+  return k;
+}
+
+// One bond along lattice axis a from voxel 1 (negative side) to voxel 2:
+// co-rotational beam (Sec 2.1.2) in voxel 1's frame (R1 = R(q1)), local
+// damping (Sec 2.1.5), rest length scaled by the mean thermal strain (Sec 2.3).
+template <int a>
+__device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, const VoxS& s2, float l, const BondK& k,
+                                             float eps, bool damp) {
+  const float a1 = k.a1, a2 = k.a2, b1 = k.a1, b2 = k.b2, b3 = k.b3;
   // position of voxel 2 in voxel 1's frame minus its rest vector l e_a:
   // R1^T (l e_a + do) - l e_a = R1^T do + l (R1^T e_a - e_a)
   V3f dO = sub(s2.o, s1.o);
@@ -249,19 +310,16 @@ __device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, cons
   o.F1 = mul(R1, from_axis<a>(F1));
   o.M1 = mul(R1, from_axis<a>(M1));
   o.M2 = mul(R1, from_axis<a>(M2));
-  if (zb != 0.f) {
-    // V_{2->1} = (v2 - Va) + (D2 - Da) x wa with D2 - Da = (l e_a + do) / 2
-    V3f wa = scl(add(s1.w, s2.w), 0.5f);
-    V3f half = scl(dO, 0.5f);
-    const float hl = mul_(0.5f, l);
-    if (a == 0) half.x = add_(half.x, hl); else if (a == 1) half.y = add_(half.y, hl); else half.z = add_(half.z, hl);
-    V3f V21 = add(scl(sub(s2.v, s1.v), 0.5f), cross3(half, wa));
-    float c = mul_(mul_(2.f, zb), fsqrt(mul_(mmin, a1)));
-    float cr = mul_(mul_(2.f, zb), fsqrt(mul_(Imin, b3)));
-    o.F1 = axpy(o.F1, c, V21);
-    V3f dw = scl(sub(s2.w, s1.w), mul_(0.5f, cr));   // cr (w2 - wa)
-    o.M1 = add(o.M1, dw);
-    o.M2 = sub(o.M2, dw);
+  if (damp) {
+    // V_{2->1} = (v2 - Va) + (D2 - Da) x wa = (v2 - v1)/2 + (l e_a + do) x (w1 + w2)/4;
+    // F1 += c V_{2->1};  M1 += cr (w2 - wa) = cr/2 (w2 - w1);  M2 -= the same
+    V3f r = dO;
+    if (a == 0) r.x = add_(r.x, l); else if (a == 1) r.y = add_(r.y, l); else r.z = add_(r.z, l);
+    const V3f rw = cross3(r, add(s1.w, s2.w));
+    o.F1 = axpy(axpy(o.F1, k.c2, sub(s2.v, s1.v)), k.c4, rw);
+    const V3f dw = sub(s2.w, s1.w);
+    o.M1 = axpy(o.M1, k.cr2, dw);
+    o.M2 = axpy(o.M2, -k.cr2, dw);
   }
   return o;
 }
@@ -330,9 +388,11 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
       for (int c = 0; c < nc; ++c) {
         int j = cl[c];
         uint32_t lq = A.lat[j];
-        V3f dd = v3(fma_((float)((int)(lq & 2047u) - vi), l, sub_(A.st_in[OX * P + j], s.o.x)),
-                    fma_((float)((int)((lq >> 11) & 2047u) - vj), l, sub_(A.st_in[OY * P + j], s.o.y)),
-                    fma_((float)((int)(lq >> 22) - vk), l, sub_(A.st_in[OZ * P + j], s.o.z)));
+        const StPtr sp(const_cast<float*>(A.st_in), P);
+        const float4 ja = sp.A[j], jb = sp.B[j], jc = sp.C[j];
+        V3f dd = v3(fma_((float)((int)(lq & 2047u) - vi), l, sub_(ja.x, s.o.x)),
+                    fma_((float)((int)((lq >> 11) & 2047u) - vj), l, sub_(ja.y, s.o.y)),
+                    fma_((float)((int)(lq >> 22) - vk), l, sub_(ja.z, s.o.z)));
         float r2 = dot3(dd, dd);
         int mj = A.mat[j];
         const DevMat& dj = mats[mj];
@@ -345,7 +405,7 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
         float Ej = voxel_E(A, j, mj);
         float kc = mul_(__fdividef(mul_(mul_(2.f, Ev), Ej), add_(Ev, Ej)), l);
         F = axpy(F, -mul_(kc, sub_(cdist, r)), nh);
-        V3f vj = v3(A.st_in[VX * P + j], A.st_in[VY * P + j], A.st_in[VZ * P + j]);
+        V3f vj = v3(jb.w, jc.x, jc.y);
         float cc = mul_(mul_(2.f, A.zc), fsqrt(mul_(fminf(d.m, dj.m), kc)));
         F = axpy(F, mul_(cc, dot3(sub(vj, s.v), nh)), nh);
       }

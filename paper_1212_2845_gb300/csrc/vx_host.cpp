@@ -221,6 +221,18 @@ int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::
       len -= 32;
     }
   }
+  // fixed-stride tile blocks
+  T.halo_stride = local_max;
+  const int64_t nt = T.n_tiles();
+  T.tile_desc.assign(8 * (size_t)nt, 0);
+  T.halo_fixed.assign((size_t)nt * T.halo_stride, -1);
+  for (int64_t t = 0; t < nt; ++t) {
+    const int32_t* a = &T.tile_a[4 * t];
+    const int32_t* b = &T.tile_b[4 * t];
+    int32_t* d = &T.tile_desc[8 * t];
+    d[0] = a[0]; d[1] = a[1]; d[2] = a[3]; d[3] = b[0]; d[4] = b[1] - b[0];
+    for (int32_t j = 0; j < a[3]; ++j) T.halo_fixed[(size_t)t * T.halo_stride + j] = T.halo[a[2] + j];
+  }
   return VX_OK;
 }
 

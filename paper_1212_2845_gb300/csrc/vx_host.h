@@ -68,6 +68,12 @@ struct Tiling {
   std::vector<uint16_t> plus;    // 3 planes of N: staging slot of the +a neighbour, 0xFFFF if none
   std::vector<uint32_t> halo_bonds;  // slot of voxel 1 | slot of voxel 2 << 12 | axis << 24
   std::vector<uint8_t> mask;     // per internal voxel: bit 2a (-a) / 2a+1 (+a) bond exists
+  // Fixed-stride copies for the pipelined kernel: per tile 8 ints
+  // (v0, n_owned, n_halo, halo-bond start, n_halo_bonds, 0, 0, 0) and the
+  // tile's halo indices at halo_fixed[t * halo_stride + j].
+  int halo_stride = 0;
+  std::vector<int32_t> tile_desc;
+  std::vector<int32_t> halo_fixed;
   int64_t n_tiles() const { return (int64_t)tile_a.size() / 4; }
   int64_t n_tile_bonds() const;  // bonds evaluated over all tiles
 };

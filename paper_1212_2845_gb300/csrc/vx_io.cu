@@ -10,10 +10,10 @@ __global__ void pack_state(const float* __restrict__ st, int64_t P, int N, const
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   int64_t v = iperm[c];
-  if (off) for (int a = 0; a < 3; ++a) off[3 * (int64_t)c + a] = st[(OX + a) * P + v];
-  if (quat) for (int a = 0; a < 4; ++a) quat[4 * (int64_t)c + a] = st[(QW + a) * P + v];
-  if (vel) for (int a = 0; a < 3; ++a) vel[3 * (int64_t)c + a] = st[(VX + a) * P + v];
-  if (angvel) for (int a = 0; a < 3; ++a) angvel[3 * (int64_t)c + a] = st[(WX + a) * P + v];
+  if (off) for (int a = 0; a < 3; ++a) off[3 * (int64_t)c + a] = st[state_index(OX + a, v, P)];
+  if (quat) for (int a = 0; a < 4; ++a) quat[4 * (int64_t)c + a] = st[state_index(QW + a, v, P)];
+  if (vel) for (int a = 0; a < 3; ++a) vel[3 * (int64_t)c + a] = st[state_index(VX + a, v, P)];
+  if (angvel) for (int a = 0; a < 3; ++a) angvel[3 * (int64_t)c + a] = st[state_index(WX + a, v, P)];
   if (fl) fl[c] = flags[v];
 }
 
@@ -23,10 +23,10 @@ __global__ void unpack_state(float* __restrict__ st, int64_t P, int N, const int
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
   int64_t v = iperm[c];
-  if (off) for (int a = 0; a < 3; ++a) st[(OX + a) * P + v] = off[3 * (int64_t)c + a];
-  if (quat) for (int a = 0; a < 4; ++a) st[(QW + a) * P + v] = quat[4 * (int64_t)c + a];
-  if (vel) for (int a = 0; a < 3; ++a) st[(VX + a) * P + v] = vel[3 * (int64_t)c + a];
-  if (angvel) for (int a = 0; a < 3; ++a) st[(WX + a) * P + v] = angvel[3 * (int64_t)c + a];
+  if (off) for (int a = 0; a < 3; ++a) st[state_index(OX + a, v, P)] = off[3 * (int64_t)c + a];
+  if (quat) for (int a = 0; a < 4; ++a) st[state_index(QW + a, v, P)] = quat[4 * (int64_t)c + a];
+  if (vel) for (int a = 0; a < 3; ++a) st[state_index(VX + a, v, P)] = vel[3 * (int64_t)c + a];
+  if (angvel) for (int a = 0; a < 3; ++a) st[state_index(WX + a, v, P)] = angvel[3 * (int64_t)c + a];
   if (fl) flags[v] = fl[c];
 }
 
@@ -36,10 +36,12 @@ __global__ void reset_state(float* __restrict__ st, int64_t P, int N, uint8_t* _
   if (v >= N) return;
   bool fixed = flags[v] & 1u;
   flags[v] &= 1u;  // keep fixed, clear static friction
-  st[OX * P + v] = 0.f; st[OY * P + v] = 0.f; st[OZ * P + v] = 0.f;
-  st[QW * P + v] = 1.f; st[QX * P + v] = 0.f; st[QY * P + v] = 0.f; st[QZ * P + v] = 0.f;
-  st[VX * P + v] = fixed ? 0.f : vx; st[VY * P + v] = fixed ? 0.f : vy; st[VZ * P + v] = fixed ? 0.f : vz;
-  st[WX * P + v] = 0.f; st[WY * P + v] = 0.f; st[WZ * P + v] = 0.f;
+  VoxS s;
+  s.o = v3(0.f, 0.f, 0.f);
+  s.q.w = 1.f; s.q.x = 0.f; s.q.y = 0.f; s.q.z = 0.f;
+  s.v = fixed ? v3(0.f, 0.f, 0.f) : v3(vx, vy, vz);
+  s.w = v3(0.f, 0.f, 0.f);
+  store_vox(st, P, v, s);
 }
 
 void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* iperm, const uint8_t* flags,

@@ -13,9 +13,10 @@ struct CollideArgs {
   int H;                  // hash buckets (power of two)
   int K;                  // quantisation: offset * 2^K
   int64_t Q;              // quantisation: lattice step rint(l 2^K)
-  int64_t pitch;
+  int64_t ostride_v;      // offsets: component a of voxel v at st[v * ostride_v + a * ostride_a]
+  int64_t ostride_a;
   float threshold;        // horizon accumulator threshold [m]
-  const float* st;        // state planes (offsets used)
+  const float* st;        // offsets (see the strides)
   const int32_t* surf;    // surface voxel list (canonical, ascending)
   const uint32_t* lat;
   const int32_t* body;    // or nullptr
@@ -40,14 +41,19 @@ struct CollideArgs {
 // form 0: fused tile kernel (tile_max threads per CTA, smem bytes of dynamic
 // shared memory); form 1: two-pass bond_pass + voxel_pass.
 void launch_step(const StepArgs& A, int form, int tile_max, size_t smem, cudaStream_t s);
-size_t fused_smem_bytes(int tile_max, int n_mats);
+size_t fused_smem_bytes(int tile_max, int n_mats, bool lut);
 // Raises the fused kernel's dynamic shared memory limit; 0 on success.
 int prepare_fused(int tile_max, size_t smem);
+// Pipelined persistent form: shared memory for the optional per-voxel arrays
+// in use, kernel preparation (returns the persistent grid) and launch.
+size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, int n_mats, bool lut);
+int prepare_pipe(int tile_max, size_t smem, int* grid);
+void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);
 void launch_rebuild(const CollideArgs& C, cudaStream_t s);
 void launch_flag_all(const CollideArgs& C, cudaStream_t s);
 
-// planar internal-order state <-> interleaved canonical-order caller layout
+// internal-order device state <-> interleaved canonical-order caller layout
 // (offset[N][3], quat[N][4], vel[N][3], angvel[N][3], flags[N]); iperm maps
 // canonical to internal indices; any destination/source pointer may be null
 void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* iperm, const uint8_t* flags,

@@ -110,7 +110,8 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.n_bodies = n_bodies;
   C.H = H;
   quant_params(voxel_size, &C.K, &C.Q);
-  C.pitch = n_surface;                 // offset planes: x[S], y[S], z[S]
+  C.ostride_v = 1;                     // offset planes: x[S], y[S], z[S]
+  C.ostride_a = n_surface;
   C.threshold = 0.f;
   C.st = offset_planes;
   C.surf = reinterpret_cast<int32_t*>(base + kOffIota);  // identity: surface index = voxel index

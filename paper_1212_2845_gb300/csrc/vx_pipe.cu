@@ -1,0 +1,321 @@
+// Pipelined form of the fused step (same arithmetic, same bits).
+//
+// Persistent CTAs walk the tiles t = blockIdx.x, + gridDim.x, ...  While tile
+// t is computed, everything tile t + gridDim.x needs (state of its owned and
+// halo voxels, material words, bond partner slots, lattice coordinates, halo
+// bonds) streams into the other half of a double-buffered shared staging area
+// with cp.async, and the descriptor and halo indices of the tile after it are
+// already on their way into registers.  Tile descriptors and halo index lists
+// live at fixed strides so that both arrive in one round trip.
+#include "vx_dev.cuh"
+#include "vx_kernels.h"
+
+namespace vx {
+namespace {
+
+__device__ __forceinline__ uint32_t sptr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void cp16(void* d, const void* s) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sptr(d)), "l"(s) : "memory");
+}
+__device__ __forceinline__ void cp8(void* d, const void* s) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sptr(d)), "l"(s) : "memory");
+}
+__device__ __forceinline__ void cp4(void* d, const void* s) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sptr(d)), "l"(s) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+// Descriptor of a tile held in registers (h0, h1: halo voxels of list
+// positions threadIdx.x and threadIdx.x + TMAX).
+struct TileRegs {
+  int v0, T, nh, hb0, nhb, h0, h1;
+  bool valid;
+};
+
+template <int TMAX>
+__device__ __forceinline__ TileRegs load_tile(const StepArgs& A, int t) {
+  TileRegs r;
+  r.valid = t < A.n_tiles;
+  if (!r.valid) { r.v0 = r.T = r.nh = r.hb0 = r.nhb = 0; r.h0 = r.h1 = -1; return r; }
+  const int4 d = reinterpret_cast<const int4*>(A.tdesc)[2 * t];
+  const int b0 = reinterpret_cast<const int4*>(A.tdesc)[2 * t + 1].x;
+  const int32_t* hf = A.hfix + (int64_t)t * A.hstride;
+  r.v0 = d.x; r.T = d.y; r.nh = d.z; r.hb0 = d.w; r.nhb = b0;
+  r.h0 = hf[threadIdx.x];
+  r.h1 = threadIdx.x + TMAX < A.hstride ? hf[threadIdx.x + TMAX] : -1;
+  return r;
+}
+
+// Staging buffer of one tile (ML = 2 TMAX slots: owned first, then the halo).
+template <int TMAX> struct Stage {
+  static constexpr int ML = 2 * TMAX;
+  float4 *A, *B, *C;
+  float* D;
+  uint32_t* vw;    // material | bond mask << 8
+  float *ph, *le;  // phase, log E (null when unused)
+  uint2* pl;       // +x, +y, +z partner slots of owned voxels
+  uint32_t* lat;
+  int32_t* body;   // null for one body
+  float* fx;       // 3 x TMAX external force (null when unused)
+  uint32_t* hb;    // halo bonds
+  // floats this layout needs
+  static __host__ __device__ int floats(bool ph, bool le, bool body, bool fext) {
+    return 13 * ML + ML + (ph ? ML : 0) + (le ? ML : 0) + 2 * TMAX + TMAX + (body ? TMAX : 0) + (fext ? 3 * TMAX : 0) +
+           ML;
+  }
+  __device__ __forceinline__ void carve(float* base, bool hph, bool hle, bool hbody, bool hfext) {
+    A = reinterpret_cast<float4*>(base);
+    B = A + ML;
+    C = B + ML;
+    pl = reinterpret_cast<uint2*>(C + ML);
+    float* p = reinterpret_cast<float*>(pl + TMAX);
+    D = p; p += ML;
+    vw = reinterpret_cast<uint32_t*>(p); p += ML;
+    lat = reinterpret_cast<uint32_t*>(p); p += TMAX;
+    hb = reinterpret_cast<uint32_t*>(p); p += ML;
+    ph = hph ? p : nullptr; p += hph ? ML : 0;
+    le = hle ? p : nullptr; p += hle ? ML : 0;
+    body = hbody ? reinterpret_cast<int32_t*>(p) : nullptr; p += hbody ? TMAX : 0;
+    fx = hfext ? p : nullptr;
+  }
+  __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
+};
+
+template <int TMAX>
+__device__ __forceinline__ void stage_voxel(const StepArgs& A, const StPtr& G, const Stage<TMAX>& S, int k, int g) {
+  cp16(&S.A[k], &G.A[g]);
+  cp16(&S.B[k], &G.B[g]);
+  cp16(&S.C[k], &G.C[g]);
+  cp4(&S.D[k], &G.D[g]);
+  cp4(&S.vw[k], &A.vw[g]);
+  if (S.ph) cp4(&S.ph[k], &A.phase[g]);
+  if (S.le) cp4(&S.le[k], &A.logE[g]);
+}
+
+template <int TMAX>
+__device__ __forceinline__ void issue_tile(const StepArgs& A, const StPtr& G, const Stage<TMAX>& S, const TileRegs& r) {
+  const int i = threadIdx.x;
+  if (i < r.T) {
+    const int g = r.v0 + i;
+    stage_voxel<TMAX>(A, G, S, i, g);
+    cp8(&S.pl[i], &A.plus2[g]);
+    cp4(&S.lat[i], &A.lat[g]);
+    if (S.body) cp4(&S.body[i], &A.body[g]);
+    if (S.fx) {
+      cp4(&S.fx[i], &A.fext[g]);
+      cp4(&S.fx[TMAX + i], &A.fext[A.pitch + g]);
+      cp4(&S.fx[2 * TMAX + i], &A.fext[2 * A.pitch + g]);
+    }
+  }
+  if (i < r.nh) stage_voxel<TMAX>(A, G, S, r.T + i, r.h0);
+  if (i + TMAX < r.nh) stage_voxel<TMAX>(A, G, S, r.T + i + TMAX, r.h1);
+  if (i < r.nhb) cp4(&S.hb[i], &A.hbonds[r.hb0 + i]);
+  if (i + TMAX < r.nhb) cp4(&S.hb[i + TMAX], &A.hbonds[r.hb0 + i + TMAX]);
+}
+
+template <int TMAX, int a>
+__device__ __forceinline__ void minus_slot(float4* F4, float2* F2, int k, const BondOut& o) {
+  F4[a * TMAX + k] = make_float4(-o.F1.x, -o.F1.y, -o.F1.z, o.M2.x);
+  F2[a * TMAX + k] = make_float2(o.M2.y, o.M2.z);
+}
+
+__device__ __forceinline__ BondK pair_consts(const StepArgs& A, const float* lut, const DevMat* mats, float4 p1,
+                                             float4 p2) {
+  int m1 = __float_as_int(p1.w), m2 = __float_as_int(p2.w);
+  if (A.lut) return lut_consts(lut, A.n_mats, m1, m2);
+  return bond_consts(A.l, p1.x, p2.x, p1.y, p2.y, fminf(mats[m1].m, mats[m2].m), fminf(mats[m1].I, mats[m2].I), A.zb);
+}
+
+__device__ __forceinline__ float4 voxel_props(const StepArgs& A, const DevMat& d, int m, float ph, float le) {
+  float E = A.logE ? expf(le) : d.E;
+  float adT = 0.f;
+  if (A.act_on) {
+    float x = A.act_w + ph;
+    x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
+    adT = __fmul_rn(d.cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
+  }
+  return make_float4(E, __fmul_rn(E, d.g_ratio), adT, __int_as_float(m));
+}
+
+template <int TMAX, int a>
+__device__ __forceinline__ void halo_bond_p(const StepArgs& A, const Stage<TMAX>& S, const float4* props,
+                                            const float* lut, const DevMat* mats, float4* F4, float2* F2, int s1,
+                                            int s2) {
+  VoxS v1 = S.vox(s1), v2 = S.vox(s2);
+  float4 p1 = props[s1], p2 = props[s2];
+  BondK k = pair_consts(A, lut, mats, p1, p2);
+  BondOut o = bond_eval<a>(v1, qmat(v1.q), v2, A.l, k, mul_(0.5f, add_(p1.z, p2.z)), A.zb != 0.f);
+  minus_slot<TMAX, a>(F4, F2, s2, o);
+}
+
+}  // namespace
+
+template <int TMAX> struct PipeSmem {
+  static constexpr int ML = 2 * TMAX;
+  static size_t bytes(bool ph, bool le, bool body, bool fext, int n_mats, bool lut) {
+    size_t f = 2 * (size_t)Stage<TMAX>::floats(ph, le, body, fext) + 4 * ML + 18 * TMAX;
+    return f * sizeof(float) + (size_t)n_mats * sizeof(DevMat) + (lut ? (size_t)8 * n_mats * n_mats * 4 : 0);
+  }
+};
+
+template <int TMAX>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs A) {
+  constexpr int ML = 2 * TMAX;
+  extern __shared__ __align__(16) float smem[];
+  const bool hph = A.phase != nullptr, hle = A.logE != nullptr, hbody = A.body != nullptr, hfx = A.fext != nullptr;
+  const int sf = Stage<TMAX>::floats(hph, hle, hbody, hfx);
+  float4* props = reinterpret_cast<float4*>(smem + 2 * sf);
+  float4* F4 = props + ML;
+  float2* F2 = reinterpret_cast<float2*>(F4 + 3 * TMAX);
+  DevMat* mats = reinterpret_cast<DevMat*>(F2 + 3 * TMAX);
+  float* lut = reinterpret_cast<float*>(mats + A.n_mats);
+  const int i = threadIdx.x;
+  const int Gs = gridDim.x;
+  int t = blockIdx.x;
+  if (t >= A.n_tiles) return;  // uniform over the CTA
+  for (int j = i; j < A.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
+    reinterpret_cast<float*>(mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
+  if (A.lut)
+    for (int j = i; j < 8 * A.n_mats * A.n_mats; j += TMAX) lut[j] = A.lut[j];
+  const StPtr G(const_cast<float*>(A.st_in), A.pitch);
+  // prologue: stage the first tile, fetch the next descriptor
+  TileRegs cur = load_tile<TMAX>(A, t);
+  {
+    Stage<TMAX> S0;
+    S0.carve(smem, hph, hle, hbody, hfx);
+    issue_tile<TMAX>(A, G, S0, cur);
+  }
+  cp_commit();
+  uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
+  TileRegs nxt = load_tile<TMAX>(A, t + Gs);
+  int b = 0;
+  for (;;) {
+    Stage<TMAX> S;
+    S.carve(smem + b * sf, hph, hle, hbody, hfx);
+    // 1. stream the next tile into the other buffer; its flags into a register
+    uint8_t fl_nxt = 0;
+    if (nxt.valid) {
+      Stage<TMAX> Sn;
+      Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx);
+      issue_tile<TMAX>(A, G, Sn, nxt);
+      fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
+    }
+    cp_commit();
+    // 2. descriptor and halo indices of the tile after it
+    const TileRegs nn = load_tile<TMAX>(A, t + 2 * Gs);
+    // 3. this tile has landed
+    cp_wait1();
+    __syncthreads();
+    const int T = cur.T;
+    const bool own = i < T;
+    if (own) {
+      uint32_t w = S.vw[i];
+      props[i] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[i] : 0.f, S.le ? S.le[i] : 0.f);
+    }
+    for (int j = i; j < cur.nh; j += TMAX) {
+      const int k = T + j;
+      uint32_t w = S.vw[k];
+      props[k] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[k] : 0.f, S.le ? S.le[k] : 0.f);
+    }
+    __syncthreads();
+    // 4. own +x, +y, +z bonds; halo bonds
+    V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
+    VoxS s;
+    float4 pr;
+    uint32_t w0 = 0;
+    if (own) {
+      s = S.vox(i);
+      pr = props[i];
+      w0 = S.vw[i];
+      const uint2 pl = S.pl[i];
+      const int px = (int)(pl.x & 0xFFFFu), py = (int)(pl.x >> 16), pz = (int)(pl.y & 0xFFFFu);
+      const M3f R1 = qmat(s.q);
+      const bool damp = A.zb != 0.f;
+#define VX_PLUS_BOND(AX, P2)                                                                               \
+      if (P2 != 0xFFFF) {                                                                                  \
+        const VoxS v2 = S.vox(P2);                                                                         \
+        const float4 q2 = props[P2];                                                                       \
+        const BondK k = pair_consts(A, lut, mats, pr, q2);                                                 \
+        BondOut o = bond_eval<AX>(s, R1, v2, A.l, k, mul_(0.5f, add_(pr.z, q2.z)), damp);                   \
+        F = add(F, o.F1);                                                                                  \
+        M = add(M, o.M1);                                                                                  \
+        if (P2 < T) minus_slot<TMAX, AX>(F4, F2, P2, o);                                                   \
+      }
+      VX_PLUS_BOND(0, px)
+      VX_PLUS_BOND(1, py)
+      VX_PLUS_BOND(2, pz)
+#undef VX_PLUS_BOND
+    }
+    for (int j = i; j < cur.nhb; j += TMAX) {
+      const uint32_t pk = S.hb[j];
+      const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
+      if (ax == 0) halo_bond_p<TMAX, 0>(A, S, props, lut, mats, F4, F2, s1, s2);
+      else if (ax == 1) halo_bond_p<TMAX, 1>(A, S, props, lut, mats, F4, F2, s1, s2);
+      else halo_bond_p<TMAX, 2>(A, S, props, lut, mats, F4, F2, s1, s2);
+    }
+    __syncthreads();
+    // 5. gather the -x, -y, -z results and integrate
+    float speed = 0.f;
+    int body = 0;
+    if (own) {
+      const uint32_t mask = (w0 >> 8) & 63u;
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+        if (mask & (1u << (2 * a))) {
+          const float4 f = F4[a * TMAX + i];
+          const float2 g = F2[a * TMAX + i];
+          F = add(F, v3(f.x, f.y, f.z));
+          M = add(M, v3(f.w, g.x, g.y));
+        }
+      VoxMeta mt;
+      mt.lat = S.lat[i];
+      mt.m = (int)(w0 & 255u);
+      mt.b = S.body ? S.body[i] : 0;
+      mt.fl = fl_cur;
+      mt.dt = A.dt_body[mt.b];
+      mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
+      mt.fext = S.fx ? v3(S.fx[i], S.fx[TMAX + i], S.fx[2 * TMAX + i]) : v3(0.f, 0.f, 0.f);
+      body = mt.b;
+      speed = voxel_finish(A, cur.v0 + i, mt, s, F, M, pr.z, pr.x, mats);
+    }
+    if (A.collide_on) horizon_max(A, body, own, speed);
+    if (!nxt.valid) break;  // uniform
+    __syncthreads();        // buffer b and the shared results are reused
+    cur = nxt;
+    nxt = nn;
+    fl_cur = fl_nxt;
+    t += Gs;
+    b ^= 1;
+  }
+}
+
+size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, int n_mats, bool lut) {
+  if (tile_max == 128) return PipeSmem<128>::bytes(ph, le, body, fext, n_mats, lut);
+  return PipeSmem<256>::bytes(ph, le, body, fext, n_mats, lut);
+}
+
+int prepare_pipe(int tile_max, size_t smem, int* grid) {
+  int per_sm = 0, dev = 0, n_sm = 0;
+  cudaError_t e;
+  if (tile_max == 128) {
+    e = cudaFuncSetAttribute(fused_pipe<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pipe<128>, 128, smem);
+  } else {
+    e = cudaFuncSetAttribute(fused_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pipe<256>, 256, smem);
+  }
+  if (e != cudaSuccess || per_sm < 1) return -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1;
+  *grid = per_sm * n_sm;
+  return 0;
+}
+
+void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {
+  int g = grid < A.n_tiles ? grid : A.n_tiles;
+  if (tile_max == 128) fused_pipe<128><<<g, 128, smem, s>>>(A);
+  else fused_pipe<256><<<g, 256, smem, s>>>(A);
+}
+
+}  // namespace vx

@@ -29,11 +29,16 @@ __device__ __forceinline__ void bond_pass_axis(const StepArgs& A, int v) {
   int m1 = A.mat[v], m2 = A.mat[u];
   const DevMat& d1 = A.mats[m1];
   const DevMat& d2 = A.mats[m2];
-  float E1 = voxel_E(A, v, m1), E2 = voxel_E(A, u, m2);
+  BondK k;
+  if (A.lut) {
+    k = lut_consts(A.lut, A.n_mats, m1, m2);
+  } else {
+    float E1 = voxel_E(A, v, m1), E2 = voxel_E(A, u, m2);
+    k = bond_consts(A.l, E1, E2, __fmul_rn(E1, d1.g_ratio), __fmul_rn(E2, d2.g_ratio), fminf(d1.m, d2.m),
+                    fminf(d1.I, d2.I), A.zb);
+  }
   float eps = mul_(0.5f, add_(thermal_strain(A, v, d1.cte), thermal_strain(A, u, d2.cte)));
-  M3f R1 = qmat(s1.q);
-  BondOut o = bond_eval<a>(s1, R1, s2, A.l, E1, E2, __fmul_rn(E1, d1.g_ratio), __fmul_rn(E2, d2.g_ratio),
-                           fminf(d1.m, d2.m), fminf(d1.I, d2.I), eps, A.zb);
+  BondOut o = bond_eval<a>(s1, qmat(s1.q), s2, A.l, k, eps, A.zb != 0.f);
   float* bf = A.bf + (int64_t)a * P + v;
   const int64_t C = 3 * P;
   bf[0 * C] = o.F1.x; bf[1 * C] = o.F1.y; bf[2 * C] = o.F1.z;
@@ -92,94 +97,103 @@ __global__ void __launch_bounds__(256) voxel_pass(StepArgs A) {
 // indices), so the bond and voxel phases run on shared memory and registers
 // only and the SM overlaps one CTA's staging with the others' arithmetic.
 // Shared memory, ML = 2 TMAX staged voxels (owned first, then the halo):
-//   st[13][ML]                      staged state
-//   E, G, adT, m, I [ML]            modulus, shear modulus, thermal strain, mass, inertia
-//   slot[3 axes][6][TMAX]           result of the bond on each owned voxel's
-//                                   -a side: (-F1, M2)
-//   hb[ML]                          the tile's halo bonds
-//   mats[n_mat]                     material table
+//   state: A, B, C float4 [ML], D float [ML]   (same planes as in HBM)
+//   props float4 [ML]: E, G, thermal strain, material index (bits)
+//   slot F4 float4 [3][TMAX], slot F2 float2 [3][TMAX]: the result of the bond
+//        on each owned voxel's -a side: (-F1, M2.x) and (M2.y, M2.z)
+//   hb uint32 [ML]: the tile's halo bonds
+//   lut float [8 n_mats^2] (when set), mats DevMat [n_mats]
+#ifndef VX_CTAS_256
+#define VX_CTAS_256 3  // resident CTAs per SM of fused_step<256> (registers <= 85)
+#endif
+
 template <int TMAX> struct FusedSmem {
   static constexpr int ML = 2 * TMAX;
-  static constexpr int kFloats = (NPLANE + 6) * ML + 18 * TMAX;
-  static size_t bytes(int n_mat) { return kFloats * sizeof(float) + (size_t)n_mat * sizeof(DevMat); }
+  static constexpr int kFloats = (NPLANE + 4 + 1) * ML + 18 * TMAX;
+  static size_t bytes(int n_mats, bool lut) {
+    return kFloats * sizeof(float) + (lut ? (size_t)8 * n_mats * n_mats * sizeof(float) : 0) +
+           (size_t)n_mats * sizeof(DevMat);
+  }
 };
 
+template <int TMAX> struct Smem {
+  float4 *A, *B, *C, *props, *slotF4;
+  float *D, *lut;
+  float2* slotF2;
+  uint32_t* hb;
+  DevMat* mats;
+  __device__ __forceinline__ Smem(float* base, int n_mats, bool has_lut) {
+    constexpr int ML = FusedSmem<TMAX>::ML;
+    A = reinterpret_cast<float4*>(base);
+    B = A + ML;
+    C = B + ML;
+    props = C + ML;
+    slotF4 = props + ML;
+    slotF2 = reinterpret_cast<float2*>(slotF4 + 3 * TMAX);
+    D = reinterpret_cast<float*>(slotF2 + 3 * TMAX);
+    hb = reinterpret_cast<uint32_t*>(D + ML);
+    lut = reinterpret_cast<float*>(hb + ML);
+    mats = reinterpret_cast<DevMat*>(lut + (has_lut ? 8 * n_mats * n_mats : 0));
+  }
+  __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
+};
+
+template <int TMAX, int a>
+__device__ __forceinline__ void store_minus_slot(const Smem<TMAX>& S, int k, const BondOut& o) {
+  S.slotF4[a * TMAX + k] = make_float4(-o.F1.x, -o.F1.y, -o.F1.z, o.M2.x);
+  S.slotF2[a * TMAX + k] = make_float2(o.M2.y, o.M2.z);
+}
+
+// Constants of the bond between staged voxels k1 and k2.
 template <int TMAX>
-__device__ __forceinline__ VoxS smem_vox(const float* s_st, int k) {
-  constexpr int ML = FusedSmem<TMAX>::ML;
-  VoxS v;
-  v.o = v3(s_st[OX * ML + k], s_st[OY * ML + k], s_st[OZ * ML + k]);
-  v.q.w = s_st[QW * ML + k]; v.q.x = s_st[QX * ML + k]; v.q.y = s_st[QY * ML + k]; v.q.z = s_st[QZ * ML + k];
-  v.v = v3(s_st[VX * ML + k], s_st[VY * ML + k], s_st[VZ * ML + k]);
-  v.w = v3(s_st[WX * ML + k], s_st[WY * ML + k], s_st[WZ * ML + k]);
-  return v;
+__device__ __forceinline__ BondK staged_consts(const StepArgs& A, const Smem<TMAX>& S, float4 p1, float4 p2) {
+  int m1 = __float_as_int(p1.w), m2 = __float_as_int(p2.w);
+  if (A.lut) return lut_consts(S.lut, A.n_mats, m1, m2);
+  const DevMat& d1 = S.mats[m1];
+  const DevMat& d2 = S.mats[m2];
+  return bond_consts(A.l, p1.x, p2.x, p1.y, p2.y, fminf(d1.m, d2.m), fminf(d1.I, d2.I), A.zb);
 }
 
 template <int TMAX, int a>
-__device__ __forceinline__ void store_minus_slot(float* s_slot, int k, const BondOut& o) {
-  float* sl = s_slot + a * 6 * TMAX + k;
-  sl[0] = -o.F1.x; sl[TMAX] = -o.F1.y; sl[2 * TMAX] = -o.F1.z;
-  sl[3 * TMAX] = o.M2.x; sl[4 * TMAX] = o.M2.y; sl[5 * TMAX] = o.M2.z;
+__device__ __forceinline__ void halo_bond(const StepArgs& A, const Smem<TMAX>& S, int s1, int s2) {
+  VoxS v1 = S.vox(s1), v2 = S.vox(s2);
+  float4 p1 = S.props[s1], p2 = S.props[s2];
+  BondK k = staged_consts<TMAX>(A, S, p1, p2);
+  BondOut o = bond_eval<a>(v1, qmat(v1.q), v2, A.l, k, mul_(0.5f, add_(p1.z, p2.z)), A.zb != 0.f);
+  store_minus_slot<TMAX, a>(S, s2, o);
 }
 
-template <int TMAX, int a>
-__device__ __forceinline__ void halo_bond(const StepArgs& A, const float* s_st, const float* s_E, const float* s_G,
-                                          const float* s_adT, const float* s_m, const float* s_I, float* s_slot,
-                                          int s1, int s2) {
-  VoxS v1 = smem_vox<TMAX>(s_st, s1), v2 = smem_vox<TMAX>(s_st, s2);
-  M3f R1 = qmat(v1.q);
-  BondOut o = bond_eval<a>(v1, R1, v2, A.l, s_E[s1], s_E[s2], s_G[s1], s_G[s2], fminf(s_m[s1], s_m[s2]),
-                           fminf(s_I[s1], s_I[s2]), mul_(0.5f, add_(s_adT[s1], s_adT[s2])), A.zb);
-  store_minus_slot<TMAX, a>(s_slot, s2, o);
-}
-
-// Material-dependent values of one staged voxel.
-__device__ __forceinline__ void slot_props(const StepArgs& A, const DevMat& d, float ph, float le, int k,
-                                           float* s_E, float* s_G, float* s_adT, float* s_m, float* s_I) {
+// Material-dependent values of one staged voxel: E, G, thermal strain, material.
+__device__ __forceinline__ float4 slot_props(const StepArgs& A, const DevMat& d, int m, float ph, float le) {
   float E = A.logE ? expf(le) : d.E;
-  s_E[k] = E;
-  s_G[k] = __fmul_rn(E, d.g_ratio);
   float adT = 0.f;
   if (A.act_on) {
     float x = A.act_w + ph;
     x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
     adT = __fmul_rn(d.cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
   }
-  s_adT[k] = adT;
-  s_m[k] = d.m;
-  s_I[k] = d.I;
+  return make_float4(E, __fmul_rn(E, d.g_ratio), adT, __int_as_float(m));
 }
 
 template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 3 : 6)) fused_step(StepArgs A) {
-  constexpr int ML = FusedSmem<TMAX>::ML;
-  extern __shared__ float smem[];
-  float* s_st = smem;
-  float* s_E = s_st + NPLANE * ML;
-  float* s_G = s_E + ML;
-  float* s_adT = s_G + ML;
-  float* s_m = s_adT + ML;
-  float* s_I = s_m + ML;
-  float* s_slot = s_I + ML;
-  uint32_t* s_hb = reinterpret_cast<uint32_t*>(s_slot + 18 * TMAX);
-  DevMat* s_mats = reinterpret_cast<DevMat*>(s_hb + ML);
+__global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? VX_CTAS_256 : 8)) fused_step(StepArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  const Smem<TMAX> S(smem, A.n_mats, A.lut != nullptr);
   const int i = threadIdx.x;
   const int4 ta = A.tile_a[blockIdx.x];
   const int4 tb = A.tile_b[blockIdx.x];
   const int v0 = ta.x, T = ta.y, NL = ta.y + ta.w, nhb = tb.y - tb.x;
-  const int P = (int)A.pitch;
   const bool own = i < T;
   const int v = v0 + i;
+  const StPtr G(const_cast<float*>(A.st_in), A.pitch);
   // ---- staging: every global read of the step, issued back to back
   const int k1 = i + TMAX;
   const int g0 = own ? v : (i < NL ? A.halo[ta.z + i - T] : -1);
   const int g1 = k1 < NL ? (k1 < T ? v0 + k1 : A.halo[ta.z + k1 - T]) : -1;
-  float r0[NPLANE], r1[NPLANE];
-#pragma unroll
-  for (int p = 0; p < NPLANE; ++p) {
-    r0[p] = g0 >= 0 ? A.st_in[g0 + p * P] : 0.f;
-    r1[p] = g1 >= 0 ? A.st_in[g1 + p * P] : 0.f;
-  }
+  float4 a0, b0, c0, a1, b1, c1;
+  float d0, d1;
+  if (g0 >= 0) { a0 = G.A[g0]; b0 = G.B[g0]; c0 = G.C[g0]; d0 = G.D[g0]; }
+  if (g1 >= 0) { a1 = G.A[g1]; b1 = G.B[g1]; c1 = G.C[g1]; d1 = G.D[g1]; }
   const int m0 = g0 >= 0 ? A.mat[g0] : 0, m1 = g1 >= 0 ? A.mat[g1] : 0;
   const float ph0 = (g0 >= 0 && A.phase) ? A.phase[g0] : 0.f, ph1 = (g1 >= 0 && A.phase) ? A.phase[g1] : 0.f;
   const float le0 = (g0 >= 0 && A.logE) ? A.logE[g0] : 0.f, le1 = (g1 >= 0 && A.logE) ? A.logE[g1] : 0.f;
@@ -191,33 +205,35 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 3 : 6))
     mask = A.mask[v];
     mt = load_meta(A, v);
   }
-  for (int j = i; j < nhb; j += TMAX) s_hb[j] = A.hbonds[tb.x + j];
+  for (int j = i; j < nhb; j += TMAX) S.hb[j] = A.hbonds[tb.x + j];
   for (int j = i; j < A.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
-    reinterpret_cast<float*>(s_mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
-#pragma unroll
-  for (int p = 0; p < NPLANE; ++p) {
-    if (g0 >= 0) s_st[p * ML + i] = r0[p];
-    if (g1 >= 0) s_st[p * ML + k1] = r1[p];
-  }
+    reinterpret_cast<float*>(S.mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
+  if (A.lut)
+    for (int j = i; j < 8 * A.n_mats * A.n_mats; j += TMAX) S.lut[j] = A.lut[j];
+  if (g0 >= 0) { S.A[i] = a0; S.B[i] = b0; S.C[i] = c0; S.D[i] = d0; }
+  if (g1 >= 0) { S.A[k1] = a1; S.B[k1] = b1; S.C[k1] = c1; S.D[k1] = d1; }
   __syncthreads();
-  if (g0 >= 0) slot_props(A, s_mats[m0], ph0, le0, i, s_E, s_G, s_adT, s_m, s_I);
-  if (g1 >= 0) slot_props(A, s_mats[m1], ph1, le1, k1, s_E, s_G, s_adT, s_m, s_I);
+  if (g0 >= 0) S.props[i] = slot_props(A, S.mats[m0], m0, ph0, le0);
+  if (g1 >= 0) S.props[k1] = slot_props(A, S.mats[m1], m1, ph1, le1);
   __syncthreads();
   // ---- bonds: this voxel's own +x, +y, +z bonds, state and rotation loaded once
   V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
   VoxS s;
+  float4 pr;
   if (own) {
-    s = smem_vox<TMAX>(s_st, i);
-    M3f R1 = qmat(s.q);
-    float E1 = s_E[i], G1 = s_G[i], adT1 = s_adT[i], mm1 = s_m[i], I1 = s_I[i];
+    s = S.vox(i);
+    pr = S.props[i];
+    const M3f R1 = qmat(s.q);
+    const bool damp = A.zb != 0.f;
 #define VX_PLUS_BOND(AX, P2)                                                                               \
     if (P2 != 0xFFFF) {                                                                                    \
-      VoxS v2 = smem_vox<TMAX>(s_st, P2);                                                                  \
-      BondOut o = bond_eval<AX>(s, R1, v2, A.l, E1, s_E[P2], G1, s_G[P2], fminf(mm1, s_m[P2]),             \
-                                fminf(I1, s_I[P2]), mul_(0.5f, add_(adT1, s_adT[P2])), A.zb);            \
+      const VoxS v2 = S.vox(P2);                                                                           \
+      const float4 q2 = S.props[P2];                                                                       \
+      const BondK k = staged_consts<TMAX>(A, S, pr, q2);                                                   \
+      BondOut o = bond_eval<AX>(s, R1, v2, A.l, k, mul_(0.5f, add_(pr.z, q2.z)), damp);                     \
       F = add(F, o.F1);                                                                                    \
       M = add(M, o.M1);                                                                                    \
-      if (P2 < T) store_minus_slot<TMAX, AX>(s_slot, P2, o);                                               \
+      if (P2 < T) store_minus_slot<TMAX, AX>(S, P2, o);                                                    \
     }
     VX_PLUS_BOND(0, px)
     VX_PLUS_BOND(1, py)
@@ -226,11 +242,11 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 3 : 6))
   }
   // bonds whose negative-side voxel is in the halo
   for (int j = i; j < nhb; j += TMAX) {
-    uint32_t pk = s_hb[j];
+    uint32_t pk = S.hb[j];
     int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
-    if (ax == 0) halo_bond<TMAX, 0>(A, s_st, s_E, s_G, s_adT, s_m, s_I, s_slot, s1, s2);
-    else if (ax == 1) halo_bond<TMAX, 1>(A, s_st, s_E, s_G, s_adT, s_m, s_I, s_slot, s1, s2);
-    else halo_bond<TMAX, 2>(A, s_st, s_E, s_G, s_adT, s_m, s_I, s_slot, s1, s2);
+    if (ax == 0) halo_bond<TMAX, 0>(A, S, s1, s2);
+    else if (ax == 1) halo_bond<TMAX, 1>(A, S, s1, s2);
+    else halo_bond<TMAX, 2>(A, S, s1, s2);
   }
   __syncthreads();
   // ---- gather the -x, -y, -z results and integrate
@@ -239,27 +255,33 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 3 : 6))
 #pragma unroll
     for (int a = 0; a < 3; ++a)
       if (mask & (1u << (2 * a))) {
-        const float* sl = s_slot + a * 6 * TMAX + i;
-        F = add(F, v3(sl[0], sl[TMAX], sl[2 * TMAX]));
-        M = add(M, v3(sl[3 * TMAX], sl[4 * TMAX], sl[5 * TMAX]));
+        const float4 f = S.slotF4[a * TMAX + i];
+        const float2 g = S.slotF2[a * TMAX + i];
+        F = add(F, v3(f.x, f.y, f.z));
+        M = add(M, v3(f.w, g.x, g.y));
       }
-    speed = voxel_finish(A, v, mt, s, F, M, s_adT[i], s_E[i], s_mats);
+    speed = voxel_finish(A, v, mt, s, F, M, pr.z, pr.x, S.mats);
   }
   if (A.collide_on) horizon_max(A, own ? mt.b : 0, own, speed);
 }
 
-size_t fused_smem_bytes(int tile_max, int n_mats) {
-  if (tile_max == 128) return FusedSmem<128>::bytes(n_mats);
-  if (tile_max == 256) return FusedSmem<256>::bytes(n_mats);
-  return FusedSmem<512>::bytes(n_mats);
+size_t fused_smem_bytes(int tile_max, int n_mats, bool lut) {
+  if (tile_max == 128) return FusedSmem<128>::bytes(n_mats, lut);
+  if (tile_max == 256) return FusedSmem<256>::bytes(n_mats, lut);
+  return FusedSmem<512>::bytes(n_mats, lut);
+}
+
+template <int TMAX> int prepare_one(size_t smem) {
+  if (cudaFuncSetAttribute(fused_step<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return -1;
+  return 0;
 }
 
 int prepare_fused(int tile_max, size_t smem) {
-  cudaError_t e = cudaErrorInvalidValue;
-  if (tile_max == 256) e = cudaFuncSetAttribute(fused_step<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else if (tile_max == 128) e = cudaFuncSetAttribute(fused_step<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else if (tile_max == 512) e = cudaFuncSetAttribute(fused_step<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  return e == cudaSuccess ? 0 : -1;
+  if (tile_max == 256) return prepare_one<256>(smem);
+  if (tile_max == 128) return prepare_one<128>(smem);
+  if (tile_max == 512) return prepare_one<512>(smem);
+  return -1;
 }
 
 void launch_step(const StepArgs& A, int form, int tile_max, size_t smem, cudaStream_t s) {

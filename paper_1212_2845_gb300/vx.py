@@ -178,6 +178,7 @@ def plan_tiles(sc, tile_max=256):
 
 FORM_FUSED = 0
 FORM_TWO_PASS = 1
+FORM_PIPELINED = 2
 
 
 def region_mask(sc, body, loc, size):

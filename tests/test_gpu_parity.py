@@ -342,7 +342,7 @@ def run_form(vx, sc, steps, form, tile_max=0):
 def test_fused_tile_sizes_bitwise_and_two_pass_close(vx, which):
     """Every operation of the step is an explicitly rounded intrinsic, so the
     fused kernel gives the same bits for every tile size and the two-pass form
-    gives the same bits as the fused one."""
+    gives the same bits as the fused one, as does the pipelined form."""
     if which == "hetero":
         sc, steps = scenes.hetero_block(dims=(20, 17, 9), seed=3), 300
     elif which == "ball":
@@ -354,6 +354,7 @@ def test_fused_tile_sizes_bitwise_and_two_pass_close(vx, which):
         out = run_form(vx, sc, steps, vx.FORM_FUSED, tm)
         for k in ("offset", "quat", "vel", "angvel", "flags"):
             assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), (tm, k)
-    two = run_form(vx, sc, steps, vx.FORM_TWO_PASS)
-    for k in ("offset", "quat", "vel", "angvel", "flags"):
-        assert np.array_equal(two[k].view(np.uint8), ref[k].view(np.uint8)), ("two-pass", k)
+    for form, tm in ((vx.FORM_TWO_PASS, 0), (vx.FORM_PIPELINED, 256), (vx.FORM_PIPELINED, 128)):
+        other = run_form(vx, sc, steps, form, tm)
+        for k in ("offset", "quat", "vel", "angvel", "flags"):
+            assert np.array_equal(other[k].view(np.uint8), ref[k].view(np.uint8)), (form, tm, k)
