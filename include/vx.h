@@ -145,12 +145,12 @@ VX_API int vx_get_counts(vx_sim* sim, int64_t* n_voxels, int64_t* n_bonds, int64
 /* Lattice anchors (rest centres) [N][3] in double precision, host memory. */
 VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
 
-/* Kernel form of the step.  VX_FORM_FUSED (default): one kernel per step,
+/* Kernel form of the step.  VX_FORM_FUSED: one kernel per step,
  * one CTA per tile, bond forces kept in shared memory.  VX_FORM_TWO_PASS: a
  * bond kernel writes every bond's forces to device memory and a voxel kernel
- * gathers them.  VX_FORM_PIPELINED: the fused step with persistent CTAs that
- * stream the next tile into shared memory (cp.async) while computing the
- * current one.  All forms compute the same arithmetic and give
+ * gathers them.  VX_FORM_PIPELINED (default): the fused step with persistent
+ * CTAs that stream the next tile into shared memory (cp.async) while
+ * computing the current one.  All forms compute the same arithmetic and give
  * bitwise-identical states.  tile_max (fused forms): 128, 256 or 512 voxels
  * per tile (pipelined: 128 or 256), 0 keeps the current size (256 at create).
  * The state is kept. */

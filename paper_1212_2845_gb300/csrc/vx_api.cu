@@ -55,7 +55,7 @@ struct vx_sim {
   Tiling T;
   int device = 0;
   int64_t pitch = 0;
-  int form = 0;            // 0 fused, 1 two-pass
+  int form = VX_FORM_PIPELINED;
   int tile_max = 256;
   size_t smem = 0;
   int cur = 0;             // index of the buffer holding the current state
