@@ -158,6 +158,15 @@ VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
 #define VX_FORM_TWO_PASS 1
 #define VX_FORM_PIPELINED 2
 VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
+/* Batched form for many independent bodies (SURVEY: thousands of bodies of
+ * uneven size, as in design automation).  group_voxels > 0: consecutive
+ * bodies are grouped to about that many voxels and spread over persistent
+ * CTAs (largest first onto the least loaded); vx_step / vx_step_async then
+ * run all n steps in ONE launch, each CTA stepping one group at a time with
+ * a barrier between steps so the group's state stays in L2.  Same arithmetic
+ * and bits as the per-step forms.  Ignored while self-collision is on.
+ * 0 turns it off.  Needs a fused form with tiles of 128 or 256. */
+VX_API int vx_set_batching(vx_sim* sim, int64_t group_voxels);
 /* Current tiling: tile size, tile count, largest staged set, dynamic shared
  * memory of the fused kernel in bytes.  Any output may be NULL. */
 VX_API int vx_get_tiling(vx_sim* sim, int32_t* tile_max, int64_t* n_tiles, int32_t* max_local, int64_t* smem_bytes);

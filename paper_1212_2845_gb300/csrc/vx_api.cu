@@ -86,6 +86,13 @@ struct vx_sim {
   uint2* plus2 = nullptr;
   size_t pipe_smem = 0;
   int pipe_grid = 0;
+  // batched form
+  int64_t group_voxels = 0;   // 0: off
+  Batch B;
+  int32_t* b_cta_start = nullptr;
+  int32_t* b_cta_groups = nullptr;
+  int32_t* b_group_tiles = nullptr;
+  size_t batch_smem = 0;
   uint8_t* mask = nullptr;
   uint8_t* flags = nullptr;
   uint8_t* mat = nullptr;
@@ -388,6 +395,20 @@ int upload_tiling(vx_sim* s) {
   return VX_OK;
 }
 
+// Shared memory of the pipelined kernels for the optional arrays in use;
+// (re)prepares the persistent kernel when it changes.
+int ensure_pipe(vx_sim* s, const StepArgs& A) {
+  int nm = (int)s->L.palette.size();
+  size_t sm = pipe_smem_bytes(s->tile_max, A.phase != nullptr, A.logE != nullptr, A.body != nullptr,
+                              A.fext != nullptr, nm, nm <= kLutMaxMats);
+  if (sm != s->pipe_smem) {
+    if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0 || prepare_batched(s->tile_max, sm) != 0)
+      return fail(VX_ERR_CUDA, "pipelined kernels need " + std::to_string(sm) + " bytes of shared memory");
+    s->pipe_smem = sm;
+  }
+  return VX_OK;
+}
+
 int ensure_two_pass(vx_sim* s) {
   if (s->bf) return VX_OK;
   int64_t N = s->L.N;
@@ -402,6 +423,42 @@ int ensure_two_pass(vx_sim* s) {
   VX_CUDA(cudaMemcpy(s->nbr, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemset(s->bf, 0, sizeof(float) * 27 * s->pitch));
   return VX_OK;
+}
+
+// Group schedule of the batched form for the current tiling and grid.
+int build_schedule(vx_sim* s) {
+  std::vector<int64_t> starts = batch_group_starts(s->L, s->group_voxels);
+  build_batch(s->T, starts, s->L.N, s->pipe_grid, s->B);
+  dfree(s->b_cta_start); dfree(s->b_cta_groups); dfree(s->b_group_tiles);
+  int rc;
+  if ((rc = dalloc(&s->b_cta_start, s->B.cta_start.size())) ||
+      (rc = dalloc(&s->b_cta_groups, std::max<size_t>(1, s->B.cta_groups.size()))) ||
+      (rc = dalloc(&s->b_group_tiles, s->B.group_tiles.size())))
+    return rc;
+  VX_CUDA(cudaMemcpy(s->b_cta_start, s->B.cta_start.data(), s->B.cta_start.size() * 4, cudaMemcpyHostToDevice));
+  if (!s->B.cta_groups.empty())
+    VX_CUDA(cudaMemcpy(s->b_cta_groups, s->B.cta_groups.data(), s->B.cta_groups.size() * 4, cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemcpy(s->b_group_tiles, s->B.group_tiles.data(), s->B.group_tiles.size() * 4, cudaMemcpyHostToDevice));
+  return VX_OK;
+}
+
+// Rebuild the tiles for the current tile size (with group boundaries when
+// the batched form is on) and upload them.
+int retile(vx_sim* s, int tile_max) {
+  Tiling T;
+  std::vector<int64_t> starts;
+  if (s->group_voxels > 0) starts = batch_group_starts(s->L, s->group_voxels);
+  int rc = build_tiling(s->L, tile_max, 2 * tile_max, T, g_err, s->group_voxels > 0 ? &starts : nullptr);
+  if (rc) return rc;
+  s->T.tile_a.swap(T.tile_a); s->T.tile_b.swap(T.tile_b); s->T.halo.swap(T.halo); s->T.plus.swap(T.plus);
+  s->T.halo_bonds.swap(T.halo_bonds); s->T.tile_desc.swap(T.tile_desc); s->T.halo_fixed.swap(T.halo_fixed);
+  s->T.halo_stride = T.halo_stride;
+  s->T.tile_max = tile_max;
+  s->T.max_local = T.max_local;
+  s->tile_max = tile_max;
+  s->pipe_smem = 0;  // re-prepare the pipelined kernels
+  s->B = Batch();
+  return upload_tiling(s);
 }
 
 // read-modify-write of the flag bytes in canonical order
@@ -561,18 +618,20 @@ int vx_set_step_form(vx_sim* s, int32_t form, int32_t tile_max) {
   if (form != VX_FORM_TWO_PASS && tile_max != 0 && tile_max != s->tile_max) {
     if (tile_max != 128 && tile_max != 256 && tile_max != 512) return fail(VX_ERR_ARG, "tile_max must be 128, 256 or 512");
     // the voxel order depends only on the lattice, so the state stays valid
-    Tiling T;
-    if ((rc = build_tiling(s->L, tile_max, 2 * tile_max, T, g_err))) return rc;
-    s->T.tile_a.swap(T.tile_a); s->T.tile_b.swap(T.tile_b); s->T.halo.swap(T.halo); s->T.plus.swap(T.plus);
-    s->T.halo_bonds.swap(T.halo_bonds); s->T.tile_desc.swap(T.tile_desc); s->T.halo_fixed.swap(T.halo_fixed);
-    s->T.halo_stride = T.halo_stride;
-    s->T.tile_max = tile_max;
-    s->T.max_local = T.max_local;
-    s->tile_max = tile_max;
-    if ((rc = upload_tiling(s))) return rc;
+    if ((rc = retile(s, tile_max))) return rc;
   }
   s->form = form;
   return VX_OK;
+}
+
+int vx_set_batching(vx_sim* s, int64_t group_voxels) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (group_voxels < 0) return fail(VX_ERR_ARG, "group_voxels must be >= 0");
+  if (group_voxels > 0 && s->form == VX_FORM_TWO_PASS) return fail(VX_ERR_STATE, "batching needs a fused form");
+  if (s->tile_max == 512 && group_voxels > 0) return fail(VX_ERR_ARG, "batching takes tiles of 128 or 256 voxels");
+  s->group_voxels = group_voxels;
+  return retile(s, s->tile_max);
 }
 
 int vx_get_tiling(vx_sim* s, int32_t* tile_max, int64_t* n_tiles, int32_t* max_local, int64_t* smem_bytes) {
@@ -824,19 +883,34 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   int rc = check_sim(s);
   if (rc) return rc;
   if (n < 0) return fail(VX_ERR_ARG, "n_steps must be >= 0");
+  if (n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps too large for one call");
   cudaStream_t st = (cudaStream_t)stream;
+  if (s->group_voxels > 0 && !s->collide_on && n > 0) {
+    // batched form: all n steps in one launch
+    StepArgs A = step_args(s);
+    if ((rc = ensure_pipe(s, A))) return rc;
+    if ((int64_t)s->B.cta_start.size() != (int64_t)s->pipe_grid + 1 && (rc = build_schedule(s))) return rc;
+    BatchArgs Bt;
+    Bt.cta_start = s->b_cta_start;
+    Bt.cta_groups = s->b_cta_groups;
+    Bt.group_tiles = s->b_group_tiles;
+    Bt.buf0 = s->st;
+    Bt.buf1 = s->st + (size_t)NPLANE * s->pitch;
+    Bt.cur0 = s->cur;
+    Bt.n_steps = (int)n;
+    Bt.step0 = s->step;
+    Bt.act_P = s->actP;
+    launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, st);
+    s->cur ^= (int)(n & 1);
+    s->step += n;
+    VX_CUDA(cudaGetLastError());
+    return VX_OK;
+  }
   for (int64_t i = 0; i < n; ++i) {
     StepArgs A = step_args(s);
     if (s->actP > 0) A.act_w = (float)(2.0 * M_PI * (double)(s->step % s->actP) / (double)s->actP);
     if (s->form == VX_FORM_PIPELINED) {
-      int nm = (int)s->L.palette.size();
-      size_t sm = pipe_smem_bytes(s->tile_max, A.phase != nullptr, A.logE != nullptr, A.body != nullptr,
-                                  A.fext != nullptr, nm, nm <= kLutMaxMats);
-      if (sm != s->pipe_smem) {
-        if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0)
-          return fail(VX_ERR_CUDA, "pipelined kernel needs " + std::to_string(sm) + " bytes of shared memory");
-        s->pipe_smem = sm;
-      }
+      if ((rc = ensure_pipe(s, A))) return rc;
       launch_pipe(A, s->tile_max, s->pipe_smem, s->pipe_grid, st);
     } else {
       launch_step(A, s->form, s->tile_max, s->smem, st);

@@ -146,7 +146,8 @@ static uint64_t spread3(uint32_t x) {
   return v;
 }
 
-int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err) {
+int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err,
+                 const std::vector<int64_t>* breaks) {
   if (tile_max < 64 || tile_max > 1024) { err = "tile size must be in [64, 1024]"; return VX_ERR_ARG; }
   local_max = std::min(local_max, kMaxLocal);
   if (local_max < 160) { err = "local_max must be at least 160 (one brick and its halo)"; return VX_ERR_ARG; }
@@ -182,8 +183,13 @@ int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::
   T.plus.assign(3 * (size_t)N, 0xFFFFu);
   std::vector<int32_t> hl;
   int64_t v0 = 0;
+  size_t nb_i = 0;
   while (v0 < N) {
     int64_t len = std::min<int64_t>(tile_max, N - v0);
+    if (breaks) {
+      while (nb_i < breaks->size() && (*breaks)[nb_i] <= v0) ++nb_i;
+      if (nb_i < breaks->size()) len = std::min<int64_t>(len, (*breaks)[nb_i] - v0);
+    }
     for (;;) {
       int64_t v1 = v0 + len;
       hl.clear();
@@ -195,7 +201,7 @@ int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::
       std::sort(hl.begin(), hl.end());
       hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
       int64_t nl = len + (int64_t)hl.size();
-      if (nl <= local_max || len <= 32) {
+      if (nl <= local_max || len <= 32 || (breaks && len < 32)) {
         if (nl > local_max) { err = "tile staging set too large"; return VX_ERR_ARG; }
         int32_t T0 = (int32_t)len;
         T.tile_a.insert(T.tile_a.end(), {(int32_t)v0, T0, (int32_t)T.halo.size(), (int32_t)hl.size()});
@@ -234,6 +240,54 @@ int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::
     for (int32_t j = 0; j < a[3]; ++j) T.halo_fixed[(size_t)t * T.halo_stride + j] = T.halo[a[2] + j];
   }
   return VX_OK;
+}
+
+std::vector<int64_t> batch_group_starts(const Lattice& L, int64_t group_voxels) {
+  // bodies are contiguous in internal order as in canonical order
+  std::vector<int64_t> starts;
+  int64_t acc = 0;
+  for (int b = 0; b < L.n_bodies; ++b) {
+    int64_t nb = L.body_first[b + 1] - L.body_first[b];
+    if (starts.empty() || acc >= group_voxels || acc + nb > 2 * group_voxels) {
+      starts.push_back(L.body_first[b]);
+      acc = 0;
+    }
+    acc += nb;
+  }
+  return starts;
+}
+
+void build_batch(const Tiling& T, const std::vector<int64_t>& starts, int64_t N, int n_ctas, Batch& B) {
+  B = Batch();
+  const int64_t nt = T.n_tiles();
+  B.group_start = starts;
+  B.group_start.push_back(N);
+  const size_t ng = starts.size();
+  int32_t t = 0;
+  for (size_t g = 0; g < ng; ++g) {
+    int32_t t0 = t;
+    while (t < nt && T.tile_a[4 * (size_t)t] < B.group_start[g + 1]) ++t;
+    B.group_tiles.push_back(t0);
+    B.group_tiles.push_back(t);
+  }
+  // longest processing time first onto the least loaded CTA
+  std::vector<int32_t> order(ng);
+  for (size_t g = 0; g < ng; ++g) order[g] = (int32_t)g;
+  auto size_of = [&](int32_t g) { return B.group_start[g + 1] - B.group_start[g]; };
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return size_of(a) > size_of(b); });
+  std::vector<int64_t> load(n_ctas, 0);
+  std::vector<std::vector<int32_t>> lists(n_ctas);
+  for (int32_t g : order) {
+    int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[c] += size_of(g);
+    lists[c].push_back(g);
+  }
+  B.cta_start.push_back(0);
+  for (int c = 0; c < n_ctas; ++c) {
+    B.cta_groups.insert(B.cta_groups.end(), lists[c].begin(), lists[c].end());
+    B.cta_start.push_back((int32_t)B.cta_groups.size());
+  }
+  B.max_cta_voxels = *std::max_element(load.begin(), load.end());
 }
 
 int64_t Tiling::n_tile_bonds() const {

@@ -82,7 +82,26 @@ struct Tiling {
 constexpr int kMaxLocal = 4095;
 
 // local_max: largest owned + halo set a tile may stage (shared memory bound);
-// tiles are shrunk brick by brick until they fit.
-int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err);
+// tiles are shortened until they fit.  breaks (optional, ascending internal
+// voxel indices): no tile crosses one.
+int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err,
+                 const std::vector<int64_t>* breaks = nullptr);
+
+// Batched schedule: consecutive bodies grouped to about group_voxels voxels
+// (a body larger than that is its own group), groups dealt to n_ctas
+// persistent CTAs longest first onto the least loaded CTA.  A group is a
+// voxel range [v0, v1) in internal order; its tiles are [t0, t1).
+struct Batch {
+  std::vector<int64_t> group_start;   // n_groups + 1 voxel offsets (internal order)
+  std::vector<int32_t> group_tiles;   // 2 per group: first tile, end tile
+  std::vector<int32_t> cta_start;     // n_ctas + 1 offsets into cta_groups
+  std::vector<int32_t> cta_groups;    // group indices, per CTA in processing order
+  int64_t max_cta_voxels = 0;         // heaviest CTA's voxels (load balance)
+};
+
+// Voxel offsets (internal order) where the groups of a batched schedule start.
+std::vector<int64_t> batch_group_starts(const Lattice& L, int64_t group_voxels);
+// Fills the tile ranges and the CTA assignment for groups starting at `starts`.
+void build_batch(const Tiling& T, const std::vector<int64_t>& starts, int64_t N, int n_ctas, Batch& B);
 
 }  // namespace vx

@@ -49,6 +49,21 @@ int prepare_fused(int tile_max, size_t smem);
 size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, int n_mats, bool lut);
 int prepare_pipe(int tile_max, size_t smem, int* grid);
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s);
+
+// Batched multi-step form (independent bodies, no collisions).
+struct BatchArgs {
+  const int32_t* cta_start;    // grid + 1
+  const int32_t* cta_groups;
+  const int32_t* group_tiles;  // 2 per group
+  float* buf0;                 // the two state buffers
+  float* buf1;
+  int cur0;                    // buffer holding the state at step0
+  int n_steps;
+  int64_t step0;
+  int64_t act_P;
+};
+int prepare_batched(int tile_max, size_t smem);
+void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);
 void launch_rebuild(const CollideArgs& C, cudaStream_t s);
 void launch_flag_all(const CollideArgs& C, cudaStream_t s);

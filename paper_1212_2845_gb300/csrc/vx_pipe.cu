@@ -34,9 +34,9 @@ struct TileRegs {
 };
 
 template <int TMAX>
-__device__ __forceinline__ TileRegs load_tile(const StepArgs& A, int t) {
+__device__ __forceinline__ TileRegs load_tile(const StepArgs& A, int t, int t_end) {
   TileRegs r;
-  r.valid = t < A.n_tiles;
+  r.valid = t < t_end;
   if (!r.valid) { r.v0 = r.T = r.nh = r.hb0 = r.nhb = 0; r.h0 = r.h1 = -1; return r; }
   const int4 d = reinterpret_cast<const int4*>(A.tdesc)[2 * t];
   const int b0 = reinterpret_cast<const int4*>(A.tdesc)[2 * t + 1].x;
@@ -149,6 +149,88 @@ __device__ __forceinline__ void halo_bond_p(const StepArgs& A, const Stage<TMAX>
   minus_slot<TMAX, a>(F4, F2, s2, o);
 }
 
+// Everything after a tile's staging has landed: material properties of the
+// staged voxels, own and halo bonds, gather and the voxel update.
+template <int TMAX>
+__device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX>& S, float4* props, float4* F4,
+                                             float2* F2, const DevMat* mats, const float* lut, const TileRegs& cur,
+                                             uint8_t fl_cur) {
+  const int i = threadIdx.x;
+  const int T = cur.T;
+  const bool own = i < T;
+  if (own) {
+    uint32_t w = S.vw[i];
+    props[i] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[i] : 0.f, S.le ? S.le[i] : 0.f);
+  }
+  for (int j = i; j < cur.nh; j += TMAX) {
+    const int k = T + j;
+    uint32_t w = S.vw[k];
+    props[k] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[k] : 0.f, S.le ? S.le[k] : 0.f);
+  }
+  __syncthreads();
+  // 4. own +x, +y, +z bonds; halo bonds
+  V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
+  VoxS s;
+  float4 pr;
+  uint32_t w0 = 0;
+  if (own) {
+    s = S.vox(i);
+    pr = props[i];
+    w0 = S.vw[i];
+    const uint2 pl = S.pl[i];
+    const int px = (int)(pl.x & 0xFFFFu), py = (int)(pl.x >> 16), pz = (int)(pl.y & 0xFFFFu);
+    const M3f R1 = qmat(s.q);
+    const bool damp = A.zb != 0.f;
+#define VX_PLUS_BOND(AX, P2)                                                                               \
+    if (P2 != 0xFFFF) {                                                                                  \
+      const VoxS v2 = S.vox(P2);                                                                         \
+      const float4 q2 = props[P2];                                                                       \
+      const BondK k = pair_consts(A, lut, mats, pr, q2);                                                 \
+      BondOut o = bond_eval<AX>(s, R1, v2, A.l, k, mul_(0.5f, add_(pr.z, q2.z)), damp);                   \
+      F = add(F, o.F1);                                                                                  \
+      M = add(M, o.M1);                                                                                  \
+      if (P2 < T) minus_slot<TMAX, AX>(F4, F2, P2, o);                                                   \
+    }
+    VX_PLUS_BOND(0, px)
+    VX_PLUS_BOND(1, py)
+    VX_PLUS_BOND(2, pz)
+#undef VX_PLUS_BOND
+  }
+  for (int j = i; j < cur.nhb; j += TMAX) {
+    const uint32_t pk = S.hb[j];
+    const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
+    if (ax == 0) halo_bond_p<TMAX, 0>(A, S, props, lut, mats, F4, F2, s1, s2);
+    else if (ax == 1) halo_bond_p<TMAX, 1>(A, S, props, lut, mats, F4, F2, s1, s2);
+    else halo_bond_p<TMAX, 2>(A, S, props, lut, mats, F4, F2, s1, s2);
+  }
+  __syncthreads();
+  // 5. gather the -x, -y, -z results and integrate
+  float speed = 0.f;
+  int body = 0;
+  if (own) {
+    const uint32_t mask = (w0 >> 8) & 63u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+      if (mask & (1u << (2 * a))) {
+        const float4 f = F4[a * TMAX + i];
+        const float2 g = F2[a * TMAX + i];
+        F = add(F, v3(f.x, f.y, f.z));
+        M = add(M, v3(f.w, g.x, g.y));
+      }
+    VoxMeta mt;
+    mt.lat = S.lat[i];
+    mt.m = (int)(w0 & 255u);
+    mt.b = S.body ? S.body[i] : 0;
+    mt.fl = fl_cur;
+    mt.dt = A.dt_body[mt.b];
+    mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
+    mt.fext = S.fx ? v3(S.fx[i], S.fx[TMAX + i], S.fx[2 * TMAX + i]) : v3(0.f, 0.f, 0.f);
+    body = mt.b;
+    speed = voxel_finish(A, cur.v0 + i, mt, s, F, M, pr.z, pr.x, mats);
+  }
+  if (A.collide_on) horizon_max(A, body, own, speed);
+}
+
 }  // namespace
 
 template <int TMAX> struct PipeSmem {
@@ -180,7 +262,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
     for (int j = i; j < 8 * A.n_mats * A.n_mats; j += TMAX) lut[j] = A.lut[j];
   const StPtr G(const_cast<float*>(A.st_in), A.pitch);
   // prologue: stage the first tile, fetch the next descriptor
-  TileRegs cur = load_tile<TMAX>(A, t);
+  TileRegs cur = load_tile<TMAX>(A, t, A.n_tiles);
   {
     Stage<TMAX> S0;
     S0.carve(smem, hph, hle, hbody, hfx);
@@ -188,7 +270,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
   }
   cp_commit();
   uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
-  TileRegs nxt = load_tile<TMAX>(A, t + Gs);
+  TileRegs nxt = load_tile<TMAX>(A, t + Gs, A.n_tiles);
   int b = 0;
   for (;;) {
     Stage<TMAX> S;
@@ -203,83 +285,11 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
     }
     cp_commit();
     // 2. descriptor and halo indices of the tile after it
-    const TileRegs nn = load_tile<TMAX>(A, t + 2 * Gs);
+    const TileRegs nn = load_tile<TMAX>(A, t + 2 * Gs, A.n_tiles);
     // 3. this tile has landed
     cp_wait1();
     __syncthreads();
-    const int T = cur.T;
-    const bool own = i < T;
-    if (own) {
-      uint32_t w = S.vw[i];
-      props[i] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[i] : 0.f, S.le ? S.le[i] : 0.f);
-    }
-    for (int j = i; j < cur.nh; j += TMAX) {
-      const int k = T + j;
-      uint32_t w = S.vw[k];
-      props[k] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[k] : 0.f, S.le ? S.le[k] : 0.f);
-    }
-    __syncthreads();
-    // 4. own +x, +y, +z bonds; halo bonds
-    V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
-    VoxS s;
-    float4 pr;
-    uint32_t w0 = 0;
-    if (own) {
-      s = S.vox(i);
-      pr = props[i];
-      w0 = S.vw[i];
-      const uint2 pl = S.pl[i];
-      const int px = (int)(pl.x & 0xFFFFu), py = (int)(pl.x >> 16), pz = (int)(pl.y & 0xFFFFu);
-      const M3f R1 = qmat(s.q);
-      const bool damp = A.zb != 0.f;
-#define VX_PLUS_BOND(AX, P2)                                                                               \
-      if (P2 != 0xFFFF) {                                                                                  \
-        const VoxS v2 = S.vox(P2);                                                                         \
-        const float4 q2 = props[P2];                                                                       \
-        const BondK k = pair_consts(A, lut, mats, pr, q2);                                                 \
-        BondOut o = bond_eval<AX>(s, R1, v2, A.l, k, mul_(0.5f, add_(pr.z, q2.z)), damp);                   \
-        F = add(F, o.F1);                                                                                  \
-        M = add(M, o.M1);                                                                                  \
-        if (P2 < T) minus_slot<TMAX, AX>(F4, F2, P2, o);                                                   \
-      }
-      VX_PLUS_BOND(0, px)
-      VX_PLUS_BOND(1, py)
-      VX_PLUS_BOND(2, pz)
-#undef VX_PLUS_BOND
-    }
-    for (int j = i; j < cur.nhb; j += TMAX) {
-      const uint32_t pk = S.hb[j];
-      const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
-      if (ax == 0) halo_bond_p<TMAX, 0>(A, S, props, lut, mats, F4, F2, s1, s2);
-      else if (ax == 1) halo_bond_p<TMAX, 1>(A, S, props, lut, mats, F4, F2, s1, s2);
-      else halo_bond_p<TMAX, 2>(A, S, props, lut, mats, F4, F2, s1, s2);
-    }
-    __syncthreads();
-    // 5. gather the -x, -y, -z results and integrate
-    float speed = 0.f;
-    int body = 0;
-    if (own) {
-      const uint32_t mask = (w0 >> 8) & 63u;
-#pragma unroll
-      for (int a = 0; a < 3; ++a)
-        if (mask & (1u << (2 * a))) {
-          const float4 f = F4[a * TMAX + i];
-          const float2 g = F2[a * TMAX + i];
-          F = add(F, v3(f.x, f.y, f.z));
-          M = add(M, v3(f.w, g.x, g.y));
-        }
-      VoxMeta mt;
-      mt.lat = S.lat[i];
-      mt.m = (int)(w0 & 255u);
-      mt.b = S.body ? S.body[i] : 0;
-      mt.fl = fl_cur;
-      mt.dt = A.dt_body[mt.b];
-      mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
-      mt.fext = S.fx ? v3(S.fx[i], S.fx[TMAX + i], S.fx[2 * TMAX + i]) : v3(0.f, 0.f, 0.f);
-      body = mt.b;
-      speed = voxel_finish(A, cur.v0 + i, mt, s, F, M, pr.z, pr.x, mats);
-    }
-    if (A.collide_on) horizon_max(A, body, own, speed);
+    compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur);
     if (!nxt.valid) break;  // uniform
     __syncthreads();        // buffer b and the shared results are reused
     cur = nxt;
@@ -287,6 +297,78 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
     fl_cur = fl_nxt;
     t += Gs;
     b ^= 1;
+  }
+}
+
+// Batched form: each CTA takes its groups of bodies one after the other and
+// runs all n_steps of a group before the next; steps are separated by a CTA
+// barrier, so a group's double-buffered state stays in L2 for the whole run.
+// Within a step the tiles of the group are pipelined as in fused_pipe; the
+// pipeline restarts after each barrier because the next step reads what this
+// one wrote.
+template <int TMAX>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepArgs A0, BatchArgs Bt) {
+  constexpr int ML = 2 * TMAX;
+  extern __shared__ __align__(16) float smem[];
+  const bool hph = A0.phase != nullptr, hle = A0.logE != nullptr, hbody = A0.body != nullptr,
+             hfx = A0.fext != nullptr;
+  const int sf = Stage<TMAX>::floats(hph, hle, hbody, hfx);
+  float4* props = reinterpret_cast<float4*>(smem + 2 * sf);
+  float4* F4 = props + ML;
+  float2* F2 = reinterpret_cast<float2*>(F4 + 3 * TMAX);
+  DevMat* mats = reinterpret_cast<DevMat*>(F2 + 3 * TMAX);
+  float* lut = reinterpret_cast<float*>(mats + A0.n_mats);
+  const int i = threadIdx.x;
+  for (int j = i; j < A0.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
+    reinterpret_cast<float*>(mats)[j] = reinterpret_cast<const float*>(A0.mats)[j];
+  if (A0.lut)
+    for (int j = i; j < 8 * A0.n_mats * A0.n_mats; j += TMAX) lut[j] = A0.lut[j];
+  __syncthreads();
+  for (int gi = Bt.cta_start[blockIdx.x]; gi < Bt.cta_start[blockIdx.x + 1]; ++gi) {
+    const int g = Bt.cta_groups[gi];
+    const int t0 = Bt.group_tiles[2 * g], t1 = Bt.group_tiles[2 * g + 1];
+    for (int k = 0; k < Bt.n_steps; ++k) {
+      StepArgs A = A0;
+      const int p = (Bt.cur0 + k) & 1;
+      A.st_in = p ? Bt.buf1 : Bt.buf0;
+      A.st_out = p ? Bt.buf0 : Bt.buf1;
+      A.step = Bt.step0 + k;
+      if (A.act_on && Bt.act_P > 0)
+        A.act_w = (float)(6.283185307179586 * (double)(A.step % Bt.act_P) / (double)Bt.act_P);
+      const StPtr G(const_cast<float*>(A.st_in), A.pitch);
+      TileRegs cur = load_tile<TMAX>(A, t0, t1);
+      {
+        Stage<TMAX> S0;
+        S0.carve(smem, hph, hle, hbody, hfx);
+        issue_tile<TMAX>(A, G, S0, cur);
+      }
+      cp_commit();
+      uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
+      TileRegs nxt = load_tile<TMAX>(A, t0 + 1, t1);
+      int b = 0;
+      for (int t = t0;; ++t) {
+        Stage<TMAX> S;
+        S.carve(smem + b * sf, hph, hle, hbody, hfx);
+        uint8_t fl_nxt = 0;
+        if (nxt.valid) {
+          Stage<TMAX> Sn;
+          Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx);
+          issue_tile<TMAX>(A, G, Sn, nxt);
+          fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
+        }
+        cp_commit();
+        const TileRegs nn = load_tile<TMAX>(A, t + 2, t1);
+        cp_wait1();
+        __syncthreads();
+        compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur);
+        __syncthreads();  // buffers reused; at the last tile: the step's writes are complete
+        if (!nxt.valid) break;
+        cur = nxt;
+        nxt = nn;
+        fl_cur = fl_nxt;
+        b ^= 1;
+      }
+    }
   }
 }
 
@@ -310,6 +392,18 @@ int prepare_pipe(int tile_max, size_t smem, int* grid) {
     return -1;
   *grid = per_sm * n_sm;
   return 0;
+}
+
+int prepare_batched(int tile_max, size_t smem) {
+  cudaError_t e;
+  if (tile_max == 128) e = cudaFuncSetAttribute(batched_pipe<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else e = cudaFuncSetAttribute(batched_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return e == cudaSuccess ? 0 : -1;
+}
+
+void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s) {
+  if (tile_max == 128) batched_pipe<128><<<grid, 128, smem, s>>>(A, B);
+  else batched_pipe<256><<<grid, 256, smem, s>>>(A, B);
 }
 
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {

@@ -60,6 +60,7 @@ SIGNATURES = {
     "vx_plan_tiles": (C.c_int, [_pdesc, _i32, _pi64, _pi64, _pi64, _pi32]),
     "vx_set_step_form": (C.c_int, [_P, _i32, _i32]),
     "vx_get_tiling": (C.c_int, [_P, _pi32, _pi64, _pi32, _pi64]),
+    "vx_set_batching": (C.c_int, [_P, _i64]),
     "vx_create": (C.c_int, [_pdesc, C.POINTER(_P)]),
     "vx_destroy": (None, [_P]),
     "vx_get_counts": (C.c_int, [_P, _pi64, _pi64, _pi64]),
@@ -274,6 +275,9 @@ class Sim:
 
     def set_step_form(self, form, tile_max=0):
         _check(self._L.vx_set_step_form(self.h, int(form), int(tile_max)))
+
+    def set_batching(self, group_voxels):
+        _check(self._L.vx_set_batching(self.h, int(group_voxels)))
 
     def tiling(self):
         tm, ml = C.c_int32(), C.c_int32()

@@ -358,3 +358,33 @@ def test_fused_tile_sizes_bitwise_and_two_pass_close(vx, which):
         other = run_form(vx, sc, steps, form, tm)
         for k in ("offset", "quat", "vel", "angvel", "flags"):
             assert np.array_equal(other[k].view(np.uint8), ref[k].view(np.uint8)), (form, tm, k)
+
+
+# ---------------------------------------------------------------------------
+# batched form: many bodies, all steps in one launch
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("group", [64, 700, 5000])
+def test_batched_form_bitwise_equals_per_step(vx, group):
+    sc = scenes.population(n_bodies=23, seed=17, lo=2, hi=12)
+    ref = run_form(vx, sc, 250, vx.FORM_PIPELINED, 256)
+    sim = vx.Sim(sc)
+    sim.set_batching(group)
+    sim.step(250)
+    out = sim.read_state()
+    assert sim.step_count == 250
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
+    sim.set_batching(0)
+    sim.step(3)                      # back to per-step launches, still consistent
+    assert sim.step_count == 253
+
+
+def test_batched_design_population_vs_oracle(vx):
+    """Config 5 inputs (per-voxel log stiffness, phases) through the batched form."""
+    sc = scenes.design_population(n_bodies=4, n=6, seed=5)
+    sim, ora = pair(vx, sc)
+    sim.set_batching(300)
+    sim.step(300)
+    ora.step(300)
+    assert pos_error(sc, sim.state(), ora.state()) < 1e-3
