@@ -241,6 +241,37 @@ VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int6
  * accumulator of body 0 [m]. */
 VX_API int vx_collision_stats(vx_sim* sim, int64_t* n_rebuilds, double* accumulator);
 
+/* ---- adjoint form: design gradients over a rollout ----------------------
+ * The loss of body b is the x travel of its centre of mass over a rollout,
+ *   L_b = sum_v m_v (x_v(n) - x_v(0)) / sum_v m_v,
+ * and the gradients are dL/d(log E_v) (voxel stiffness, Sec 2.1.4 mixes it
+ * into every bond) and dL/d(phase_v) (actuation, Sec 2.3), obtained by the
+ * reverse of the step of Sec 2.1-2.2: co-rotational beam bonds, damping,
+ * floor contact and friction (its stick/slip decisions held as taken in the
+ * forward run), integration.  The timestep is held fixed (no derivative
+ * through the stability limit).  The paper has no gradients; they serve
+ * design optimisation of the kind its examples show.
+ *
+ * vx_rollout_forward: run n_steps steps from the current state with the
+ * current step form, keeping a copy of the state and flags every
+ * checkpoint_every steps on the device (ceil(n_steps / K) copies of 53 bytes
+ * per voxel).  loss_body: host array [n_bodies] receiving L_b, or NULL.
+ * Returns VX_ERR_STATE if voxel-voxel collisions are on (no adjoint for
+ * them), VX_ERR_UNSTABLE if the state became non-finite.  Synchronous.
+ *
+ * vx_rollout_backward: gradients of sum_b w_b L_b for the last forward
+ * rollout.  w_body: host array [n_bodies] or NULL for all ones.  grad_logE,
+ * grad_phase: DEVICE arrays [n_voxels] (canonical order) overwritten with
+ * the gradients; either may be NULL.  The state is recomputed segment by
+ * segment from the checkpoints into a device buffer of (K + 1) states; the
+ * simulator's own state (the end of the rollout) is not touched.  Returns
+ * VX_ERR_STATE if no rollout was recorded or the simulator was stepped,
+ * reset, written or reconfigured since.  Synchronous.  */
+VX_API int vx_rollout_forward(vx_sim* sim, int64_t n_steps, int32_t checkpoint_every, float* loss_body,
+                              void* stream);
+VX_API int vx_rollout_backward(vx_sim* sim, const float* w_body, float* grad_logE, float* grad_phase,
+                               void* stream);
+
 /* ---- collision candidates with no device allocation ----------------------
  * The paper has no counterpart to this entry point: it exists for callers
  * that cannot allocate device memory where they need collision candidates

@@ -1,0 +1,553 @@
+// Reverse-mode (adjoint) kernels of one lattice step, for gradients of a
+// rollout loss with respect to per-voxel log stiffness and actuation phase.
+//
+// One adjoint step n takes the state S_n (recomputed from a checkpoint), the
+// flags at step n and the adjoint lam_{n+1} of S_{n+1}, and produces lam_n:
+//   bond_pass, force_sums  recompute the bond results and the bond force and
+//                          moment sums of every voxel with the forward step's
+//                          own arithmetic (same bits, so every friction
+//                          decision is replayed exactly)
+//   finish_adj             reverse of the voxel update (Sec 2.2.1 external
+//                          force and ground damping, Sec 2.2.2 floor contact
+//                          and Coulomb friction with its discrete decisions
+//                          frozen, Sec 2.1.3 integration with the quaternion
+//                          update): adjoints of the bond sums, the direct part
+//                          of lam_n, dL/dE and dL/d(thermal strain)
+//   bond_adj               reverse of every bond (co-rotational beam of
+//                          Sec 2.1.2, composite material of Sec 2.1.4, damping
+//                          of Sec 2.1.5, thermal rest length of Sec 2.3)
+//   gather_adj             lam_n of every voxel, summed in a fixed order, and
+//                          the parameter gradients accumulated
+// The timestep is a constant of the rollout (no derivative through dt).
+// Fixed voxels carry their adjoint through unchanged.  Voxel-voxel contact
+// (self-collision) has no adjoint here; the host refuses rollouts with it on.
+//
+// Values that only enter derivatives are recomputed in plain FP32; only the
+// quantities that decide a branch must match the forward step bit for bit.
+#include "vx_dev.cuh"
+#include "vx_kernels.h"
+
+namespace vx {
+namespace {
+
+// ---- plain FP32 helpers for the reverse sweep
+__device__ __forceinline__ V3f A3(V3f a, V3f b) { return v3(a.x + b.x, a.y + b.y, a.z + b.z); }
+__device__ __forceinline__ V3f S3(V3f a, V3f b) { return v3(a.x - b.x, a.y - b.y, a.z - b.z); }
+__device__ __forceinline__ V3f M3(V3f a, float s) { return v3(a.x * s, a.y * s, a.z * s); }
+__device__ __forceinline__ float D3(V3f a, V3f b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ V3f X3(V3f a, V3f b) {
+  return v3(a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x);
+}
+// R v and R^T v, R given by its rows
+__device__ __forceinline__ V3f Rv(const M3f& R, V3f v) { return v3(D3(R.r0, v), D3(R.r1, v), D3(R.r2, v)); }
+__device__ __forceinline__ V3f RTv(const M3f& R, V3f v) {
+  return v3(R.r0.x * v.x + R.r1.x * v.y + R.r2.x * v.z, R.r0.y * v.x + R.r1.y * v.y + R.r2.y * v.z,
+            R.r0.z * v.x + R.r1.z * v.y + R.r2.z * v.z);
+}
+// G += a b^T
+__device__ __forceinline__ void outer_add(M3f& G, V3f a, V3f b) {
+  G.r0 = A3(G.r0, M3(b, a.x));
+  G.r1 = A3(G.r1, M3(b, a.y));
+  G.r2 = A3(G.r2, M3(b, a.z));
+}
+
+// dL/dq of R = qmat(q) (the unit-quaternion formula as written) from dL/dR.
+__device__ __forceinline__ Qf qmat_adj(Qf q, const M3f& g) {
+  const float w = q.w, x = q.x, y = q.y, z = q.z;
+  const float g00 = g.r0.x, g01 = g.r0.y, g02 = g.r0.z, g10 = g.r1.x, g11 = g.r1.y, g12 = g.r1.z;
+  const float g20 = g.r2.x, g21 = g.r2.y, g22 = g.r2.z;
+  Qf r;
+  r.w = 2.f * (-z * g01 + y * g02 + z * g10 - x * g12 - y * g20 + x * g21);
+  r.x = 2.f * (y * g01 + z * g02 + y * g10 - 2.f * x * g11 - w * g12 + z * g20 + w * g21 - 2.f * x * g22);
+  r.y = 2.f * (-2.f * y * g00 + x * g01 + w * g02 + x * g10 + z * g12 - w * g20 + z * g21 - 2.f * y * g22);
+  r.z = 2.f * (-2.f * z * g00 - w * g01 + x * g02 + w * g10 - 2.f * z * g11 + y * g12 + x * g20 + y * g21);
+  return r;
+}
+
+// Inputs of one bond besides the two voxel states.
+struct BondPar { float E1, E2, G1, G2, mmin, Imin, eps; };
+// Adjoints of one bond's inputs.  Voxel 1 gets -dO, -dv, w1, q1; voxel 2 gets
+// +dO, +dv, w2, q2; both get half of d(eps) as d(thermal strain).
+struct BondAdj { V3f dO, dv, w1, w2; Qf q1, q2; float E1, E2, G1, G2, eps; };
+
+// Reverse of bond_eval along lattice axis a: recomputes the forward values the
+// derivatives need, then applies the chain rule from (gF1, gM1, gM2), the
+// adjoints of the bond's force on voxel 1 and moments on voxels 1 and 2.
+template <int a>
+__device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, float l, float zb, V3f gF1, V3f gM1,
+                         V3f gM2, BondAdj& g) {
+  // ---- forward values
+  const float sE = bp.E1 + bp.E2, sG = bp.G1 + bp.G2;
+  const float Ec = 2.f * bp.E1 * bp.E2 / sE, Gc = 2.f * bp.G1 * bp.G2 / sG;
+  const float l2 = l * l, l3 = l2 * l;
+  const float a1 = Ec * l, a2 = Gc * l3 * (1.f / 6.f), b1 = a1, b2 = 0.5f * Ec * l2, b3 = Ec * l3 * (1.f / 6.f);
+  const M3f R = qmat(s1.q);
+  const V3f dO = S3(s2.o, s1.o);
+  V3f rd = (a == 0) ? R.r0 : (a == 1 ? R.r1 : R.r2);  // R^T e_a - e_a
+  if (a == 0) rd.x -= 1.f; else if (a == 1) rd.y -= 1.f; else rd.z -= 1.f;
+  const V3f p = to_axis<a>(A3(RTv(R, dO), M3(rd, l)));
+  const float X = p.x - l * bp.eps, Y = p.y, Z = p.z;
+  // relative rotation (W, vq) = sign * conj(q1) q2 and theta = f(W, |vq|^2) vq
+  const Qf A1 = s1.q, B2 = s2.q;
+  const float qw = A1.w * B2.w + A1.x * B2.x + A1.y * B2.y + A1.z * B2.z;
+  const float qx = A1.w * B2.x - A1.x * B2.w - A1.y * B2.z + A1.z * B2.y;
+  const float qy = A1.w * B2.y + A1.x * B2.z - A1.y * B2.w - A1.z * B2.x;
+  const float qz = A1.w * B2.z - A1.x * B2.y + A1.y * B2.x - A1.z * B2.w;
+  const float sg = qw < 0.f ? -1.f : 1.f;
+  const float W = sg * qw;
+  const V3f vq = v3(sg * qx, sg * qy, sg * qz);
+  const float s2q = D3(vq, vq);
+  float f, fW, fs2;  // f = 2 atan2(s, W) / s and its partial derivatives in W and s^2
+  if (s2q < 0.04f * W * W) {
+    // f = (2 / W) Q(t2), Q(t2) = atan(t) / t, t2 = s^2 / W^2 (series to t^10)
+    const float iw = 1.f / W, t2 = s2q * iw * iw;
+    const float P = 1.f / 3.f + t2 * (-0.2f + t2 * (1.f / 7.f + t2 * (-1.f / 9.f + t2 * (1.f / 11.f))));
+    const float Pp = -0.2f + t2 * (2.f / 7.f + t2 * (-3.f / 9.f + t2 * (4.f / 11.f)));
+    const float Q = 1.f - t2 * P, Qp = -P - t2 * Pp;
+    f = 2.f * iw * Q;
+    fW = -2.f * Q * iw * iw - 4.f * s2q * Qp * iw * iw * iw * iw;
+    fs2 = 2.f * Qp * iw * iw * iw;
+  } else {
+    const float s = sqrtf(s2q), at = atan2f(s, W), den = s2q + W * W;
+    f = 2.f * at / s;
+    fW = -2.f / den;
+    fs2 = (W / den - at / s) / s2q;
+  }
+  const V3f th = to_axis<a>(M3(vq, f));
+  const V3f F1w = from_axis<a>(v3(a1 * X, b1 * Y - b2 * th.z, b1 * Z + b2 * th.y));
+  const V3f M1w = from_axis<a>(v3(a2 * th.x, -b2 * Z - b3 * th.y, b2 * Y - b3 * th.z));
+  const V3f M2w = from_axis<a>(v3(-a2 * th.x, -b2 * Z - 2.f * b3 * th.y, b2 * Y - 2.f * b3 * th.z));
+
+  // ---- reverse
+  V3f g_dO = v3(0.f, 0.f, 0.f);
+  float g_a1 = 0.f, g_a2 = 0.f, g_b2 = 0.f, g_b3 = 0.f;
+  g.dv = v3(0.f, 0.f, 0.f);
+  g.w1 = g.w2 = v3(0.f, 0.f, 0.f);
+  if (zb != 0.f) {
+    // F1 += c2 dv + c4 (r x (w1 + w2)), M1 += cr2 dw, M2 -= cr2 dw with
+    // c2 = zb sqrt(m a1), c4 = c2 / 2, cr2 = zb sqrt(I b3)
+    const float sqa = sqrtf(bp.mmin * a1), sqb = sqrtf(bp.Imin * b3);
+    const float c2 = zb * sqa, c4 = 0.5f * c2, cr2 = zb * sqb;
+    V3f r = dO;
+    if (a == 0) r.x += l; else if (a == 1) r.y += l; else r.z += l;
+    const V3f ws = A3(s1.w, s2.w), rw = X3(r, ws);
+    const V3f dv = S3(s2.v, s1.v), dw = S3(s2.w, s1.w);
+    const V3f gMd = S3(gM1, gM2);
+    g.dv = M3(gF1, c2);
+    const V3f g_dw = M3(gMd, cr2);
+    const V3f g_rw = M3(gF1, c4);
+    const V3f g_ws = X3(g_rw, r);
+    g.w1 = S3(g_ws, g_dw);
+    g.w2 = A3(g_ws, g_dw);
+    g_dO = X3(ws, g_rw);
+    const float g_c2 = D3(gF1, dv) + 0.5f * D3(gF1, rw);
+    g_a1 += zb * g_c2 * 0.5f * bp.mmin / sqa;
+    g_b3 += zb * D3(gMd, dw) * 0.5f * bp.Imin / sqb;
+  }
+  // F1 = R F1w, M1 = R M1w, M2 = R M2w
+  M3f gR;
+  gR.r0 = gR.r1 = gR.r2 = v3(0.f, 0.f, 0.f);
+  outer_add(gR, gF1, F1w);
+  outer_add(gR, gM1, M1w);
+  outer_add(gR, gM2, M2w);
+  const V3f gF = to_axis<a>(RTv(R, gF1)), gm1 = to_axis<a>(RTv(R, gM1)), gm2 = to_axis<a>(RTv(R, gM2));
+  // local forces and moments (the negated rows of [K] u, Sec 2.1.2)
+  float g_X = 0.f, g_Y = 0.f, g_Z = 0.f;
+  V3f g_th = v3(0.f, 0.f, 0.f);
+  g_a1 += gF.x * X + gF.y * Y + gF.z * Z;  // b1 = a1
+  g_X += a1 * gF.x;
+  g_Y += b1 * gF.y; g_b2 -= gF.y * th.z; g_th.z -= b2 * gF.y;
+  g_Z += b1 * gF.z; g_b2 += gF.z * th.y; g_th.y += b2 * gF.z;
+  g_a2 += (gm1.x - gm2.x) * th.x; g_th.x += a2 * (gm1.x - gm2.x);
+  g_b2 -= (gm1.y + gm2.y) * Z; g_Z -= b2 * (gm1.y + gm2.y);
+  g_b3 -= (gm1.y + 2.f * gm2.y) * th.y; g_th.y -= b3 * (gm1.y + 2.f * gm2.y);
+  g_b2 += (gm1.z + gm2.z) * Y; g_Y += b2 * (gm1.z + gm2.z);
+  g_b3 -= (gm1.z + 2.f * gm2.z) * th.z; g_th.z -= b3 * (gm1.z + 2.f * gm2.z);
+  // X = p.x - l eps, p = Pi_a (R^T dO + l (R^T e_a - e_a))
+  g.eps = -l * g_X;
+  const V3f g_pw = from_axis<a>(v3(g_X, g_Y, g_Z));
+  outer_add(gR, dO, g_pw);
+  g_dO = A3(g_dO, Rv(R, g_pw));
+  if (a == 0) gR.r0 = A3(gR.r0, M3(g_pw, l));
+  else if (a == 1) gR.r1 = A3(gR.r1, M3(g_pw, l));
+  else gR.r2 = A3(gR.r2, M3(g_pw, l));
+  g.dO = g_dO;
+  // theta = Pi_a (f vq)
+  const V3f g_thq = from_axis<a>(g_th);
+  const float g_f = D3(g_thq, vq);
+  const V3f g_vq = A3(M3(g_thq, f), M3(vq, 2.f * fs2 * g_f));
+  const float gw = sg * fW * g_f, gx = sg * g_vq.x, gy = sg * g_vq.y, gz = sg * g_vq.z;
+  // (qw, qx, qy, qz) = conj(q1) q2
+  g.q2.w = A1.w * gw - A1.x * gx - A1.y * gy - A1.z * gz;
+  g.q2.x = A1.x * gw + A1.w * gx - A1.z * gy + A1.y * gz;
+  g.q2.y = A1.y * gw + A1.z * gx + A1.w * gy - A1.x * gz;
+  g.q2.z = A1.z * gw - A1.y * gx + A1.x * gy + A1.w * gz;
+  const Qf gq1R = qmat_adj(s1.q, gR);
+  g.q1.w = B2.w * gw + B2.x * gx + B2.y * gy + B2.z * gz + gq1R.w;
+  g.q1.x = B2.x * gw - B2.w * gx + B2.z * gy - B2.y * gz + gq1R.x;
+  g.q1.y = B2.y * gw - B2.z * gx - B2.w * gy + B2.x * gz + gq1R.y;
+  g.q1.z = B2.z * gw + B2.y * gx - B2.x * gy - B2.w * gz + gq1R.z;
+  // a1 = Ec l, a2 = Gc l^3 / 6, b2 = Ec l^2 / 2, b3 = Ec l^3 / 6 (Sec 2.1.2);
+  // Ec, Gc harmonic means of the two voxels' moduli (Sec 2.1.4)
+  const float g_Ec = l * g_a1 + 0.5f * l2 * g_b2 + l3 * (1.f / 6.f) * g_b3;
+  const float g_Gc = l3 * (1.f / 6.f) * g_a2;
+  const float iE = 1.f / (sE * sE), iG = 1.f / (sG * sG);
+  g.E1 = g_Ec * 2.f * bp.E2 * bp.E2 * iE;
+  g.E2 = g_Ec * 2.f * bp.E1 * bp.E1 * iE;
+  g.G1 = g_Gc * 2.f * bp.G2 * bp.G2 * iG;
+  g.G2 = g_Gc * 2.f * bp.G1 * bp.G1 * iG;
+}
+
+// Bond-adjoint planes per axis: dO (3), dv (3), w1 (3), w2 (3), q1 (4), q2 (4),
+// dE of voxel 1, dE of voxel 2 (shear modulus folded in), half of d(eps).
+constexpr int kBA = 23;
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) force_sums(StepArgs A, AdjArgs J) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= A.N) return;
+  const int64_t P = A.pitch, C = 3 * P;
+  // the forward step's gather: +x, +y, +z (F1, M1), then -x, -y, -z (-F1, M2)
+  V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
+  for (int a = 0; a < 3; ++a)
+    if (A.nbr[(int64_t)(2 * a + 1) * A.N + v] >= 0) {
+      const float* bf = A.bf + (int64_t)a * P + v;
+      F = add(F, v3(bf[0], bf[C], bf[2 * C]));
+      M = add(M, v3(bf[3 * C], bf[4 * C], bf[5 * C]));
+    }
+  for (int a = 0; a < 3; ++a) {
+    const int un = A.nbr[(int64_t)(2 * a) * A.N + v];
+    if (un >= 0) {
+      const float* bf = A.bf + (int64_t)a * P + un;
+      F = add(F, v3(-bf[0], -bf[C], -bf[2 * C]));
+      M = add(M, v3(bf[6 * C], bf[7 * C], bf[8 * C]));
+    }
+  }
+  J.fm[0 * P + v] = F.x; J.fm[1 * P + v] = F.y; J.fm[2 * P + v] = F.z;
+  J.fm[3 * P + v] = M.x; J.fm[4 * P + v] = M.y; J.fm[5 * P + v] = M.z;
+}
+
+// Reverse of voxel_finish without voxel-voxel contact.
+__global__ void __launch_bounds__(256) finish_adj(StepArgs A, AdjArgs J) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= A.N) return;
+  const int64_t P = A.pitch;
+  const StPtr Lin(const_cast<float*>(J.lam_in), P), Lout(J.lam_out, P);
+  const VoxS lam = Lin.load(v);
+  const VoxMeta mt = load_meta(A, v);
+  if (mt.fl & 1u) {  // fixed: S_{n+1} = S_n
+    Lout.store(v, lam);
+    for (int c = 0; c < 6; ++c) J.gfm[c * P + v] = 0.f;
+    J.gdir[v] = 0.f;
+    J.gdir[P + v] = 0.f;
+    return;
+  }
+  const DevMat& d = A.mats[mt.m];
+  const float l = A.l, dt = mt.dt;
+  const float Ev = voxel_E(A, v, mt.m);
+  const float adT = thermal_strain(A, v, d.cte);
+  const VoxS s = load_vox(A.st_in, P, v);
+  V3f F = v3(J.fm[v], J.fm[P + v], J.fm[2 * P + v]);
+  V3f M = v3(J.fm[3 * P + v], J.fm[4 * P + v], J.fm[5 * P + v]);
+
+  // ---- forward, with the forward step's rounding wherever a branch depends on it
+  F = add(F, mt.fext);
+  F.z = fma_(d.m, A.gz, F.z);
+  const float kv = mul_(Ev, l);
+  float cg = 0.f, cgr = 0.f;
+  if (A.zg != 0.f) {
+    cg = mul_(mul_(2.f, A.zg), fsqrt(mul_(d.m, kv)));
+    cgr = mul_(mul_(2.f, A.zg), fsqrt(mul_(mul_(d.I, kv), mul_(mul_(l, l), 1.f / 6.f))));
+    F = axpy(F, -cg, s.v);
+    M = axpy(M, -cgr, s.w);
+  }
+  const float hl = mul_(0.5f, l);
+  const float h = fma_(hl, adT, hl);
+  bool contact = false, zero_l = false;
+  int dir = 0;  // direction of dynamic friction: 1 along v_l, 2 along F_l
+  float pen = 0.f, cz = 0.f, mud = 0.f, un = 1.f, ux = 0.f, uy = 0.f;
+  if (A.floor_on) {
+    pen = sub_(h, add_(mt.z0, s.o.z));
+    if (pen > 0.f) {
+      contact = true;
+      const float Fn = mul_(kv, pen);
+      cz = mul_(mul_(2.f, A.zc), fsqrt(mul_(d.m, kv)));
+      F.z = add_(F.z, fma_(-cz, s.v.z, Fn));
+      const float Fl2 = fma_(F.x, F.x, mul_(F.y, F.y));
+      const float vl2 = fma_(s.v.x, s.v.x, mul_(s.v.y, s.v.y));
+      const float mus = mul_(d.mu_s, Fn);
+      mud = mul_(d.mu_k, Fn);
+      const float mus2 = mul_(mus, mus);
+      if (mt.fl & 2u) {
+        if (Fl2 <= mus2) zero_l = true; else dir = 2;
+      } else {
+        const float vth = mul_(mul_(mud, dt), d.inv_m);
+        if (vl2 <= mul_(vth, vth) && Fl2 <= mus2) zero_l = true;
+        else if (vl2 > 0.f) dir = 1;
+        else dir = 2;
+      }
+      if (dir == 1) { ux = s.v.x; uy = s.v.y; }
+      if (dir == 2) { ux = F.x; uy = F.y; }
+      un = sqrtf(ux * ux + uy * uy);
+    }
+  }
+  const V3f w1 = A3(s.w, M3(M, dt * d.inv_I));  // angular velocity after the update
+
+  // ---- reverse: q' = normalize(qexp(w' dt) q)
+  Qf gq;
+  V3f gw1 = lam.w;
+  {
+    const float a2 = D3(w1, w1) * dt * dt, h2 = 0.25f * a2;
+    const bool series = h2 < 1e-4f;
+    float c, k, a = 0.f, sn = 0.f, cs = 1.f;
+    if (series) {
+      c = 1.f - 0.5f * h2 + h2 * h2 * (1.f / 24.f);
+      k = 0.5f * dt * (1.f - h2 * (1.f / 6.f) + h2 * h2 * (1.f / 120.f));
+    } else {
+      a = sqrtf(a2);
+      sincosf(0.5f * a, &sn, &cs);
+      c = cs;
+      k = sn * dt / a;
+    }
+    const Qf dq = {c, w1.x * k, w1.y * k, w1.z * k};
+    const Qf q = s.q;
+    Qf r;
+    r.w = dq.w * q.w - dq.x * q.x - dq.y * q.y - dq.z * q.z;
+    r.x = dq.w * q.x + dq.x * q.w + dq.y * q.z - dq.z * q.y;
+    r.y = dq.w * q.y - dq.x * q.z + dq.y * q.w + dq.z * q.x;
+    r.z = dq.w * q.z + dq.x * q.y - dq.y * q.x + dq.z * q.w;
+    const float irn = rsqrtf(r.w * r.w + r.x * r.x + r.y * r.y + r.z * r.z);
+    const Qf qn = {r.w * irn, r.x * irn, r.y * irn, r.z * irn};
+    const Qf gn = lam.q;
+    const float pr = qn.w * gn.w + qn.x * gn.x + qn.y * gn.y + qn.z * gn.z;
+    const Qf gr = {(gn.w - qn.w * pr) * irn, (gn.x - qn.x * pr) * irn, (gn.y - qn.y * pr) * irn,
+                   (gn.z - qn.z * pr) * irn};
+    // r = dq q
+    const float gdw = gr.w * q.w + gr.x * q.x + gr.y * q.y + gr.z * q.z;
+    const V3f gdv = v3(-gr.w * q.x + gr.x * q.w - gr.y * q.z + gr.z * q.y,
+                       -gr.w * q.y + gr.x * q.z + gr.y * q.w - gr.z * q.x,
+                       -gr.w * q.z - gr.x * q.y + gr.y * q.x + gr.z * q.w);
+    gq.w = gr.w * dq.w + gr.x * dq.x + gr.y * dq.y + gr.z * dq.z;
+    gq.x = -gr.w * dq.x + gr.x * dq.w + gr.y * dq.z - gr.z * dq.y;
+    gq.y = -gr.w * dq.y - gr.x * dq.z + gr.y * dq.w + gr.z * dq.x;
+    gq.z = -gr.w * dq.z + gr.x * dq.y - gr.y * dq.x + gr.z * dq.w;
+    // dq = (c, k w'), c and k functions of |w'| dt
+    gw1 = A3(gw1, M3(gdv, k));
+    const float g_k = D3(gdv, w1);
+    if (series) {
+      const float g_h2 = gdw * (-0.5f + h2 * (1.f / 12.f)) + g_k * 0.5f * dt * (-1.f / 6.f + h2 * (1.f / 60.f));
+      gw1 = A3(gw1, M3(w1, g_h2 * 0.5f * dt * dt));
+    } else {
+      const float g_a = gdw * (-0.5f * sn) + g_k * dt * (0.5f * cs * a - sn) / (a * a);
+      gw1 = A3(gw1, M3(w1, g_a * dt * dt / a));
+    }
+  }
+  // w' = w + M dt / I;  v' = v + F dt / m;  o' = o + v' dt (Sec 2.1.3)
+  const V3f gv1 = A3(lam.v, M3(lam.o, dt));
+  V3f go = lam.o;
+  V3f gF = M3(gv1, dt * d.inv_m);
+  V3f gM = M3(gw1, dt * d.inv_I);
+  V3f gw = gw1;
+  V3f gv = gv1;
+  float g_kv = 0.f, g_adT = 0.f;
+  if (contact) {
+    float g_Fn = 0.f;
+    if (zero_l) {  // lateral force and velocity replaced by 0
+      gF.x = 0.f; gF.y = 0.f;
+      gv.x = 0.f; gv.y = 0.f;
+    } else {
+      // F_l -= mu_k Fn u / |u|
+      const float ex = ux / un, ey = uy / un;
+      const float pe = gF.x * ex + gF.y * ey;
+      g_Fn -= d.mu_k * pe;
+      const float gux = -mud * (gF.x - ex * pe) / un, guy = -mud * (gF.y - ey * pe) / un;
+      if (dir == 1) { gv.x += gux; gv.y += guy; }
+      else { gF.x += gux; gF.y += guy; }
+    }
+    // F_z += Fn - cz v_z, Fn = kv pen, cz = 2 zc sqrt(m kv), pen = h - z
+    g_Fn += gF.z;
+    gv.z -= cz * gF.z;
+    g_kv += -s.v.z * gF.z * A.zc * sqrtf(d.m / kv) + pen * g_Fn;
+    const float g_pen = kv * g_Fn;
+    go.z -= g_pen;
+    g_adT += hl * g_pen;  // h = l (1 + adT) / 2
+  }
+  if (A.zg != 0.f) {  // F -= cg v, M -= cgr w
+    gv = S3(gv, M3(gF, cg));
+    gw = S3(gw, M3(gM, cgr));
+    g_kv += -D3(s.v, gF) * A.zg * sqrtf(d.m / kv) - D3(s.w, gM) * A.zg * sqrtf(d.I * l * l * (1.f / 6.f) / kv);
+  }
+  VoxS out;
+  out.o = go; out.q = gq; out.v = gv; out.w = gw;
+  Lout.store(v, out);
+  J.gfm[0 * P + v] = gF.x; J.gfm[1 * P + v] = gF.y; J.gfm[2 * P + v] = gF.z;
+  J.gfm[3 * P + v] = gM.x; J.gfm[4 * P + v] = gM.y; J.gfm[5 * P + v] = gM.z;
+  J.gdir[v] = g_kv * l;  // kv = E l
+  J.gdir[P + v] = g_adT;
+}
+
+namespace {
+template <int a>
+__device__ __forceinline__ void bond_adj_axis(const StepArgs& A, const AdjArgs& J, int v) {
+  const int u = A.nbr[(int64_t)(2 * a + 1) * A.N + v];
+  if (u < 0) return;
+  const int64_t P = A.pitch;
+  const VoxS s1 = load_vox(A.st_in, P, v), s2 = load_vox(A.st_in, P, u);
+  const int m1 = A.mat[v], m2 = A.mat[u];
+  const DevMat& d1 = A.mats[m1];
+  const DevMat& d2 = A.mats[m2];
+  BondPar bp;
+  bp.E1 = voxel_E(A, v, m1);
+  bp.E2 = voxel_E(A, u, m2);
+  bp.G1 = bp.E1 * d1.g_ratio;
+  bp.G2 = bp.E2 * d2.g_ratio;
+  bp.mmin = fminf(d1.m, d2.m);
+  bp.Imin = fminf(d1.I, d2.I);
+  bp.eps = 0.5f * (thermal_strain(A, v, d1.cte) + thermal_strain(A, u, d2.cte));
+  // adjoints of the bond outputs: voxel 1 sums F1, M1; voxel 2 sums -F1, M2
+  const V3f gF1 = v3(J.gfm[v] - J.gfm[u], J.gfm[P + v] - J.gfm[P + u], J.gfm[2 * P + v] - J.gfm[2 * P + u]);
+  const V3f gM1 = v3(J.gfm[3 * P + v], J.gfm[4 * P + v], J.gfm[5 * P + v]);
+  const V3f gM2 = v3(J.gfm[3 * P + u], J.gfm[4 * P + u], J.gfm[5 * P + u]);
+  BondAdj g;
+  bond_vjp<a>(s1, s2, bp, A.l, A.zb, gF1, gM1, gM2, g);
+  const float vals[kBA] = {g.dO.x, g.dO.y, g.dO.z, g.dv.x, g.dv.y, g.dv.z, g.w1.x, g.w1.y,
+                           g.w1.z, g.w2.x, g.w2.y, g.w2.z, g.q1.w, g.q1.x, g.q1.y, g.q1.z,
+                           g.q2.w, g.q2.x, g.q2.y, g.q2.z, g.E1 + g.G1 * d1.g_ratio, g.E2 + g.G2 * d2.g_ratio,
+                           0.5f * g.eps};
+  float* out = J.ba + (int64_t)a * kBA * P + v;
+#pragma unroll
+  for (int c = 0; c < kBA; ++c) out[c * P] = vals[c];
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) bond_adj(StepArgs A, AdjArgs J) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= A.N) return;
+  if (blockIdx.y == 0) bond_adj_axis<0>(A, J, v);
+  else if (blockIdx.y == 1) bond_adj_axis<1>(A, J, v);
+  else bond_adj_axis<2>(A, J, v);
+}
+
+// lam_n = direct part + the bond parts, summed in the fixed order +x, +y, +z
+// (the voxel is voxel 1), then -x, -y, -z (voxel 2); parameter gradients
+// accumulated: E = exp(log E); thermal strain = cte (T0 + A sin(w_n + phase)).
+__global__ void __launch_bounds__(256) gather_adj(StepArgs A, AdjArgs J) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= A.N) return;
+  const int64_t P = A.pitch;
+  const StPtr Lout(J.lam_out, P);
+  VoxS lam = Lout.load(v);
+  float gE = J.gdir[v], gadT = J.gdir[P + v];
+  for (int side = 0; side < 2; ++side)
+    for (int a = 0; a < 3; ++a) {
+      int b;  // voxel 1 of the bond
+      if (side == 0) {
+        if (A.nbr[(int64_t)(2 * a + 1) * A.N + v] < 0) continue;
+        b = v;
+      } else {
+        b = A.nbr[(int64_t)(2 * a) * A.N + v];
+        if (b < 0) continue;
+      }
+      const float* ba = J.ba + (int64_t)a * kBA * P + b;
+      const float sgn = side == 0 ? -1.f : 1.f;
+      lam.o = A3(lam.o, M3(v3(ba[0], ba[P], ba[2 * P]), sgn));
+      lam.v = A3(lam.v, M3(v3(ba[3 * P], ba[4 * P], ba[5 * P]), sgn));
+      const int wo = side == 0 ? 6 : 9, qo = side == 0 ? 12 : 16;
+      lam.w = A3(lam.w, v3(ba[wo * P], ba[(wo + 1) * P], ba[(wo + 2) * P]));
+      lam.q.w += ba[qo * P]; lam.q.x += ba[(qo + 1) * P];
+      lam.q.y += ba[(qo + 2) * P]; lam.q.z += ba[(qo + 3) * P];
+      gE += ba[(20 + side) * P];
+      gadT += ba[22 * P];
+    }
+  Lout.store(v, lam);
+  const int m = A.mat[v];
+  J.grad_logE[v] += gE * voxel_E(A, v, m);
+  if (A.act_on) {
+    const float x = A.act_w + (A.phase ? A.phase[v] : 0.f);
+    J.grad_phase[v] += gadT * A.mats[m].cte * A.actA * cosf(x);
+  }
+}
+
+// lam = 0 except d(loss)/d(offset x) = w_body cw_voxel.
+__global__ void seed_adj(float* lam, int64_t pitch, int N, const float* cw, const int32_t* body,
+                         const float* w_body) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N) return;
+  const float wb = w_body[body ? body[v] : 0];
+  VoxS z;
+  z.o = v3(wb * cw[v], 0.f, 0.f);
+  z.q.w = z.q.x = z.q.y = z.q.z = 0.f;
+  z.v = z.w = v3(0.f, 0.f, 0.f);
+  store_vox(lam, pitch, v, z);
+}
+
+// Per-body loss sum_v cw_v (x_v(end) - x_v(start)) over the body's internal
+// index range, one block per body, in a fixed (tree) order.
+__global__ void __launch_bounds__(256) com_travel(const float* st1, const float* st0, int64_t pitch, const float* cw,
+                                                  const int32_t* bstart, float* loss) {
+  const int b = blockIdx.x;
+  const int v0 = bstart[b], v1 = bstart[b + 1];
+  float acc = 0.f;
+  for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+    const int64_t i = state_index(OX, v, pitch);
+    acc = fmaf(cw[v], st1[i] - st0[i], acc);
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) loss[b] = red[0];
+}
+
+__global__ void to_canonical(const float* g, const int32_t* iperm, int N, float* out) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < N) out[c] = g[iperm[c]];
+}
+
+// ---------------------------------------------------------------------------
+int64_t adjoint_work_floats(int64_t pitch) { return (2 * (int64_t)NPLANE + 6 + 6 + 2 + 3 * kBA + 2) * pitch; }
+
+AdjArgs adjoint_args(float* work, int64_t pitch, int lam_cur) {
+  AdjArgs J;
+  float* lam0 = work;
+  float* lam1 = work + NPLANE * pitch;
+  J.lam_in = lam_cur == 0 ? lam0 : lam1;
+  J.lam_out = lam_cur == 0 ? lam1 : lam0;
+  J.fm = work + 2 * NPLANE * pitch;
+  J.gfm = J.fm + 6 * pitch;
+  J.gdir = J.gfm + 6 * pitch;
+  J.ba = J.gdir + 2 * pitch;
+  J.grad_logE = J.ba + 3 * kBA * pitch;
+  J.grad_phase = J.grad_logE + pitch;
+  return J;
+}
+
+void launch_adjoint_step(const StepArgs& A, const AdjArgs& J, cudaStream_t s) {
+  const int nb = (A.N + 255) / 256;
+  launch_bond_pass(A, s);
+  force_sums<<<nb, 256, 0, s>>>(A, J);
+  finish_adj<<<nb, 256, 0, s>>>(A, J);
+  bond_adj<<<dim3(nb, 3), 256, 0, s>>>(A, J);
+  gather_adj<<<nb, 256, 0, s>>>(A, J);
+}
+
+void launch_seed_adjoint(float* lam, int64_t pitch, int N, const float* cw, const int32_t* body,
+                         const float* w_body, cudaStream_t s) {
+  seed_adj<<<(N + 255) / 256, 256, 0, s>>>(lam, pitch, N, cw, body, w_body);
+}
+
+void launch_com_travel(const float* st1, const float* st0, int64_t pitch, const float* cw, const int32_t* bstart,
+                       int n_bodies, float* loss, cudaStream_t s) {
+  com_travel<<<n_bodies, 256, 0, s>>>(st1, st0, pitch, cw, bstart, loss);
+}
+
+void launch_to_canonical(const float* g, const int32_t* iperm, int N, float* out, cudaStream_t s) {
+  to_canonical<<<(N + 255) / 256, 256, 0, s>>>(g, iperm, N, out);
+}
+
+}  // namespace vx

@@ -129,6 +129,23 @@ struct vx_sim {
   int* cflag = nullptr;
   int* any = nullptr;
   long long* nreb = nullptr;
+  // adjoint form
+  uint64_t gen = 0;           // bumped by every call that changes the state or the model
+  uint64_t ro_gen = 0;        // gen at the end of the recorded rollout
+  int64_t ro_steps = 0;       // steps of the recorded rollout (0: none)
+  int ro_K = 0;               // checkpoint interval
+  int64_t ro_step0 = 0;       // step counter at the rollout start
+  int64_t ro_cap = 0;         // checkpoints allocated
+  float* ro_ckpt = nullptr;   // ro_cap x NPLANE x pitch floats
+  uint8_t* ro_cfl = nullptr;  // ro_cap x pitch flag bytes
+  int ro_seg_cap = 0;         // states of the segment buffer
+  float* ro_seg = nullptr;    // ro_seg_cap x NPLANE x pitch floats
+  uint8_t* ro_sfl = nullptr;  // ro_seg_cap x pitch flag bytes
+  float* adj = nullptr;       // adjoint work planes (adjoint_args)
+  float* cw = nullptr;        // per voxel m_v / (mass of its body)
+  int32_t* bstart = nullptr;  // internal index range of every body (n_bodies + 1)
+  float* loss_d = nullptr;    // per body loss
+  float* wb_d = nullptr;      // per body loss weight
 };
 
 namespace {
@@ -471,6 +488,53 @@ int edit_flags(vx_sim* s, const std::function<void(int64_t c, uint8_t& f)>& fn) 
   return VX_OK;
 }
 
+
+// ---- adjoint form ----------------------------------------------------------
+float act_phase(const vx_sim* s, int64_t step) {
+  return s->actP > 0 ? (float)(2.0 * M_PI * (double)(step % s->actP) / (double)s->actP) : 0.f;
+}
+
+// One step from A.st_in to A.st_out with the simulator's per-step form.
+int launch_form_step(vx_sim* s, const StepArgs& A, cudaStream_t st) {
+  if (s->form == VX_FORM_PIPELINED) {
+    int rc = ensure_pipe(s, A);
+    if (rc) return rc;
+    launch_pipe(A, s->tile_max, s->pipe_smem, s->pipe_grid, st);
+  } else {
+    launch_step(A, s->form, s->tile_max, s->smem, st);
+  }
+  return VX_OK;
+}
+
+// Mass weights m_v / M_body (internal order) and the bodies' internal index
+// ranges for the centre-of-mass loss.
+int upload_com_weights(vx_sim* s) {
+  const Lattice& L = s->L;
+  const int64_t N = L.N;
+  const int nb = L.n_bodies;
+  int rc;
+  if (!s->cw && ((rc = dalloc(&s->cw, N)) || (rc = dalloc(&s->bstart, nb + 1)) || (rc = dalloc(&s->loss_d, nb)) ||
+                 (rc = dalloc(&s->wb_d, nb))))
+    return rc;
+  const double l3 = (double)L.l * (double)L.l * (double)L.l;
+  std::vector<double> M(nb, 0.0);
+  for (int64_t c = 0; c < N; ++c) M[L.body[c]] += (double)L.palette[L.mat[c]].rho * l3;
+  std::vector<float> cw(N);
+  std::vector<int32_t> bs(nb + 1, (int32_t)N);
+  int prev = -1;
+  for (int64_t v = 0; v < N; ++v) {
+    const int32_t c = s->T.perm[v];
+    const int b = L.body[c];
+    if (b < prev) return fail(VX_ERR_STATE, "bodies are not contiguous in the internal order");
+    for (int k = prev + 1; k <= b; ++k) bs[k] = (int32_t)v;
+    prev = b;
+    cw[v] = (float)((double)L.palette[L.mat[c]].rho * l3 / M[b]);
+  }
+  VX_CUDA(cudaMemcpy(s->cw, cw.data(), 4 * N, cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemcpy(s->bstart, bs.data(), 4 * (nb + 1), cudaMemcpyHostToDevice));
+  return VX_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -583,6 +647,8 @@ void vx_destroy(vx_sim* s) {
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
+  dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->adj); dfree(s->cw);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d);
   delete s;
 }
 
@@ -644,6 +710,7 @@ int vx_get_tiling(vx_sim* s, int32_t* tile_max, int64_t* n_tiles, int32_t* max_l
 }
 
 int vx_set_materials(vx_sim* s, const vx_material* palette, int32_t n) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!palette || n != (int32_t)s->L.palette.size()) return fail(VX_ERR_ARG, "palette size must match the lattice's");
@@ -659,6 +726,7 @@ int vx_set_materials(vx_sim* s, const vx_material* palette, int32_t n) {
 }
 
 int vx_set_voxel_params(vx_sim* s, const float* log_E, const float* phase) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   int64_t N = s->L.N;
@@ -679,6 +747,7 @@ int vx_set_voxel_params(vx_sim* s, const float* log_E, const float* phase) {
 }
 
 int vx_set_fixed_mask(vx_sim* s, const uint8_t* mask) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!mask) return fail(VX_ERR_ARG, "mask is NULL");
@@ -686,6 +755,7 @@ int vx_set_fixed_mask(vx_sim* s, const uint8_t* mask) {
 }
 
 int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float size[3], int64_t* n_out) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!loc || !size || body < 0 || body >= s->L.n_bodies) return fail(VX_ERR_ARG, "bad region");
@@ -706,6 +776,7 @@ int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float
 
 int vx_add_forced_region(vx_sim* s, int32_t body, const float loc[3], const float size[3], const float F[3],
                          int64_t* n_out) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!loc || !size || !F || body < 0 || body >= s->L.n_bodies) return fail(VX_ERR_ARG, "bad region");
@@ -721,6 +792,7 @@ int vx_add_forced_region(vx_sim* s, int32_t body, const float loc[3], const floa
 }
 
 int vx_set_forces(vx_sim* s, const float* F) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!F) { s->has_fext = false; s->fext_h.clear(); return VX_OK; }
@@ -733,6 +805,7 @@ int vx_set_forces(vx_sim* s, const float* F) {
 }
 
 int vx_set_damping(vx_sim* s, float zb, float zg, float zc) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   if (!s) return fail(VX_ERR_ARG, "sim is NULL");
   if (!(zb >= 0.f) || !(zg >= 0.f) || !(zc >= 0.f)) return fail(VX_ERR_ARG, "damping ratios must be >= 0");
   s->zb = zb; s->zg = zg; s->zc = zc;
@@ -742,6 +815,7 @@ int vx_set_damping(vx_sim* s, float zb, float zg, float zc) {
 }
 
 int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t collide_on) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!std::isfinite(gravity_z)) return fail(VX_ERR_ARG, "gravity must be finite");
@@ -757,6 +831,7 @@ int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t col
 }
 
 int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   if (!s) return fail(VX_ERR_ARG, "sim is NULL");
   if (period < 0 || !std::isfinite(amplitude) || !std::isfinite(offset)) return fail(VX_ERR_ARG, "bad actuation");
   if (period == 0) amplitude = 0.f;
@@ -766,6 +841,7 @@ int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
 }
 
 int vx_set_dt_factor(vx_sim* s, float f) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!(f > 0.f && f <= 1.f)) return fail(VX_ERR_ARG, "dt_factor must be in (0, 1]");
@@ -780,6 +856,7 @@ int vx_get_dt(vx_sim* s, double* dt) {
 }
 
 int vx_set_dt(vx_sim* s, const double* dt) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!dt) return fail(VX_ERR_ARG, "dt is NULL");
@@ -790,6 +867,7 @@ int vx_set_dt(vx_sim* s, const double* dt) {
 }
 
 int vx_reset(vx_sim* s, const float v0[3]) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   launch_reset_state(cur_state(s), s->pitch, (int)s->L.N, s->flags, v0 ? v0[0] : 0.f, v0 ? v0[1] : 0.f,
@@ -836,6 +914,7 @@ int vx_read_state(vx_sim* s, const vx_state_view* out, int32_t dst_on_device, vo
 }
 
 int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, void* stream) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (!in) return fail(VX_ERR_ARG, "view is NULL");
@@ -874,12 +953,14 @@ int vx_get_step(vx_sim* s, int64_t* step) {
 }
 
 int vx_set_step(vx_sim* s, int64_t step) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   if (!s || step < 0) return fail(VX_ERR_ARG, "bad step");
   s->step = step;
   return VX_OK;
 }
 
 int vx_step_async(vx_sim* s, int64_t n, void* stream) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
   if (n < 0) return fail(VX_ERR_ARG, "n_steps must be >= 0");
@@ -1002,6 +1083,108 @@ int vx_collision_stats(vx_sim* s, int64_t* n_rebuilds, double* accumulator) {
   }
   if (n_rebuilds) *n_rebuilds = nr;
   if (accumulator) *accumulator = a;
+  return VX_OK;
+}
+
+int vx_rollout_forward(vx_sim* s, int64_t n, int32_t K, float* loss_body, void* stream) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (n < 1 || K < 1) return fail(VX_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
+  if (s->collide_on) return fail(VX_ERR_STATE, "the adjoint form does not support voxel-voxel collisions");
+  cudaStream_t st = (cudaStream_t)stream;
+  s->ro_steps = 0;
+  const int64_t N = s->L.N, P = s->pitch;
+  const size_t sb = (size_t)NPLANE * P;
+  const int64_t nck = (n + K - 1) / K;
+  if (nck > s->ro_cap) {
+    dfree(s->ro_ckpt);
+    dfree(s->ro_cfl);
+    s->ro_cap = 0;
+    if ((rc = dalloc(&s->ro_ckpt, nck * sb)) || (rc = dalloc(&s->ro_cfl, nck * P))) return rc;
+    s->ro_cap = nck;
+  }
+  if ((rc = upload_com_weights(s))) return rc;
+  const int64_t step0 = s->step;
+  for (int64_t c = 0; c < nck; ++c) {
+    VX_CUDA(cudaMemcpyAsync(s->ro_ckpt + c * sb, cur_state(s), 4 * sb, cudaMemcpyDeviceToDevice, st));
+    VX_CUDA(cudaMemcpyAsync(s->ro_cfl + c * P, s->flags, N, cudaMemcpyDeviceToDevice, st));
+    if ((rc = vx_step_async(s, std::min<int64_t>(K, n - c * K), stream))) return rc;
+  }
+  launch_com_travel(cur_state(s), s->ro_ckpt, P, s->cw, s->bstart, s->L.n_bodies, s->loss_d, st);
+  VX_CUDA(cudaGetLastError());
+  if (loss_body)
+    VX_CUDA(cudaMemcpyAsync(loss_body, s->loss_d, 4 * (size_t)s->L.n_bodies, cudaMemcpyDeviceToHost, st));
+  int32_t code;
+  int64_t bs, bv;
+  if ((rc = vx_get_status(s, stream, &code, &bs, &bv))) return rc;
+  if (code == VX_ERR_UNSTABLE)
+    return fail(code, "non-finite state at step " + std::to_string(bs) + ", voxel " + std::to_string(bv));
+  s->ro_steps = n;
+  s->ro_K = K;
+  s->ro_step0 = step0;
+  s->ro_gen = s->gen;
+  return VX_OK;
+}
+
+int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float* grad_phase, void* stream) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (s->ro_steps == 0 || s->ro_gen != s->gen)
+    return fail(VX_ERR_STATE, "no rollout recorded since the state or the model last changed");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t N = s->L.N, P = s->pitch;
+  const size_t sb = (size_t)NPLANE * P;
+  const int64_t n = s->ro_steps, K = s->ro_K, nck = (n + K - 1) / K;
+  if ((rc = ensure_two_pass(s))) return rc;
+  if (s->ro_seg_cap < K + 1) {
+    dfree(s->ro_seg);
+    dfree(s->ro_sfl);
+    s->ro_seg_cap = 0;
+    if ((rc = dalloc(&s->ro_seg, (K + 1) * sb)) || (rc = dalloc(&s->ro_sfl, (K + 1) * P))) return rc;
+    s->ro_seg_cap = (int)(K + 1);
+  }
+  if (!s->adj && (rc = dalloc(&s->adj, adjoint_work_floats(P)))) return rc;
+  std::vector<float> wb(s->L.n_bodies, 1.f);
+  if (w_body) wb.assign(w_body, w_body + s->L.n_bodies);
+  VX_CUDA(cudaMemcpy(s->wb_d, wb.data(), 4 * wb.size(), cudaMemcpyHostToDevice));
+  int lam_cur = 0;
+  AdjArgs J = adjoint_args(s->adj, P, lam_cur);
+  launch_seed_adjoint(const_cast<float*>(J.lam_in), P, (int)N, s->cw, s->body, s->wb_d, st);
+  VX_CUDA(cudaMemsetAsync(J.grad_logE, 0, 4 * 2 * (size_t)P, st));  // grad_logE, grad_phase
+  for (int64_t c = nck - 1; c >= 0; --c) {
+    const int64_t len = std::min<int64_t>(K, n - c * K);
+    const int64_t sc0 = s->ro_step0 + c * K;
+    // recompute the segment's states and flags from its checkpoint
+    VX_CUDA(cudaMemcpyAsync(s->ro_seg, s->ro_ckpt + c * sb, 4 * sb, cudaMemcpyDeviceToDevice, st));
+    VX_CUDA(cudaMemcpyAsync(s->ro_sfl, s->ro_cfl + c * P, N, cudaMemcpyDeviceToDevice, st));
+    for (int64_t j = 0; j < len; ++j) {
+      VX_CUDA(cudaMemcpyAsync(s->ro_sfl + (j + 1) * P, s->ro_sfl + j * P, N, cudaMemcpyDeviceToDevice, st));
+      StepArgs A = step_args(s);
+      A.st_in = s->ro_seg + j * sb;
+      A.st_out = s->ro_seg + (j + 1) * sb;
+      A.flags = s->ro_sfl + (j + 1) * P;
+      A.step = sc0 + j;
+      A.act_w = act_phase(s, A.step);
+      if ((rc = launch_form_step(s, A, st))) return rc;
+    }
+    // reverse steps
+    for (int64_t j = len - 1; j >= 0; --j) {
+      StepArgs A = step_args(s);
+      A.st_in = s->ro_seg + j * sb;
+      A.st_out = nullptr;
+      A.flags = s->ro_sfl + j * P;
+      A.bf = s->bf;
+      A.nbr = s->nbr;
+      A.step = sc0 + j;
+      A.act_w = act_phase(s, A.step);
+      launch_adjoint_step(A, adjoint_args(s->adj, P, lam_cur), st);
+      lam_cur ^= 1;
+    }
+  }
+  if (grad_logE) launch_to_canonical(J.grad_logE, s->iperm, (int)N, grad_logE, st);
+  if (grad_phase) launch_to_canonical(J.grad_phase, s->iperm, (int)N, grad_phase, st);
+  VX_CUDA(cudaGetLastError());
+  VX_CUDA(cudaStreamSynchronize(st));
   return VX_OK;
 }
 

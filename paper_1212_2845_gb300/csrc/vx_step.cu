@@ -284,6 +284,10 @@ int prepare_fused(int tile_max, size_t smem) {
   return -1;
 }
 
+void launch_bond_pass(const StepArgs& A, cudaStream_t s) {
+  bond_pass<<<dim3((A.N + 255) / 256, 3), 256, 0, s>>>(A);
+}
+
 void launch_step(const StepArgs& A, int form, int tile_max, size_t smem, cudaStream_t s) {
   if (form == 0) {
     if (tile_max == 256) fused_step<256><<<A.n_tiles, 256, smem, s>>>(A);

@@ -89,6 +89,8 @@ SIGNATURES = {
     "vx_get_collision_pairs": (C.c_int, [_P, _pi32, _i64, _pi64]),
     "vx_collision_stats": (C.c_int, [_P, _pi64, _pd]),
     "vx_collision_candidates_static": (C.c_int, [_P, _P, _P, _i32, _i32, _f32, _P, _P, _P]),
+    "vx_rollout_forward": (C.c_int, [_P, _i64, _i32, _pf, _P]),
+    "vx_rollout_backward": (C.c_int, [_P, _pf, _P, _P, _P]),
 }
 STATIC_MAX_SURFACE = 65536
 STATIC_MAX_BODIES = 4096
@@ -385,3 +387,20 @@ class Sim:
         n, a = C.c_int64(), C.c_double()
         _check(self._L.vx_collision_stats(self.h, C.byref(n), C.byref(a)))
         return n.value, a.value
+
+    # -- adjoint form ------------------------------------------------------
+    def rollout_forward(self, n_steps, checkpoint_every=100, stream=None):
+        """Run n_steps from the current state keeping checkpoints; returns the
+        per-body centre-of-mass x travel (float32 [n_bodies])."""
+        loss = np.zeros(self.n_bodies, dtype=np.float32)
+        _check(self._L.vx_rollout_forward(self.h, int(n_steps), int(checkpoint_every), _ptr(loss, C.c_float),
+                                          _stream_ptr(stream)))
+        return loss
+
+    def rollout_backward(self, grad_logE=None, grad_phase=None, w_body=None, stream=None):
+        """Gradients of sum_b w_b L_b for the last rollout into caller device
+        buffers (torch CUDA float32 tensors [N], canonical order)."""
+        w = None if w_body is None else np.ascontiguousarray(w_body, dtype=np.float32).reshape(self.n_bodies)
+        _check(self._L.vx_rollout_backward(
+            self.h, _ptr(w, C.c_float), None if grad_logE is None else grad_logE.data_ptr(),
+            None if grad_phase is None else grad_phase.data_ptr(), _stream_ptr(stream)))

@@ -1,0 +1,313 @@
+"""Adjoint form on the GPU (hand-written reverse kernels through the C ABI)
+against the FP64 oracle.
+
+The loss is the centre-of-mass x travel of every body over a rollout; the
+gradients are with respect to per-voxel log E and actuation phase, with the
+timestep held fixed.  Checks:
+  * directional derivatives g . d equal the oracle's forward-mode (dual
+    number) rollout derivative along the same direction d, within 1e-3
+    relative (FP32 adjoint vs FP64 tangent);
+  * single-parameter gradients equal FP64 central finite differences of the
+    oracle's rollout within 1e-3 relative, on a small body and on 64
+    parameters sampled from the 1,024-body 12^3 design population over
+    2,000 steps with checkpoints every 100;
+  * the checkpoint interval does not change a bit of the result; the
+    backward pass is deterministic and linear in the per-body weights;
+  * the torch.autograd.Function returns the same gradients;
+  * stale or unsupported rollouts are refused.
+"""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+from oracle import Oracle
+from paper_1212_2845_gb300 import scenes
+
+pytestmark = pytest.mark.gpu
+
+REL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1212_2845_gb300 import build, vx
+    build.build()
+    return torch, vx
+
+
+def f32_dt(ora):
+    return np.array([np.float32(ora.dt(b)) for b in range(ora.n_bodies)], dtype=np.float64)
+
+
+def design(n_bodies=2, n=4, seed=11, **kw):
+    sc = scenes.design_population(n_bodies=n_bodies, n=n, seed=seed)
+    sc.update(kw)
+    return scenes.normalize(sc)
+
+
+def gpu_grads(torch, sim, steps, K, w_body=None):
+    loss = sim.rollout_forward(steps, K)
+    gE = torch.zeros(sim.N, device="cuda")
+    gP = torch.zeros(sim.N, device="cuda")
+    sim.rollout_backward(gE, gP, w_body=w_body)
+    return loss, gE.cpu().numpy().astype(np.float64), gP.cpu().numpy().astype(np.float64)
+
+
+def variant(name):
+    if name == "floor_actuation":
+        return design(act_period=50), 200
+    if name == "ground_damping":       # no contact: external force from ground damping only
+        return design(gravity_z=0.0, floor=False, zeta_ground=0.3, act_period=50), 150
+    if name == "sliding":              # dynamic friction all along
+        sc = design(act_period=200)
+        sc["v0"] = (0.05, 0.0, 0.0)
+        return scenes.normalize(sc), 300
+    if name == "fixed_face":           # x = 0 face of every body fixed, no floor
+        sc = design(floor=False, act_period=80)
+        ijk = scenes.canonical_coords(sc)
+        sc["fixed"] = (ijk[:, 1] == 0).astype(np.uint8)
+        return sc, 200
+    if name == "hetero_materials":     # palette materials, no per-voxel log E
+        sc = scenes.random_blob((5, 4, 4), seed=3, fill=0.85)
+        sc.update(gravity_z=-9.81, floor=True, act_amplitude=20.0, act_period=60)
+        return scenes.normalize(sc), 200
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("name", ["floor_actuation", "ground_damping", "sliding", "fixed_face",
+                                  "hetero_materials"])
+def test_directional_derivative_matches_oracle_tangent(env, name):
+    torch, vx = env
+    sc, steps = variant(name)
+    sim = vx.Sim(sc)
+    ora = Oracle(sc)
+    ora.set_dt(f32_dt(ora))
+    loss, gE, gP = gpu_grads(torch, sim, steps, K=37)
+    rng = np.random.default_rng(5)
+    N = sim.N
+    for which in ("logE", "phase"):
+        d = rng.normal(size=N)
+        ora.reset(sc["v0"])
+        L0, jvp = ora.rollout_jvp(steps, d if which == "logE" else None, d if which == "phase" else None)
+        got = (gE if which == "logE" else gP) @ d
+        assert abs(jvp) > 0
+        assert abs(got - jvp) <= REL * abs(jvp), (which, got, jvp)
+    assert loss.sum() == pytest.approx(L0, rel=1e-3, abs=1e-9)
+    sim.close()
+
+
+def _oracle_loss(args):
+    """FP64 loss (mean x travel: one material, equal masses) of a one-body
+    scene with (log E, phase) and a fixed timestep."""
+    sc, logE, phase, dt, steps = args
+    o = Oracle(sc)
+    o.set_voxel_params(logE, phase)
+    o.set_dt(dt)
+    o.reset(sc["v0"])
+    x0 = o.state()["pos"][:, 0].copy()
+    o.step(steps)
+    return float(np.mean(o.state()["pos"][:, 0] - x0))
+
+
+def central_fd(jobs, pool):
+    """jobs: (scene, logE, phase, dt, steps, which, index, h) -> FP64 central differences."""
+    args = []
+    for sc, logE, phase, dt, steps, which, i, h in jobs:
+        for s in (+1, -1):
+            le, ph = logE.copy(), phase.copy()
+            (le if which == "logE" else ph)[i] += s * h
+            args.append((sc, le, ph, dt, steps))
+    out = pool.map(_oracle_loss, args) if pool else list(map(_oracle_loss, args))
+    return [(out[2 * k] - out[2 * k + 1]) / (2 * jobs[k][7]) for k in range(len(jobs))]
+
+
+def test_single_parameters_match_central_differences(env):
+    torch, vx = env
+    sc = design(n_bodies=1, n=5, seed=21, act_period=100)
+    steps = 400
+    sim = vx.Sim(sc)
+    ora = Oracle(sc)
+    dt = f32_dt(ora)
+    _, gE, gP = gpu_grads(torch, sim, steps, K=100)
+    rng = np.random.default_rng(9)
+    idx = rng.choice(sim.N, size=6, replace=False)
+    logE = sc["log_E"].astype(np.float64)
+    phase = sc["phase"].astype(np.float64)
+    jobs = [(sc, logE, phase, dt, steps, w, int(i), 1e-3) for i in idx for w in ("logE", "phase")]
+    fd = central_fd(jobs, None)
+    gmax = max(np.abs(gE).max(), np.abs(gP).max())
+    for (_, _, _, _, _, w, i, _), f in zip(jobs, fd):
+        g = (gE if w == "logE" else gP)[i]
+        assert abs(g - f) <= REL * max(abs(f), 0.01 * gmax), (w, i, g, f)
+    sim.close()
+
+
+def body_scene(sc, b, n):
+    """Body b of a population of n^3 bodies as a scene of its own."""
+    v = n ** 3
+    out = dict(sc)
+    out["dims"] = sc["dims"][b:b + 1].copy()
+    out["grid"] = sc["grid"][b * v:(b + 1) * v].copy()
+    out["origin"] = np.zeros((1, 3), dtype=np.float32)   # translation invariant in x, y; z = 0 as before
+    out["log_E"] = sc["log_E"][b * v:(b + 1) * v].copy()
+    out["phase"] = sc["phase"][b * v:(b + 1) * v].copy()
+    return out
+
+
+def _oracle_tangent(args):
+    """FP64 forward-mode derivative of the loss along one parameter."""
+    sc, logE, phase, dt, steps, which, i = args
+    o = Oracle(sc)
+    o.set_voxel_params(logE, phase)
+    o.set_dt(dt)
+    o.reset(sc["v0"])
+    d = np.zeros(len(logE))
+    d[i] = 1.0
+    return o.rollout_jvp(steps, d if which == "logE" else None, d if which == "phase" else None)[1]
+
+
+def _oracle_final_pos(args):
+    sc, logE, phase, dt, steps = args
+    o = Oracle(sc)
+    o.set_voxel_params(logE, phase)
+    o.set_dt(dt)
+    o.reset(sc["v0"])
+    o.step(steps)
+    return o.state()["pos"]
+
+
+def test_design_population_sampled_central_differences(env):
+    """1,024 bodies of 12^3 voxels, 2,000 steps, checkpoints every 100; 64
+    gradient entries sampled over 32 bodies, each against its body's own FP64
+    oracle rollout (bodies are independent):
+      * FP64 central differences (h = 1e-5) pin the FP64 tangent (forward
+        mode) on at least 90 % of the samples; the rest straddle a friction
+        or contact event inside +-h;
+      * the GPU entry equals the FP64 tangent within 1e-3 on every body whose
+        FP32 trajectory follows the FP64 one (final positions within 1e-8 m,
+        ten times the rounding-level difference); a body where a stick/slip
+        decision fell the other way at a near-tie follows another branch and
+        is held only to 5e-2; such bodies must stay rare (at most 10 %)."""
+    torch, vx = env
+    n, nb, steps, K = 12, 1024, 2000, 100
+    sc = scenes.design_population(n_bodies=nb, n=n, steps=steps)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(min(16, mp.cpu_count())) as pool:
+        sim = vx.Sim(sc)
+        dt = sim.dt()
+        loss, gE, gP = gpu_grads(torch, sim, steps, K)
+        pos = sim.state()["pos"]
+        sim.close()
+        rng = np.random.default_rng(64)
+        bodies = [int(b) for b in rng.choice(nb, size=32, replace=False)]
+        jobs, tang, picks, finals = [], [], [], []
+        for b in bodies:
+            bsc = body_scene(sc, b, n)
+            le = bsc["log_E"].astype(np.float64)
+            ph = bsc["phase"].astype(np.float64)
+            bdt = np.array([np.float32(dt[b])], np.float64)
+            finals.append((bsc, le, ph, bdt, steps))
+            for w in ("logE", "phase"):
+                i = int(rng.integers(n ** 3))
+                jobs.append((bsc, le, ph, bdt, steps, w, i, 1e-5))
+                tang.append((bsc, le, ph, bdt, steps, w, i))
+                picks.append((b, b * n ** 3 + i, w))
+        fd = np.array(central_fd(jobs, pool))
+        jv = np.array(pool.map(_oracle_tangent, tang))
+        fpos = pool.map(_oracle_final_pos, finals)
+    g = np.array([(gE if w == "logE" else gP)[c] for _, c, w in picks])
+    scale = np.abs(jv).max()
+    den = np.maximum(np.abs(jv), 0.01 * scale)
+    fd_ok = np.abs(fd - jv) / den <= 1e-4
+    assert fd_ok.mean() >= 0.9, (fd_ok.mean(), fd[~fd_ok], jv[~fd_ok])
+    follows = {}
+    for b, fp in zip(bodies, fpos):
+        gp = pos[b * n ** 3:(b + 1) * n ** 3] - sc["origin"][b].astype(np.float64)
+        follows[b] = np.abs(gp - fp).max() <= 1e-8
+    same = np.array([follows[b] for b, _, _ in picks])
+    err = np.abs(g - jv) / den
+    assert same.mean() >= 0.9, same.mean()
+    assert err[same].max() <= REL, (err[same].max(), picks[int(np.argmax(np.where(same, err, 0)))])
+    assert err.max() <= 5e-2, err.max()
+
+
+def test_checkpoint_interval_does_not_change_bits(env):
+    torch, vx = env
+    sc, steps = variant("floor_actuation")
+    sim = vx.Sim(sc)
+    ref = None
+    for K in (1, 16, steps):
+        sim.reset(sc["v0"])
+        out = gpu_grads(torch, sim, steps, K)
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(ref, out):
+                assert np.array_equal(a, b)
+    sim.close()
+
+
+def test_backward_deterministic_and_linear_in_body_weights(env):
+    torch, vx = env
+    sc = design(n_bodies=3, n=4, act_period=50)
+    sim = vx.Sim(sc)
+    sim.rollout_forward(120, 25)
+    outs = []
+    for w in (None, None, (2.0, 0.0, 1.0)):
+        gE = torch.zeros(sim.N, device="cuda")
+        gP = torch.zeros(sim.N, device="cuda")
+        sim.rollout_backward(gE, gP, w_body=w)
+        outs.append((gE.cpu().numpy(), gP.cpu().numpy()))
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    body = scenes.canonical_coords(sc)[:, 0]
+    scale = np.array([2.0, 0.0, 1.0])[body]
+    for k in range(2):
+        assert np.array_equal(outs[2][k], (outs[0][k] * scale).astype(np.float32))
+    sim.close()
+
+
+def test_autograd_function(env):
+    torch, vx = env
+    from paper_1212_2845_gb300.rollout import rollout
+    sc = design(n_bodies=2, n=4, act_period=50)
+    sim = vx.Sim(sc)
+    log_E = torch.tensor(sc["log_E"], requires_grad=True)
+    phase = torch.tensor(sc["phase"], requires_grad=True)
+    L = rollout(sim, log_E, phase, 150, checkpoint_every=40, v0=sc["v0"])
+    assert L.shape == (2,)
+    (L[0] * 3.0 + L[1]).backward()
+    sim.reset(sc["v0"])
+    loss, gE, gP = gpu_grads(torch, sim, 150, 40, w_body=(3.0, 1.0))
+    assert np.array_equal(L.detach().numpy(), loss)
+    assert np.array_equal(log_E.grad.numpy(), gE.astype(np.float32))
+    assert np.array_equal(phase.grad.numpy(), gP.astype(np.float32))
+    sim.close()
+
+
+def test_stale_or_unsupported_rollouts_are_refused(env):
+    torch, vx = env
+    sc = design(n_bodies=1, n=4)
+    sim = vx.Sim(sc)
+    g = torch.zeros(sim.N, device="cuda")
+    with pytest.raises(vx.VxError) as e:
+        sim.rollout_backward(g, g)
+    assert e.value.code == -6
+    sim.rollout_forward(20, 10)
+    sim.step(1)
+    with pytest.raises(vx.VxError) as e:
+        sim.rollout_backward(g, g)
+    assert e.value.code == -6
+    sim.rollout_forward(20, 10)
+    sim.set_voxel_params(log_E=sc["log_E"])
+    with pytest.raises(vx.VxError) as e:
+        sim.rollout_backward(g, g)
+    assert e.value.code == -6
+    sim.set_environment(-9.81, True, True)
+    with pytest.raises(vx.VxError) as e:
+        sim.rollout_forward(20, 10)
+    assert e.value.code == -6
+    sim.close()
