@@ -1,23 +1,24 @@
 // Reverse-mode (adjoint) kernels of one lattice step, for gradients of a
 // rollout loss with respect to per-voxel log stiffness and actuation phase.
 //
-// One adjoint step n takes the state S_n (recomputed from a checkpoint), the
-// flags at step n and the adjoint lam_{n+1} of S_{n+1}, and produces lam_n:
-//   bond_pass, force_sums  recompute the bond results and the bond force and
-//                          moment sums of every voxel with the forward step's
-//                          own arithmetic (same bits, so every friction
-//                          decision is replayed exactly)
-//   finish_adj             reverse of the voxel update (Sec 2.2.1 external
-//                          force and ground damping, Sec 2.2.2 floor contact
-//                          and Coulomb friction with its discrete decisions
-//                          frozen, Sec 2.1.3 integration with the quaternion
-//                          update): adjoints of the bond sums, the direct part
-//                          of lam_n, dL/dE and dL/d(thermal strain)
-//   bond_adj               reverse of every bond (co-rotational beam of
-//                          Sec 2.1.2, composite material of Sec 2.1.4, damping
-//                          of Sec 2.1.5, thermal rest length of Sec 2.3)
-//   gather_adj             lam_n of every voxel, summed in a fixed order, and
-//                          the parameter gradients accumulated
+// One adjoint step n takes the state S_n and the flags at step n (recomputed
+// from a checkpoint), the bond force and moment sums of every voxel at step n
+// (recorded by the same recomputation), and the adjoint lam_{n+1} of S_{n+1};
+// it produces lam_n in two launches:
+//   finish_adj   one thread per voxel: reverse of the voxel update (Sec 2.2.1
+//                external force and ground damping, Sec 2.2.2 floor contact
+//                and Coulomb friction with its discrete decisions replayed
+//                bit for bit, Sec 2.1.3 integration with the quaternion
+//                update): adjoints of the bond sums, the direct part of lam_n,
+//                dL/dE and dL/d(thermal strain) of the voxel itself
+//   adj_tile     one CTA per tile of the step's tiling, staged with its halo
+//                in shared memory like the forward step: reverse of every
+//                bond (co-rotational beam of Sec 2.1.2, composite material of
+//                Sec 2.1.4, damping of Sec 2.1.5, thermal rest length of
+//                Sec 2.3); each owned voxel keeps its own +x, +y, +z bonds'
+//                parts in registers and finds its -x, -y, -z parts in shared
+//                slots, sums them in a fixed order into lam_n and accumulates
+//                the parameter gradients.  Bond adjoints never leave the chip.
 // The timestep is a constant of the rollout (no derivative through dt).
 // Fixed voxels carry their adjoint through unchanged.  Voxel-voxel contact
 // (self-collision) has no adjoint here; the host refuses rollouts with it on.
@@ -77,8 +78,11 @@ template <int a>
 __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, float l, float zb, V3f gF1, V3f gM1,
                          V3f gM2, BondAdj& g) {
   // ---- forward values
+  // (derivative-only values: hardware reciprocal, reciprocal square root and
+  // fast division, a few ulp, are accurate enough)
   const float sE = bp.E1 + bp.E2, sG = bp.G1 + bp.G2;
-  const float Ec = 2.f * bp.E1 * bp.E2 / sE, Gc = 2.f * bp.G1 * bp.G2 / sG;
+  const float iE = __fdividef(1.f, sE), iG = __fdividef(1.f, sG);
+  const float Ec = 2.f * bp.E1 * bp.E2 * iE, Gc = 2.f * bp.G1 * bp.G2 * iG;
   const float l2 = l * l, l3 = l2 * l;
   const float a1 = Ec * l, a2 = Gc * l3 * (1.f / 6.f), b1 = a1, b2 = 0.5f * Ec * l2, b3 = Ec * l3 * (1.f / 6.f);
   const M3f R = qmat(s1.q);
@@ -100,7 +104,7 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   float f, fW, fs2;  // f = 2 atan2(s, W) / s and its partial derivatives in W and s^2
   if (s2q < 0.04f * W * W) {
     // f = (2 / W) Q(t2), Q(t2) = atan(t) / t, t2 = s^2 / W^2 (series to t^10)
-    const float iw = 1.f / W, t2 = s2q * iw * iw;
+    const float iw = __fdividef(1.f, W), t2 = s2q * iw * iw;
     const float P = 1.f / 3.f + t2 * (-0.2f + t2 * (1.f / 7.f + t2 * (-1.f / 9.f + t2 * (1.f / 11.f))));
     const float Pp = -0.2f + t2 * (2.f / 7.f + t2 * (-3.f / 9.f + t2 * (4.f / 11.f)));
     const float Q = 1.f - t2 * P, Qp = -P - t2 * Pp;
@@ -108,10 +112,10 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
     fW = -2.f * Q * iw * iw - 4.f * s2q * Qp * iw * iw * iw * iw;
     fs2 = 2.f * Qp * iw * iw * iw;
   } else {
-    const float s = sqrtf(s2q), at = atan2f(s, W), den = s2q + W * W;
-    f = 2.f * at / s;
-    fW = -2.f / den;
-    fs2 = (W / den - at / s) / s2q;
+    const float is = rsqrtf(s2q), s = s2q * is, at = atan2f(s, W), iden = __fdividef(1.f, s2q + W * W);
+    f = 2.f * at * is;
+    fW = -2.f * iden;
+    fs2 = (W * iden - at * is) * is * is;
   }
   const V3f th = to_axis<a>(M3(vq, f));
   const V3f F1w = from_axis<a>(v3(a1 * X, b1 * Y - b2 * th.z, b1 * Z + b2 * th.y));
@@ -126,8 +130,8 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   if (zb != 0.f) {
     // F1 += c2 dv + c4 (r x (w1 + w2)), M1 += cr2 dw, M2 -= cr2 dw with
     // c2 = zb sqrt(m a1), c4 = c2 / 2, cr2 = zb sqrt(I b3)
-    const float sqa = sqrtf(bp.mmin * a1), sqb = sqrtf(bp.Imin * b3);
-    const float c2 = zb * sqa, c4 = 0.5f * c2, cr2 = zb * sqb;
+    const float ra = rsqrtf(bp.mmin * a1), rb = rsqrtf(bp.Imin * b3);
+    const float c2 = zb * bp.mmin * a1 * ra, c4 = 0.5f * c2, cr2 = zb * bp.Imin * b3 * rb;
     V3f r = dO;
     if (a == 0) r.x += l; else if (a == 1) r.y += l; else r.z += l;
     const V3f ws = A3(s1.w, s2.w), rw = X3(r, ws);
@@ -141,8 +145,8 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
     g.w2 = A3(g_ws, g_dw);
     g_dO = X3(ws, g_rw);
     const float g_c2 = D3(gF1, dv) + 0.5f * D3(gF1, rw);
-    g_a1 += zb * g_c2 * 0.5f * bp.mmin / sqa;
-    g_b3 += zb * D3(gMd, dw) * 0.5f * bp.Imin / sqb;
+    g_a1 += zb * g_c2 * 0.5f * bp.mmin * ra;
+    g_b3 += zb * D3(gMd, dw) * 0.5f * bp.Imin * rb;
   }
   // F1 = R F1w, M1 = R M1w, M2 = R M2w
   M3f gR;
@@ -191,44 +195,16 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   // Ec, Gc harmonic means of the two voxels' moduli (Sec 2.1.4)
   const float g_Ec = l * g_a1 + 0.5f * l2 * g_b2 + l3 * (1.f / 6.f) * g_b3;
   const float g_Gc = l3 * (1.f / 6.f) * g_a2;
-  const float iE = 1.f / (sE * sE), iG = 1.f / (sG * sG);
-  g.E1 = g_Ec * 2.f * bp.E2 * bp.E2 * iE;
-  g.E2 = g_Ec * 2.f * bp.E1 * bp.E1 * iE;
-  g.G1 = g_Gc * 2.f * bp.G2 * bp.G2 * iG;
-  g.G2 = g_Gc * 2.f * bp.G1 * bp.G1 * iG;
+  const float hE = 2.f * g_Ec * iE * iE, hG = 2.f * g_Gc * iG * iG;
+  g.E1 = hE * bp.E2 * bp.E2;
+  g.E2 = hE * bp.E1 * bp.E1;
+  g.G1 = hG * bp.G2 * bp.G2;
+  g.G2 = hG * bp.G1 * bp.G1;
 }
-
-// Bond-adjoint planes per axis: dO (3), dv (3), w1 (3), w2 (3), q1 (4), q2 (4),
-// dE of voxel 1, dE of voxel 2 (shear modulus folded in), half of d(eps).
-constexpr int kBA = 23;
 
 }  // namespace
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) force_sums(StepArgs A, AdjArgs J) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= A.N) return;
-  const int64_t P = A.pitch, C = 3 * P;
-  // the forward step's gather: +x, +y, +z (F1, M1), then -x, -y, -z (-F1, M2)
-  V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
-  for (int a = 0; a < 3; ++a)
-    if (A.nbr[(int64_t)(2 * a + 1) * A.N + v] >= 0) {
-      const float* bf = A.bf + (int64_t)a * P + v;
-      F = add(F, v3(bf[0], bf[C], bf[2 * C]));
-      M = add(M, v3(bf[3 * C], bf[4 * C], bf[5 * C]));
-    }
-  for (int a = 0; a < 3; ++a) {
-    const int un = A.nbr[(int64_t)(2 * a) * A.N + v];
-    if (un >= 0) {
-      const float* bf = A.bf + (int64_t)a * P + un;
-      F = add(F, v3(-bf[0], -bf[C], -bf[2 * C]));
-      M = add(M, v3(bf[6 * C], bf[7 * C], bf[8 * C]));
-    }
-  }
-  J.fm[0 * P + v] = F.x; J.fm[1 * P + v] = F.y; J.fm[2 * P + v] = F.z;
-  J.fm[3 * P + v] = M.x; J.fm[4 * P + v] = M.y; J.fm[5 * P + v] = M.z;
-}
-
 // Reverse of voxel_finish without voxel-voxel contact.
 __global__ void __launch_bounds__(256) finish_adj(StepArgs A, AdjArgs J) {
   int v = blockIdx.x * blockDim.x + threadIdx.x;
@@ -389,84 +365,174 @@ __global__ void __launch_bounds__(256) finish_adj(StepArgs A, AdjArgs J) {
 }
 
 namespace {
-template <int a>
-__device__ __forceinline__ void bond_adj_axis(const StepArgs& A, const AdjArgs& J, int v) {
-  const int u = A.nbr[(int64_t)(2 * a + 1) * A.N + v];
-  if (u < 0) return;
-  const int64_t P = A.pitch;
-  const VoxS s1 = load_vox(A.st_in, P, v), s2 = load_vox(A.st_in, P, u);
-  const int m1 = A.mat[v], m2 = A.mat[u];
-  const DevMat& d1 = A.mats[m1];
-  const DevMat& d2 = A.mats[m2];
+
+// Shared memory of adj_tile<TMAX>: ML = 2 TMAX staged voxels (owned first,
+// then the halo) and the -a slots of the owned voxels.
+//   state A, B, C float4 [ML], D float [ML]  (the state planes)
+//   g4 float4 [ML] (dL/dF, dL/dM.x), g2 float2 [ML] (dL/dM.y, dL/dM.z)
+//   props float4 [ML]: E, G, thermal strain, material index (bits)
+//   slot float4 [4][3][TMAX]: voxel-2 part of the bond on the owned voxel's
+//        -a side: (o.xyz, v.x) (v.yz, w.xy) (w.z, q.wxy) (q.z, E, eps/2, -)
+//   mats DevMat [n_mats]
+template <int TMAX> struct AdjTile {
+  static constexpr int ML = 2 * TMAX;
+  static constexpr int kFloats = (NPLANE + 6 + 4) * ML + 48 * TMAX;
+  static size_t bytes(int n_mats) { return kFloats * sizeof(float) + (size_t)n_mats * sizeof(DevMat); }
+  float4 *A, *B, *C, *g4, *props, *slot;
+  float* D;
+  float2* g2;
+  DevMat* mats;
+  __device__ __forceinline__ explicit AdjTile(float* base) {
+    A = reinterpret_cast<float4*>(base);
+    B = A + ML;
+    C = B + ML;
+    g4 = C + ML;
+    props = g4 + ML;
+    slot = props + ML;
+    g2 = reinterpret_cast<float2*>(slot + 12 * TMAX);
+    D = reinterpret_cast<float*>(g2 + ML);
+    mats = reinterpret_cast<DevMat*>(D + ML);
+  }
+  __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
+  __device__ __forceinline__ V3f gF(int k) const { const float4 g = g4[k]; return v3(g.x, g.y, g.z); }
+  __device__ __forceinline__ V3f gM(int k) const { const float4 g = g4[k]; const float2 h = g2[k]; return v3(g.w, h.x, h.y); }
+};
+
+// Adjoint contributions to one voxel from its bonds (15 values).
+struct VoxAdj { V3f o, v, w; Qf q; float E, eps; };
+
+__device__ __forceinline__ VoxAdj voxadj_zero() {
+  VoxAdj r;
+  r.o = r.v = r.w = v3(0.f, 0.f, 0.f);
+  r.q.w = r.q.x = r.q.y = r.q.z = 0.f;
+  r.E = r.eps = 0.f;
+  return r;
+}
+__device__ __forceinline__ void voxadj_add(VoxAdj& r, const VoxAdj& b) {
+  r.o = A3(r.o, b.o); r.v = A3(r.v, b.v); r.w = A3(r.w, b.w);
+  r.q.w += b.q.w; r.q.x += b.q.x; r.q.y += b.q.y; r.q.z += b.q.z;
+  r.E += b.E; r.eps += b.eps;
+}
+
+// Reverse of the bond between staged voxels k1 (negative side) and k2 along
+// axis a; returns the voxel-1 part, stores the voxel-2 part in slot (a, k2)
+// when k2 is owned.
+template <int TMAX, int a>
+__device__ __forceinline__ VoxAdj tile_bond(const StepArgs& A, const AdjTile<TMAX>& S, int k1, int k2, int T) {
+  const VoxS s1 = S.vox(k1), s2 = S.vox(k2);
+  const float4 p1 = S.props[k1], p2 = S.props[k2];
+  const DevMat& d1 = S.mats[__float_as_int(p1.w)];
+  const DevMat& d2 = S.mats[__float_as_int(p2.w)];
   BondPar bp;
-  bp.E1 = voxel_E(A, v, m1);
-  bp.E2 = voxel_E(A, u, m2);
-  bp.G1 = bp.E1 * d1.g_ratio;
-  bp.G2 = bp.E2 * d2.g_ratio;
+  bp.E1 = p1.x; bp.E2 = p2.x; bp.G1 = p1.y; bp.G2 = p2.y;
   bp.mmin = fminf(d1.m, d2.m);
   bp.Imin = fminf(d1.I, d2.I);
-  bp.eps = 0.5f * (thermal_strain(A, v, d1.cte) + thermal_strain(A, u, d2.cte));
-  // adjoints of the bond outputs: voxel 1 sums F1, M1; voxel 2 sums -F1, M2
-  const V3f gF1 = v3(J.gfm[v] - J.gfm[u], J.gfm[P + v] - J.gfm[P + u], J.gfm[2 * P + v] - J.gfm[2 * P + u]);
-  const V3f gM1 = v3(J.gfm[3 * P + v], J.gfm[4 * P + v], J.gfm[5 * P + v]);
-  const V3f gM2 = v3(J.gfm[3 * P + u], J.gfm[4 * P + u], J.gfm[5 * P + u]);
+  bp.eps = 0.5f * (p1.z + p2.z);
   BondAdj g;
-  bond_vjp<a>(s1, s2, bp, A.l, A.zb, gF1, gM1, gM2, g);
-  const float vals[kBA] = {g.dO.x, g.dO.y, g.dO.z, g.dv.x, g.dv.y, g.dv.z, g.w1.x, g.w1.y,
-                           g.w1.z, g.w2.x, g.w2.y, g.w2.z, g.q1.w, g.q1.x, g.q1.y, g.q1.z,
-                           g.q2.w, g.q2.x, g.q2.y, g.q2.z, g.E1 + g.G1 * d1.g_ratio, g.E2 + g.G2 * d2.g_ratio,
-                           0.5f * g.eps};
-  float* out = J.ba + (int64_t)a * kBA * P + v;
-#pragma unroll
-  for (int c = 0; c < kBA; ++c) out[c * P] = vals[c];
+  bond_vjp<a>(s1, s2, bp, A.l, A.zb, S3(S.gF(k1), S.gF(k2)), S.gM(k1), S.gM(k2), g);
+  if (k2 < T) {
+    float4* sl = S.slot + a * TMAX + k2;
+    sl[0] = make_float4(g.dO.x, g.dO.y, g.dO.z, g.dv.x);
+    sl[3 * TMAX] = make_float4(g.dv.y, g.dv.z, g.w2.x, g.w2.y);
+    sl[6 * TMAX] = make_float4(g.w2.z, g.q2.w, g.q2.x, g.q2.y);
+    sl[9 * TMAX] = make_float4(g.q2.z, g.E2 + g.G2 * d2.g_ratio, 0.5f * g.eps, 0.f);
+  }
+  VoxAdj r;
+  r.o = v3(-g.dO.x, -g.dO.y, -g.dO.z);
+  r.v = v3(-g.dv.x, -g.dv.y, -g.dv.z);
+  r.w = g.w1;
+  r.q = g.q1;
+  r.E = g.E1 + g.G1 * d1.g_ratio;
+  r.eps = 0.5f * g.eps;
+  return r;
 }
+
+template <int TMAX>
+__device__ __forceinline__ VoxAdj read_slot(const AdjTile<TMAX>& S, int a, int k) {
+  const float4* sl = S.slot + a * TMAX + k;
+  const float4 x = sl[0], y = sl[3 * TMAX], z = sl[6 * TMAX], u = sl[9 * TMAX];
+  VoxAdj r;
+  r.o = v3(x.x, x.y, x.z);
+  r.v = v3(x.w, y.x, y.y);
+  r.w = v3(y.z, y.w, z.x);
+  r.q.w = z.y; r.q.x = z.z; r.q.y = z.w; r.q.z = u.x;
+  r.E = u.y;
+  r.eps = u.z;
+  return r;
+}
+
+// Material-dependent values of one staged voxel: E, G, thermal strain, material.
+__device__ __forceinline__ float4 adj_props(const StepArgs& A, int64_t g, const DevMat& d, int m) {
+  const float E = voxel_E(A, g, m);
+  return make_float4(E, E * d.g_ratio, thermal_strain(A, g, d.cte), __int_as_float(m));
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(256) bond_adj(StepArgs A, AdjArgs J) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= A.N) return;
-  if (blockIdx.y == 0) bond_adj_axis<0>(A, J, v);
-  else if (blockIdx.y == 1) bond_adj_axis<1>(A, J, v);
-  else bond_adj_axis<2>(A, J, v);
-}
-
-// lam_n = direct part + the bond parts, summed in the fixed order +x, +y, +z
-// (the voxel is voxel 1), then -x, -y, -z (voxel 2); parameter gradients
-// accumulated: E = exp(log E); thermal strain = cte (T0 + A sin(w_n + phase)).
-__global__ void __launch_bounds__(256) gather_adj(StepArgs A, AdjArgs J) {
-  int v = blockIdx.x * blockDim.x + threadIdx.x;
-  if (v >= A.N) return;
+template <int TMAX>
+__global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 2 : 4)) adj_tile(StepArgs A, AdjArgs J) {
+  extern __shared__ __align__(16) float smem[];
+  const AdjTile<TMAX> S(smem);
+  const int i = threadIdx.x;
+  const int4 ta = A.tile_a[blockIdx.x];
+  const int4 tb = A.tile_b[blockIdx.x];
+  const int v0 = ta.x, T = ta.y, NL = ta.y + ta.w;
+  const bool own = i < T;
+  const int v = v0 + i;
   const int64_t P = A.pitch;
+  const StPtr G(const_cast<float*>(A.st_in), P);
+  for (int j = i; j < A.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
+    reinterpret_cast<float*>(S.mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
+  // ---- staging: state, bond-sum adjoints and properties of owned + halo voxels
+  for (int k = i; k < NL; k += TMAX) {
+    const int g = k < T ? v0 + k : A.halo[ta.z + k - T];
+    S.A[k] = G.A[g]; S.B[k] = G.B[g]; S.C[k] = G.C[g]; S.D[k] = G.D[g];
+    S.g4[k] = make_float4(J.gfm[g], J.gfm[P + g], J.gfm[2 * P + g], J.gfm[3 * P + g]);
+    S.g2[k] = make_float2(J.gfm[4 * P + g], J.gfm[5 * P + g]);
+  }
+  __syncthreads();
+  for (int k = i; k < NL; k += TMAX) {
+    const int g = k < T ? v0 + k : A.halo[ta.z + k - T];
+    const int m = A.mat[g];
+    S.props[k] = adj_props(A, g, S.mats[m], m);
+  }
+  __syncthreads();
+  // ---- own +x, +y, +z bonds (voxel-1 part kept), halo bonds
+  VoxAdj acc = voxadj_zero();
+  if (own) {
+    const int px = A.plus[v], py = A.plus[A.N + v], pz = A.plus[2 * A.N + v];
+    if (px != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 0>(A, S, i, px, T));
+    if (py != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 1>(A, S, i, py, T));
+    if (pz != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 2>(A, S, i, pz, T));
+  }
+  for (int j = tb.x + i; j < tb.y; j += TMAX) {
+    const uint32_t pk = A.hbonds[j];
+    const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
+    if (ax == 0) tile_bond<TMAX, 0>(A, S, s1, s2, T);
+    else if (ax == 1) tile_bond<TMAX, 1>(A, S, s1, s2, T);
+    else tile_bond<TMAX, 2>(A, S, s1, s2, T);
+  }
+  __syncthreads();
+  if (!own) return;
+  // ---- lam_n = direct part + own bonds (+x, +y, +z) + -x, -y, -z slots
+  const uint32_t mask = A.mask[v];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    if (mask & (1u << (2 * a))) voxadj_add(acc, read_slot<TMAX>(S, a, i));
   const StPtr Lout(J.lam_out, P);
   VoxS lam = Lout.load(v);
-  float gE = J.gdir[v], gadT = J.gdir[P + v];
-  for (int side = 0; side < 2; ++side)
-    for (int a = 0; a < 3; ++a) {
-      int b;  // voxel 1 of the bond
-      if (side == 0) {
-        if (A.nbr[(int64_t)(2 * a + 1) * A.N + v] < 0) continue;
-        b = v;
-      } else {
-        b = A.nbr[(int64_t)(2 * a) * A.N + v];
-        if (b < 0) continue;
-      }
-      const float* ba = J.ba + (int64_t)a * kBA * P + b;
-      const float sgn = side == 0 ? -1.f : 1.f;
-      lam.o = A3(lam.o, M3(v3(ba[0], ba[P], ba[2 * P]), sgn));
-      lam.v = A3(lam.v, M3(v3(ba[3 * P], ba[4 * P], ba[5 * P]), sgn));
-      const int wo = side == 0 ? 6 : 9, qo = side == 0 ? 12 : 16;
-      lam.w = A3(lam.w, v3(ba[wo * P], ba[(wo + 1) * P], ba[(wo + 2) * P]));
-      lam.q.w += ba[qo * P]; lam.q.x += ba[(qo + 1) * P];
-      lam.q.y += ba[(qo + 2) * P]; lam.q.z += ba[(qo + 3) * P];
-      gE += ba[(20 + side) * P];
-      gadT += ba[22 * P];
-    }
+  lam.o = A3(lam.o, acc.o);
+  lam.v = A3(lam.v, acc.v);
+  lam.w = A3(lam.w, acc.w);
+  lam.q.w += acc.q.w; lam.q.x += acc.q.x; lam.q.y += acc.q.y; lam.q.z += acc.q.z;
   Lout.store(v, lam);
-  const int m = A.mat[v];
-  J.grad_logE[v] += gE * voxel_E(A, v, m);
+  // parameter gradients: E = exp(log E); thermal strain = cte (T0 + A sin(w_n + phase))
+  const float4 pr = S.props[i];
+  J.grad_logE[v] += (J.gdir[v] + acc.E) * pr.x;
   if (A.act_on) {
+    const int m = __float_as_int(pr.w);
     const float x = A.act_w + (A.phase ? A.phase[v] : 0.f);
-    J.grad_phase[v] += gadT * A.mats[m].cte * A.actA * cosf(x);
+    J.grad_phase[v] += (J.gdir[P + v] + acc.eps) * S.mats[m].cte * A.actA * cosf(x);
   }
 }
 
@@ -510,7 +576,7 @@ __global__ void to_canonical(const float* g, const int32_t* iperm, int N, float*
 }
 
 // ---------------------------------------------------------------------------
-int64_t adjoint_work_floats(int64_t pitch) { return (2 * (int64_t)NPLANE + 6 + 6 + 2 + 3 * kBA + 2) * pitch; }
+int64_t adjoint_work_floats(int64_t pitch) { return (2 * (int64_t)NPLANE + 6 + 2 + 2) * pitch; }
 
 AdjArgs adjoint_args(float* work, int64_t pitch, int lam_cur) {
   AdjArgs J;
@@ -518,24 +584,35 @@ AdjArgs adjoint_args(float* work, int64_t pitch, int lam_cur) {
   float* lam1 = work + NPLANE * pitch;
   J.lam_in = lam_cur == 0 ? lam0 : lam1;
   J.lam_out = lam_cur == 0 ? lam1 : lam0;
-  J.fm = work + 2 * NPLANE * pitch;
-  J.gfm = J.fm + 6 * pitch;
+  J.fm = nullptr;
+  J.gfm = work + 2 * NPLANE * pitch;
   J.gdir = J.gfm + 6 * pitch;
-  J.ba = J.gdir + 2 * pitch;
-  J.grad_logE = J.ba + 3 * kBA * pitch;
+  J.grad_logE = J.gdir + 2 * pitch;
   J.grad_phase = J.grad_logE + pitch;
   return J;
 }
 
-void launch_adjoint_step(const StepArgs& A, const AdjArgs& J, cudaStream_t s) {
-  const int nb = (A.N + 255) / 256;
-  launch_bond_pass(A, s);
-  force_sums<<<nb, 256, 0, s>>>(A, J);
-  finish_adj<<<nb, 256, 0, s>>>(A, J);
-  bond_adj<<<dim3(nb, 3), 256, 0, s>>>(A, J);
-  gather_adj<<<nb, 256, 0, s>>>(A, J);
+size_t adj_tile_smem_bytes(int tile_max, int n_mats) {
+  if (tile_max == 128) return AdjTile<128>::bytes(n_mats);
+  if (tile_max == 256) return AdjTile<256>::bytes(n_mats);
+  return AdjTile<512>::bytes(n_mats);
 }
 
+int prepare_adj_tile(int tile_max, size_t smem) {
+  cudaError_t e;
+  if (tile_max == 128) e = cudaFuncSetAttribute(adj_tile<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else if (tile_max == 256) e = cudaFuncSetAttribute(adj_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else if (tile_max == 512) e = cudaFuncSetAttribute(adj_tile<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  else return -1;
+  return e == cudaSuccess ? 0 : -1;
+}
+
+void launch_adjoint_step(const StepArgs& A, const AdjArgs& J, int tile_max, size_t smem, cudaStream_t s) {
+  finish_adj<<<(A.N + 255) / 256, 256, 0, s>>>(A, J);
+  if (tile_max == 128) adj_tile<128><<<A.n_tiles, 128, smem, s>>>(A, J);
+  else if (tile_max == 256) adj_tile<256><<<A.n_tiles, 256, smem, s>>>(A, J);
+  else adj_tile<512><<<A.n_tiles, 512, smem, s>>>(A, J);
+}
 void launch_seed_adjoint(float* lam, int64_t pitch, int N, const float* cw, const int32_t* body,
                          const float* w_body, cudaStream_t s) {
   seed_adj<<<(N + 255) / 256, 256, 0, s>>>(lam, pitch, N, cw, body, w_body);

@@ -141,6 +141,8 @@ struct vx_sim {
   int ro_seg_cap = 0;         // states of the segment buffer
   float* ro_seg = nullptr;    // ro_seg_cap x NPLANE x pitch floats
   uint8_t* ro_sfl = nullptr;  // ro_seg_cap x pitch flag bytes
+  float* ro_sfm = nullptr;    // (ro_seg_cap - 1) x 6 x pitch floats: bond sums of every segment step
+  size_t adj_smem = 0;        // dynamic shared memory adj_tile is prepared for
   float* adj = nullptr;       // adjoint work planes (adjoint_args)
   float* cw = nullptr;        // per voxel m_v / (mass of its body)
   int32_t* bstart = nullptr;  // internal index range of every body (n_bodies + 1)
@@ -199,6 +201,7 @@ StepArgs step_args(vx_sim* s) {
   A.cand = s->cand;
   A.vmax_bits = s->vmax;
   A.status = s->status;
+  A.fm_out = nullptr;
   return A;
 }
 
@@ -647,7 +650,8 @@ void vx_destroy(vx_sim* s) {
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
-  dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->adj); dfree(s->cw);
+  dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
+  dfree(s->cw);
   dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d);
   delete s;
 }
@@ -1135,15 +1139,23 @@ int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float*
   const int64_t N = s->L.N, P = s->pitch;
   const size_t sb = (size_t)NPLANE * P;
   const int64_t n = s->ro_steps, K = s->ro_K, nck = (n + K - 1) / K;
-  if ((rc = ensure_two_pass(s))) return rc;
   if (s->ro_seg_cap < K + 1) {
     dfree(s->ro_seg);
     dfree(s->ro_sfl);
+    dfree(s->ro_sfm);
     s->ro_seg_cap = 0;
-    if ((rc = dalloc(&s->ro_seg, (K + 1) * sb)) || (rc = dalloc(&s->ro_sfl, (K + 1) * P))) return rc;
+    if ((rc = dalloc(&s->ro_seg, (K + 1) * sb)) || (rc = dalloc(&s->ro_sfl, (K + 1) * P)) ||
+        (rc = dalloc(&s->ro_sfm, K * 6 * P)))
+      return rc;
     s->ro_seg_cap = (int)(K + 1);
   }
   if (!s->adj && (rc = dalloc(&s->adj, adjoint_work_floats(P)))) return rc;
+  const size_t asm_bytes = adj_tile_smem_bytes(s->tile_max, (int)s->L.palette.size());
+  if (asm_bytes != s->adj_smem) {
+    if (prepare_adj_tile(s->tile_max, asm_bytes) != 0)
+      return fail(VX_ERR_CUDA, "adjoint kernel needs " + std::to_string(asm_bytes) + " bytes of shared memory");
+    s->adj_smem = asm_bytes;
+  }
   std::vector<float> wb(s->L.n_bodies, 1.f);
   if (w_body) wb.assign(w_body, w_body + s->L.n_bodies);
   VX_CUDA(cudaMemcpy(s->wb_d, wb.data(), 4 * wb.size(), cudaMemcpyHostToDevice));
@@ -1154,7 +1166,7 @@ int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float*
   for (int64_t c = nck - 1; c >= 0; --c) {
     const int64_t len = std::min<int64_t>(K, n - c * K);
     const int64_t sc0 = s->ro_step0 + c * K;
-    // recompute the segment's states and flags from its checkpoint
+    // recompute the segment's states, flags and bond sums from its checkpoint
     VX_CUDA(cudaMemcpyAsync(s->ro_seg, s->ro_ckpt + c * sb, 4 * sb, cudaMemcpyDeviceToDevice, st));
     VX_CUDA(cudaMemcpyAsync(s->ro_sfl, s->ro_cfl + c * P, N, cudaMemcpyDeviceToDevice, st));
     for (int64_t j = 0; j < len; ++j) {
@@ -1163,6 +1175,7 @@ int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float*
       A.st_in = s->ro_seg + j * sb;
       A.st_out = s->ro_seg + (j + 1) * sb;
       A.flags = s->ro_sfl + (j + 1) * P;
+      A.fm_out = s->ro_sfm + j * 6 * P;
       A.step = sc0 + j;
       A.act_w = act_phase(s, A.step);
       if ((rc = launch_form_step(s, A, st))) return rc;
@@ -1173,11 +1186,11 @@ int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float*
       A.st_in = s->ro_seg + j * sb;
       A.st_out = nullptr;
       A.flags = s->ro_sfl + j * P;
-      A.bf = s->bf;
-      A.nbr = s->nbr;
       A.step = sc0 + j;
       A.act_w = act_phase(s, A.step);
-      launch_adjoint_step(A, adjoint_args(s->adj, P, lam_cur), st);
+      AdjArgs Jj = adjoint_args(s->adj, P, lam_cur);
+      Jj.fm = s->ro_sfm + j * 6 * P;
+      launch_adjoint_step(A, Jj, s->tile_max, s->adj_smem, st);
       lam_cur ^= 1;
     }
   }

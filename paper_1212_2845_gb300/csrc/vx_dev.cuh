@@ -83,7 +83,9 @@ struct StepArgs {
   const int32_t* cand;     // per surface voxel, kCandCap slots (internal indices, ascending)
   unsigned* vmax_bits;     // per body, float bits of max |v|
   int* status;             // [0] bits, [1] first bad voxel (internal), [2..3] step
+  float* fm_out;           // 6 planes: bond force and moment sum of every voxel, or nullptr
 };
+
 
 // ---------------------------------------------------------------------------
 // small vector / quaternion helpers (FP32)
@@ -322,6 +324,15 @@ __device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, cons
     o.M2 = axpy(o.M2, -k.cr2, dw);
   }
   return o;
+}
+
+// Stores the bond force and moment sums of voxel v when the caller asked for
+// them (the adjoint form records them while it recomputes a segment).
+__device__ __forceinline__ void store_bond_sums(const StepArgs& A, int64_t v, V3f F, V3f M) {
+  if (!A.fm_out) return;
+  float* o = A.fm_out + v;
+  const int64_t P = A.pitch;
+  o[0] = F.x; o[P] = F.y; o[2 * P] = F.z; o[3 * P] = M.x; o[4 * P] = M.y; o[5 * P] = M.z;
 }
 
 __device__ __forceinline__ void record_bad(const StepArgs& A, int v) {

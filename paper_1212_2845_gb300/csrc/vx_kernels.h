@@ -68,24 +68,25 @@ void launch_horizon(const CollideArgs& C, cudaStream_t s);
 // bond_pass of the two-pass form alone (bond results into A.bf)
 void launch_bond_pass(const StepArgs& A, cudaStream_t s);
 
-// Adjoint form: buffers of one reverse step (pitch floats per plane, all in
-// one work array laid out by adjoint_args).
+// Adjoint form: buffers of one reverse step (pitch floats per plane; all
+// but fm live in one work array laid out by adjoint_args).
 struct AdjArgs {
   const float* lam_in;   // adjoint of the state at step n + 1 (state layout)
   float* lam_out;        // adjoint of the state at step n (state layout)
-  float* fm;             // 6 planes: bond force and moment sums (recomputed)
+  const float* fm;       // 6 planes: bond force and moment sums at step n (recorded)
   float* gfm;            // 6 planes: their adjoints
-  float* gdir;           // 2 planes: direct dL/dE and dL/d(thermal strain)
-  float* ba;             // 3 axes x 23 planes: per-bond adjoints
+  float* gdir;           // 2 planes: the voxel's own dL/dE and dL/d(thermal strain)
   float* grad_logE;      // accumulated dL/d(log E), internal order
   float* grad_phase;     // accumulated dL/d(phase), internal order
 };
 int64_t adjoint_work_floats(int64_t pitch);
 // lam_cur: which of the two adjoint state buffers holds lam_{n+1}
 AdjArgs adjoint_args(float* work, int64_t pitch, int lam_cur);
-// One reverse step: A.st_in = S_n, A.flags = flags at step n, A.bf and A.nbr
-// of the two-pass form, A.act_w / A.step of step n.
-void launch_adjoint_step(const StepArgs& A, const AdjArgs& J, cudaStream_t s);
+size_t adj_tile_smem_bytes(int tile_max, int n_mats);
+int prepare_adj_tile(int tile_max, size_t smem);
+// One reverse step: A.st_in = S_n, A.flags = flags at step n, A.act_w and
+// A.step of step n, the fused form's tile arrays; J.fm = bond sums at step n.
+void launch_adjoint_step(const StepArgs& A, const AdjArgs& J, int tile_max, size_t smem, cudaStream_t s);
 void launch_seed_adjoint(float* lam, int64_t pitch, int N, const float* cw, const int32_t* body,
                          const float* w_body, cudaStream_t s);
 // loss[b] = sum over the body's internal range of cw (x(end) - x(start))

@@ -226,6 +226,7 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
     mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
     mt.fext = S.fx ? v3(S.fx[i], S.fx[TMAX + i], S.fx[2 * TMAX + i]) : v3(0.f, 0.f, 0.f);
     body = mt.b;
+    store_bond_sums(A, cur.v0 + i, F, M);
     speed = voxel_finish(A, cur.v0 + i, mt, s, F, M, pr.z, pr.x, mats);
   }
   if (A.collide_on) horizon_max(A, body, own, speed);

@@ -84,6 +84,7 @@ __global__ void __launch_bounds__(256) voxel_pass(StepArgs A) {
       }
     }
     VoxS s = load_vox(A.st_in, P, v);
+    store_bond_sums(A, v, F, M);
     speed = voxel_finish(A, v, mt, s, F, M, thermal_strain(A, v, A.mats[mt.m].cte), voxel_E(A, v, mt.m), A.mats);
   }
   if (A.collide_on) horizon_max(A, body, active, speed);
@@ -260,6 +261,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? VX_CTAS
         F = add(F, v3(f.x, f.y, f.z));
         M = add(M, v3(f.w, g.x, g.y));
       }
+    store_bond_sums(A, v, F, M);
     speed = voxel_finish(A, v, mt, s, F, M, pr.z, pr.x, S.mats);
   }
   if (A.collide_on) horizon_max(A, own ? mt.b : 0, own, speed);
