@@ -200,6 +200,108 @@ def large_lattice(stream, peak, steps=200, warmup=5):
     return out
 
 
+def _events_time(stream, fn):
+    """Seconds taken on `stream` by what fn() enqueues (CUDA events)."""
+    import torch
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    fn()
+    b.record(stream)
+    stream.synchronize()
+    return a.elapsed_time(b) * 1e-3
+
+
+def batched_form(stream, peak, n_bodies=4096, steps=200, warmup=5):
+    """Population of independent bodies (edges U{4..24}, seed 4): the plain
+    per-step launches against the autotuned batched form replayed as one
+    captured launch of `steps` steps.  State ~0.47 GB: larger than L2."""
+    from paper_1212_2845_gb300 import vx
+    sc = scenes.population(n_bodies=n_bodies)
+    sim = vx.Sim(sc)
+    N = sim.N
+    b_alg = 112
+    sim.step(warmup)
+    t_plain = _events_time(stream, lambda: sim.step_async(steps, stream))
+    st0 = sim.status(stream)[0]
+    tm, gv, rate = sim.autotune_batching(20, stream)
+    if gv == 0:                      # per-step launches won the sample: still time a batched launch
+        sim.set_batching(4096)
+    sim.graph_capture(steps, stream)
+    sim.graph_launch(stream)         # warm-up replay
+    t_graph = _events_time(stream, lambda: sim.graph_launch(stream))
+    st1 = sim.status(stream)[0]
+    if st0 or st1:
+        raise RuntimeError("population became unstable")
+    out = {"workload": f"population_{n_bodies} (edges U{{4..24}}, seed 4)", "voxels": N, "bonds": sim.n_bonds,
+           "steps": steps, "l2": "inputs larger than L2", "bytes_per_voxel_step": b_alg,
+           "per_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
+                        "frac": b_alg * N * steps / t_plain / 1e9 / peak, "kernel": "fused_pipe<256>"},
+           "batched": {"value": N * steps / t_graph, "unit": METRIC, "ms_per_step": 1e3 * t_graph / steps,
+                       "frac": b_alg * N * steps / t_graph / 1e9 / peak, "kernel": f"batched_pipe<{sim.tiling()['tile_max']}>",
+                       "launch": "one captured CUDA graph replay", "group_voxels": gv if gv else 4096},
+           "autotune": {"tile_max": tm, "group_voxels": gv, "sample_voxel_steps_per_s": rate, "sample_steps": 20}}
+    sim.close()
+    return out
+
+
+def adjoint_form(stream, peak, n_bodies=1024, steps=2000, K=100):
+    """Design population (n_bodies x 12^3, per-voxel log E and phase, seed 5):
+    the plain per-step launches against the adjoint rollout (forward with
+    checkpoints every K steps + backward with recomputation) over `steps`."""
+    import torch
+    from paper_1212_2845_gb300 import vx
+    sc = scenes.design_population(n_bodies=n_bodies, steps=steps)
+    sim = vx.Sim(sc)
+    N = sim.N
+    sim.step(5)
+    t_plain = _events_time(stream, lambda: sim.step_async(200, stream)) / 200 * steps
+    sim.reset(sc["v0"])
+    gE = torch.empty(N, device="cuda")
+    gP = torch.empty(N, device="cuda")
+    with torch.cuda.stream(stream):
+        sim.rollout_forward(steps, K, stream)          # warm-up: allocations, kernel preparation
+        sim.rollout_backward(gE, gP, stream=stream)
+        sim.reset(sc["v0"])
+        t_fwd = _events_time(stream, lambda: sim.rollout_forward(steps, K, stream))
+        t_bwd = _events_time(stream, lambda: sim.rollout_backward(gE, gP, stream=stream))
+    b_fwd, b_bwd = 116, 290
+    out = {"workload": f"design_population_{n_bodies}x12^3 (log E, phase per voxel, seed 5)", "voxels": N,
+           "bonds": sim.n_bonds, "steps": steps, "checkpoint_every": K, "l2": "inputs larger than L2",
+           "plain_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
+                          "frac": b_fwd * N * steps / t_plain / 1e9 / peak},
+           "rollout_forward": {"value": N * steps / t_fwd, "unit": METRIC, "s": t_fwd},
+           "backward": {"value": N * steps / t_bwd, "unit": METRIC, "s": t_bwd,
+                        "bytes_per_voxel_step": b_bwd, "frac": b_bwd * N * steps / t_bwd / 1e9 / peak,
+                        "kernels": "fused_pipe<256> (recompute) + finish_adj + adj_tile<256>"},
+           "gradient": {"value": N * steps / (t_fwd + t_bwd), "unit": METRIC,
+                        "cost_vs_plain_rollout": (t_fwd + t_bwd) / t_plain}}
+    sim.close()
+    return out
+
+
+def small_lattice(stream, steps=1000):
+    """Cantilever 10x10x10 (1,000 voxels): latency-bound.  Per-step launches
+    against one captured persistent launch of all steps (batched form, one
+    group: the body stays in one CTA's hands for every step)."""
+    from paper_1212_2845_gb300 import vx
+    sc = scenes.cantilever()
+    sim = vx.Sim(sc)
+    sim.step(10)
+    t_plain = _events_time(stream, lambda: sim.step_async(steps, stream))
+    sim.set_batching(1 << 20)
+    sim.graph_capture(steps, stream)
+    sim.graph_launch(stream)
+    t_graph = _events_time(stream, lambda: sim.graph_launch(stream))
+    if sim.status(stream)[0]:
+        raise RuntimeError("cantilever became unstable")
+    out = {"workload": "cantilever_10x10x10", "voxels": sim.N, "steps": steps,
+           "per_step_launches": {"steps_per_s": steps / t_plain, "us_per_step": 1e6 * t_plain / steps},
+           "one_captured_launch": {"steps_per_s": steps / t_graph, "us_per_step": 1e6 * t_graph / steps}}
+    sim.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -211,6 +313,11 @@ def main():
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--only-large", action="store_true",
                     help="time only the large-shell plain step (profiling aid)")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint / small-lattice lines")
+    ap.add_argument("--only-adjoint", action="store_true", help="time only the adjoint form (profiling aid)")
+    ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
+    ap.add_argument("--bodies", type=int, default=0, help="bodies for --only-adjoint / --only-batched")
+    ap.add_argument("--form-steps", type=int, default=0, help="steps for --only-adjoint / --only-batched")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     sc = scenes.hetero_block()
@@ -224,6 +331,16 @@ def main():
     if args.only_large:
         peak, _ = load_peaks()
         print(json.dumps(large_lattice(torch.cuda.Stream(), peak, steps=args.steps, warmup=args.warmup)))
+        return
+    if args.only_adjoint:
+        peak, _ = load_peaks()
+        print(json.dumps(adjoint_form(torch.cuda.Stream(), peak, n_bodies=args.bodies or 1024,
+                                      steps=args.form_steps or 2000)))
+        return
+    if args.only_batched:
+        peak, _ = load_peaks()
+        print(json.dumps(batched_form(torch.cuda.Stream(), peak, n_bodies=args.bodies or 4096,
+                                      steps=args.form_steps or 200)))
         return
     if ws > 1:
         import torch.distributed as dist
@@ -288,6 +405,9 @@ def main():
     }
     if not args.no_large:
         line["large_lattice"] = large_lattice(stream, peak)
+    if not args.no_forms:
+        line["forms"] = {"batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
+                         "small_lattice": small_lattice(stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
     print(json.dumps(line), flush=True)

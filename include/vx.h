@@ -241,6 +241,32 @@ VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int6
  * accumulator of body 0 [m]. */
 VX_API int vx_collision_stats(vx_sim* sim, int64_t* n_rebuilds, double* accumulator);
 
+/* ---- captured launches and autotuning of the batched form ---------------
+ * The paper steps one body per call; these serve populations of independent
+ * bodies (design automation, which the paper names as a use).
+ *
+ * vx_graph_capture: capture n_steps of the batched form (vx_set_batching
+ * must be on, collisions off) as one CUDA graph holding one persistent
+ * launch.  The captured kernel reads its first step number and state buffer
+ * from a device counter, so each replay continues from the current step.
+ * Any later change of the model or the step form (vx_set_* calls other than
+ * state writes) makes the graph stale; vx_graph_launch then returns
+ * VX_ERR_STATE until the next capture.
+ * vx_graph_launch: replay on `stream` (asynchronous; the status word is read
+ * by vx_get_status as after vx_step_async).
+ *
+ * vx_autotune_batching: time tile sizes {128, 256} x group sizes {per-step
+ * launches, 1024, 4096, 16384, 65536 voxels} on sample_steps steps from the
+ * current state (restored afterwards), keep the fastest for the lattice's
+ * size class (log2 voxels, log2 mean body size, per-voxel arrays in use) in
+ * a process-wide cache, and apply it.  A cached class is applied without
+ * timing.  Outputs (any may be NULL): tile size, group size (0 = per-step
+ * launches) and the sampled voxel-steps/s.  Synchronous. */
+VX_API int vx_graph_capture(vx_sim* sim, int64_t n_steps, void* stream);
+VX_API int vx_graph_launch(vx_sim* sim, void* stream);
+VX_API int vx_autotune_batching(vx_sim* sim, int32_t sample_steps, int32_t* tile_max, int64_t* group_voxels,
+                                double* voxel_steps_per_s, void* stream);
+
 /* ---- adjoint form: design gradients over a rollout ----------------------
  * The loss of body b is the x travel of its centre of mass over a rollout,
  *   L_b = sum_v m_v (x_v(n) - x_v(0)) / sum_v m_v,

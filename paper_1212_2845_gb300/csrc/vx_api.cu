@@ -7,6 +7,9 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <string>
 #include <vector>
 
@@ -131,6 +134,13 @@ struct vx_sim {
   long long* nreb = nullptr;
   // adjoint form
   uint64_t gen = 0;           // bumped by every call that changes the state or the model
+  uint64_t cfg = 0;           // bumped by every call that changes the model or the step form
+  // captured batched launch (vx_graph_capture)
+  cudaGraphExec_t gexec = nullptr;
+  int64_t g_n = 0;            // steps per replay
+  uint64_t g_cfg = 0;         // cfg at capture
+  int64_t* ctr_d = nullptr;   // device (step, buffer) read by the captured kernel
+  int64_t ctr_h[2] = {0, 0};
   uint64_t ro_gen = 0;        // gen at the end of the recorded rollout
   int64_t ro_steps = 0;       // steps of the recorded rollout (0: none)
   int ro_K = 0;               // checkpoint interval
@@ -492,6 +502,21 @@ int edit_flags(vx_sim* s, const std::function<void(int64_t c, uint8_t& f)>& fn) 
 }
 
 
+BatchArgs batch_args(vx_sim* s, int64_t n) {
+  BatchArgs Bt;
+  Bt.cta_start = s->b_cta_start;
+  Bt.cta_groups = s->b_cta_groups;
+  Bt.group_tiles = s->b_group_tiles;
+  Bt.buf0 = s->st;
+  Bt.buf1 = s->st + (size_t)NPLANE * s->pitch;
+  Bt.cur0 = s->cur;
+  Bt.n_steps = (int)n;
+  Bt.step0 = s->step;
+  Bt.act_P = s->actP;
+  Bt.ctr = nullptr;
+  return Bt;
+}
+
 // ---- adjoint form ----------------------------------------------------------
 float act_phase(const vx_sim* s, int64_t step) {
   return s->actP > 0 ? (float)(2.0 * M_PI * (double)(step % s->actP) / (double)s->actP) : 0.f;
@@ -536,6 +561,30 @@ int upload_com_weights(vx_sim* s) {
   VX_CUDA(cudaMemcpy(s->cw, cw.data(), 4 * N, cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemcpy(s->bstart, bs.data(), 4 * (nb + 1), cudaMemcpyHostToDevice));
   return VX_OK;
+}
+
+
+// ---- batched-form autotuning ------------------------------------------------
+// Size class of a lattice for the tuning cache: log2 of the voxel count, log2
+// of the mean body size, and the optional per-voxel arrays that change the
+// kernels' staging.
+struct TuneKey {
+  int lg_n, lg_body, lut, le, ph, fx;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(lg_n, lg_body, lut, le, ph, fx) < std::tie(o.lg_n, o.lg_body, o.lut, o.le, o.ph, o.fx);
+  }
+};
+struct TuneVal { int tile_max; int64_t group_voxels; double rate; };
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneVal> g_tune;
+
+int ilog2(int64_t x) { int r = 0; while (x > 1) { x >>= 1; ++r; } return r; }
+
+TuneKey tune_key(const vx_sim* s) {
+  const int64_t N = s->L.N;
+  return TuneKey{ilog2(N), ilog2(std::max<int64_t>(1, N / s->L.n_bodies)),
+                 (int)(s->L.palette.size() <= (size_t)kLutMaxMats && s->logE_h.empty()), (int)!s->logE_h.empty(),
+                 (int)s->has_phase, (int)s->has_fext};
 }
 
 }  // namespace
@@ -652,7 +701,8 @@ void vx_destroy(vx_sim* s) {
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
-  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d);
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
 
@@ -678,6 +728,7 @@ int vx_get_anchors(vx_sim* s, double* anchors) {
 }
 
 int vx_set_step_form(vx_sim* s, int32_t form, int32_t tile_max) {
+  if (s) ++s->cfg;  // invalidates a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (form != VX_FORM_FUSED && form != VX_FORM_TWO_PASS && form != VX_FORM_PIPELINED)
@@ -695,6 +746,7 @@ int vx_set_step_form(vx_sim* s, int32_t form, int32_t tile_max) {
 }
 
 int vx_set_batching(vx_sim* s, int64_t group_voxels) {
+  if (s) ++s->cfg;  // invalidates a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (group_voxels < 0) return fail(VX_ERR_ARG, "group_voxels must be >= 0");
@@ -714,7 +766,7 @@ int vx_get_tiling(vx_sim* s, int32_t* tile_max, int64_t* n_tiles, int32_t* max_l
 }
 
 int vx_set_materials(vx_sim* s, const vx_material* palette, int32_t n) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!palette || n != (int32_t)s->L.palette.size()) return fail(VX_ERR_ARG, "palette size must match the lattice's");
@@ -730,7 +782,7 @@ int vx_set_materials(vx_sim* s, const vx_material* palette, int32_t n) {
 }
 
 int vx_set_voxel_params(vx_sim* s, const float* log_E, const float* phase) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   int64_t N = s->L.N;
@@ -751,7 +803,7 @@ int vx_set_voxel_params(vx_sim* s, const float* log_E, const float* phase) {
 }
 
 int vx_set_fixed_mask(vx_sim* s, const uint8_t* mask) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!mask) return fail(VX_ERR_ARG, "mask is NULL");
@@ -759,7 +811,7 @@ int vx_set_fixed_mask(vx_sim* s, const uint8_t* mask) {
 }
 
 int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float size[3], int64_t* n_out) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!loc || !size || body < 0 || body >= s->L.n_bodies) return fail(VX_ERR_ARG, "bad region");
@@ -780,7 +832,7 @@ int vx_add_fixed_region(vx_sim* s, int32_t body, const float loc[3], const float
 
 int vx_add_forced_region(vx_sim* s, int32_t body, const float loc[3], const float size[3], const float F[3],
                          int64_t* n_out) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!loc || !size || !F || body < 0 || body >= s->L.n_bodies) return fail(VX_ERR_ARG, "bad region");
@@ -796,7 +848,7 @@ int vx_add_forced_region(vx_sim* s, int32_t body, const float loc[3], const floa
 }
 
 int vx_set_forces(vx_sim* s, const float* F) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!F) { s->has_fext = false; s->fext_h.clear(); return VX_OK; }
@@ -809,7 +861,7 @@ int vx_set_forces(vx_sim* s, const float* F) {
 }
 
 int vx_set_damping(vx_sim* s, float zb, float zg, float zc) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   if (!s) return fail(VX_ERR_ARG, "sim is NULL");
   if (!(zb >= 0.f) || !(zg >= 0.f) || !(zc >= 0.f)) return fail(VX_ERR_ARG, "damping ratios must be >= 0");
   s->zb = zb; s->zg = zg; s->zc = zc;
@@ -819,7 +871,7 @@ int vx_set_damping(vx_sim* s, float zb, float zg, float zc) {
 }
 
 int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t collide_on) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!std::isfinite(gravity_z)) return fail(VX_ERR_ARG, "gravity must be finite");
@@ -835,7 +887,7 @@ int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t col
 }
 
 int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   if (!s) return fail(VX_ERR_ARG, "sim is NULL");
   if (period < 0 || !std::isfinite(amplitude) || !std::isfinite(offset)) return fail(VX_ERR_ARG, "bad actuation");
   if (period == 0) amplitude = 0.f;
@@ -845,7 +897,7 @@ int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
 }
 
 int vx_set_dt_factor(vx_sim* s, float f) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!(f > 0.f && f <= 1.f)) return fail(VX_ERR_ARG, "dt_factor must be in (0, 1]");
@@ -860,7 +912,7 @@ int vx_get_dt(vx_sim* s, double* dt) {
 }
 
 int vx_set_dt(vx_sim* s, const double* dt) {
-  if (s) ++s->gen;  // invalidates a recorded rollout
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
   if (!dt) return fail(VX_ERR_ARG, "dt is NULL");
@@ -975,16 +1027,7 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     StepArgs A = step_args(s);
     if ((rc = ensure_pipe(s, A))) return rc;
     if ((int64_t)s->B.cta_start.size() != (int64_t)s->pipe_grid + 1 && (rc = build_schedule(s))) return rc;
-    BatchArgs Bt;
-    Bt.cta_start = s->b_cta_start;
-    Bt.cta_groups = s->b_cta_groups;
-    Bt.group_tiles = s->b_group_tiles;
-    Bt.buf0 = s->st;
-    Bt.buf1 = s->st + (size_t)NPLANE * s->pitch;
-    Bt.cur0 = s->cur;
-    Bt.n_steps = (int)n;
-    Bt.step0 = s->step;
-    Bt.act_P = s->actP;
+    BatchArgs Bt = batch_args(s, n);
     launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, st);
     s->cur ^= (int)(n & 1);
     s->step += n;
@@ -1198,6 +1241,132 @@ int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float*
   if (grad_phase) launch_to_canonical(J.grad_phase, s->iperm, (int)N, grad_phase, st);
   VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaStreamSynchronize(st));
+  return VX_OK;
+}
+
+int vx_graph_capture(vx_sim* s, int64_t n, void* stream) {
+  (void)stream;
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (n < 1 || n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps must be in [1, 2^31)");
+  if (s->group_voxels <= 0) return fail(VX_ERR_STATE, "graph capture takes the batched form (vx_set_batching)");
+  if (s->collide_on) return fail(VX_ERR_STATE, "the batched form has no voxel-voxel collisions");
+  StepArgs A = step_args(s);
+  if ((rc = ensure_pipe(s, A))) return rc;
+  if ((int64_t)s->B.cta_start.size() != (int64_t)s->pipe_grid + 1 && (rc = build_schedule(s))) return rc;
+  if (!s->ctr_d && (rc = dalloc(&s->ctr_d, 2))) return rc;
+  BatchArgs Bt = batch_args(s, n);
+  Bt.ctr = s->ctr_d;
+  cudaStream_t cs;
+  VX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, cs);
+    e = cudaStreamEndCapture(cs, &g);
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+  if (g) cudaGraphDestroy(g);
+  cudaStreamDestroy(cs);
+  if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  s->gexec = ge;
+  s->g_n = n;
+  s->g_cfg = s->cfg;
+  return VX_OK;
+}
+
+int vx_graph_launch(vx_sim* s, void* stream) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (!s->gexec || s->g_cfg != s->cfg)
+    return fail(VX_ERR_STATE, "no graph captured for the current model and step form");
+  ++s->gen;
+  cudaStream_t st = (cudaStream_t)stream;
+  s->ctr_h[0] = s->step;
+  s->ctr_h[1] = s->cur;
+  VX_CUDA(cudaMemcpyAsync(s->ctr_d, s->ctr_h, sizeof(s->ctr_h), cudaMemcpyHostToDevice, st));
+  VX_CUDA(cudaGraphLaunch(s->gexec, st));
+  s->cur ^= (int)(s->g_n & 1);
+  s->step += s->g_n;
+  return VX_OK;
+}
+
+int vx_autotune_batching(vx_sim* s, int32_t sample_steps, int32_t* tile_max_out, int64_t* group_voxels_out,
+                         double* rate_out, void* stream) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (sample_steps < 1) return fail(VX_ERR_ARG, "sample_steps must be >= 1");
+  if (s->collide_on) return fail(VX_ERR_STATE, "the batched form has no voxel-voxel collisions");
+  cudaStream_t st = (cudaStream_t)stream;
+  const TuneKey key = tune_key(s);
+  TuneVal best{0, -1, 0.0};
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) best = it->second;
+  }
+  if (best.group_voxels < 0) {
+    // time every candidate from the same state, then put the state back
+    const int64_t N = s->L.N, P = s->pitch;
+    const size_t sb = (size_t)NPLANE * P;
+    float* save = nullptr;
+    uint8_t* save_fl = nullptr;
+    if ((rc = dalloc(&save, sb)) || (rc = dalloc(&save_fl, N))) { dfree(save); return rc; }
+    const int64_t step0 = s->step;
+    const int cur0 = s->cur;
+    auto restore = [&]() -> int {
+      s->cur = cur0;
+      s->step = step0;
+      VX_CUDA(cudaMemcpyAsync(cur_state(s), save, 4 * sb, cudaMemcpyDeviceToDevice, st));
+      VX_CUDA(cudaMemcpyAsync(s->flags, save_fl, N, cudaMemcpyDeviceToDevice, st));
+      return VX_OK;
+    };
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    auto run = [&]() -> int {
+      VX_CUDA(cudaMemcpyAsync(save, cur_state(s), 4 * sb, cudaMemcpyDeviceToDevice, st));
+      VX_CUDA(cudaMemcpyAsync(save_fl, s->flags, N, cudaMemcpyDeviceToDevice, st));
+      const int tiles[2] = {128, 256};
+      const int64_t groups[5] = {0, 1024, 4096, 16384, 65536};
+      for (int tm : tiles)
+        for (int64_t gv : groups) {
+          int r;
+          if ((r = vx_set_step_form(s, VX_FORM_PIPELINED, tm)) || (r = vx_set_batching(s, gv))) return r;
+          if ((r = vx_step_async(s, 2, st)) || (r = restore())) return r;  // warm-up (prepares kernels)
+          VX_CUDA(cudaEventRecord(e0, st));
+          if ((r = vx_step_async(s, sample_steps, st))) return r;
+          VX_CUDA(cudaEventRecord(e1, st));
+          VX_CUDA(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          VX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+          int32_t code;
+          int64_t bs, bv;
+          if ((r = vx_get_status(s, st, &code, &bs, &bv))) return r;
+          if ((r = restore())) return r;
+          if (code != VX_OK) return fail(code, "autotuning sample became unstable");
+          const double rate = (double)N * sample_steps / (1e-3 * ms);
+          if (rate > best.rate) best = TuneVal{tm, gv, rate};
+        }
+      return VX_OK;
+    };
+    rc = run();
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    dfree(save);
+    dfree(save_fl);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best;
+  }
+  if ((rc = vx_set_step_form(s, VX_FORM_PIPELINED, best.tile_max)) || (rc = vx_set_batching(s, best.group_voxels)))
+    return rc;
+  if (tile_max_out) *tile_max_out = best.tile_max;
+  if (group_voxels_out) *group_voxels_out = best.group_voxels;
+  if (rate_out) *rate_out = best.rate;
   return VX_OK;
 }
 

@@ -61,6 +61,7 @@ struct BatchArgs {
   int n_steps;
   int64_t step0;
   int64_t act_P;
+  const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
 };
 int prepare_batched(int tile_max, size_t smem);
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s);

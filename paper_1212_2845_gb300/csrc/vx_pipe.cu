@@ -324,16 +324,19 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
     reinterpret_cast<float*>(mats)[j] = reinterpret_cast<const float*>(A0.mats)[j];
   if (A0.lut)
     for (int j = i; j < 8 * A0.n_mats * A0.n_mats; j += TMAX) lut[j] = A0.lut[j];
+  // first step and buffer: kernel arguments, or a device counter (graph replays)
+  const int64_t step0 = Bt.ctr ? Bt.ctr[0] : Bt.step0;
+  const int cur0 = Bt.ctr ? (int)Bt.ctr[1] : Bt.cur0;
   __syncthreads();
   for (int gi = Bt.cta_start[blockIdx.x]; gi < Bt.cta_start[blockIdx.x + 1]; ++gi) {
     const int g = Bt.cta_groups[gi];
     const int t0 = Bt.group_tiles[2 * g], t1 = Bt.group_tiles[2 * g + 1];
     for (int k = 0; k < Bt.n_steps; ++k) {
       StepArgs A = A0;
-      const int p = (Bt.cur0 + k) & 1;
+      const int p = (cur0 + k) & 1;
       A.st_in = p ? Bt.buf1 : Bt.buf0;
       A.st_out = p ? Bt.buf0 : Bt.buf1;
-      A.step = Bt.step0 + k;
+      A.step = step0 + k;
       if (A.act_on && Bt.act_P > 0)
         A.act_w = (float)(6.283185307179586 * (double)(A.step % Bt.act_P) / (double)Bt.act_P);
       const StPtr G(const_cast<float*>(A.st_in), A.pitch);

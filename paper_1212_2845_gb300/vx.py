@@ -90,6 +90,9 @@ SIGNATURES = {
     "vx_collision_stats": (C.c_int, [_P, _pi64, _pd]),
     "vx_collision_candidates_static": (C.c_int, [_P, _P, _P, _i32, _i32, _f32, _P, _P, _P]),
     "vx_rollout_forward": (C.c_int, [_P, _i64, _i32, _pf, _P]),
+    "vx_graph_capture": (C.c_int, [_P, _i64, _P]),
+    "vx_graph_launch": (C.c_int, [_P, _P]),
+    "vx_autotune_batching": (C.c_int, [_P, _i32, _pi32, _pi64, _pd, _P]),
     "vx_rollout_backward": (C.c_int, [_P, _pf, _P, _P, _P]),
 }
 STATIC_MAX_SURFACE = 65536
@@ -371,6 +374,21 @@ class Sim:
         st, bs, bv = C.c_int32(), C.c_int64(), C.c_int64()
         _check(self._L.vx_get_status(self.h, _stream_ptr(stream), C.byref(st), C.byref(bs), C.byref(bv)))
         return st.value, bs.value, bv.value
+
+    # -- captured launches and autotuning (batched form) -------------------
+    def graph_capture(self, n_steps, stream=None):
+        _check(self._L.vx_graph_capture(self.h, int(n_steps), _stream_ptr(stream)))
+
+    def graph_launch(self, stream=None):
+        _check(self._L.vx_graph_launch(self.h, _stream_ptr(stream)))
+
+    def autotune_batching(self, sample_steps=20, stream=None):
+        """Pick tile and group size by timing (cached per size class); returns
+        (tile_max, group_voxels, sampled voxel-steps/s)."""
+        tm, gv, r = C.c_int32(), C.c_int64(), C.c_double()
+        _check(self._L.vx_autotune_batching(self.h, int(sample_steps), C.byref(tm), C.byref(gv), C.byref(r),
+                                            _stream_ptr(stream)))
+        return tm.value, gv.value, r.value
 
     # -- collisions --------------------------------------------------------
     def rebuild_collisions(self, stream=None):

@@ -388,3 +388,48 @@ def test_batched_design_population_vs_oracle(vx):
     sim.step(300)
     ora.step(300)
     assert pos_error(sc, sim.state(), ora.state()) < 1e-3
+
+
+def test_graph_replays_continue_the_rollout(vx):
+    """One captured batched launch of 7 steps replayed 3 times equals 21
+    steps (odd step count: the state buffer alternates between replays;
+    actuation: each replay continues the step counter)."""
+    sc = scenes.population(n_bodies=23, seed=17, lo=2, hi=12)
+    sc["act_period"] = 40
+    ref = run_form(vx, sc, 21, vx.FORM_PIPELINED, 256)
+    sim = vx.Sim(sc)
+    sim.set_batching(700)
+    sim.graph_capture(7)
+    for _ in range(3):
+        sim.graph_launch()
+    assert sim.status()[0] == 0
+    out = sim.read_state()
+    assert sim.step_count == 21
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
+    sim.set_damping(1.0, 0.0, 0.5)               # model changed: the graph is stale
+    with pytest.raises(vx.VxError) as e:
+        sim.graph_launch()
+    assert e.value.code == -6
+    sim.close()
+
+
+def test_autotuner_restores_state_and_keeps_results(vx):
+    sc = scenes.population(n_bodies=40, seed=3, lo=3, hi=14)
+    ref = run_form(vx, sc, 60, vx.FORM_PIPELINED, 256)
+    sim = vx.Sim(sc)
+    sim.step(20)
+    before = sim.read_state()
+    tm, gv, rate = sim.autotune_batching(10)
+    assert tm in (128, 256) and gv in (0, 1024, 4096, 16384, 65536) and rate > 0
+    after = sim.read_state()
+    assert sim.step_count == 20
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k
+    assert sim.tiling()["tile_max"] == tm
+    sim.step(40)                                  # the tuned form continues bit for bit
+    out = sim.read_state()
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
+    assert sim.autotune_batching(10)[:2] == (tm, gv)   # cached for the size class
+    sim.close()
