@@ -241,6 +241,17 @@ VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int6
  * accumulator of body 0 [m]. */
 VX_API int vx_collision_stats(vx_sim* sim, int64_t* n_rebuilds, double* accumulator);
 
+/* ---- FP64 audit (the only FP64 arithmetic on the GPU) -------------------
+ * Deterministic FP64 reductions over the current state: out[0..2] total
+ * linear momentum sum m v; out[3..5] angular momentum about the world origin
+ * sum (D x m v + I w) with D the absolute centre (anchor + offset, formed in
+ * FP64) and I = m l^2 / 6; out[6] translational and out[7] rotational
+ * kinetic energy; out[8] elastic energy of the bonds, 1/2 u^T [K] u of each
+ * bond's reduced beam (Sec 2.1.2) in its co-rotational frame, stretch taken
+ * beyond the thermal rest length (Sec 2.3); out[9] gravitational energy
+ * -sum m g z.  Units SI.  Synchronous (waits for `stream`).  */
+VX_API int vx_audit(vx_sim* sim, double* out, void* stream);
+
 /* ---- captured launches and autotuning of the batched form ---------------
  * The paper steps one body per call; these serve populations of independent
  * bodies (design automation, which the paper names as a use).

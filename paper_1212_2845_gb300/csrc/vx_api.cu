@@ -141,6 +141,8 @@ struct vx_sim {
   uint64_t g_cfg = 0;         // cfg at capture
   int64_t* ctr_d = nullptr;   // device (step, buffer) read by the captured kernel
   int64_t ctr_h[2] = {0, 0};
+  // FP64 audit
+  double* aud = nullptr;      // per-body origins, per-material values, block partials, result
   uint64_t ro_gen = 0;        // gen at the end of the recorded rollout
   int64_t ro_steps = 0;       // steps of the recorded rollout (0: none)
   int ro_K = 0;               // checkpoint interval
@@ -439,11 +441,11 @@ int ensure_pipe(vx_sim* s, const StepArgs& A) {
   return VX_OK;
 }
 
-int ensure_two_pass(vx_sim* s) {
-  if (s->bf) return VX_OK;
-  int64_t N = s->L.N;
+int ensure_nbr(vx_sim* s) {
+  if (s->nbr) return VX_OK;
+  const int64_t N = s->L.N;
   int rc;
-  if ((rc = dalloc(&s->bf, 27 * s->pitch)) || (rc = dalloc(&s->nbr, 6 * N))) return rc;
+  if ((rc = dalloc(&s->nbr, 6 * N))) return rc;
   std::vector<int32_t> nb(6 * (size_t)N);
   for (int sl = 0; sl < 6; ++sl)
     for (int64_t c = 0; c < N; ++c) {
@@ -451,6 +453,14 @@ int ensure_two_pass(vx_sim* s) {
       nb[(size_t)sl * N + s->T.iperm[c]] = u < 0 ? -1 : s->T.iperm[u];
     }
   VX_CUDA(cudaMemcpy(s->nbr, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice));
+  return VX_OK;
+}
+
+int ensure_two_pass(vx_sim* s) {
+  int rc;
+  if ((rc = ensure_nbr(s))) return rc;
+  if (s->bf) return VX_OK;
+  if ((rc = dalloc(&s->bf, 27 * s->pitch))) return rc;
   VX_CUDA(cudaMemset(s->bf, 0, sizeof(float) * 27 * s->pitch));
   return VX_OK;
 }
@@ -701,7 +711,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
-  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
@@ -1367,6 +1377,52 @@ int vx_autotune_batching(vx_sim* s, int32_t sample_steps, int32_t* tile_max_out,
   if (tile_max_out) *tile_max_out = best.tile_max;
   if (group_voxels_out) *group_voxels_out = best.group_voxels;
   if (rate_out) *rate_out = best.rate;
+  return VX_OK;
+}
+
+int vx_audit(vx_sim* s, double* out, void* stream) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (!out) return fail(VX_ERR_ARG, "out is NULL");
+  if ((rc = ensure_nbr(s))) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  const Lattice& L = s->L;
+  const int nb = L.n_bodies, nm = (int)L.palette.size(), np = audit_partials((int)L.N);
+  const size_t n_in = 3 * (size_t)nb + 4 * (size_t)nm;
+  const size_t n_all = n_in + 10 * (size_t)np + 10;
+  dfree(s->aud);
+  if ((rc = dalloc(&s->aud, n_all))) return rc;
+  std::vector<double> h(n_in);
+  for (int b = 0; b < nb; ++b)
+    for (int a = 0; a < 3; ++a) h[3 * b + a] = (double)L.origin[3 * b + a];
+  const double l = (double)L.l;
+  double* hm = h.data() + 3 * nb;
+  for (int m = 0; m < nm; ++m) {
+    const vx_material& p = L.palette[m];
+    const double mass = (double)p.rho * l * l * l;
+    hm[m] = (double)p.E;
+    hm[nm + m] = 1.0 / (2.0 * (1.0 + (double)p.nu));
+    hm[2 * nm + m] = mass;
+    hm[3 * nm + m] = mass * l * l / 6.0;
+  }
+  VX_CUDA(cudaMemcpy(s->aud, h.data(), n_in * sizeof(double), cudaMemcpyHostToDevice));
+  AuditArgs U;
+  U.l = l;
+  U.gz = (double)s->gz;
+  U.origin = s->aud;
+  U.E = s->aud + 3 * nb;
+  U.g_ratio = U.E + nm;
+  U.mass = U.E + 2 * nm;
+  U.inertia = U.E + 3 * nm;
+  StepArgs A = step_args(s);
+  A.nbr = s->nbr;
+  A.act_w = act_phase(s, s->step);
+  double* partial = s->aud + n_in;
+  double* res = partial + 10 * (size_t)np;
+  launch_audit(A, U, partial, res, st);
+  VX_CUDA(cudaGetLastError());
+  VX_CUDA(cudaMemcpyAsync(out, res, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  VX_CUDA(cudaStreamSynchronize(st));
   return VX_OK;
 }
 

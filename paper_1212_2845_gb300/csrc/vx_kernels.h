@@ -88,6 +88,21 @@ int prepare_adj_tile(int tile_max, size_t smem);
 // One reverse step: A.st_in = S_n, A.flags = flags at step n, A.act_w and
 // A.step of step n, the fused form's tile arrays; J.fm = bond sums at step n.
 void launch_adjoint_step(const StepArgs& A, const AdjArgs& J, int tile_max, size_t smem, cudaStream_t s);
+// FP64 audit (momentum, angular momentum, energies); needs A.nbr.  The
+// per-material and per-body values are FP64 copies of the host's inputs.
+struct AuditArgs {
+  double l, gz;
+  const double* origin;   // 3 per body
+  const double* E;        // per material: E, G / E, rho l^3, m l^2 / 6
+  const double* g_ratio;
+  const double* mass;
+  const double* inertia;
+};
+int audit_partials(int N);
+// out[10] (device): P (3), L about the origin (3), KE linear, KE rotational,
+// U elastic, U gravity; partial: audit_partials(N) x 10 doubles
+void launch_audit(const StepArgs& A, const AuditArgs& U, double* partial, double* out, cudaStream_t s);
+
 void launch_seed_adjoint(float* lam, int64_t pitch, int N, const float* cw, const int32_t* body,
                          const float* w_body, cudaStream_t s);
 // loss[b] = sum over the body's internal range of cw (x(end) - x(start))

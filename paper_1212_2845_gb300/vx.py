@@ -91,6 +91,7 @@ SIGNATURES = {
     "vx_collision_candidates_static": (C.c_int, [_P, _P, _P, _i32, _i32, _f32, _P, _P, _P]),
     "vx_rollout_forward": (C.c_int, [_P, _i64, _i32, _pf, _P]),
     "vx_graph_capture": (C.c_int, [_P, _i64, _P]),
+    "vx_audit": (C.c_int, [_P, _pd, _P]),
     "vx_graph_launch": (C.c_int, [_P, _P]),
     "vx_autotune_batching": (C.c_int, [_P, _i32, _pi32, _pi64, _pd, _P]),
     "vx_rollout_backward": (C.c_int, [_P, _pf, _P, _P, _P]),
@@ -374,6 +375,13 @@ class Sim:
         st, bs, bv = C.c_int32(), C.c_int64(), C.c_int64()
         _check(self._L.vx_get_status(self.h, _stream_ptr(stream), C.byref(st), C.byref(bs), C.byref(bv)))
         return st.value, bs.value, bv.value
+
+    def audit(self, stream=None):
+        """FP64 audit: dict of momentum P (3), angular momentum L (3), kinetic
+        (linear, rotational), elastic and gravitational energy."""
+        out = np.zeros(10)
+        _check(self._L.vx_audit(self.h, _ptr(out, C.c_double), _stream_ptr(stream)))
+        return dict(P=out[0:3], L=out[3:6], ke_lin=out[6], ke_rot=out[7], u_elastic=out[8], u_gravity=out[9])
 
     # -- captured launches and autotuning (batched form) -------------------
     def graph_capture(self, n_steps, stream=None):
