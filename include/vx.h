@@ -158,8 +158,8 @@ VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
 #define VX_FORM_TWO_PASS 1
 #define VX_FORM_PIPELINED 2
 VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
-/* Batched form for many independent bodies (SURVEY: thousands of bodies of
- * uneven size, as in design automation).  group_voxels > 0: consecutive
+/* Batched form for many independent bodies (thousands of bodies of uneven
+ * size, as in the design automation the paper motivates).  group_voxels > 0: consecutive
  * bodies are grouped to about that many voxels and spread over persistent
  * CTAs (largest first onto the least loaded); vx_step / vx_step_async then
  * run all n steps in ONE launch, each CTA stepping one group at a time with
