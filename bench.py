@@ -281,14 +281,18 @@ def adjoint_form(stream, peak, n_bodies=1024, steps=2000, K=100):
 
 
 def small_lattice(stream, steps=1000):
-    """Cantilever 10x10x10 (1,000 voxels): latency-bound.  Per-step launches
-    against one captured persistent launch of all steps (batched form, one
-    group: the body stays in one CTA's hands for every step)."""
+    """Cantilever 10x10x10 (1,000 voxels, 4 tiles): latency-bound.  Per-step
+    launches, one cooperative multi-step launch (grid barrier between steps),
+    and one captured persistent batched launch (the body in one CTA)."""
     from paper_1212_2845_gb300 import vx
     sc = scenes.cantilever()
     sim = vx.Sim(sc)
     sim.step(10)
+    sim.set_multistep(0)
     t_plain = _events_time(stream, lambda: sim.step_async(steps, stream))
+    sim.set_multistep(1)
+    sim.step_async(steps, stream)
+    t_multi = _events_time(stream, lambda: sim.step_async(steps, stream))
     sim.set_batching(1 << 20)
     sim.graph_capture(steps, stream)
     sim.graph_launch(stream)
@@ -297,9 +301,23 @@ def small_lattice(stream, steps=1000):
         raise RuntimeError("cantilever became unstable")
     out = {"workload": "cantilever_10x10x10", "voxels": sim.N, "steps": steps,
            "per_step_launches": {"steps_per_s": steps / t_plain, "us_per_step": 1e6 * t_plain / steps},
-           "one_captured_launch": {"steps_per_s": steps / t_graph, "us_per_step": 1e6 * t_graph / steps}}
+           "multi_step_launch": {"steps_per_s": steps / t_multi, "us_per_step": 1e6 * t_multi / steps},
+           "captured_batched_launch": {"steps_per_s": steps / t_graph, "us_per_step": 1e6 * t_graph / steps}}
     sim.close()
     return out
+
+
+def multi_step_line(sim, stream, flush, steps=500):
+    """The same lattice stepped by one call of `steps` steps (one cooperative
+    launch on this size), L2 flushed before the call."""
+    sim.set_multistep(1)
+    sim.step_async(steps, stream)
+    flush.fill_(3.0)
+    t = _events_time(stream, lambda: sim.step_async(steps, stream))
+    if sim.status(stream)[0]:
+        raise RuntimeError("simulation reported a bad status")
+    return {"us_per_step": 1e6 * t / steps, "value": sim.N * steps / t, "unit": METRIC, "steps_per_call": steps,
+            "l2": "flushed before each call; the lattice stays in L2 across the steps of a call"}
 
 
 def main():
@@ -406,7 +424,8 @@ def main():
     if not args.no_large:
         line["large_lattice"] = large_lattice(stream, peak)
     if not args.no_forms:
-        line["forms"] = {"batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
+        line["forms"] = {"multi_step_call": multi_step_line(sim, stream, flush),
+                         "batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
                          "small_lattice": small_lattice(stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)

@@ -138,7 +138,11 @@ VX_API int vx_plan_tiles(const vx_desc* desc, int32_t tile_max, int64_t* n_tiles
 /* Build the lattice (Sec 2.1: voxelised geometry, composite bonds,
  * precomputed surface list) on the current CUDA device and reset the state
  * to rest.  Defaults: zeta_bond 1, zeta_ground 0, zeta_collision 1, no
- * gravity, floor or collisions, no actuation, dt_factor 0.9. */
+ * gravity, floor or collisions, no actuation, dt_factor 0.9.  Errors:
+ * VX_ERR_ARG for an invalid description, VX_ERR_OOM when device memory runs
+ * out (for tests, the environment variable VX_DEVICE_ALLOC_CAP=<bytes> makes
+ * every larger device allocation of the library fail this way),
+ * VX_ERR_CUDA without a usable device. */
 VX_API int vx_create(const vx_desc* desc, vx_sim** out);
 VX_API void vx_destroy(vx_sim* sim);
 VX_API int vx_get_counts(vx_sim* sim, int64_t* n_voxels, int64_t* n_bonds, int64_t* n_surface);
@@ -167,6 +171,25 @@ VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
  * and bits as the per-step forms.  Ignored while self-collision is on.
  * 0 turns it off.  Needs a fused form with tiles of 128 or 256. */
 VX_API int vx_set_batching(vx_sim* sim, int64_t group_voxels);
+/* Multi-step launches (on by default): in the pipelined form without
+ * batching or collisions, on lattices of at most 4 tiles per persistent CTA
+ * (about 300,000 voxels), vx_step / vx_step_async with n_steps > 1 run all
+ * steps in ONE cooperative launch of co-resident persistent CTAs that meet
+ * at a grid barrier between steps, so the lattice stays in L2 and no launch
+ * separates the steps.  Same arithmetic and bits as one launch per step.
+ * The barrier waits are bounded (about a second); if one gives up, the
+ * launch ends and vx_get_status / vx_step report VX_ERR_TIMEOUT.  If the
+ * device cannot hold the grid at once the call falls back to one launch per
+ * step.  on = 0 always launches once per step. */
+VX_API int vx_set_multistep(vx_sim* sim, int32_t on);
+/* Fault-injection aid for tests of the bounded waits: the budget of one grid
+ * barrier wait in 64 ns naps (0 restores the default of 2^24, about one
+ * second) and a number of phantom CTAs the barrier also waits for (0 in
+ * normal use; any other value makes every barrier run out, after which the
+ * launch ends with VX_ERR_TIMEOUT and the state is that of a partial step
+ * sequence: reset or write it before stepping on).  Host-side only; no GPU
+ * fault is involved. */
+VX_API int vx_set_barrier_limits(vx_sim* sim, int64_t max_spins, int32_t phantom_ctas);
 /* Current tiling: tile size, tile count, largest staged set, dynamic shared
  * memory of the fused kernel in bytes.  Any output may be NULL. */
 VX_API int vx_get_tiling(vx_sim* sim, int32_t* tile_max, int64_t* n_tiles, int32_t* max_local, int64_t* smem_bytes);

@@ -600,9 +600,9 @@ size_t adj_tile_smem_bytes(int tile_max, int n_mats) {
 
 int prepare_adj_tile(int tile_max, size_t smem) {
   cudaError_t e;
-  if (tile_max == 128) e = cudaFuncSetAttribute(adj_tile<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else if (tile_max == 256) e = cudaFuncSetAttribute(adj_tile<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else if (tile_max == 512) e = cudaFuncSetAttribute(adj_tile<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (tile_max == 128) e = allow_smem(adj_tile<128>, smem);
+  else if (tile_max == 256) e = allow_smem(adj_tile<256>, smem);
+  else if (tile_max == 512) e = allow_smem(adj_tile<512>, smem);
   else return -1;
   return e == cudaSuccess ? 0 : -1;
 }

@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <functional>
 #include <map>
@@ -35,9 +36,22 @@ int fail(int code, const std::string& msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                         \
   } while (0)
 
+// Fault injection for tests: VX_DEVICE_ALLOC_CAP=<bytes> in the environment
+// makes every larger device allocation fail as out of memory.
+bool over_alloc_cap(size_t bytes) {
+  const char* c = std::getenv("VX_DEVICE_ALLOC_CAP");
+  if (!c || !*c) return false;
+  char* end = nullptr;
+  const unsigned long long cap = std::strtoull(c, &end, 10);
+  return end && *end == 0 && bytes > cap;
+}
+
 template <class T> int dalloc(T** p, size_t n) {
   *p = nullptr;
   if (n == 0) n = 1;
+  if (over_alloc_cap(n * sizeof(T)))
+    return fail(VX_ERR_OOM, "device allocation of " + std::to_string(n * sizeof(T)) +
+                                " bytes is above VX_DEVICE_ALLOC_CAP");
   cudaError_t e = cudaMalloc((void**)p, n * sizeof(T));
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -89,6 +103,12 @@ struct vx_sim {
   uint2* plus2 = nullptr;
   size_t pipe_smem = 0;
   int pipe_grid = 0;
+  // multi-step form (one cooperative launch for n steps)
+  int multistep = 1;          // use it for vx_step(n > 1) in the pipelined form without collisions
+  int multi_grid = 0;
+  unsigned* bar = nullptr;    // grid barrier words
+  int64_t bar_spins = 1ll << 24;  // barrier wait budget: 2^24 naps of 64 ns, about one second
+  int32_t bar_extra = 0;      // phantom CTAs (fault injection)
   // batched form
   int64_t group_voxels = 0;   // 0: off
   Batch B;
@@ -434,7 +454,8 @@ int ensure_pipe(vx_sim* s, const StepArgs& A) {
   size_t sm = pipe_smem_bytes(s->tile_max, A.phase != nullptr, A.logE != nullptr, A.body != nullptr,
                               A.fext != nullptr, nm, nm <= kLutMaxMats);
   if (sm != s->pipe_smem) {
-    if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0 || prepare_batched(s->tile_max, sm) != 0)
+    if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0 || prepare_batched(s->tile_max, sm) != 0 ||
+        prepare_multi(s->tile_max, sm, (int)s->T.n_tiles(), &s->multi_grid) != 0)
       return fail(VX_ERR_CUDA, "pipelined kernels need " + std::to_string(sm) + " bytes of shared memory");
     s->pipe_smem = sm;
   }
@@ -711,7 +732,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
-  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
@@ -1044,6 +1065,38 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     VX_CUDA(cudaGetLastError());
     return VX_OK;
   }
+  bool multi = s->multistep && s->form == VX_FORM_PIPELINED && !s->collide_on && n > 1;
+  if (multi) {
+    StepArgs A = step_args(s);
+    if ((rc = ensure_pipe(s, A))) return rc;
+    // for lattices of a few tiles per CTA, where launches and per-step ramp-up
+    // dominate; on larger ones the per-step launches overlap and the barrier
+    // costs more
+    multi = s->T.n_tiles() <= 4 * (int64_t)s->pipe_grid;
+  }
+  if (multi) {
+    // multi-step form: all n steps in one cooperative launch
+    StepArgs A = step_args(s);
+    if (!s->bar && (rc = dalloc(&s->bar, 2))) return rc;
+    VX_CUDA(cudaMemsetAsync(s->bar, 0, 2 * sizeof(unsigned), st));
+    MultiArgs M;
+    M.buf0 = s->st;
+    M.buf1 = s->st + (size_t)NPLANE * s->pitch;
+    M.cur0 = s->cur;
+    M.n_steps = (int)n;
+    M.step0 = s->step;
+    M.act_P = s->actP;
+    M.ctr = nullptr;
+    M.bar = s->bar;
+    M.spins = s->bar_spins;
+    M.extra = (unsigned)s->bar_extra;
+    if (launch_multi(A, M, s->tile_max, s->pipe_smem, s->multi_grid, st) == cudaSuccess) {
+      s->cur ^= (int)(n & 1);
+      s->step += n;
+      return VX_OK;
+    }
+    cudaGetLastError();  // not co-resident on this device: fall back to one launch per step
+  }
   for (int64_t i = 0; i < n; ++i) {
     StepArgs A = step_args(s);
     if (s->actP > 0) A.act_w = (float)(2.0 * M_PI * (double)(s->step % s->actP) / (double)s->actP);
@@ -1073,6 +1126,7 @@ int vx_get_status(vx_sim* s, void* stream, int32_t* status, int64_t* bad_step, i
   VX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
   int code = VX_OK;
   if (h[0] & kStatusUnstable) code = VX_ERR_UNSTABLE;
+  else if (h[0] & kStatusTimeout) code = VX_ERR_TIMEOUT;
   else if (h[0] & kStatusCapacity) code = VX_ERR_CAPACITY;
   long long bs;
   std::memcpy(&bs, &h[2], 8);
@@ -1092,6 +1146,7 @@ int vx_step(vx_sim* s, int64_t n, void* stream) {
     return fail(code, "non-finite state at step " + std::to_string(bs) + ", voxel " + std::to_string(bv));
   if (code == VX_ERR_CAPACITY)
     return fail(code, "collision candidate list overflow (more than " + std::to_string(kCandCap) + " per voxel)");
+  if (code == VX_ERR_TIMEOUT) return fail(code, "a grid barrier of the multi-step launch gave up waiting");
   return VX_OK;
 }
 
@@ -1423,6 +1478,23 @@ int vx_audit(vx_sim* s, double* out, void* stream) {
   VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaMemcpyAsync(out, res, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
   VX_CUDA(cudaStreamSynchronize(st));
+  return VX_OK;
+}
+
+int vx_set_multistep(vx_sim* s, int32_t on) {
+  if (s) ++s->cfg;
+  int rc = check_sim(s);
+  if (rc) return rc;
+  s->multistep = on ? 1 : 0;
+  return VX_OK;
+}
+
+int vx_set_barrier_limits(vx_sim* s, int64_t max_spins, int32_t phantom_ctas) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (max_spins < 0 || phantom_ctas < 0) return fail(VX_ERR_ARG, "limits must be >= 0");
+  s->bar_spins = max_spins == 0 ? (1ll << 24) : max_spins;
+  s->bar_extra = phantom_ctas;
   return VX_OK;
 }
 

@@ -36,6 +36,7 @@ struct DevMat {
 constexpr int kCandCap = 48;        // collision candidates per surface voxel
 constexpr int kStatusUnstable = 1;  // status word bits
 constexpr int kStatusCapacity = 2;
+constexpr int kStatusTimeout = 4;   // a bounded device wait gave up
 
 struct StepArgs {
   int N;

@@ -7,6 +7,22 @@
 
 namespace vx {
 
+// Raises a kernel's dynamic shared memory limit to the most the device allows
+// next to the kernel's static shared memory.  Setting the largest value (not
+// the size one simulator needs) means simulators of different sizes in one
+// process never lower each other's limit.  Fails if `need` is above it.
+template <class F> inline cudaError_t allow_smem(F* kernel, size_t need) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaFuncAttributes fa;
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, (const void*)kernel);
+  if (e != cudaSuccess) return e;
+  const int allowed = optin - (int)fa.sharedSizeBytes;
+  if (allowed < 0 || (size_t)allowed < need) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute((const void*)kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, allowed);
+}
+
 struct CollideArgs {
   int S;                  // surface voxels
   int n_bodies;
@@ -64,6 +80,24 @@ struct BatchArgs {
   const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
 };
 int prepare_batched(int tile_max, size_t smem);
+
+// Multi-step form: one cooperative launch of min(n_tiles, co-resident CTAs)
+// CTAs runs n_steps with a bounded grid barrier (bar: 2 device words, zero
+// at launch) between steps.
+struct MultiArgs {
+  float* buf0;                 // the two state buffers
+  float* buf1;
+  int cur0;                    // buffer holding the state at step0
+  int n_steps;
+  int64_t step0;
+  int64_t act_P;
+  const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
+  unsigned* bar;               // barrier count and generation
+  long long spins;             // wait budget of one barrier (64 ns naps)
+  unsigned extra;              // CTAs the barrier waits for beyond the grid (fault injection; 0)
+};
+int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid);
+cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);
 // bond_pass of the two-pass form alone (bond results into A.bf)

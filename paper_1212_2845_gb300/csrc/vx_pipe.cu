@@ -242,25 +242,16 @@ template <int TMAX> struct PipeSmem {
   }
 };
 
+// One step over this CTA's tiles t = blockIdx.x, + gridDim.x, ... (pipelined
+// staging).  Ends with every copy landed; the caller separates two calls
+// with a barrier because the shared buffers are reused.
 template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs A) {
-  constexpr int ML = 2 * TMAX;
-  extern __shared__ __align__(16) float smem[];
+__device__ __forceinline__ void pipe_tiles(const StepArgs& A, float* smem, int sf, float4* props, float4* F4,
+                                           float2* F2, const DevMat* mats, const float* lut) {
   const bool hph = A.phase != nullptr, hle = A.logE != nullptr, hbody = A.body != nullptr, hfx = A.fext != nullptr;
-  const int sf = Stage<TMAX>::floats(hph, hle, hbody, hfx);
-  float4* props = reinterpret_cast<float4*>(smem + 2 * sf);
-  float4* F4 = props + ML;
-  float2* F2 = reinterpret_cast<float2*>(F4 + 3 * TMAX);
-  DevMat* mats = reinterpret_cast<DevMat*>(F2 + 3 * TMAX);
-  float* lut = reinterpret_cast<float*>(mats + A.n_mats);
   const int i = threadIdx.x;
   const int Gs = gridDim.x;
   int t = blockIdx.x;
-  if (t >= A.n_tiles) return;  // uniform over the CTA
-  for (int j = i; j < A.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
-    reinterpret_cast<float*>(mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
-  if (A.lut)
-    for (int j = i; j < 8 * A.n_mats * A.n_mats; j += TMAX) lut[j] = A.lut[j];
   const StPtr G(const_cast<float*>(A.st_in), A.pitch);
   // prologue: stage the first tile, fetch the next descriptor
   TileRegs cur = load_tile<TMAX>(A, t, A.n_tiles);
@@ -298,6 +289,98 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
     fl_cur = fl_nxt;
     t += Gs;
     b ^= 1;
+  }
+}
+
+template <int TMAX> struct PipeLayout {
+  int sf;
+  float4 *props, *F4;
+  float2* F2;
+  DevMat* mats;
+  float* lut;
+  __device__ __forceinline__ PipeLayout(float* smem, const StepArgs& A) {
+    constexpr int ML = 2 * TMAX;
+    sf = Stage<TMAX>::floats(A.phase != nullptr, A.logE != nullptr, A.body != nullptr, A.fext != nullptr);
+    props = reinterpret_cast<float4*>(smem + 2 * sf);
+    F4 = props + ML;
+    F2 = reinterpret_cast<float2*>(F4 + 3 * TMAX);
+    mats = reinterpret_cast<DevMat*>(F2 + 3 * TMAX);
+    lut = reinterpret_cast<float*>(mats + A.n_mats);
+  }
+  __device__ __forceinline__ void load_tables(const StepArgs& A) const {
+    for (int j = threadIdx.x; j < A.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
+      reinterpret_cast<float*>(mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
+    if (A.lut)
+      for (int j = threadIdx.x; j < 8 * A.n_mats * A.n_mats; j += TMAX) lut[j] = A.lut[j];
+  }
+};
+
+template <int TMAX>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs A) {
+  extern __shared__ __align__(16) float smem[];
+  if ((int)blockIdx.x >= A.n_tiles) return;  // uniform over the CTA
+  const PipeLayout<TMAX> L(smem, A);
+  L.load_tables(A);
+  pipe_tiles<TMAX>(A, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+}
+
+// Grid-wide barrier of a cooperative launch (every CTA co-resident).  The
+// last CTA to arrive resets the count and releases the generation; the others
+// wait on it with a bounded spin.  Returns false (and sets the timeout status
+// bit) if the wait gave up, after which the caller ends the launch.  Every
+// thread then performs its own acquire, so its later loads (including
+// cp.async) see every write released before the barrier.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned n_ctas, long long max_spins, int* status) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    unsigned gen, prev, now;
+    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(bar) : "memory");
+    if (prev + 1 == n_ctas) {
+      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
+      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
+    } else {
+      for (long long it = 0;; ++it) {
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
+        if (now != gen) break;
+        if (it >= max_spins) {
+          atomicOr(status, kStatusTimeout);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+  }
+  __syncthreads();
+  asm volatile("{\n .reg .u32 t;\n ld.acquire.gpu.global.u32 t, [%0];\n}" ::"l"(bar + 1) : "memory");
+  return ok != 0;
+}
+
+// Multi-step form: one cooperative launch runs n steps of the whole lattice;
+// every CTA walks its tiles of a step (as fused_pipe), then all CTAs meet at
+// a grid barrier before the next step reads what this one wrote.  The
+// lattice stays in L2 between steps and no launch separates them.
+template <int TMAX>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) multi_pipe(StepArgs A0, MultiArgs M) {
+  extern __shared__ __align__(16) float smem[];
+  const PipeLayout<TMAX> L(smem, A0);
+  L.load_tables(A0);
+  const int64_t step0 = M.ctr ? M.ctr[0] : M.step0;
+  const int cur0 = M.ctr ? (int)M.ctr[1] : M.cur0;
+  __syncthreads();
+  for (int k = 0; k < M.n_steps; ++k) {
+    StepArgs A = A0;
+    const int p = (cur0 + k) & 1;
+    A.st_in = p ? M.buf1 : M.buf0;
+    A.st_out = p ? M.buf0 : M.buf1;
+    A.step = step0 + k;
+    if (A.act_on && M.act_P > 0)
+      A.act_w = (float)(6.283185307179586 * (double)(A.step % M.act_P) / (double)M.act_P);
+    pipe_tiles<TMAX>(A, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+    if (k + 1 < M.n_steps && !grid_barrier(M.bar, gridDim.x + M.extra, M.spins, A0.status)) return;
   }
 }
 
@@ -385,10 +468,10 @@ int prepare_pipe(int tile_max, size_t smem, int* grid) {
   int per_sm = 0, dev = 0, n_sm = 0;
   cudaError_t e;
   if (tile_max == 128) {
-    e = cudaFuncSetAttribute(fused_pipe<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_smem(fused_pipe<128>, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pipe<128>, 128, smem);
   } else {
-    e = cudaFuncSetAttribute(fused_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    e = allow_smem(fused_pipe<256>, smem);
     if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pipe<256>, 256, smem);
   }
   if (e != cudaSuccess || per_sm < 1) return -1;
@@ -400,14 +483,39 @@ int prepare_pipe(int tile_max, size_t smem, int* grid) {
 
 int prepare_batched(int tile_max, size_t smem) {
   cudaError_t e;
-  if (tile_max == 128) e = cudaFuncSetAttribute(batched_pipe<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  else e = cudaFuncSetAttribute(batched_pipe<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (tile_max == 128) e = allow_smem(batched_pipe<128>, smem);
+  else e = allow_smem(batched_pipe<256>, smem);
   return e == cudaSuccess ? 0 : -1;
 }
 
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s) {
   if (tile_max == 128) batched_pipe<128><<<grid, 128, smem, s>>>(A, B);
   else batched_pipe<256><<<grid, 256, smem, s>>>(A, B);
+}
+
+int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid) {
+  int per_sm = 0, dev = 0, n_sm = 0;
+  cudaError_t e;
+  if (tile_max == 128) {
+    e = allow_smem(multi_pipe<128>, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_pipe<128>, 128, smem);
+  } else {
+    e = allow_smem(multi_pipe<256>, smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_pipe<256>, 256, smem);
+  }
+  if (e != cudaSuccess || per_sm < 1) return -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return -1;
+  const int co = per_sm * n_sm;
+  *grid = n_tiles < co ? n_tiles : co;
+  return 0;
+}
+
+cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s) {
+  void* args[2] = {const_cast<StepArgs*>(&A), const_cast<MultiArgs*>(&M)};
+  if (tile_max == 128)
+    return cudaLaunchCooperativeKernel((const void*)multi_pipe<128>, dim3(grid), dim3(128), args, smem, s);
+  return cudaLaunchCooperativeKernel((const void*)multi_pipe<256>, dim3(grid), dim3(256), args, smem, s);
 }
 
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {

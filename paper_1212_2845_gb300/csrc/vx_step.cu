@@ -274,7 +274,7 @@ size_t fused_smem_bytes(int tile_max, int n_mats, bool lut) {
 }
 
 template <int TMAX> int prepare_one(size_t smem) {
-  if (cudaFuncSetAttribute(fused_step<TMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+  if (allow_smem(fused_step<TMAX>, smem) != cudaSuccess)
     return -1;
   return 0;
 }

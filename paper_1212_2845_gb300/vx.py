@@ -61,6 +61,8 @@ SIGNATURES = {
     "vx_set_step_form": (C.c_int, [_P, _i32, _i32]),
     "vx_get_tiling": (C.c_int, [_P, _pi32, _pi64, _pi32, _pi64]),
     "vx_set_batching": (C.c_int, [_P, _i64]),
+    "vx_set_multistep": (C.c_int, [_P, _i32]),
+    "vx_set_barrier_limits": (C.c_int, [_P, _i64, _i32]),
     "vx_create": (C.c_int, [_pdesc, C.POINTER(_P)]),
     "vx_destroy": (None, [_P]),
     "vx_get_counts": (C.c_int, [_P, _pi64, _pi64, _pi64]),
@@ -284,6 +286,12 @@ class Sim:
 
     def set_batching(self, group_voxels):
         _check(self._L.vx_set_batching(self.h, int(group_voxels)))
+
+    def set_multistep(self, on):
+        _check(self._L.vx_set_multistep(self.h, int(bool(on))))
+
+    def set_barrier_limits(self, max_spins=0, phantom_ctas=0):
+        _check(self._L.vx_set_barrier_limits(self.h, int(max_spins), int(phantom_ctas)))
 
     def tiling(self):
         tm, ml = C.c_int32(), C.c_int32()

@@ -433,3 +433,45 @@ def test_autotuner_restores_state_and_keeps_results(vx):
         assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
     assert sim.autotune_batching(10)[:2] == (tm, gv)   # cached for the size class
     sim.close()
+
+
+@pytest.mark.parametrize("which", ["hetero_small", "population"])
+def test_multistep_launch_bitwise_equals_per_step_launches(vx, which):
+    """One cooperative launch of n steps (grid barrier between steps) gives the
+    bits of n separate launches."""
+    if which == "hetero_small":
+        sc = scenes.hetero_block(dims=(20, 18, 12), seed=9)
+    else:
+        sc = scenes.population(n_bodies=30, seed=8, lo=3, hi=14)
+    out = []
+    for multi in (0, 1):
+        sim = vx.Sim(sc)
+        sim.set_multistep(multi)
+        sim.step(301)
+        out.append(sim.read_state())
+        assert sim.step_count == 301
+        sim.close()
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(out[0][k].view(np.uint8), out[1][k].view(np.uint8)), k
+
+
+def test_simulators_of_different_sizes_coexist(vx):
+    """Kernel launch limits set for one simulator never break another one in
+    the same process (every form, stepped in turn)."""
+    a = vx.Sim(scenes.hetero_block(dims=(20, 18, 12), seed=9))       # phase: larger staging
+    b = vx.Sim(scenes.cantilever())
+    for form in (vx.FORM_PIPELINED, vx.FORM_FUSED):
+        a.set_step_form(form)
+        b.set_step_form(form)
+        a.step(3)
+        b.step(3)
+        a.step(3)
+    a.set_step_form(vx.FORM_PIPELINED)
+    a.set_batching(1000)
+    b.set_batching(1000)
+    a.step(4)
+    b.step(4)
+    a.step(4)
+    assert a.status()[0] == 0 and b.status()[0] == 0
+    a.close()
+    b.close()
