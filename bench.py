@@ -181,21 +181,22 @@ def time_steps(sim, stream, steps, warmup, flush=None):
     return np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
 
 
-def large_lattice(stream, peak, steps=200, warmup=5):
-    """Plain step on a hollow shell of outer radius 200 and thickness 8 voxels
-    (3.86M voxels, state ~400 MB per step: larger than L2), on the floor."""
+def large_lattice(stream, peak, steps=200, warmup=5, R=200):
+    """Plain step on a hollow shell of outer radius R (200: 3.86M voxels, state
+    ~400 MB per step, larger than L2) and thickness 8 voxels, on the floor."""
     from paper_1212_2845_gb300 import vx
-    sc = scenes.hollow_ball(R=200, t=8, collide=False)
+    sc = scenes.hollow_ball(R=R, t=8, collide=False)
     sim = vx.Sim(sc)
     t = time_steps(sim, stream, steps, warmup)
     avg = float(t.mean())
     b_alg = 108  # state r/w 104, flags 2, material 1, bond mask 1
-    out = {"workload": "hollow_shell_R200_t8 (plain step, fused kernel, no self-collision)", "voxels": sim.N,
+    out = {"workload": f"hollow_shell_R{R}_t8 (plain step, fused kernel, no self-collision)", "voxels": sim.N,
            "bonds": sim.n_bonds, "value": sim.N / avg, "unit": METRIC, "ms_per_step": avg * 1e3,
            "l2": "inputs larger than L2",
            "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg,
-                        "kernel": "fused_pipe<256>", "traffic": measured_traffic("hollow_shell_R200_t8")}}
+                        "kernel": "fused_pipe<256>",
+                        "traffic": measured_traffic("hollow_shell_R200_t8") if R == 200 else None}}
     sim.close()
     return out
 
@@ -335,6 +336,7 @@ def main():
     ap.add_argument("--only-adjoint", action="store_true", help="time only the adjoint form (profiling aid)")
     ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
     ap.add_argument("--bodies", type=int, default=0, help="bodies for --only-adjoint / --only-batched")
+    ap.add_argument("--shell-radius", type=int, default=200, help="outer radius of the --only-large shell")
     ap.add_argument("--form-steps", type=int, default=0, help="steps for --only-adjoint / --only-batched")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
@@ -348,7 +350,8 @@ def main():
     torch.cuda.set_device(local_rank)
     if args.only_large:
         peak, _ = load_peaks()
-        print(json.dumps(large_lattice(torch.cuda.Stream(), peak, steps=args.steps, warmup=args.warmup)))
+        print(json.dumps(large_lattice(torch.cuda.Stream(), peak, steps=args.steps, warmup=args.warmup,
+                                       R=args.shell_radius)))
         return
     if args.only_adjoint:
         peak, _ = load_peaks()
