@@ -130,9 +130,11 @@ VX_API int vx_region_mask(const vx_desc* desc, int32_t body, const float loc[3],
  * tile_max voxels (128, 256 or 512); each tile also stages its halo (face
  * neighbours outside it).  Outputs (nullable): number of tiles, halo entries
  * over all tiles, bonds over all tiles (bonds on a tile border counted in both
- * tiles), and the largest owned + halo set of one tile. */
+ * tiles), the largest owned + halo set of one tile, and the longest list of
+ * bonds entering one tile from its halo (both at most 2 tile_max: tiles are
+ * shortened until they fit the kernels' staging). */
 VX_API int vx_plan_tiles(const vx_desc* desc, int32_t tile_max, int64_t* n_tiles, int64_t* n_halo,
-                         int64_t* n_tile_bonds, int32_t* max_local);
+                         int64_t* n_tile_bonds, int32_t* max_local, int32_t* max_halo_bonds);
 
 /* ---- lifetime ------------------------------------------------------------ */
 /* Build the lattice (Sec 2.1: voxelised geometry, composite bonds,

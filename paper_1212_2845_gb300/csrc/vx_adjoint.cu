@@ -213,11 +213,14 @@ __global__ void __launch_bounds__(256) finish_adj(StepArgs A, AdjArgs J) {
   const StPtr Lin(const_cast<float*>(J.lam_in), P), Lout(J.lam_out, P);
   const VoxS lam = Lin.load(v);
   const VoxMeta mt = load_meta(A, v);
+  float4* g4 = reinterpret_cast<float4*>(J.gfm);          // dL/dF, dL/dM.x
+  float2* g2 = reinterpret_cast<float2*>(J.gfm + 4 * P);   // dL/dM.y, dL/dM.z
+  float2* gd = reinterpret_cast<float2*>(J.gdir);          // dL/dE, dL/d(thermal strain)
   if (mt.fl & 1u) {  // fixed: S_{n+1} = S_n
     Lout.store(v, lam);
-    for (int c = 0; c < 6; ++c) J.gfm[c * P + v] = 0.f;
-    J.gdir[v] = 0.f;
-    J.gdir[P + v] = 0.f;
+    g4[v] = make_float4(0.f, 0.f, 0.f, 0.f);
+    g2[v] = make_float2(0.f, 0.f);
+    gd[v] = make_float2(0.f, 0.f);
     return;
   }
   const DevMat& d = A.mats[mt.m];
@@ -358,10 +361,9 @@ __global__ void __launch_bounds__(256) finish_adj(StepArgs A, AdjArgs J) {
   VoxS out;
   out.o = go; out.q = gq; out.v = gv; out.w = gw;
   Lout.store(v, out);
-  J.gfm[0 * P + v] = gF.x; J.gfm[1 * P + v] = gF.y; J.gfm[2 * P + v] = gF.z;
-  J.gfm[3 * P + v] = gM.x; J.gfm[4 * P + v] = gM.y; J.gfm[5 * P + v] = gM.z;
-  J.gdir[v] = g_kv * l;  // kv = E l
-  J.gdir[P + v] = g_adT;
+  g4[v] = make_float4(gF.x, gF.y, gF.z, gM.x);
+  g2[v] = make_float2(gM.y, gM.z);
+  gd[v] = make_float2(g_kv * l, g_adT);  // kv = E l
 }
 
 namespace {
@@ -376,10 +378,11 @@ namespace {
 //   mats DevMat [n_mats]
 template <int TMAX> struct AdjTile {
   static constexpr int ML = 2 * TMAX;
-  static constexpr int kFloats = (NPLANE + 6 + 4) * ML + 48 * TMAX;
+  static constexpr int kFloats = (NPLANE + 6 + 4) * ML + 48 * TMAX + NPLANE * TMAX;
   static size_t bytes(int n_mats) { return kFloats * sizeof(float) + (size_t)n_mats * sizeof(DevMat); }
   float4 *A, *B, *C, *g4, *props, *slot;
-  float* D;
+  float4 *LA, *LB, *LC;  // owned voxels' direct adjoint (finish_adj's part of lam_n)
+  float *D, *LD;
   float2* g2;
   DevMat* mats;
   __device__ __forceinline__ explicit AdjTile(float* base) {
@@ -389,9 +392,13 @@ template <int TMAX> struct AdjTile {
     g4 = C + ML;
     props = g4 + ML;
     slot = props + ML;
-    g2 = reinterpret_cast<float2*>(slot + 12 * TMAX);
+    LA = slot + 12 * TMAX;
+    LB = LA + TMAX;
+    LC = LB + TMAX;
+    g2 = reinterpret_cast<float2*>(LC + TMAX);
     D = reinterpret_cast<float*>(g2 + ML);
-    mats = reinterpret_cast<DevMat*>(D + ML);
+    LD = D + ML;
+    mats = reinterpret_cast<DevMat*>(LD + TMAX);
   }
   __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
   __device__ __forceinline__ V3f gF(int k) const { const float4 g = g4[k]; return v3(g.x, g.y, g.z); }
@@ -461,10 +468,17 @@ __device__ __forceinline__ VoxAdj read_slot(const AdjTile<TMAX>& S, int a, int k
   return r;
 }
 
-// Material-dependent values of one staged voxel: E, G, thermal strain, material.
-__device__ __forceinline__ float4 adj_props(const StepArgs& A, int64_t g, const DevMat& d, int m) {
-  const float E = voxel_E(A, g, m);
-  return make_float4(E, E * d.g_ratio, thermal_strain(A, g, d.cte), __int_as_float(m));
+// Material-dependent values of one staged voxel from its log E and phase:
+// E, G, thermal strain (Sec 2.3, the forward step's formula), material.
+__device__ __forceinline__ float4 adj_props_v(const StepArgs& A, const DevMat& d, int m, float le, float ph) {
+  const float E = A.logE ? expf(le) : d.E;
+  float adT = 0.f;
+  if (A.act_on) {
+    float x = A.act_w + ph;
+    x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
+    adT = __fmul_rn(d.cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
+  }
+  return make_float4(E, E * d.g_ratio, adT, __int_as_float(m));
 }
 
 }  // namespace
@@ -481,32 +495,60 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 2 : 4))
   const int v = v0 + i;
   const int64_t P = A.pitch;
   const StPtr G(const_cast<float*>(A.st_in), P);
+  const StPtr Lg(J.lam_out, P);
+  const float4* gf4 = reinterpret_cast<const float4*>(J.gfm);
+  const float2* gf2 = reinterpret_cast<const float2*>(J.gfm + 4 * P);
+  // ---- staging: every global read of the tile issued back to back (the
+  // halo indices first, then state, bond-sum adjoints and inputs of both
+  // staged voxels of this thread, the owned voxel's partner slots, direct
+  // adjoint and gradients, and up to two halo bonds)
+  const int k1 = i + TMAX;
+  const int g0 = own ? v : (i < NL ? A.halo[ta.z + i - T] : -1);
+  const int g1 = k1 < NL ? (k1 < T ? v0 + k1 : A.halo[ta.z + k1 - T]) : -1;
+  float4 a0, b0, c0, a1, b1, c1, h0, h1;
+  float2 e0, e1;
+  float d0 = 0.f, d1 = 0.f;
+  if (g0 >= 0) { a0 = G.A[g0]; b0 = G.B[g0]; c0 = G.C[g0]; d0 = G.D[g0]; h0 = gf4[g0]; e0 = gf2[g0]; }
+  if (g1 >= 0) { a1 = G.A[g1]; b1 = G.B[g1]; c1 = G.C[g1]; d1 = G.D[g1]; h1 = gf4[g1]; e1 = gf2[g1]; }
+  const int m0 = g0 >= 0 ? A.mat[g0] : 0, m1 = g1 >= 0 ? A.mat[g1] : 0;
+  const float le0 = (g0 >= 0 && A.logE) ? A.logE[g0] : 0.f, le1 = (g1 >= 0 && A.logE) ? A.logE[g1] : 0.f;
+  const float ph0 = (g0 >= 0 && A.phase) ? A.phase[g0] : 0.f, ph1 = (g1 >= 0 && A.phase) ? A.phase[g1] : 0.f;
+  int px = 0xFFFF, py = 0xFFFF, pz = 0xFFFF;
+  uint32_t mask = 0;
+  float4 la, lb, lc;
+  float ld = 0.f, glE = 0.f, glP = 0.f;
+  float2 gdv = make_float2(0.f, 0.f);
+  if (own) {
+    px = A.plus[v]; py = A.plus[A.N + v]; pz = A.plus[2 * A.N + v];
+    mask = A.mask[v];
+    la = Lg.A[v]; lb = Lg.B[v]; lc = Lg.C[v]; ld = Lg.D[v];
+    gdv = reinterpret_cast<const float2*>(J.gdir)[v];
+    glE = J.grad_logE[v];
+    glP = J.grad_phase[v];
+  }
+  const uint32_t hb0 = tb.x + i < tb.y ? A.hbonds[tb.x + i] : 0xFFFFFFFFu;
+  const uint32_t hb1 = tb.x + k1 < tb.y ? A.hbonds[tb.x + k1] : 0xFFFFFFFFu;
   for (int j = i; j < A.n_mats * (int)(sizeof(DevMat) / 4); j += TMAX)
     reinterpret_cast<float*>(S.mats)[j] = reinterpret_cast<const float*>(A.mats)[j];
-  // ---- staging: state, bond-sum adjoints and properties of owned + halo voxels
-  for (int k = i; k < NL; k += TMAX) {
-    const int g = k < T ? v0 + k : A.halo[ta.z + k - T];
-    S.A[k] = G.A[g]; S.B[k] = G.B[g]; S.C[k] = G.C[g]; S.D[k] = G.D[g];
-    S.g4[k] = make_float4(J.gfm[g], J.gfm[P + g], J.gfm[2 * P + g], J.gfm[3 * P + g]);
-    S.g2[k] = make_float2(J.gfm[4 * P + g], J.gfm[5 * P + g]);
-  }
+  if (g0 >= 0) { S.A[i] = a0; S.B[i] = b0; S.C[i] = c0; S.D[i] = d0; S.g4[i] = h0; S.g2[i] = e0; }
+  if (g1 >= 0) { S.A[k1] = a1; S.B[k1] = b1; S.C[k1] = c1; S.D[k1] = d1; S.g4[k1] = h1; S.g2[k1] = e1; }
+  if (own) { S.LA[i] = la; S.LB[i] = lb; S.LC[i] = lc; S.LD[i] = ld; }
   __syncthreads();
-  for (int k = i; k < NL; k += TMAX) {
-    const int g = k < T ? v0 + k : A.halo[ta.z + k - T];
-    const int m = A.mat[g];
-    S.props[k] = adj_props(A, g, S.mats[m], m);
-  }
+  if (g0 >= 0) S.props[i] = adj_props_v(A, S.mats[m0], m0, le0, ph0);
+  if (g1 >= 0) S.props[k1] = adj_props_v(A, S.mats[m1], m1, le1, ph1);
   __syncthreads();
   // ---- own +x, +y, +z bonds (voxel-1 part kept), halo bonds
   VoxAdj acc = voxadj_zero();
   if (own) {
-    const int px = A.plus[v], py = A.plus[A.N + v], pz = A.plus[2 * A.N + v];
     if (px != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 0>(A, S, i, px, T));
     if (py != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 1>(A, S, i, py, T));
     if (pz != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 2>(A, S, i, pz, T));
   }
-  for (int j = tb.x + i; j < tb.y; j += TMAX) {
-    const uint32_t pk = A.hbonds[j];
+  // bonds entering from the halo (at most two per thread: the list fits 2 TMAX)
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const uint32_t pk = r == 0 ? hb0 : hb1;
+    if (pk == 0xFFFFFFFFu) continue;
     const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
     if (ax == 0) tile_bond<TMAX, 0>(A, S, s1, s2, T);
     else if (ax == 1) tile_bond<TMAX, 1>(A, S, s1, s2, T);
@@ -515,24 +557,22 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 2 : 4))
   __syncthreads();
   if (!own) return;
   // ---- lam_n = direct part + own bonds (+x, +y, +z) + -x, -y, -z slots
-  const uint32_t mask = A.mask[v];
 #pragma unroll
   for (int a = 0; a < 3; ++a)
     if (mask & (1u << (2 * a))) voxadj_add(acc, read_slot<TMAX>(S, a, i));
-  const StPtr Lout(J.lam_out, P);
-  VoxS lam = Lout.load(v);
+  VoxS lam = unpack_vox(S.LA[i], S.LB[i], S.LC[i], S.LD[i]);
   lam.o = A3(lam.o, acc.o);
   lam.v = A3(lam.v, acc.v);
   lam.w = A3(lam.w, acc.w);
   lam.q.w += acc.q.w; lam.q.x += acc.q.x; lam.q.y += acc.q.y; lam.q.z += acc.q.z;
-  Lout.store(v, lam);
+  Lg.store(v, lam);
   // parameter gradients: E = exp(log E); thermal strain = cte (T0 + A sin(w_n + phase))
   const float4 pr = S.props[i];
-  J.grad_logE[v] += (J.gdir[v] + acc.E) * pr.x;
+  J.grad_logE[v] = glE + (gdv.x + acc.E) * pr.x;
   if (A.act_on) {
     const int m = __float_as_int(pr.w);
-    const float x = A.act_w + (A.phase ? A.phase[v] : 0.f);
-    J.grad_phase[v] += (J.gdir[P + v] + acc.eps) * S.mats[m].cte * A.actA * cosf(x);
+    const float x = A.act_w + ph0;
+    J.grad_phase[v] = glP + (gdv.y + acc.eps) * S.mats[m].cte * A.actA * cosf(x);
   }
 }
 

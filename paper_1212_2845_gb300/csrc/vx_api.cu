@@ -648,7 +648,7 @@ int vx_plan_dt(const vx_desc* desc, const float* log_E, float dt_factor, double*
 }
 
 int vx_plan_tiles(const vx_desc* desc, int32_t tile_max, int64_t* n_tiles, int64_t* n_halo, int64_t* n_tile_bonds,
-                  int32_t* max_local) {
+                  int32_t* max_local, int32_t* max_halo_bonds) {
   Lattice L;
   int rc = build_lattice(desc, L, g_err);
   if (rc) return rc;
@@ -659,6 +659,7 @@ int vx_plan_tiles(const vx_desc* desc, int32_t tile_max, int64_t* n_tiles, int64
   if (n_halo) *n_halo = (int64_t)T.halo.size();
   if (n_tile_bonds) *n_tile_bonds = T.n_tile_bonds();
   if (max_local) *max_local = T.max_local;
+  if (max_halo_bonds) *max_halo_bonds = T.max_halo_bonds;
   return VX_OK;
 }
 

@@ -193,16 +193,22 @@ int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::
     for (;;) {
       int64_t v1 = v0 + len;
       hl.clear();
+      int64_t nhb = 0;  // bonds entering from the halo (negative-side voxel outside the run)
       for (int64_t v = v0; v < v1; ++v)
         for (int s = 0; s < 6; ++s) {
           int32_t u = nb(v, s);
-          if (u >= 0 && (u < v0 || u >= v1)) hl.push_back(u);
+          if (u >= 0 && (u < v0 || u >= v1)) {
+            hl.push_back(u);
+            if ((s & 1) == 0) ++nhb;
+          }
         }
       std::sort(hl.begin(), hl.end());
       hl.erase(std::unique(hl.begin(), hl.end()), hl.end());
       int64_t nl = len + (int64_t)hl.size();
-      if (nl <= local_max || len <= 32 || (breaks && len < 32)) {
-        if (nl > local_max) { err = "tile staging set too large"; return VX_ERR_ARG; }
+      // both the staged set and the halo-bond list live in local_max slots
+      const bool fits = nl <= local_max && nhb <= local_max;
+      if (fits || len <= 32 || (breaks && len < 32)) {
+        if (!fits) { err = "tile staging set too large"; return VX_ERR_ARG; }
         int32_t T0 = (int32_t)len;
         T.tile_a.insert(T.tile_a.end(), {(int32_t)v0, T0, (int32_t)T.halo.size(), (int32_t)hl.size()});
         auto local = [&](int32_t u) -> uint32_t {
@@ -221,6 +227,7 @@ int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::
         T.tile_b.insert(T.tile_b.end(), {hb0, (int32_t)T.halo_bonds.size(), 0, 0});
         T.halo.insert(T.halo.end(), hl.begin(), hl.end());
         T.max_local = std::max<int>(T.max_local, (int)nl);
+        T.max_halo_bonds = std::max<int>(T.max_halo_bonds, (int)nhb);
         v0 = v1;
         break;
       }

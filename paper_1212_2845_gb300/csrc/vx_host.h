@@ -60,6 +60,7 @@ void quant_params(float l, int* K, int64_t* Q);
 struct Tiling {
   int tile_max = 0;
   int max_local = 0;             // max over tiles of owned + halo voxels
+  int max_halo_bonds = 0;        // max over tiles of bonds entering from the halo (<= local_max)
   std::vector<int32_t> perm;     // internal -> canonical
   std::vector<int32_t> iperm;    // canonical -> internal
   std::vector<int32_t> tile_a;   // 4 per tile: v0, n_owned, halo start, n_halo
@@ -81,8 +82,9 @@ struct Tiling {
 // Local slots must stay below 4096 (12-bit packing).
 constexpr int kMaxLocal = 4095;
 
-// local_max: largest owned + halo set a tile may stage (shared memory bound);
-// tiles are shortened until they fit.  breaks (optional, ascending internal
+// local_max: largest owned + halo set, and largest list of bonds entering
+// from the halo, a tile may stage (shared memory bound); tiles are shortened
+// until both fit.  breaks (optional, ascending internal
 // voxel indices): no tile crosses one.
 int build_tiling(const Lattice& L, int tile_max, int local_max, Tiling& T, std::string& err,
                  const std::vector<int64_t>* breaks = nullptr);

@@ -57,7 +57,7 @@ SIGNATURES = {
     "vx_plan_counts": (C.c_int, [_pdesc, _pi64, _pi64, _pi64]),
     "vx_plan_dt": (C.c_int, [_pdesc, _pf, _f32, _pd]),
     "vx_region_mask": (C.c_int, [_pdesc, _i32, _pf, _pf, _pu8, _pi64]),
-    "vx_plan_tiles": (C.c_int, [_pdesc, _i32, _pi64, _pi64, _pi64, _pi32]),
+    "vx_plan_tiles": (C.c_int, [_pdesc, _i32, _pi64, _pi64, _pi64, _pi32, _pi32]),
     "vx_set_step_form": (C.c_int, [_P, _i32, _i32]),
     "vx_get_tiling": (C.c_int, [_P, _pi32, _pi64, _pi32, _pi64]),
     "vx_set_batching": (C.c_int, [_P, _i64]),
@@ -180,9 +180,10 @@ def plan_dt(sc, log_E=None, dt_factor=None):
 def plan_tiles(sc, tile_max=256):
     h = _DescHolder(sc)
     n = [C.c_int64() for _ in range(3)]
-    ml = C.c_int32()
-    _check(lib().vx_plan_tiles(C.byref(h.desc), int(tile_max), *[C.byref(x) for x in n], C.byref(ml)))
-    return dict(n_tiles=n[0].value, n_halo=n[1].value, n_tile_bonds=n[2].value, max_local=ml.value)
+    ml, mh = C.c_int32(), C.c_int32()
+    _check(lib().vx_plan_tiles(C.byref(h.desc), int(tile_max), *[C.byref(x) for x in n], C.byref(ml), C.byref(mh)))
+    return dict(n_tiles=n[0].value, n_halo=n[1].value, n_tile_bonds=n[2].value, max_local=ml.value,
+                max_halo_bonds=mh.value)
 
 
 FORM_FUSED = 0

@@ -117,3 +117,14 @@ def test_tile_plan_invariants(mk, tile_max):
     # bounded by the halo entries
     assert nb <= t["n_tile_bonds"] <= nb + t["n_halo"] * 6
     assert 0 < t["max_local"] <= 2 * tile_max
+    assert 0 <= t["max_halo_bonds"] <= 2 * tile_max
+
+
+@pytest.mark.parametrize("tile_max", [128, 256])
+def test_sparse_lattice_halo_bond_lists_fit_the_staging(tile_max):
+    """A sparse random lattice (many tile faces per voxel) still gets tiles
+    whose halo-bond lists fit the kernels' staging of 2 tile_max entries."""
+    sc = scenes.random_blob((24, 24, 24), seed=11, fill=0.55, n_mat=2)
+    t = vx.plan_tiles(sc, tile_max)
+    assert 0 < t["max_halo_bonds"] <= 2 * tile_max
+    assert 0 < t["max_local"] <= 2 * tile_max
