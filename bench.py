@@ -281,6 +281,33 @@ def adjoint_form(stream, peak, n_bodies=1024, steps=2000, K=100):
     return out
 
 
+def collision_form(stream, steps=600):
+    """Hollow ball drop (shell R 100, t 8: 926,584 voxels) with floor contact
+    and surface-voxel self-collision on, from the start through the impact
+    (about step 370): per-step launches including the horizon update, the
+    device-flagged candidate rebuilds and the voxel contacts; the cost of one
+    forced rebuild is timed on its own."""
+    from paper_1212_2845_gb300 import vx
+    sc = scenes.hollow_ball(R=100, t=8)
+    sim = vx.Sim(sc)
+    N = sim.N
+    n0, _ = sim.collision_stats()
+    t_run = _events_time(stream, lambda: sim.step_async(steps, stream))
+    if sim.status(stream)[0]:
+        raise RuntimeError("ball drop reported a bad status")
+    n1, _ = sim.collision_stats()
+    pairs = len(sim.collision_pairs())
+    sim.rebuild_collisions(stream)
+    t_reb = _events_time(stream, lambda: sim.rebuild_collisions(stream))
+    out = {"workload": "hollow_ball_R100_t8 drop (floor + self-collision)", "voxels": N, "bonds": sim.n_bonds,
+           "surface_voxels": sim.n_surface, "steps": steps, "value": N * steps / t_run, "unit": METRIC,
+           "us_per_step": 1e6 * t_run / steps, "rebuilds_in_run": n1 - n0,
+           "us_per_forced_rebuild": 1e6 * t_reb, "candidate_pairs_at_end": pairs,
+           "bytes_per_voxel_step": 108, "l2": "inputs larger than L2"}
+    sim.close()
+    return out
+
+
 def small_lattice(stream, steps=1000):
     """Cantilever 10x10x10 (1,000 voxels, 4 tiles): latency-bound.  Per-step
     launches, one cooperative multi-step launch (grid barrier between steps),
@@ -335,6 +362,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true", help="skip the batched / adjoint / small-lattice lines")
     ap.add_argument("--only-adjoint", action="store_true", help="time only the adjoint form (profiling aid)")
     ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
+    ap.add_argument("--only-collisions", action="store_true", help="time only the ball drop with collisions")
     ap.add_argument("--bodies", type=int, default=0, help="bodies for --only-adjoint / --only-batched")
     ap.add_argument("--shell-radius", type=int, default=200, help="outer radius of the --only-large shell")
     ap.add_argument("--form-steps", type=int, default=0, help="steps for --only-adjoint / --only-batched")
@@ -357,6 +385,9 @@ def main():
         peak, _ = load_peaks()
         print(json.dumps(adjoint_form(torch.cuda.Stream(), peak, n_bodies=args.bodies or 1024,
                                       steps=args.form_steps or 2000)))
+        return
+    if args.only_collisions:
+        print(json.dumps(collision_form(torch.cuda.Stream(), steps=args.form_steps or 600)))
         return
     if args.only_batched:
         peak, _ = load_peaks()
@@ -429,6 +460,7 @@ def main():
     if not args.no_forms:
         line["forms"] = {"multi_step_call": multi_step_line(sim, stream, flush),
                          "batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
+                         "collisions": collision_form(stream),
                          "small_lattice": small_lattice(stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)

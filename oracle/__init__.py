@@ -71,6 +71,7 @@ def lib():
             "orc_quant_params": (None, [C.c_double, _I32, C.POINTER(C.c_int64)]),
             "orc_rollout_jvp": (C.c_int, [_P, C.c_long, _D, _D, _D, _D]),
             "orc_linear_static": (C.c_int, [_P, _D, _D]),
+            "orc_stiffness": (None, [_P, _D, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -273,6 +274,16 @@ class Oracle:
         if rc != 0:
             raise FloatingPointError("oracle: non-finite state in dual rollout")
         return loss.value, dloss.value
+
+    def stiffness(self):
+        """Global stiffness K (6N x 6N, per voxel x, y, z, rx, ry, rz) of the
+        lattice at rest assembled from the printed beam matrix, and the lumped
+        mass of every DOF (m, m, m, I, I, I)."""
+        n = 6 * self.N
+        K = np.zeros((n, n))
+        m = np.zeros(n)
+        self._L.orc_stiffness(self.h, _dp(K), _dp(m))
+        return K, m
 
     def linear_static(self, f):
         f = _f64(f, (-1, 6))

@@ -884,11 +884,12 @@ int orc_rollout_jvp(orc_sim* o, long n_steps, const double* dlogE, const double*
 // Assembles the paper's 12x12 beam matrix [K] (Sec 2.1.2) for every bond,
 // rotated onto its lattice axis, and solves K u = f for the free DOFs with
 // dense Gaussian elimination.  u, f: N x 6 (dx,dy,dz,rx,ry,rz).
-int orc_linear_static(orc_sim* o, const double* f, double* u) {
-  Sim<double>& S = o->S;
+// Assembles the global 6N x 6N stiffness of the lattice at rest from each
+// bond's printed 12x12 [K] (Sec 2.1.2), rotated onto its lattice axis.
+static void assemble_stiffness(const Sim<double>& S, std::vector<double>& K) {
   const Topo& T = S.T;
   int N = T.N, n = 6 * N;
-  std::vector<double> K((size_t)n * n, 0.0);
+  K.assign((size_t)n * n, 0.0);
   for (const auto& bd : T.bonds) {
     BeamK<double> k = beam_constants(S, bd.v1, bd.v2);
     double a1 = k.a1, a2 = k.a2, b1 = k.b1, b2 = k.b2, b3 = k.b3;
@@ -917,6 +918,26 @@ int orc_linear_static(orc_sim* o, const double* f, double* u) {
     for (int r = 0; r < 12; ++r)
       for (int c = 0; c < 12; ++c) K[(size_t)gdof(r) * n + gdof(c)] += Ke[r][c];
   }
+}
+
+// Global stiffness (6N x 6N, DOFs x, y, z, rx, ry, rz per voxel) and the
+// lumped mass of every DOF (m for translations, I = m l^2 / 6 for rotations):
+// the linearised dynamics M u'' = -K u of the step at rest.
+void orc_stiffness(orc_sim* o, double* K, double* mdiag) {
+  Sim<double>& S = o->S;
+  std::vector<double> Kv;
+  assemble_stiffness(S, Kv);
+  std::copy(Kv.begin(), Kv.end(), K);
+  for (int v = 0; v < S.T.N; ++v)
+    for (int d = 0; d < 6; ++d) mdiag[6 * v + d] = d < 3 ? S.mass[v] : S.inertia[v];
+}
+
+int orc_linear_static(orc_sim* o, const double* f, double* u) {
+  Sim<double>& S = o->S;
+  const Topo& T = S.T;
+  int N = T.N, n = 6 * N;
+  std::vector<double> K;
+  assemble_stiffness(S, K);
   std::vector<int> free_dofs;
   for (int v = 0; v < N; ++v)
     if (!S.fixed[v]) for (int d = 0; d < 6; ++d) free_dofs.push_back(6 * v + d);

@@ -475,3 +475,32 @@ def test_simulators_of_different_sizes_coexist(vx):
     assert a.status()[0] == 0 and b.status()[0] == 0
     a.close()
     b.close()
+
+
+def test_cantilever_impulse_response_modes(vx):
+    """The kernels ring at the linearised lattice's bending frequencies (the
+    oracle's assembled [K] and lumped masses) after a tip impulse, and follow
+    the oracle's trajectory sample by sample."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_pins import thin_cantilever_scene, bending_frequencies, spectrum_peaks
+    sc = thin_cantilever_scene()
+    ora = Oracle(sc)
+    f_lin = np.unique(np.round(bending_frequencies(ora, sc), 6))[:3]
+    sim = vx.Sim(sc)
+    ora.set_dt(f32_dt(ora))
+    vel = np.zeros((20, 3), np.float32)
+    vel[19, 2] = 1e-3
+    sim.write_state(vel=vel)
+    ora.set_state(vel=vel.astype(np.float64))
+    every, n = 10, 32768
+    zg, zo = np.empty(n), np.empty(n)
+    for i in range(n):
+        sim.step(every)
+        ora.step(every)
+        zg[i] = sim.state()["pos"][19, 2]
+        zo[i] = ora.state()["pos"][19, 2]
+    peaks = spectrum_peaks(zg, every * ora.dt(), f_lin)
+    assert np.all(np.abs(peaks / f_lin - 1.0) <= 2e-3), (peaks, f_lin)
+    amp = np.abs(zo - zo.mean()).max()
+    assert np.abs(zg - zo).max() <= 1e-3 * amp

@@ -494,3 +494,76 @@ def test_forward_mode_matches_central_differences():
     fd = (run(h, h) - run(-h, -h)) / (2 * h)
     assert L == pytest.approx(run(0, 0), rel=1e-12)
     assert dL == pytest.approx(fd, rel=1e-5, abs=1e-12 * abs(L))
+
+
+# ---------------------------------------------------------------------------
+# dynamics: modal frequencies of the thin cantilever (validation section)
+# ---------------------------------------------------------------------------
+
+def thin_cantilever_scene(zeta=0.0):
+    sc = scenes._base([[20, 1, 1]], np.ones(20, np.uint8), 1e-3, [scenes.material(1e6, 0.35, 1000.0)],
+                      zeta_bond=zeta)
+    sc["fixed"] = (np.arange(20) == 0).astype(np.uint8)
+    return sc
+
+
+def bending_frequencies(o, sc):
+    """Frequencies [Hz] of the linearised lattice M u'' = -K u (printed [K],
+    lumped m and I) whose mode moves the tip voxel in z."""
+    import scipy.linalg as sla
+    K, m = o.stiffness()
+    free = np.repeat(sc["fixed"] == 0, 6)
+    w2, phi = sla.eigh(K[np.ix_(free, free)], np.diag(m[free]))
+    f = np.sqrt(np.maximum(w2, 0.0)) / (2 * np.pi)
+    tip_z = 6 * 18 + 2                      # voxel 19 is the 19th free voxel
+    return np.array([f[k] for k in range(len(f)) if abs(phi[tip_z, k]) > 1e-6 * np.abs(phi[tip_z]).max()])
+
+
+def spectrum_peaks(z, dt, guesses):
+    """Peak frequencies of z(t) near each guess (Hann window, parabolic
+    interpolation of the log magnitude around the largest bin)."""
+    z = np.asarray(z) - np.mean(z)
+    spec = np.abs(np.fft.rfft(z * np.hanning(len(z))))
+    freqs = np.fft.rfftfreq(len(z), dt)
+    out = []
+    for g in guesses:
+        lo, hi = np.searchsorted(freqs, 0.85 * g), np.searchsorted(freqs, 1.15 * g)
+        k = lo + int(np.argmax(spec[lo:hi]))
+        a, b, c = np.log(spec[k - 1:k + 2])
+        out.append(freqs[k] + 0.5 * (a - c) / (a - 2 * b + c) * (freqs[1] - freqs[0]))
+    return np.array(out)
+
+
+def test_cantilever_modes_match_beam_theory():
+    """The linearised lattice of a 20x1x1, 1 mm, 1 MPa cantilever (voxel 0
+    fixed) has the Euler-Bernoulli bending frequencies
+    K_n / (2 pi) sqrt(E I / (m L^4)), K_n = 3.516, 22.03, 61.70 (Volterra's
+    constants), for the free length L = 19.5 mm from the clamped voxel's
+    centre to the tip face: the discretisation error grows with the mode."""
+    sc = thin_cantilever_scene()
+    o = Oracle(sc)
+    f = np.unique(np.round(bending_frequencies(o, sc), 6))[:3]
+    EI = 1e6 * (1e-3) ** 4 / 12.0
+    mbar = 1000.0 * (1e-3) ** 2
+    L = 19.5e-3
+    beam = np.array([Kn / (2 * np.pi) * np.sqrt(EI / (mbar * L ** 4)) for Kn in (3.516, 22.03, 61.70)])
+    assert np.all(np.abs(f / beam - 1.0) <= [0.002, 0.01, 0.02]), (f, beam)
+
+
+def test_cantilever_impulse_response_rings_at_the_lattice_frequencies():
+    """An impulse at the tip (no damping) rings at the linearised lattice's
+    bending frequencies: the explicit step reproduces M u'' = -K u."""
+    sc = thin_cantilever_scene()
+    o = Oracle(sc)
+    f_lin = np.unique(np.round(bending_frequencies(o, sc), 6))[:3]
+    vel = np.zeros((20, 3))
+    vel[19, 2] = 1e-3
+    o.set_state(vel=vel)
+    dt = o.dt()
+    every, n = 10, 32768
+    z = np.empty(n)
+    for i in range(n):
+        o.step(every)
+        z[i] = o.state()["pos"][19, 2]
+    peaks = spectrum_peaks(z, every * dt, f_lin)
+    assert np.all(np.abs(peaks / f_lin - 1.0) <= 2e-3), (peaks, f_lin)
