@@ -255,6 +255,15 @@ VX_API int vx_step_async(vx_sim* sim, int64_t n_steps, void* stream);
 /* Wait for `stream`, then report: status (VX_OK / VX_ERR_UNSTABLE /
  * VX_ERR_CAPACITY), first bad step and voxel (canonical index) or -1. */
 VX_API int vx_get_status(vx_sim* sim, void* stream, int32_t* status, int64_t* bad_step, int64_t* bad_voxel);
+/* Relaxation to a static state (the use of App. A: a fixed and loaded,
+ * damped structure stepped until it stops moving): steps in chunks of
+ * check_every steps until the largest voxel speed is at most v_tol [m/s]
+ * after at least one chunk, or max_steps steps are done.  Outputs (any may
+ * be NULL): steps taken, the last largest speed [m/s], converged (1) or not
+ * (0).  Not converging is not an error; VX_ERR_UNSTABLE as vx_step.
+ * Synchronous (one device-to-host read per chunk). */
+VX_API int vx_relax(vx_sim* sim, int64_t max_steps, double v_tol, int32_t check_every, int64_t* steps_taken,
+                    double* max_speed, int32_t* converged, void* stream);
 
 /* ---- collisions (Sec 2.2.2) ---------------------------------------------- */
 /* Rebuild the surface-voxel candidate list from the current positions now. */

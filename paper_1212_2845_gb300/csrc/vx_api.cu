@@ -163,6 +163,7 @@ struct vx_sim {
   int64_t ctr_h[2] = {0, 0};
   // FP64 audit
   double* aud = nullptr;      // per-body origins, per-material values, block partials, result
+  unsigned* vmax_d = nullptr; // relaxation: largest speed (float bits)
   uint64_t ro_gen = 0;        // gen at the end of the recorded rollout
   int64_t ro_steps = 0;       // steps of the recorded rollout (0: none)
   int ro_K = 0;               // checkpoint interval
@@ -733,7 +734,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
-  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
@@ -1496,6 +1497,40 @@ int vx_set_barrier_limits(vx_sim* s, int64_t max_spins, int32_t phantom_ctas) {
   if (max_spins < 0 || phantom_ctas < 0) return fail(VX_ERR_ARG, "limits must be >= 0");
   s->bar_spins = max_spins == 0 ? (1ll << 24) : max_spins;
   s->bar_extra = phantom_ctas;
+  return VX_OK;
+}
+
+int vx_relax(vx_sim* s, int64_t max_steps, double v_tol, int32_t check_every, int64_t* steps_taken,
+             double* max_speed, int32_t* converged, void* stream) {
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (max_steps < 0 || check_every < 1 || !(v_tol >= 0.0))
+    return fail(VX_ERR_ARG, "max_steps >= 0, check_every >= 1 and v_tol >= 0 are required");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (!s->vmax_d && (rc = dalloc(&s->vmax_d, 1))) return rc;
+  int64_t done = 0;
+  float vmax = 0.f;
+  bool ok = false;
+  for (;;) {
+    VX_CUDA(cudaMemsetAsync(s->vmax_d, 0, sizeof(unsigned), st));
+    launch_max_speed(cur_state(s), s->pitch, (int)s->L.N, s->vmax_d, st);
+    unsigned bits = 0;
+    VX_CUDA(cudaMemcpyAsync(&bits, s->vmax_d, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    int32_t code;
+    int64_t bs, bv;
+    if ((rc = vx_get_status(s, stream, &code, &bs, &bv))) return rc;  // waits for the stream
+    if (code == VX_ERR_UNSTABLE)
+      return fail(code, "non-finite state at step " + std::to_string(bs) + ", voxel " + std::to_string(bv));
+    std::memcpy(&vmax, &bits, sizeof(vmax));
+    if (done > 0 && (double)vmax <= v_tol) { ok = true; break; }
+    if (done >= max_steps) break;
+    const int64_t n = std::min<int64_t>(check_every, max_steps - done);
+    if ((rc = vx_step_async(s, n, stream))) return rc;
+    done += n;
+  }
+  if (steps_taken) *steps_taken = done;
+  if (max_speed) *max_speed = (double)vmax;
+  if (converged) *converged = ok ? 1 : 0;
   return VX_OK;
 }
 

@@ -44,6 +44,23 @@ __global__ void reset_state(float* __restrict__ st, int64_t P, int N, uint8_t* _
   store_vox(st, P, v, s);
 }
 
+// Largest speed |v| over the voxels (the bits of a non-negative float order
+// like unsigned integers, so an atomic max is exact and order-independent).
+__global__ void max_speed(const float* __restrict__ st, int64_t P, int N, unsigned* __restrict__ out) {
+  float m = 0.f;
+  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < N; v += gridDim.x * blockDim.x) {
+    const VoxS s = load_vox(st, P, v);
+    m = fmaxf(m, sqrtf(s.v.x * s.v.x + s.v.y * s.v.y + s.v.z * s.v.z));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));
+}
+
+void launch_max_speed(const float* st, int64_t pitch, int N, unsigned* out, cudaStream_t s) {
+  const int nb = (N + 255) / 256 < 1024 ? (N + 255) / 256 : 1024;
+  max_speed<<<nb, 256, 0, s>>>(st, pitch, N, out);
+}
+
 void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* iperm, const uint8_t* flags,
                        float* off, float* quat, float* vel, float* angvel, uint8_t* fl, cudaStream_t s) {
   pack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, iperm, flags, off, quat, vel, angvel, fl);

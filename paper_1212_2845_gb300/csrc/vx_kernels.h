@@ -154,6 +154,8 @@ void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* ipe
 void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, uint8_t* flags, const float* off,
                          const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
                          cudaStream_t s);
+// atomic max of |v| over the voxels into *out (float bits; zero it first)
+void launch_max_speed(const float* st, int64_t pitch, int N, unsigned* out, cudaStream_t s);
 // rest state: zero offsets, identity quaternions, v0 for non-fixed voxels
 void launch_reset_state(float* st, int64_t pitch, int N, uint8_t* flags, float v0x, float v0y, float v0z,
                         cudaStream_t s);

@@ -94,6 +94,7 @@ SIGNATURES = {
     "vx_rollout_forward": (C.c_int, [_P, _i64, _i32, _pf, _P]),
     "vx_graph_capture": (C.c_int, [_P, _i64, _P]),
     "vx_audit": (C.c_int, [_P, _pd, _P]),
+    "vx_relax": (C.c_int, [_P, _i64, C.c_double, _i32, _pi64, _pd, _pi32, _P]),
     "vx_graph_launch": (C.c_int, [_P, _P]),
     "vx_autotune_batching": (C.c_int, [_P, _i32, _pi32, _pi64, _pd, _P]),
     "vx_rollout_backward": (C.c_int, [_P, _pf, _P, _P, _P]),
@@ -379,6 +380,14 @@ class Sim:
 
     def step_async(self, n=1, stream=None):
         _check(self._L.vx_step_async(self.h, int(n), _stream_ptr(stream)))
+
+    def relax(self, max_steps, v_tol, check_every=100, stream=None):
+        """Step until the largest voxel speed is <= v_tol [m/s] (checked every
+        check_every steps) or max_steps; returns (steps, max speed, converged)."""
+        n, v, c = C.c_int64(), C.c_double(), C.c_int32()
+        _check(self._L.vx_relax(self.h, int(max_steps), float(v_tol), int(check_every), C.byref(n), C.byref(v),
+                                C.byref(c), _stream_ptr(stream)))
+        return n.value, v.value, bool(c.value)
 
     def status(self, stream=None):
         st, bs, bv = C.c_int32(), C.c_int64(), C.c_int64()

@@ -504,3 +504,35 @@ def test_cantilever_impulse_response_modes(vx):
     assert np.all(np.abs(peaks / f_lin - 1.0) <= 2e-3), (peaks, f_lin)
     amp = np.abs(zo - zo.mean()).max()
     assert np.abs(zg - zo).max() <= 1e-3 * amp
+
+
+def test_relaxation_to_static_matches_linear_solve(vx):
+    """App. A's static use: the -Y face of the 5x10x5 beam fixed, a small load
+    on the +Y face (1 N, elastic range), damped stepping until every voxel
+    speed is below 1e-4 m/s (the loaded tip moves at ~0.5 m/s; FP32 rounding
+    of the forces keeps speeds near 1e-7-1e-6 m/s even at rest).  The relaxed
+    deflection equals the oracle's linear direct-stiffness solve of the
+    printed [K] to geometric nonlinearity (< 1 %)."""
+    sc = scenes._base([(5, 10, 5)], np.ones(250, np.uint8), 1e-3, [scenes.material(1e7, 0.3)],
+                      zeta_bond=1.0, zeta_ground=0.2)
+    sim = vx.Sim(sc)
+    sim.add_fixed_region(0, (0, 0, 0), (1, 0.01, 1))
+    sim.add_forced_region(0, (0, 0.99, 0), (1, 0.01, 1), (0, 0, -1.0))
+    steps, vmax, ok = sim.relax(400000, 1e-4, check_every=500)
+    assert ok and vmax <= 1e-4 and 0 < steps < 400000, (steps, vmax)
+    ora = Oracle(sc)
+    fixed = ora.region_mask(0, (0, 0, 0), (1, 0.01, 1))
+    ora.set_fixed(fixed)
+    m = ora.region_mask(0, scenes.f32((0, 0.99, 0)), scenes.f32((1, 0.01, 1))).astype(bool)
+    f = np.zeros((ora.N, 6))
+    f[m, 2] = -1.0 / m.sum()
+    u = ora.linear_static(f)
+    g = sim.state()
+    dz = g["pos"][:, 2] - sim.anchors()[:, 2]
+    tip = m
+    assert dz[tip].mean() == pytest.approx(u[tip, 2].mean(), rel=1e-2)
+    assert np.abs(dz - u[:, 2]).max() <= 2e-2 * np.abs(u[:, 2]).max()
+    # already static: converges at the first check
+    n2, v2, ok2 = sim.relax(10000, 1e-4, check_every=500)
+    assert ok2 and n2 == 500
+    sim.close()
