@@ -152,6 +152,7 @@ struct vx_sim {
   int* cflag = nullptr;
   int* any = nullptr;
   long long* nreb = nullptr;
+  unsigned* cbar = nullptr;  // grid barrier words of the rebuild launch
   // adjoint form
   uint64_t gen = 0;           // bumped by every call that changes the state or the model
   uint64_t cfg = 0;           // bumped by every call that changes the model or the step form
@@ -268,6 +269,8 @@ CollideArgs collide_args(vx_sim* s) {
   C.any = s->any;
   C.n_rebuilds = s->nreb;
   C.status = s->status;
+  C.bar = s->cbar;
+  C.spins = s->bar_spins;
   return C;
 }
 
@@ -356,7 +359,7 @@ int alloc_collisions(vx_sim* s) {
   int rc;
   if ((rc = dalloc(&s->surf, S)) || (rc = dalloc(&s->sidx, L.N)) || (rc = dalloc(&s->xq, 3 * S)) ||
       (rc = dalloc(&s->bucket, S)) || (rc = dalloc(&s->hcount, H)) || (rc = dalloc(&s->hcursor, H)) ||
-      (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, (H + 1023) / 1024)) ||
+      (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, kRebuildMaxGrid)) || (rc = dalloc(&s->cbar, 2)) ||
       (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
@@ -374,6 +377,7 @@ int alloc_collisions(vx_sim* s) {
   VX_CUDA(cudaMemset(s->cflag, 0, L.n_bodies * sizeof(int)));
   VX_CUDA(cudaMemset(s->any, 0, sizeof(int)));
   VX_CUDA(cudaMemset(s->nreb, 0, sizeof(long long)));
+  VX_CUDA(cudaMemset(s->cbar, 0, 2 * sizeof(unsigned)));
   s->coll_alloc = true;
   return VX_OK;
 }
@@ -734,7 +738,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
-  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
@@ -964,6 +968,7 @@ int vx_reset(vx_sim* s, const float v0[3]) {
   VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaMemset(s->status, 0, 16));
   VX_CUDA(cudaMemset(s->vmax, 0, 4 * s->L.n_bodies));
+  if (s->cbar) VX_CUDA(cudaMemset(s->cbar, 0, 2 * sizeof(unsigned)));  // clean after a timed-out launch
   s->step = 0;
   if (s->collide_on && (rc = force_rebuild(s, 0))) return rc;
   VX_CUDA(cudaDeviceSynchronize());

@@ -10,17 +10,22 @@
 // Rebuild pipeline (all on the stream, no host round trip):
 //   horizon_update  accumulates 2 max|v| dt per body and raises a body's
 //                   rebuild flag at the threshold
-//   quantise        integer coordinates, cell (edge = horizon) and hash bucket
-//                   of every surface voxel; counts per bucket
-//   scan            exclusive prefix sum of the bucket counts
-//   scatter         surface voxels grouped by bucket (order within a bucket
+//   rebuild_all     one cooperative launch whose phases are separated by
+//                   grid barriers; it returns at once when no body is flagged
+//                   (the usual step), otherwise:
+//     quantise      integer coordinates, cell (edge = horizon) and hash
+//                   bucket of every surface voxel; counts per bucket
+//     scan          exclusive prefix sum of the bucket counts (per-CTA chunk
+//                   scans, then chunk offsets)
+//     scatter       surface voxels grouped by bucket (order within a bucket
 //                   is irrelevant: lists are sorted below)
-//   query           27 neighbour cells per surface voxel of a flagged body;
+//     query         27 neighbour cells per surface voxel of a flagged body;
 //                   candidates sorted ascending by canonical index
-//   finish          clears flags, counts the rebuild
-// Every kernel returns at once when no body is flagged.
+//     finish        clears flags, counts the rebuild
 #include "vx_dev.cuh"
 #include "vx_kernels.h"
+
+#include <algorithm>
 
 namespace vx {
 
@@ -50,10 +55,7 @@ __global__ void horizon_update(CollideArgs C) {
   C.acc[b] = acc;
 }
 
-__global__ void quantise(CollideArgs C) {
-  if (*C.any == 0) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= C.S) return;
+__device__ __forceinline__ void quantise_one(const CollideArgs& C, int s) {
   int v = C.surf[s];
   uint32_t lp = C.lat[v];
   int64_t ijk[3] = {(int64_t)(lp & 2047u), (int64_t)((lp >> 11) & 2047u), (int64_t)(lp >> 22)};
@@ -69,16 +71,8 @@ __global__ void quantise(CollideArgs C) {
   atomicAdd(&C.hcount[h], 1u);
 }
 
-__global__ void zero_counts(CollideArgs C) {
-  if (*C.any == 0) return;
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < C.H; i += gridDim.x * blockDim.x) {
-    C.hcount[i] = 0u;
-    C.hcursor[i] = 0u;
-  }
-}
-
-// Exclusive scan of hcount[0..H) into hstart[0..H] in three phases:
-// per-block scan, scan of the block sums (one block), add the block offsets.
+// Exclusive scan of x over the CTA (all threads call it); returns this
+// thread's prefix and the CTA total.
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot, uint32_t* block_total) {
   int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t inc = x;
@@ -103,51 +97,7 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
   return pre;
 }
 
-__global__ void __launch_bounds__(1024) scan_blocks(CollideArgs C) {
-  if (*C.any == 0) return;
-  __shared__ uint32_t warp_tot[32];
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  uint32_t x = i < C.H ? C.hcount[i] : 0u;
-  uint32_t tot;
-  uint32_t pre = block_exclusive_scan(x, warp_tot, &tot);
-  if (i < C.H) C.hstart[i] = pre;
-  if (threadIdx.x == 0) C.bsum[blockIdx.x] = tot;
-}
-
-__global__ void __launch_bounds__(1024) scan_sums(CollideArgs C, int nb) {
-  if (*C.any == 0) return;
-  __shared__ uint32_t warp_tot[32];
-  uint32_t carry = 0u;
-  for (int base = 0; base < nb; base += blockDim.x) {
-    int i = base + threadIdx.x;
-    uint32_t x = i < nb ? C.bsum[i] : 0u;
-    uint32_t tot;
-    uint32_t pre = block_exclusive_scan(x, warp_tot, &tot);
-    if (i < nb) C.bsum[i] = carry + pre;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) C.hstart[C.H] = carry;
-}
-
-__global__ void __launch_bounds__(1024) scan_add(CollideArgs C) {
-  if (*C.any == 0) return;
-  int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < C.H) C.hstart[i] += C.bsum[blockIdx.x];
-}
-
-__global__ void scatter(CollideArgs C) {
-  if (*C.any == 0) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= C.S) return;
-  uint32_t h = C.bucket[s];
-  uint32_t pos = C.hstart[h] + atomicAdd(&C.hcursor[h], 1u);
-  C.sorted[pos] = s;
-}
-
-__global__ void query(CollideArgs C) {
-  if (*C.any == 0) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= C.S) return;
+__device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   int v = C.surf[s];
   int b = C.body ? C.body[v] : 0;
   if (!C.flag[b]) return;
@@ -194,12 +144,60 @@ __global__ void query(CollideArgs C) {
   if (overflow) atomicOr(C.status, kStatusCapacity);
 }
 
-__global__ void finish(CollideArgs C) {
-  // one block: every thread must see the same *any before it is cleared
-  if (*C.any == 0) return;
-  for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) C.flag[b] = 0;
-  __syncthreads();
-  if (threadIdx.x == 0) { *C.any = 0; *C.n_rebuilds += 1; }
+constexpr int kRebuildThreads = 256;
+
+// The whole rebuild in one cooperative launch (all CTAs co-resident; phases
+// separated by grid barriers, whose waits are bounded: on a timeout the
+// launch ends with the timeout status bit set).
+__global__ void __launch_bounds__(kRebuildThreads) rebuild_all(CollideArgs C) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t offset;
+  if (*C.any == 0) return;  // the same value for every CTA: set by an earlier launch
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
+  const unsigned G = gridDim.x;
+  // zero the bucket counters
+  for (int i = tid; i < C.H; i += nthr) { C.hcount[i] = 0u; C.hcursor[i] = 0u; }
+  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
+  for (int s = tid; s < C.S; s += nthr) quantise_one(C, s);
+  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
+  // scan: CTA c owns buckets [c chunk, (c + 1) chunk)
+  const int chunk = (C.H + (int)G - 1) / (int)G;
+  const int b0 = min(C.H, (int)blockIdx.x * chunk), b1 = min(C.H, b0 + chunk);
+  uint32_t carry = 0u;
+  for (int base = b0; base < b1; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const uint32_t x = i < b1 ? C.hcount[i] : 0u;
+    uint32_t tot;
+    const uint32_t pre = block_exclusive_scan(x, warp_tot, &tot);
+    if (i < b1) C.hstart[i] = carry + pre;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) C.bsum[blockIdx.x] = carry;
+  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
+  {
+    // offset of this CTA's chunk: sum of the chunk totals before it (fixed order)
+    uint32_t part = 0u;
+    for (int c = threadIdx.x; c < (int)blockIdx.x; c += blockDim.x) part += C.bsum[c];
+    uint32_t tot;
+    block_exclusive_scan(part, warp_tot, &tot);
+    if (threadIdx.x == 0) offset = tot;
+    __syncthreads();
+    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) C.hstart[i] += offset;
+    if (blockIdx.x == G - 1 && threadIdx.x == 0) C.hstart[C.H] = offset + carry;
+  }
+  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
+  for (int s = tid; s < C.S; s += nthr) {
+    const uint32_t h = C.bucket[s];
+    C.sorted[C.hstart[h] + atomicAdd(&C.hcursor[h], 1u)] = s;
+  }
+  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
+  for (int s = tid; s < C.S; s += nthr) query_one(C, s);
+  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
+  if (blockIdx.x == 0) {
+    for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) C.flag[b] = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) { *C.any = 0; *C.n_rebuilds += 1; }
+  }
 }
 
 // Raise every body's rebuild flag (forced rebuild).
@@ -211,19 +209,28 @@ __global__ void flag_all(CollideArgs C) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *C.any = 1;
 }
 
+int rebuild_grid_limit() {
+  static int cached[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cached[dev]) {
+    int per_sm = 0, n_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rebuild_all, kRebuildThreads, 0) != cudaSuccess ||
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
+      return 0;
+    cached[dev] = per_sm * n_sm;
+  }
+  return cached[dev];
+}
+
 void launch_rebuild(const CollideArgs& C, cudaStream_t st) {
-  int S = C.S;
-  if (S == 0) return;
-  int tb = 256;
-  int nb = (C.H + 1023) / 1024;
-  zero_counts<<<nb, 1024, 0, st>>>(C);
-  quantise<<<(S + tb - 1) / tb, tb, 0, st>>>(C);
-  scan_blocks<<<nb, 1024, 0, st>>>(C);
-  scan_sums<<<1, 1024, 0, st>>>(C, nb);
-  scan_add<<<nb, 1024, 0, st>>>(C);
-  scatter<<<(S + tb - 1) / tb, tb, 0, st>>>(C);
-  query<<<(S + 127) / 128, 128, 0, st>>>(C);
-  finish<<<1, 256, 0, st>>>(C);
+  if (C.S == 0) return;
+  const int limit = rebuild_grid_limit();
+  const int want = (std::max(C.S, C.H) + kRebuildThreads - 1) / kRebuildThreads;
+  int grid = std::min(std::min(want, limit), kRebuildMaxGrid);
+  if (grid < 1) grid = 1;
+  void* args[1] = {const_cast<CollideArgs*>(&C)};
+  cudaLaunchCooperativeKernel((const void*)rebuild_all, dim3(grid), dim3(kRebuildThreads), args, 0, st);
 }
 
 void launch_flag_all(const CollideArgs& C, cudaStream_t st) {

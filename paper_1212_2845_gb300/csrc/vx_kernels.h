@@ -52,7 +52,11 @@ struct CollideArgs {
   int* any;               // any body flagged
   long long* n_rebuilds;
   int* status;
+  unsigned* bar;          // grid barrier words of the rebuild launch (zero at setup)
+  long long spins;        // barrier wait budget (64 ns naps)
 };
+// the rebuild launch uses at most this many CTAs (bsum holds one entry per CTA)
+constexpr int kRebuildMaxGrid = 1024;
 
 // form 0: fused tile kernel (tile_max threads per CTA, smem bytes of dynamic
 // shared memory); form 1: two-pass bond_pass + voxel_pass.

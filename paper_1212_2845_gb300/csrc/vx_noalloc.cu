@@ -41,11 +41,11 @@ constexpr size_t kOffCount = kOffBucket + align256(kMaxSurface * sizeof(uint32_t
 constexpr size_t kOffCursor = kOffCount + align256(kMaxBuckets * sizeof(uint32_t));
 constexpr size_t kOffStart = kOffCursor + align256(kMaxBuckets * sizeof(uint32_t));
 constexpr size_t kOffBsum = kOffStart + align256((kMaxBuckets + 1) * sizeof(uint32_t));
-constexpr size_t kOffSorted = kOffBsum + align256((kMaxBuckets / 1024 + 1) * sizeof(uint32_t));
+constexpr size_t kOffSorted = kOffBsum + align256(kRebuildMaxGrid * sizeof(uint32_t));
 constexpr size_t kOffIota = kOffSorted + align256(kMaxSurface * sizeof(int32_t));
 constexpr size_t kOffAcc = kOffIota + align256(kMaxSurface * sizeof(int32_t));
 constexpr size_t kOffFlag = kOffAcc + align256(kMaxBodies * sizeof(float));
-constexpr size_t kOffMisc = kOffFlag + align256(kMaxBodies * sizeof(int));  // any, status[4], n_rebuilds
+constexpr size_t kOffMisc = kOffFlag + align256(kMaxBodies * sizeof(int));  // any, status[4], n_rebuilds, barrier
 constexpr size_t kScratchBytes = kOffMisc + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -133,7 +133,10 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.any = reinterpret_cast<int*>(base + kOffMisc);
   C.status = reinterpret_cast<int*>(base + kOffMisc + 16);
   C.n_rebuilds = reinterpret_cast<long long*>(base + kOffMisc + 64);
+  C.bar = reinterpret_cast<unsigned*>(base + kOffMisc + 128);
+  C.spins = 1ll << 24;
   cudaError_t e = cudaMemsetAsync(C.status, 0, 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
   iota_kernel<<<(n_surface + 255) / 256, 256, 0, st>>>(const_cast<int32_t*>(C.surf), n_surface);
   launch_flag_all(C, st);

@@ -324,41 +324,6 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
   pipe_tiles<TMAX>(A, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
 }
 
-// Grid-wide barrier of a cooperative launch (every CTA co-resident).  The
-// last CTA to arrive resets the count and releases the generation; the others
-// wait on it with a bounded spin.  Returns false (and sets the timeout status
-// bit) if the wait gave up, after which the caller ends the launch.  Every
-// thread then performs its own acquire, so its later loads (including
-// cp.async) see every write released before the barrier.
-__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned n_ctas, long long max_spins, int* status) {
-  __shared__ int ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    ok = 1;
-    unsigned gen, prev, now;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
-    asm volatile("atom.acq_rel.gpu.global.add.u32 %0, [%1], 1;" : "=r"(prev) : "l"(bar) : "memory");
-    if (prev + 1 == n_ctas) {
-      asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
-      asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
-    } else {
-      for (long long it = 0;; ++it) {
-        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
-        if (now != gen) break;
-        if (it >= max_spins) {
-          atomicOr(status, kStatusTimeout);
-          ok = 0;
-          break;
-        }
-        __nanosleep(64);
-      }
-    }
-  }
-  __syncthreads();
-  asm volatile("{\n .reg .u32 t;\n ld.acquire.gpu.global.u32 t, [%0];\n}" ::"l"(bar + 1) : "memory");
-  return ok != 0;
-}
-
 // Multi-step form: one cooperative launch runs n steps of the whole lattice;
 // every CTA walks its tiles of a step (as fused_pipe), then all CTAs meet at
 // a grid barrier before the next step reads what this one wrote.  The
