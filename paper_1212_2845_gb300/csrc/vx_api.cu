@@ -457,7 +457,7 @@ int upload_tiling(vx_sim* s) {
 int ensure_pipe(vx_sim* s, const StepArgs& A) {
   int nm = (int)s->L.palette.size();
   size_t sm = pipe_smem_bytes(s->tile_max, A.phase != nullptr, A.logE != nullptr, A.body != nullptr,
-                              A.fext != nullptr, nm, nm <= kLutMaxMats);
+                              A.fext != nullptr, A.collide_on != 0, nm, nm <= kLutMaxMats);
   if (sm != s->pipe_smem) {
     if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0 || prepare_batched(s->tile_max, sm) != 0 ||
         prepare_multi(s->tile_max, sm, (int)s->T.n_tiles(), &s->multi_grid) != 0)

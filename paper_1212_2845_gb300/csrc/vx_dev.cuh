@@ -386,6 +386,7 @@ struct VoxMeta {
   uint8_t fl;     // flags
   float dt, z0;   // body timestep, anchor height of the voxel centre
   V3f fext;
+  int si;         // surface index (collisions on) or -1
 };
 
 __device__ __forceinline__ VoxMeta load_meta(const StepArgs& A, int v) {
@@ -398,6 +399,7 @@ __device__ __forceinline__ VoxMeta load_meta(const StepArgs& A, int v) {
   mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
   const int64_t P = A.pitch;
   mt.fext = A.fext ? v3(A.fext[v], A.fext[P + v], A.fext[2 * P + v]) : v3(0.f, 0.f, 0.f);
+  mt.si = A.collide_on ? A.sidx[v] : -1;
   return mt;
 }
 
@@ -426,7 +428,7 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
   const float hl = mul_(0.5f, l);
   float h = fma_(hl, adT, hl);  // current half size l (1 + adT) / 2
   if (A.collide_on) {
-    int si = A.sidx[v];
+    int si = mt.si;
     if (si >= 0) {
       const uint32_t lp = mt.lat;
       int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);

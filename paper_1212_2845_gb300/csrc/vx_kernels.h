@@ -66,7 +66,7 @@ size_t fused_smem_bytes(int tile_max, int n_mats, bool lut);
 int prepare_fused(int tile_max, size_t smem);
 // Pipelined persistent form: shared memory for the optional per-voxel arrays
 // in use, kernel preparation (returns the persistent grid) and launch.
-size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, int n_mats, bool lut);
+size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, bool col, int n_mats, bool lut);
 int prepare_pipe(int tile_max, size_t smem, int* grid);
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s);
 

@@ -58,13 +58,14 @@ template <int TMAX> struct Stage {
   uint32_t* lat;
   int32_t* body;   // null for one body
   float* fx;       // 3 x TMAX external force (null when unused)
+  int32_t* si;     // surface index of owned voxels (null without collisions)
   uint32_t* hb;    // halo bonds
   // floats this layout needs
-  static __host__ __device__ int floats(bool ph, bool le, bool body, bool fext) {
+  static __host__ __device__ int floats(bool ph, bool le, bool body, bool fext, bool col) {
     return 13 * ML + ML + (ph ? ML : 0) + (le ? ML : 0) + 2 * TMAX + TMAX + (body ? TMAX : 0) + (fext ? 3 * TMAX : 0) +
-           ML;
+           ML + (col ? TMAX : 0);
   }
-  __device__ __forceinline__ void carve(float* base, bool hph, bool hle, bool hbody, bool hfext) {
+  __device__ __forceinline__ void carve(float* base, bool hph, bool hle, bool hbody, bool hfext, bool hcol) {
     A = reinterpret_cast<float4*>(base);
     B = A + ML;
     C = B + ML;
@@ -77,7 +78,8 @@ template <int TMAX> struct Stage {
     ph = hph ? p : nullptr; p += hph ? ML : 0;
     le = hle ? p : nullptr; p += hle ? ML : 0;
     body = hbody ? reinterpret_cast<int32_t*>(p) : nullptr; p += hbody ? TMAX : 0;
-    fx = hfext ? p : nullptr;
+    fx = hfext ? p : nullptr; p += hfext ? 3 * TMAX : 0;
+    si = hcol ? reinterpret_cast<int32_t*>(p) : nullptr;
   }
   __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
 };
@@ -102,6 +104,7 @@ __device__ __forceinline__ void issue_tile(const StepArgs& A, const StPtr& G, co
     cp8(&S.pl[i], &A.plus2[g]);
     cp4(&S.lat[i], &A.lat[g]);
     if (S.body) cp4(&S.body[i], &A.body[g]);
+    if (S.si) cp4(&S.si[i], &A.sidx[g]);
     if (S.fx) {
       cp4(&S.fx[i], &A.fext[g]);
       cp4(&S.fx[TMAX + i], &A.fext[A.pitch + g]);
@@ -225,6 +228,7 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
     mt.dt = A.dt_body[mt.b];
     mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
     mt.fext = S.fx ? v3(S.fx[i], S.fx[TMAX + i], S.fx[2 * TMAX + i]) : v3(0.f, 0.f, 0.f);
+    mt.si = S.si ? S.si[i] : -1;
     body = mt.b;
     store_bond_sums(A, cur.v0 + i, F, M);
     speed = voxel_finish(A, cur.v0 + i, mt, s, F, M, pr.z, pr.x, mats);
@@ -236,8 +240,8 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
 
 template <int TMAX> struct PipeSmem {
   static constexpr int ML = 2 * TMAX;
-  static size_t bytes(bool ph, bool le, bool body, bool fext, int n_mats, bool lut) {
-    size_t f = 2 * (size_t)Stage<TMAX>::floats(ph, le, body, fext) + 4 * ML + 18 * TMAX;
+  static size_t bytes(bool ph, bool le, bool body, bool fext, bool col, int n_mats, bool lut) {
+    size_t f = 2 * (size_t)Stage<TMAX>::floats(ph, le, body, fext, col) + 4 * ML + 18 * TMAX;
     return f * sizeof(float) + (size_t)n_mats * sizeof(DevMat) + (lut ? (size_t)8 * n_mats * n_mats * 4 : 0);
   }
 };
@@ -249,6 +253,7 @@ template <int TMAX>
 __device__ __forceinline__ void pipe_tiles(const StepArgs& A, float* smem, int sf, float4* props, float4* F4,
                                            float2* F2, const DevMat* mats, const float* lut) {
   const bool hph = A.phase != nullptr, hle = A.logE != nullptr, hbody = A.body != nullptr, hfx = A.fext != nullptr;
+  const bool hcol = A.collide_on != 0;
   const int i = threadIdx.x;
   const int Gs = gridDim.x;
   int t = blockIdx.x;
@@ -257,7 +262,7 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& A, float* smem, int s
   TileRegs cur = load_tile<TMAX>(A, t, A.n_tiles);
   {
     Stage<TMAX> S0;
-    S0.carve(smem, hph, hle, hbody, hfx);
+    S0.carve(smem, hph, hle, hbody, hfx, hcol);
     issue_tile<TMAX>(A, G, S0, cur);
   }
   cp_commit();
@@ -266,12 +271,12 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& A, float* smem, int s
   int b = 0;
   for (;;) {
     Stage<TMAX> S;
-    S.carve(smem + b * sf, hph, hle, hbody, hfx);
+    S.carve(smem + b * sf, hph, hle, hbody, hfx, hcol);
     // 1. stream the next tile into the other buffer; its flags into a register
     uint8_t fl_nxt = 0;
     if (nxt.valid) {
       Stage<TMAX> Sn;
-      Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx);
+      Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx, hcol);
       issue_tile<TMAX>(A, G, Sn, nxt);
       fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
     }
@@ -300,7 +305,8 @@ template <int TMAX> struct PipeLayout {
   float* lut;
   __device__ __forceinline__ PipeLayout(float* smem, const StepArgs& A) {
     constexpr int ML = 2 * TMAX;
-    sf = Stage<TMAX>::floats(A.phase != nullptr, A.logE != nullptr, A.body != nullptr, A.fext != nullptr);
+    sf = Stage<TMAX>::floats(A.phase != nullptr, A.logE != nullptr, A.body != nullptr, A.fext != nullptr,
+                             A.collide_on != 0);
     props = reinterpret_cast<float4*>(smem + 2 * sf);
     F4 = props + ML;
     F2 = reinterpret_cast<float2*>(F4 + 3 * TMAX);
@@ -360,8 +366,8 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
   constexpr int ML = 2 * TMAX;
   extern __shared__ __align__(16) float smem[];
   const bool hph = A0.phase != nullptr, hle = A0.logE != nullptr, hbody = A0.body != nullptr,
-             hfx = A0.fext != nullptr;
-  const int sf = Stage<TMAX>::floats(hph, hle, hbody, hfx);
+             hfx = A0.fext != nullptr, hcol = A0.collide_on != 0;
+  const int sf = Stage<TMAX>::floats(hph, hle, hbody, hfx, hcol);
   float4* props = reinterpret_cast<float4*>(smem + 2 * sf);
   float4* F4 = props + ML;
   float2* F2 = reinterpret_cast<float2*>(F4 + 3 * TMAX);
@@ -391,7 +397,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
       TileRegs cur = load_tile<TMAX>(A, t0, t1);
       {
         Stage<TMAX> S0;
-        S0.carve(smem, hph, hle, hbody, hfx);
+        S0.carve(smem, hph, hle, hbody, hfx, hcol);
         issue_tile<TMAX>(A, G, S0, cur);
       }
       cp_commit();
@@ -400,11 +406,11 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
       int b = 0;
       for (int t = t0;; ++t) {
         Stage<TMAX> S;
-        S.carve(smem + b * sf, hph, hle, hbody, hfx);
+        S.carve(smem + b * sf, hph, hle, hbody, hfx, hcol);
         uint8_t fl_nxt = 0;
         if (nxt.valid) {
           Stage<TMAX> Sn;
-          Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx);
+          Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx, hcol);
           issue_tile<TMAX>(A, G, Sn, nxt);
           fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
         }
@@ -424,9 +430,9 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
   }
 }
 
-size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, int n_mats, bool lut) {
-  if (tile_max == 128) return PipeSmem<128>::bytes(ph, le, body, fext, n_mats, lut);
-  return PipeSmem<256>::bytes(ph, le, body, fext, n_mats, lut);
+size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, bool col, int n_mats, bool lut) {
+  if (tile_max == 128) return PipeSmem<128>::bytes(ph, le, body, fext, col, n_mats, lut);
+  return PipeSmem<256>::bytes(ph, le, body, fext, col, n_mats, lut);
 }
 
 int prepare_pipe(int tile_max, size_t smem, int* grid) {
