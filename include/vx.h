@@ -216,8 +216,12 @@ VX_API int vx_set_forces(vx_sim* sim, const float* F);
 /* Damping ratios (paper App. B SetBondDampZ, SetSlowDampZ, SetCollisionDampZ);
  * each in [0, 1]; larger values may be unstable (the paper says the same). */
 VX_API int vx_set_damping(vx_sim* sim, float zeta_bond, float zeta_ground, float zeta_collision);
-/* Gravity along z [m/s^2] (e.g. -9.81), floor plane z = 0 on/off,
- * voxel self-collision on/off (Sec 2.2). */
+/* Gravity along z [m/s^2] (e.g. -9.81), floor plane z = 0 on/off, and
+ * voxel-voxel collisions (Sec 2.2.2): 0 off; 1 within each body (bodies are
+ * separate worlds); 2 one shared world, in which voxels of different bodies
+ * collide too (never excluded by lattice distance), one horizon accumulator
+ * covers all bodies and every body runs on the smallest body timestep.
+ * Other values return VX_ERR_ARG. */
 VX_API int vx_set_environment(vx_sim* sim, float gravity_z, int32_t floor_on, int32_t collide_on);
 /* Volumetric actuation (Sec 2.3): the temperature offset of voxel v at step n
  * is offset + amplitude * sin(2 pi n / period + phase_v) (period 0: offset

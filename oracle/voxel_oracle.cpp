@@ -343,6 +343,12 @@ template <class R> static void compute_dt(Sim<R>& S) {
   S.dt.assign(T.n_bodies, 0.0);
   for (int b = 0; b < T.n_bodies; ++b)
     S.dt[b] = wmax[b] > 0 ? S.prm.dt_factor / (2.0 * M_PI * wmax[b]) : 0.0;
+  if (S.prm.collide_on == 2) {  // one world, one clock: the smallest timestep
+    double dmin = 0.0;
+    for (int b = 0; b < T.n_bodies; ++b)
+      if (S.dt[b] > 0 && (dmin == 0.0 || S.dt[b] < dmin)) dmin = S.dt[b];
+    for (int b = 0; b < T.n_bodies; ++b) S.dt[b] = dmin;
+  }
 }
 
 // Temperature offset of a voxel at step n (Sec 2.3): T_c - T_r.
@@ -403,31 +409,60 @@ template <class R> static void bond_force(const Sim<R>& S, int id, const std::ve
   }
 }
 
-// Collision candidates of one body (Sec 2.2.2): surface voxels i<j of the same
-// body, lattice Manhattan distance > 3, quantised centre distance < 2 voxels.
+// Collision candidates (Sec 2.2.2): surface voxels i<j, quantised centre
+// distance < 2 voxels; two voxels of one body must also be more than 3 apart
+// in lattice Manhattan distance.  Voxels of different bodies pair only in the
+// shared-world mode (collide_on == 2: all bodies in one world), where they
+// are never excluded.
 template <class R> static bool cand_pred(const Sim<R>& S, int i, int j, const std::vector<std::array<int64_t, 3>>& xq) {
   const Topo& T = S.T;
-  if (T.body[i] != T.body[j]) return false;
-  int man = std::abs(T.vi[i] - T.vi[j]) + std::abs(T.vj[i] - T.vj[j]) + std::abs(T.vk[i] - T.vk[j]);
-  if (man <= 3) return false;
+  if (T.body[i] != T.body[j]) {
+    if (S.prm.collide_on != 2) return false;
+  } else {
+    int man = std::abs(T.vi[i] - T.vi[j]) + std::abs(T.vj[i] - T.vj[j]) + std::abs(T.vk[i] - T.vk[j]);
+    if (man <= 3) return false;
+  }
   int64_t dx = xq[i][0] - xq[j][0], dy = xq[i][1] - xq[j][1], dz = xq[i][2] - xq[j][2];
   int64_t two = 2 * S.qQ;
   return dx * dx + dy * dy + dz * dz < two * two;
 }
 
+// Quantised centre: lattice index * Q + rint(offset * 2^K), plus in the
+// shared-world mode the body origin rint(origin * 2^K), so that all bodies
+// share one integer frame.
 template <class R> static std::vector<std::array<int64_t, 3>> quantise_positions(const Sim<R>& S) {
   const Topo& T = S.T;
   std::vector<std::array<int64_t, 3>> xq(T.N);
   for (int v = 0; v < T.N; ++v) {
     V3<double> an = S.anchor(v);
     int c[3] = {T.vi[v], T.vj[v], T.vk[v]};
+    const V3<double>& org = S.origin[T.body[v]];
     for (int a = 0; a < 3; ++a) {
       double o = val(S.D[v][a]) - an[a];
-      xq[v][a] = (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(o, S.qK));
+      int64_t qo = S.prm.collide_on == 2 ? (int64_t)std::nearbyint(std::ldexp(org[a], S.qK)) : 0;
+      xq[v][a] = qo + (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(o, S.qK));
     }
   }
   return xq;
 }
+
+// Shared world: every body's candidates at once (pairs may cross bodies).
+template <class R> static void rebuild_world(Sim<R>& S) {
+  const Topo& T = S.T;
+  auto xq = quantise_positions(S);
+  for (int i = 0; i < T.N; ++i) S.partners[i].clear();
+  for (int i = 0; i < T.N; ++i) {
+    if (!T.surface[i]) continue;
+    for (int j = i + 1; j < T.N; ++j) {
+      if (!T.surface[j]) continue;
+      if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
+    }
+  }
+  for (int i = 0; i < T.N; ++i) std::sort(S.partners[i].begin(), S.partners[i].end());
+  S.n_rebuilds++;
+}
+
+template <class R> static void rebuild_all_candidates(Sim<R>& S);
 
 template <class R> static void rebuild_candidates(Sim<R>& S, int body) {
   const Topo& T = S.T;
@@ -453,6 +488,11 @@ template <class R> static double horizon_threshold(const Sim<R>& S) {
   for (int v = 0; v < S.T.N; ++v) amax = std::max(amax, std::fabs(S.cte[v]));
   double cmax = S.T.l * (1.0 + amax * (std::fabs(S.prm.act_T0) + std::fabs(S.prm.act_A)));
   return 2.0 * S.T.l - cmax;
+}
+
+template <class R> static void rebuild_all_candidates(Sim<R>& S) {
+  if (S.prm.collide_on == 2) rebuild_world(S);
+  else for (int b = 0; b < S.T.n_bodies; ++b) rebuild_candidates(S, b);
 }
 
 // One synchronous step of every voxel (Sec 2.1: all forces, then all positions).
@@ -547,8 +587,14 @@ template <class R> static int step(Sim<R>& S) {
     vmax[T.body[v]] = std::max(vmax[T.body[v]], sp);
   }
   S.n++;
-  // (4) collision horizon (Sec 2.2.2)
-  if (p.collide_on) {
+  // (4) collision horizon (Sec 2.2.2); in the shared world one accumulator
+  // over every body (relative motion between bodies counts too)
+  if (p.collide_on == 2) {
+    double vm = 0.0;
+    for (int b = 0; b < T.n_bodies; ++b) vm = std::max(vm, vmax[b]);
+    S.acc[0] += 2.0 * vm * S.dt[0];
+    if (S.acc[0] >= horizon_threshold(S)) { rebuild_world(S); S.acc[0] = 0.0; }
+  } else if (p.collide_on) {
     double thr = horizon_threshold(S);
     for (int b = 0; b < T.n_bodies; ++b) {
       S.acc[b] += 2.0 * vmax[b] * S.dt[b];
@@ -701,13 +747,13 @@ int orc_region_mask(orc_sim* o, int body, const double* loc, const double* size,
 
 void orc_reset(orc_sim* o, const double* v0) {
   reset_state(o->S, v0);
-  if (o->S.prm.collide_on)
-    for (int b = 0; b < o->S.T.n_bodies; ++b) rebuild_candidates(o->S, b);
+  if (o->S.prm.collide_on) rebuild_all_candidates(o->S);
 }
 
 // Rebuild every body's collision candidates from the current positions.
 void orc_reset_candidates(orc_sim* o) {
-  for (int b = 0; b < o->S.T.n_bodies; ++b) { rebuild_candidates(o->S, b); o->S.acc[b] = 0.0; }
+  rebuild_all_candidates(o->S);
+  for (int b = 0; b < o->S.T.n_bodies; ++b) o->S.acc[b] = 0.0;
 }
 
 double orc_get_dt(orc_sim* o, int body) { return o->S.dt[body]; }
@@ -799,7 +845,8 @@ long orc_pairs_from_offsets(orc_sim* o, const double* off, int32_t* pairs, long 
   for (int v = 0; v < T.N; ++v) {
     int c[3] = {T.vi[v], T.vj[v], T.vk[v]};
     for (int a = 0; a < 3; ++a)
-      xq[v][a] = (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(off[3 * v + a], S.qK));
+      xq[v][a] = (S.prm.collide_on == 2 ? (int64_t)std::nearbyint(std::ldexp(S.origin[T.body[v]][a], S.qK)) : 0) +
+                 (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(off[3 * v + a], S.qK));
   }
   long n = 0;
   for (int i = 0; i < T.N; ++i) {
@@ -817,15 +864,21 @@ long orc_partners_of(orc_sim* o, const double* off, int i, int32_t* out, long ca
   Sim<double>& S = o->S;
   const Topo& T = S.T;
   if (!T.surface[i]) return 0;
+  const bool world = S.prm.collide_on == 2;
   auto q = [&](int v, int a) {
     int c[3] = {T.vi[v], T.vj[v], T.vk[v]};
-    return (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(off[3 * v + a], S.qK));
+    return (world ? (int64_t)std::nearbyint(std::ldexp(S.origin[T.body[v]][a], S.qK)) : 0) +
+           (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(off[3 * v + a], S.qK));
   };
   long n = 0;
   for (int j = 0; j < T.N; ++j) {
-    if (j == i || !T.surface[j] || T.body[j] != T.body[i]) continue;
-    int man = std::abs(T.vi[i] - T.vi[j]) + std::abs(T.vj[i] - T.vj[j]) + std::abs(T.vk[i] - T.vk[j]);
-    if (man <= 3) continue;
+    if (j == i || !T.surface[j]) continue;
+    if (T.body[j] != T.body[i]) {
+      if (!world) continue;
+    } else {
+      int man = std::abs(T.vi[i] - T.vi[j]) + std::abs(T.vj[i] - T.vj[j]) + std::abs(T.vk[i] - T.vk[j]);
+      if (man <= 3) continue;
+    }
     int64_t dx = q(i, 0) - q(j, 0), dy = q(i, 1) - q(j, 1), dz = q(i, 2) - q(j, 2);
     if (dx * dx + dy * dy + dz * dz < 4 * S.qQ * S.qQ) { if (n < cap) out[n] = j; ++n; }
   }

@@ -153,6 +153,7 @@ struct vx_sim {
   int* any = nullptr;
   long long* nreb = nullptr;
   unsigned* cbar = nullptr;  // grid barrier words of the rebuild launch
+  int64_t* qorg = nullptr;   // shared world: quantised body origins rint(origin 2^K), 3 per body
   // adjoint form
   uint64_t gen = 0;           // bumped by every call that changes the state or the model
   uint64_t cfg = 0;           // bumped by every call that changes the model or the step form
@@ -271,6 +272,7 @@ CollideArgs collide_args(vx_sim* s) {
   C.status = s->status;
   C.bar = s->cbar;
   C.spins = s->bar_spins;
+  C.qorg = s->collide_on == 2 ? s->qorg : nullptr;
   return C;
 }
 
@@ -338,6 +340,12 @@ int upload_dt(vx_sim* s) {
 
 int recompute_dt(vx_sim* s) {
   stable_dt(s->L, s->logE_h.empty() ? nullptr : s->logE_h.data(), s->dt_factor, s->dt);
+  if (s->collide_on == 2) {  // one world, one clock: every body takes the smallest timestep
+    double dmin = 0.0;
+    for (double d : s->dt)
+      if (d > 0.0 && (dmin == 0.0 || d < dmin)) dmin = d;
+    for (double& d : s->dt) d = dmin;
+  }
   return upload_dt(s);
 }
 
@@ -738,7 +746,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
-  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar);
+  dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar); dfree(s->qorg);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
@@ -912,11 +920,21 @@ int vx_set_environment(vx_sim* s, float gravity_z, int32_t floor_on, int32_t col
   int rc = check_sim(s);
   if (rc) return rc;
   if (!std::isfinite(gravity_z)) return fail(VX_ERR_ARG, "gravity must be finite");
+  if (collide_on < 0 || collide_on > 2) return fail(VX_ERR_ARG, "collide_on must be 0, 1 or 2");
   s->gz = gravity_z;
   s->floor_on = floor_on ? 1 : 0;
   int was = s->collide_on;
-  s->collide_on = collide_on ? 1 : 0;
-  if (s->collide_on && !was) {
+  s->collide_on = collide_on;
+  if (collide_on == 2 && !s->qorg) {
+    const int nb = s->L.n_bodies;
+    std::vector<int64_t> q(3 * (size_t)nb);
+    for (int b = 0; b < nb; ++b)
+      for (int a = 0; a < 3; ++a) q[3 * b + a] = (int64_t)std::nearbyint(std::ldexp((double)s->L.origin[3 * b + a], s->qK));
+    if ((rc = dalloc(&s->qorg, q.size()))) return rc;
+    VX_CUDA(cudaMemcpy(s->qorg, q.data(), q.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  }
+  if ((collide_on == 2) != (was == 2) && (rc = recompute_dt(s))) return rc;
+  if (s->collide_on && s->collide_on != was) {
     if ((rc = force_rebuild(s, 0))) return rc;
     VX_CUDA(cudaDeviceSynchronize());
   }

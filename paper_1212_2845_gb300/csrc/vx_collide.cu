@@ -2,14 +2,17 @@
 //
 // A pair (i, j) of surface voxels of one body is a candidate when their
 // lattice Manhattan distance exceeds 3 and their centres are closer than the
-// 2-voxel collision horizon.  The distance test runs on integers: each
+// 2-voxel collision horizon.  In a shared world (bodies collide with each
+// other) voxels of different bodies pair on distance alone, and every body's
+// quantised origin rint(origin 2^K) puts all bodies in one integer frame.  The distance test runs on integers: each
 // coordinate is anchor * Q + rint(offset * 2^K) (2^K ~ 65536 / l, exact power
 // of two scaling of the FP32 offset), so the candidate set is a bit-exact
 // function of the FP32 state.
 //
 // Rebuild pipeline (all on the stream, no host round trip):
 //   horizon_update  accumulates 2 max|v| dt per body and raises a body's
-//                   rebuild flag at the threshold
+//                   rebuild flag at the threshold (in a shared world of
+//                   several bodies, one accumulator for all of them)
 //   rebuild_all     one cooperative launch whose phases are separated by
 //                   grid barriers; it returns at once when no body is flagged
 //                   (the usual step), otherwise:
@@ -41,6 +44,32 @@ __device__ __forceinline__ uint32_t cell_hash(int64_t cx, int64_t cy, int64_t cz
   return (uint32_t)h & mask;
 }
 
+// Shared world: one accumulator over all bodies (relative motion between
+// bodies counts), kept in slot 0; a rebuild flags every body.  One block.
+__global__ void horizon_update_world(CollideArgs C) {
+  __shared__ float red[256];
+  float m = 0.f;
+  for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) {
+    m = fmaxf(m, __uint_as_float(C.vmax_bits[b]));
+    C.vmax_bits[b] = 0u;
+  }
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const float acc = C.acc[0] + 2.f * red[0] * C.dt_body[0];
+  const bool rebuild = acc >= C.threshold;
+  __syncthreads();
+  if (rebuild)
+    for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) C.flag[b] = 1;
+  if (threadIdx.x == 0) {
+    C.acc[0] = rebuild ? 0.f : acc;
+    if (rebuild) atomicExch(C.any, 1);
+  }
+}
+
 __global__ void horizon_update(CollideArgs C) {
   int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= C.n_bodies) return;
@@ -59,10 +88,11 @@ __device__ __forceinline__ void quantise_one(const CollideArgs& C, int s) {
   int v = C.surf[s];
   uint32_t lp = C.lat[v];
   int64_t ijk[3] = {(int64_t)(lp & 2047u), (int64_t)((lp >> 11) & 2047u), (int64_t)(lp >> 22)};
+  const int64_t* qo = C.qorg ? C.qorg + 3 * (C.body ? C.body[v] : 0) : nullptr;
   int64_t xq[3];
   for (int a = 0; a < 3; ++a) {
     float o = C.st[(int64_t)v * C.ostride_v + a * C.ostride_a];
-    xq[a] = ijk[a] * C.Q + llrintf(ldexpf(o, C.K));
+    xq[a] = (qo ? qo[a] : 0) + ijk[a] * C.Q + llrintf(ldexpf(o, C.K));
     C.xq[(int64_t)a * C.S + s] = xq[a];
   }
   int64_t cs = 2 * C.Q;
@@ -122,10 +152,13 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
           int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
           if (floordiv(x1, cs) != ncx || floordiv(y1, cs) != ncy || floordiv(z1, cs) != ncz) continue;
           int u = C.surf[t];
-          if (C.body && C.body[u] != b) continue;
-          uint32_t lq = C.lat[u];
-          int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
-          if (man <= 3) continue;
+          if (C.body && C.body[u] != b) {
+            if (!C.qorg) continue;  // bodies are separate worlds
+          } else {
+            uint32_t lq = C.lat[u];
+            int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
+            if (man <= 3) continue;
+          }
           int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
           if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
           if (n < kCandCap) list[n++] = u; else overflow = true;
@@ -238,6 +271,10 @@ void launch_flag_all(const CollideArgs& C, cudaStream_t st) {
 }
 
 void launch_horizon(const CollideArgs& C, cudaStream_t st) {
+  if (C.qorg) {
+    horizon_update_world<<<1, 256, 0, st>>>(C);
+    return;
+  }
   horizon_update<<<(C.n_bodies + 255) / 256, 256, 0, st>>>(C);
 }
 

@@ -442,6 +442,12 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
         V3f dd = v3(fma_((float)((int)(lq & 2047u) - vi), l, sub_(ja.x, s.o.x)),
                     fma_((float)((int)((lq >> 11) & 2047u) - vj), l, sub_(ja.y, s.o.y)),
                     fma_((float)((int)(lq >> 22) - vk), l, sub_(ja.z, s.o.z)));
+        if (A.body) {  // a partner of another body (shared world): add the origins' difference
+          const int bj = A.body[j];
+          if (bj != mt.b)
+            dd = add(dd, v3(sub_(A.origin[3 * bj], A.origin[3 * mt.b]), sub_(A.origin[3 * bj + 1], A.origin[3 * mt.b + 1]),
+                            sub_(A.origin[3 * bj + 2], A.origin[3 * mt.b + 2])));
+        }
         float r2 = dot3(dd, dd);
         int mj = A.mat[j];
         const DevMat& dj = mats[mj];

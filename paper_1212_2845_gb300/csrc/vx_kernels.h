@@ -52,6 +52,7 @@ struct CollideArgs {
   int* any;               // any body flagged
   long long* n_rebuilds;
   int* status;
+  const int64_t* qorg;    // shared world: quantised body origins (3 per body), else nullptr
   unsigned* bar;          // grid barrier words of the rebuild launch (zero at setup)
   long long spins;        // barrier wait budget (64 ns naps)
 };

@@ -134,6 +134,7 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.status = reinterpret_cast<int*>(base + kOffMisc + 16);
   C.n_rebuilds = reinterpret_cast<long long*>(base + kOffMisc + 64);
   C.bar = reinterpret_cast<unsigned*>(base + kOffMisc + 128);
+  C.qorg = nullptr;
   C.spins = 1ll << 24;
   cudaError_t e = cudaMemsetAsync(C.status, 0, 16, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st);

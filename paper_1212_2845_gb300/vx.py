@@ -251,7 +251,8 @@ class Sim:
         _check(self._L.vx_set_damping(self.h, zb, zg, zc))
 
     def set_environment(self, gravity_z, floor, collide):
-        _check(self._L.vx_set_environment(self.h, float(gravity_z), int(bool(floor)), int(bool(collide))))
+        # collide: False/0 off, True/1 within each body, 2 one shared world
+        _check(self._L.vx_set_environment(self.h, float(gravity_z), int(bool(floor)), int(collide)))
 
     def set_actuation(self, amplitude, period, offset=0.0):
         _check(self._L.vx_set_actuation(self.h, float(amplitude), int(period), float(offset)))

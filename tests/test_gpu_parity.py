@@ -536,3 +536,39 @@ def test_relaxation_to_static_matches_linear_solve(vx):
     n2, v2, ok2 = sim.relax(10000, 1e-4, check_every=500)
     assert ok2 and n2 == 500
     sim.close()
+
+
+def test_shared_world_collision_matches_oracle(vx):
+    """Two cubes in one world approach head-on, collide and bounce: the
+    kernels follow the oracle, and the candidate set of the final GPU
+    snapshot (cross-body pairs included) equals the oracle's brute force on
+    the same offsets bit for bit."""
+    import sys, os
+    sys.path.insert(0, os.path.dirname(__file__))
+    from test_oracle_pins import two_cubes
+    sc, v = two_cubes()
+    sim, ora = pair(vx, sc)
+    assert sim.dt()[0] == sim.dt()[1]
+    N = sim.N
+    vel = np.zeros((N, 3), np.float32)
+    vel[: N // 2, 0] = v
+    vel[N // 2:, 0] = -v
+    sim.write_state(vel=vel)
+    sim.rebuild_collisions()
+    ora.set_state(vel=vel.astype(np.float64))
+    ora.reset_candidates()
+    cross = 0
+    for _ in range(40):
+        sim.step(100)
+        ora.step(100)
+        cross += sum(1 for i, j in sim.collision_pairs() if (i < N // 2) != (j < N // 2))
+    g, o = sim.state(), ora.state()
+    assert cross > 0
+    assert pos_error(sc, g, o) < 1e-3
+    assert g["vel"][: N // 2, 0].mean() < 0 < g["vel"][N // 2:, 0].mean()
+    off = sim.read_state()["offset"].astype(np.float64)
+    sim.rebuild_collisions()
+    got = {tuple(int(x) for x in p) for p in sim.collision_pairs()}
+    ref = {tuple(int(x) for x in p) for p in ora.pairs_from_offsets(off)}
+    assert got == ref
+    sim.close()

@@ -567,3 +567,63 @@ def test_cantilever_impulse_response_rings_at_the_lattice_frequencies():
         z[i] = o.state()["pos"][19, 2]
     peaks = spectrum_peaks(z, every * dt, f_lin)
     assert np.all(np.abs(peaks / f_lin - 1.0) <= 2e-3), (peaks, f_lin)
+
+
+# ---------------------------------------------------------------------------
+# shared world (several bodies colliding with each other)
+# ---------------------------------------------------------------------------
+
+def two_cubes(gap_voxels=3, v=0.2, n=3):
+    """Two n^3 cubes of 1 mm voxels on the x axis, `gap_voxels` empty voxels
+    apart, approaching head-on at +-v; one shared world (collide = 2)."""
+    l = 1e-3
+    sc = scenes._base([(n, n, n), (n, n, n)], np.ones(2 * n ** 3, np.uint8), l, [scenes.material(1e6)],
+                      collide=2, zeta_collision=0.0, zeta_bond=1.0)
+    sc["origin"] = scenes.f32([[0.0, 0.0, 0.0], [(n + gap_voxels) * l, 0.0, 0.0]])
+    return sc, v
+
+
+def test_shared_world_bodies_collide_and_bounce():
+    """Voxels of different bodies are candidates only in the shared world,
+    the contact pairs are exactly antisymmetric (total momentum constant to
+    rounding), the bodies bounce apart, and both bodies run on the smaller
+    timestep."""
+    sc, v = two_cubes()
+    o = Oracle(sc)
+    assert o.dt(0) == o.dt(1)
+    N = o.N
+    vel = np.zeros((N, 3))
+    vel[: N // 2, 0] = v
+    vel[N // 2:, 0] = -v
+    o.set_state(vel=vel)
+    o.reset_candidates()
+    assert len(o.candidate_pairs()) == 0                 # 3 voxels apart: outside the horizon
+    p0 = o.momentum()[:3]
+    seen_cross = 0
+    for _ in range(40):
+        o.step(100)
+        pairs = o.candidate_pairs()
+        seen_cross += sum(1 for i, j in pairs if (i < N // 2) != (j < N // 2))
+    s = o.state()
+    assert seen_cross > 0
+    assert np.abs(o.momentum()[:3] - p0).max() <= 1e-12 * v * o.N * 1e-6
+    m = 1000.0 * 1e-9
+    va = s["vel"][: N // 2, 0].mean()
+    vb = s["vel"][N // 2:, 0].mean()
+    assert va < 0 < vb                                     # bounced apart
+
+
+def test_separate_worlds_never_pair_bodies():
+    sc, v = two_cubes(gap_voxels=0)                         # touching faces
+    sc["collide"] = True                                    # self-collision only
+    o = Oracle(sc)
+    o.reset_candidates()
+    N = o.N
+    assert all((i < N // 2) == (j < N // 2) for i, j in o.candidate_pairs())
+    sc["collide"] = 2
+    o = Oracle(sc)
+    o.reset_candidates()
+    cross = [(i, j) for i, j in o.candidate_pairs() if (i < N // 2) != (j < N // 2)]
+    # face-to-face neighbours across the two bodies (3 x 3 facing voxels, each
+    # within 2 voxels of its facing partner and its in-plane neighbours)
+    assert len(cross) > 0 and all(i < N // 2 <= j for i, j in cross)
