@@ -308,6 +308,30 @@ def collision_form(stream, steps=600):
     return out
 
 
+def collision_schemes(stream, steps=2000):
+    """The paper's comparison of collision schemes on a synthetic clapper
+    (880 voxels, arms closing and touching during the run): candidates among
+    all voxels or surface voxels only, rebuilt every step or when the horizon
+    accumulator requires it.  Iteration rate of each scheme over the same
+    steps (per-step launches)."""
+    from paper_1212_2845_gb300 import vx
+    sc = scenes.clapper()
+    out = {"workload": "clapper (880 voxels, 2 bilayer arms, +-10 K, contact during the run)", "steps": steps}
+    for name, all_voxels, every in (("all+every", True, True), ("surf+every", False, True),
+                                    ("all+horizon", True, False), ("surf+horizon", False, False)):
+        sim = vx.Sim(sc)
+        sim.set_multistep(0)
+        sim.set_collision_scheme(all_voxels, every)
+        n0, _ = sim.collision_stats()
+        t = _events_time(stream, lambda: sim.step_async(steps, stream))
+        if sim.status(stream)[0]:
+            raise RuntimeError("clapper reported a bad status")
+        n1, _ = sim.collision_stats()
+        out[name] = {"steps_per_s": steps / t, "us_per_step": 1e6 * t / steps, "rebuilds": n1 - n0}
+        sim.close()
+    return out
+
+
 def small_lattice(stream, steps=1000):
     """Cantilever 10x10x10 (1,000 voxels, 4 tiles): latency-bound.  Per-step
     launches, one cooperative multi-step launch (grid barrier between steps),
@@ -387,7 +411,9 @@ def main():
                                       steps=args.form_steps or 2000)))
         return
     if args.only_collisions:
-        print(json.dumps(collision_form(torch.cuda.Stream(), steps=args.form_steps or 600)))
+        st = torch.cuda.Stream()
+        print(json.dumps({"ball": collision_form(st, steps=args.form_steps or 600),
+                          "schemes": collision_schemes(st)}))
         return
     if args.only_batched:
         peak, _ = load_peaks()
@@ -461,6 +487,7 @@ def main():
         line["forms"] = {"multi_step_call": multi_step_line(sim, stream, flush),
                          "batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
                          "collisions": collision_form(stream),
+                         "collision_schemes": collision_schemes(stream),
                          "small_lattice": small_lattice(stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)

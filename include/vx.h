@@ -185,8 +185,8 @@ VX_API int vx_set_batching(vx_sim* sim, int64_t group_voxels);
  * step.  on = 0 always launches once per step. */
 VX_API int vx_set_multistep(vx_sim* sim, int32_t on);
 /* Fault-injection aid for tests of the bounded waits: the budget of one grid
- * barrier wait in 64 ns naps (0 restores the default of 2^24, about one
- * second) and a number of phantom CTAs the barrier also waits for (0 in
+ * barrier wait in units of 128 SM clock cycles (0 restores the default of
+ * 2^24, about one second) and a number of phantom CTAs the barrier also waits for (0 in
  * normal use; any other value makes every barrier run out, after which the
  * launch ends with VX_ERR_TIMEOUT and the state is that of a partial step
  * sequence: reset or write it before stepping on).  Host-side only; no GPU
@@ -272,6 +272,12 @@ VX_API int vx_relax(vx_sim* sim, int64_t max_steps, double v_tol, int32_t check_
 /* ---- collisions (Sec 2.2.2) ---------------------------------------------- */
 /* Rebuild the surface-voxel candidate list from the current positions now. */
 VX_API int vx_rebuild_collisions(vx_sim* sim, void* stream);
+/* Collision scheme (the paper compares these, Sec 3 "Speedup of self
+ * collision schemes"): all_voxels = 1 searches every voxel instead of the
+ * precomputed surface voxels; every_step = 1 rebuilds the candidates every
+ * step instead of when the horizon accumulator says so.  Defaults 0, 0
+ * (surface + horizon).  Rebuilds the candidates now if collisions are on. */
+VX_API int vx_set_collision_scheme(vx_sim* sim, int32_t all_voxels, int32_t every_step);
 /* Current candidate pairs (i < j, canonical indices, sorted by i then j) into
  * host memory pairs [cap][2]; n_out = total count (may exceed cap). */
 VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int64_t* n_out);
@@ -368,7 +374,7 @@ VX_API int vx_rollout_backward(vx_sim* sim, const float* w_body, float* grad_log
  * Limits: n_surface <= VX_STATIC_MAX_SURFACE, n_bodies <= VX_STATIC_MAX_BODIES
  * (larger inputs return VX_ERR_ARG); more than 48 candidates for a voxel
  * returns VX_ERR_CAPACITY.  Scratch comes from one fixed device array of
- * about 4 MiB that every GPU loading the library holds until exit.  The first
+ * about 5 MiB that every GPU loading the library holds until exit.  The first
  * call on a device (with that device current) looks up the array's address;
  * make it before any stream capture.  Calls share the array: calls whose GPU
  * work overlaps race and must be serialised by the caller.  Work is enqueued

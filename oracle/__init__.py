@@ -72,6 +72,7 @@ def lib():
             "orc_rollout_jvp": (C.c_int, [_P, C.c_long, _D, _D, _D, _D]),
             "orc_linear_static": (C.c_int, [_P, _D, _D]),
             "orc_stiffness": (None, [_P, _D, _D]),
+            "orc_set_collision_scheme": (None, [_P, C.c_int, C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -141,6 +142,12 @@ class Oracle:
         le = None if log_E is None else _f64(log_E)
         ph = None if phase is None else _f64(phase)
         self._L.orc_set_voxel_params(self.h, _dp(le), _dp(ph))
+
+    def set_collision_scheme(self, all_voxels=False, every_step=False):
+        """The paper's collision-scheme comparison: candidates among all
+        voxels (not only surface voxels); rebuild every step (not on the
+        horizon trigger)."""
+        self._L.orc_set_collision_scheme(self.h, int(bool(all_voxels)), int(bool(every_step)))
 
     def set_fixed(self, mask):
         m = np.ascontiguousarray(mask, dtype=np.uint8)

@@ -250,6 +250,9 @@ struct Params {
   double zeta_bond = 1.0, zeta_ground = 0.0, zeta_collision = 1.0;
   double gravity_z = 0.0;
   int floor_on = 0, collide_on = 0;
+  // collision scheme (the paper's comparison): candidates among all voxels
+  // instead of surface voxels; rebuild every step instead of on the horizon
+  int cand_all = 0, cand_every = 0;
   double act_A = 0.0, act_T0 = 0.0;
   long act_P = 0;
   double dt_factor = 0.9;
@@ -452,9 +455,9 @@ template <class R> static void rebuild_world(Sim<R>& S) {
   auto xq = quantise_positions(S);
   for (int i = 0; i < T.N; ++i) S.partners[i].clear();
   for (int i = 0; i < T.N; ++i) {
-    if (!T.surface[i]) continue;
+    if (!S.prm.cand_all && !T.surface[i]) continue;
     for (int j = i + 1; j < T.N; ++j) {
-      if (!T.surface[j]) continue;
+      if (!S.prm.cand_all && !T.surface[j]) continue;
       if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
     }
   }
@@ -470,9 +473,9 @@ template <class R> static void rebuild_candidates(Sim<R>& S, int body) {
   int lo = T.body_first[body], hi = T.body_first[body + 1];
   for (int i = lo; i < hi; ++i) S.partners[i].clear();
   for (int i = lo; i < hi; ++i) {
-    if (!T.surface[i]) continue;
+    if (!S.prm.cand_all && !T.surface[i]) continue;
     for (int j = i + 1; j < hi; ++j) {
-      if (!T.surface[j]) continue;
+      if (!S.prm.cand_all && !T.surface[j]) continue;
       if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
     }
   }
@@ -589,7 +592,9 @@ template <class R> static int step(Sim<R>& S) {
   S.n++;
   // (4) collision horizon (Sec 2.2.2); in the shared world one accumulator
   // over every body (relative motion between bodies counts too)
-  if (p.collide_on == 2) {
+  if (p.collide_on && p.cand_every) {
+    rebuild_all_candidates(S);
+  } else if (p.collide_on == 2) {
     double vm = 0.0;
     for (int b = 0; b < T.n_bodies; ++b) vm = std::max(vm, vmax[b]);
     S.acc[0] += 2.0 * vm * S.dt[0];
@@ -709,6 +714,11 @@ void orc_set_params(orc_sim* o, double zeta_bond, double zeta_ground, double zet
   p.gravity_z = gravity_z; p.floor_on = floor_on; p.collide_on = collide_on;
   p.act_A = act_A; p.act_P = act_P; p.act_T0 = act_T0; p.dt_factor = dt_factor;
   compute_dt(o->S);
+}
+
+void orc_set_collision_scheme(orc_sim* o, int all_voxels, int every_step) {
+  o->S.prm.cand_all = all_voxels ? 1 : 0;
+  o->S.prm.cand_every = every_step ? 1 : 0;
 }
 
 void orc_set_voxel_params(orc_sim* o, const double* logE, const double* phase) {
@@ -850,9 +860,9 @@ long orc_pairs_from_offsets(orc_sim* o, const double* off, int32_t* pairs, long 
   }
   long n = 0;
   for (int i = 0; i < T.N; ++i) {
-    if (!T.surface[i]) continue;
+    if (!S.prm.cand_all && !T.surface[i]) continue;
     for (int j = i + 1; j < T.N; ++j) {
-      if (!T.surface[j]) continue;
+      if (!S.prm.cand_all && !T.surface[j]) continue;
       if (cand_pred(S, i, j, xq)) { if (n < cap) { pairs[2 * n] = i; pairs[2 * n + 1] = j; } ++n; }
     }
   }
@@ -863,7 +873,7 @@ long orc_pairs_from_offsets(orc_sim* o, const double* off, int32_t* pairs, long 
 long orc_partners_of(orc_sim* o, const double* off, int i, int32_t* out, long cap) {
   Sim<double>& S = o->S;
   const Topo& T = S.T;
-  if (!T.surface[i]) return 0;
+  if (!S.prm.cand_all && !T.surface[i]) return 0;
   const bool world = S.prm.collide_on == 2;
   auto q = [&](int v, int a) {
     int c[3] = {T.vi[v], T.vj[v], T.vk[v]};
@@ -872,7 +882,7 @@ long orc_partners_of(orc_sim* o, const double* off, int i, int32_t* out, long ca
   };
   long n = 0;
   for (int j = 0; j < T.N; ++j) {
-    if (j == i || !T.surface[j]) continue;
+    if (j == i || (!S.prm.cand_all && !T.surface[j])) continue;
     if (T.body[j] != T.body[i]) {
       if (!world) continue;
     } else {

@@ -107,7 +107,7 @@ struct vx_sim {
   int multistep = 1;          // use it for vx_step(n > 1) in the pipelined form without collisions
   int multi_grid = 0;
   unsigned* bar = nullptr;    // grid barrier words
-  int64_t bar_spins = 1ll << 24;  // barrier wait budget: 2^24 naps of 64 ns, about one second
+  int64_t bar_spins = 1ll << 24;  // barrier wait budget in 128-cycle units: about one second
   int32_t bar_extra = 0;      // phantom CTAs (fault injection)
   // batched form
   int64_t group_voxels = 0;   // 0: off
@@ -133,12 +133,16 @@ struct vx_sim {
   float* stage = nullptr;
   // collisions
   bool coll_alloc = false;
+  int coll_all = 0;          // candidates among all voxels (not only surface voxels)
+  int coll_every = 0;        // rebuild every step (not on the horizon trigger)
+  int64_t coll_S = 0;        // voxels in the candidate search
   int H = 0, qK = 0;
   int64_t qQ = 0;
   float threshold = 0.f;
   int32_t* surf = nullptr;
   int32_t* sidx = nullptr;
   int64_t* xq = nullptr;
+  int4* cell = nullptr;
   uint32_t* bucket = nullptr;
   uint32_t* hcount = nullptr;
   uint32_t* hcursor = nullptr;
@@ -242,7 +246,7 @@ StepArgs step_args(vx_sim* s) {
 
 CollideArgs collide_args(vx_sim* s) {
   CollideArgs C;
-  C.S = (int)s->L.n_surface;
+  C.S = (int)s->coll_S;
   C.n_bodies = s->L.n_bodies;
   C.H = s->H;
   C.K = s->qK;
@@ -256,6 +260,7 @@ CollideArgs collide_args(vx_sim* s) {
   C.body = s->body;
   C.dt_body = s->dtb;
   C.xq = s->xq;
+  C.cell = s->cell;
   C.bucket = s->bucket;
   C.hcount = s->hcount;
   C.hcursor = s->hcursor;
@@ -360,21 +365,23 @@ void update_threshold(vx_sim* s) {
 int alloc_collisions(vx_sim* s) {
   if (s->coll_alloc) return VX_OK;
   const Lattice& L = s->L;
-  int64_t S = L.n_surface;
+  int64_t S = s->coll_all ? L.N : L.n_surface;
+  s->coll_S = S;
   int H = 1024;
   while ((int64_t)H < 2 * S) H <<= 1;
   s->H = H;
   int rc;
   if ((rc = dalloc(&s->surf, S)) || (rc = dalloc(&s->sidx, L.N)) || (rc = dalloc(&s->xq, 3 * S)) ||
+      (rc = dalloc(&s->cell, S)) ||
       (rc = dalloc(&s->bucket, S)) || (rc = dalloc(&s->hcount, H)) || (rc = dalloc(&s->hcursor, H)) ||
       (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, kRebuildMaxGrid)) || (rc = dalloc(&s->cbar, 2)) ||
       (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
     return rc;
-  // surface voxels in ascending internal order
+  // searched voxels (surface voxels, or all) in ascending internal order
   std::vector<int32_t> surf(S), sidx(L.N, -1);
-  for (int64_t i = 0; i < S; ++i) surf[i] = s->T.iperm[L.surf_list[i]];
+  for (int64_t i = 0; i < S; ++i) surf[i] = s->coll_all ? (int32_t)i : s->T.iperm[L.surf_list[i]];
   std::sort(surf.begin(), surf.end());
   for (int64_t i = 0; i < S; ++i) sidx[surf[i]] = (int32_t)i;
   s->surf_h = surf;
@@ -388,6 +395,14 @@ int alloc_collisions(vx_sim* s) {
   VX_CUDA(cudaMemset(s->cbar, 0, 2 * sizeof(unsigned)));
   s->coll_alloc = true;
   return VX_OK;
+}
+
+void free_collisions(vx_sim* s) {
+  dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket); dfree(s->hcount); dfree(s->hcursor);
+  dfree(s->hstart); dfree(s->bsum); dfree(s->cbar); dfree(s->sorted); dfree(s->ccount); dfree(s->cand);
+  dfree(s->acc); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
+  s->coll_alloc = false;
+  s->coll_S = 0;
 }
 
 int force_rebuild(vx_sim* s, cudaStream_t st) {
@@ -741,7 +756,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->iperm); dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds); dfree(s->mask);
   dfree(s->tdesc); dfree(s->hfix); dfree(s->vw); dfree(s->plus2);
   dfree(s->phase); dfree(s->logE); dfree(s->fext); dfree(s->mats); dfree(s->lut); dfree(s->dtb); dfree(s->origin);
-  dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->bucket);
+  dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
@@ -1135,7 +1150,8 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     s->step += 1;
     if (s->collide_on) {
       CollideArgs C = collide_args(s);
-      launch_horizon(C, st);
+      if (s->coll_every) launch_flag_all(C, st);  // rebuild every step
+      else launch_horizon(C, st);
       launch_rebuild(C, st);
     }
   }
@@ -1187,7 +1203,7 @@ int vx_get_collision_pairs(vx_sim* s, int32_t* pairs, int64_t cap, int64_t* n_ou
   int rc = check_sim(s);
   if (rc) return rc;
   if (cap > 0 && !pairs) return fail(VX_ERR_ARG, "pairs is NULL");
-  int64_t S = s->L.n_surface;
+  int64_t S = s->coll_S;
   if (!s->coll_alloc || S == 0) { if (n_out) *n_out = 0; return VX_OK; }
   VX_CUDA(cudaDeviceSynchronize());
   std::vector<int32_t> cnt(S), cand(S * kCandCap);
@@ -1554,6 +1570,24 @@ int vx_relax(vx_sim* s, int64_t max_steps, double v_tol, int32_t check_every, in
   if (steps_taken) *steps_taken = done;
   if (max_speed) *max_speed = (double)vmax;
   if (converged) *converged = ok ? 1 : 0;
+  return VX_OK;
+}
+
+int vx_set_collision_scheme(vx_sim* s, int32_t all_voxels, int32_t every_step) {
+  if (s) { ++s->gen; ++s->cfg; }
+  int rc = check_sim(s);
+  if (rc) return rc;
+  const int all = all_voxels ? 1 : 0;
+  if (all != s->coll_all && s->coll_alloc) {
+    VX_CUDA(cudaDeviceSynchronize());
+    free_collisions(s);
+  }
+  s->coll_all = all;
+  s->coll_every = every_step ? 1 : 0;
+  if (s->collide_on) {
+    if ((rc = force_rebuild(s, 0))) return rc;
+    VX_CUDA(cudaDeviceSynchronize());
+  }
   return VX_OK;
 }
 

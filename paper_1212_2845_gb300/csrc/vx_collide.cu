@@ -96,7 +96,9 @@ __device__ __forceinline__ void quantise_one(const CollideArgs& C, int s) {
     C.xq[(int64_t)a * C.S + s] = xq[a];
   }
   int64_t cs = 2 * C.Q;
-  uint32_t h = cell_hash(floordiv(xq[0], cs), floordiv(xq[1], cs), floordiv(xq[2], cs), C.H - 1);
+  const int64_t cx = floordiv(xq[0], cs), cy = floordiv(xq[1], cs), cz = floordiv(xq[2], cs);
+  C.cell[s] = make_int4((int)cx, (int)cy, (int)cz, 0);  // cells of a world fit in 32 bits
+  uint32_t h = cell_hash(cx, cy, cz, C.H - 1);
   C.bucket[s] = h;
   atomicAdd(&C.hcount[h], 1u);
 }
@@ -133,7 +135,8 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   if (!C.flag[b]) return;
   int64_t x0 = C.xq[s], y0 = C.xq[(int64_t)C.S + s], z0 = C.xq[2 * (int64_t)C.S + s];
   int64_t cs = 2 * C.Q;
-  int64_t cx = floordiv(x0, cs), cy = floordiv(y0, cs), cz = floordiv(z0, cs);
+  const int4 c0 = C.cell[s];
+  const int cx = c0.x, cy = c0.y, cz = c0.z;
   uint32_t lp = C.lat[v];
   int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);
   int64_t r2max = cs * cs;  // (2 Q)^2
@@ -143,14 +146,15 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   for (int dz = -1; dz <= 1; ++dz)
     for (int dy = -1; dy <= 1; ++dy)
       for (int dx = -1; dx <= 1; ++dx) {
-        int64_t ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
+        const int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
         uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
         uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
         for (uint32_t e = e0; e < e1; ++e) {
           int t = C.sorted[e];
           if (t == s) continue;
+          const int4 c1 = C.cell[t];
+          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
           int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
-          if (floordiv(x1, cs) != ncx || floordiv(y1, cs) != ncy || floordiv(z1, cs) != ncz) continue;
           int u = C.surf[t];
           if (C.body && C.body[u] != b) {
             if (!C.qorg) continue;  // bodies are separate worlds

@@ -344,10 +344,13 @@ __device__ __forceinline__ void record_bad(const StepArgs& A, int v) {
 
 // Grid-wide barrier of a cooperative launch (every CTA co-resident).  The
 // last CTA to arrive resets the count and releases the generation; the others
-// wait on it with a bounded spin.  Returns false (and sets the timeout status
-// bit) if the wait gave up, after which the caller ends the launch.  Every
-// thread then performs its own acquire, so its later loads (including
-// cp.async) see every write released before the barrier.
+// poll it, busily for the first few hundred polls (CTAs of one launch arrive
+// within microseconds) and then with short naps, for at most a budget of
+// max_spins x 128 SM clock cycles (2^24: about a second at 2 GHz).  Returns
+// false (and sets the timeout status bit) if the wait gave up, after which
+// the caller ends the launch.  Every thread then performs its own acquire,
+// so its later loads (including cp.async) see every write released before
+// the barrier.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned n_ctas, long long max_spins, int* status) {
   __shared__ int ok;
   __syncthreads();
@@ -360,15 +363,16 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned n_ctas, lon
       asm volatile("st.relaxed.gpu.global.u32 [%0], 0;" ::"l"(bar) : "memory");
       asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(bar + 1) : "memory");
     } else {
-      for (long long it = 0;; ++it) {
+      const long long t0 = clock64(), budget = max_spins * 128;
+      for (int it = 0;; ++it) {
         asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(now) : "l"(bar + 1) : "memory");
         if (now != gen) break;
-        if (it >= max_spins) {
+        if (clock64() - t0 > budget) {
           atomicOr(status, kStatusTimeout);
           ok = 0;
           break;
         }
-        __nanosleep(64);
+        if (it >= 256) __nanosleep(32);
       }
     }
   }

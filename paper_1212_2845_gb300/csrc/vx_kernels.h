@@ -38,6 +38,7 @@ struct CollideArgs {
   const int32_t* body;    // or nullptr
   const float* dt_body;
   int64_t* xq;            // 3 planes of S
+  int4* cell;             // S: integer cell (edge = horizon) of each searched voxel
   uint32_t* bucket;       // S
   uint32_t* hcount;       // H
   uint32_t* hcursor;      // H
@@ -54,7 +55,7 @@ struct CollideArgs {
   int* status;
   const int64_t* qorg;    // shared world: quantised body origins (3 per body), else nullptr
   unsigned* bar;          // grid barrier words of the rebuild launch (zero at setup)
-  long long spins;        // barrier wait budget (64 ns naps)
+  long long spins;        // barrier wait budget (units of 128 SM cycles)
 };
 // the rebuild launch uses at most this many CTAs (bsum holds one entry per CTA)
 constexpr int kRebuildMaxGrid = 1024;
@@ -98,7 +99,7 @@ struct MultiArgs {
   int64_t act_P;
   const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
   unsigned* bar;               // barrier count and generation
-  long long spins;             // wait budget of one barrier (64 ns naps)
+  long long spins;             // wait budget of one barrier (units of 128 SM cycles)
   unsigned extra;              // CTAs the barrier waits for beyond the grid (fault injection; 0)
 };
 int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid);

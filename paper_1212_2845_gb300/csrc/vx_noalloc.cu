@@ -9,7 +9,7 @@
 // the hash grid and sort buffers come from one fixed array in this file.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (kScratchBytes, about 4 MiB) until the process exits.  Host
+// library holds it (kScratchBytes, about 5 MiB) until the process exits.  Host
 // code cannot use the array's name as a device address, so the first call on
 // each device, with that device current, looks up the address with
 // cudaGetSymbolAddress and keeps it for later calls.  Make that first call
@@ -36,7 +36,8 @@ constexpr int64_t kMaxBuckets = 2 * kMaxSurface;  // power of two, >= 2 S
 
 constexpr size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 constexpr size_t kOffXq = 0;
-constexpr size_t kOffBucket = kOffXq + align256(3 * kMaxSurface * sizeof(int64_t));
+constexpr size_t kOffCell = kOffXq + align256(3 * kMaxSurface * sizeof(int64_t));
+constexpr size_t kOffBucket = kOffCell + align256(kMaxSurface * sizeof(int4));
 constexpr size_t kOffCount = kOffBucket + align256(kMaxSurface * sizeof(uint32_t));
 constexpr size_t kOffCursor = kOffCount + align256(kMaxBuckets * sizeof(uint32_t));
 constexpr size_t kOffStart = kOffCursor + align256(kMaxBuckets * sizeof(uint32_t));
@@ -119,6 +120,7 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.body = n_bodies > 1 ? body : nullptr;
   C.dt_body = nullptr;
   C.xq = reinterpret_cast<int64_t*>(base + kOffXq);
+  C.cell = reinterpret_cast<int4*>(base + kOffCell);
   C.bucket = reinterpret_cast<uint32_t*>(base + kOffBucket);
   C.hcount = reinterpret_cast<uint32_t*>(base + kOffCount);
   C.hcursor = reinterpret_cast<uint32_t*>(base + kOffCursor);

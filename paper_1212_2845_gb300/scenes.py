@@ -196,6 +196,33 @@ def random_blob(dims=(6, 5, 4), seed=0, fill=0.8, n_mat=3):
     return sc
 
 
+def clapper(scale=1, period=4000, amplitude=10.0):
+    """Synthetic stand-in for the paper's collision test geometry (its exact
+    shape is not given): a fixed base slab and two upright arms, each a
+    bilayer of an expanding (cte +0.02/K) and a contracting (cte -0.02/K)
+    layer of 1 MPa voxels, the contracting layers facing each other.  The
+    temperature swings +-amplitude, so the arms bend toward each other and
+    apart again and their tips collide periodically (with the default 10 K
+    the tips meet after ~700 steps and touch for ~1,000; the paper's 30 K,
+    60 % strain, drives the arms through each other in this small-strain
+    beam model).  scale multiplies every dimension (scale 1: 880 voxels)."""
+    c = int(scale)
+    nx, ny, nz = 20 * c, 4 * c, 23 * c
+    g = np.zeros((nz, ny, nx), dtype=np.uint8)
+    g[: 3 * c, :, :] = 1                                   # base (passive)
+    arm = slice(3 * c, nz)
+    g[arm, :, 0: 2 * c] = 2                                # left arm: outer expanding
+    g[arm, :, 2 * c: 4 * c] = 3                            #           inner contracting
+    g[arm, :, 16 * c: 18 * c] = 3                          # right arm: inner contracting
+    g[arm, :, 18 * c: 20 * c] = 2                          #            outer expanding
+    pal = [material(1e6), material(1e6, cte=0.02), material(1e6, cte=-0.02)]
+    sc = _base([(nx, ny, nz)], g.ravel(), 1e-3, pal, collide=True, act_amplitude=amplitude,
+               act_period=period, steps=period, name=f"clapper_x{c}")
+    ijk = canonical_coords(sc)
+    sc["fixed"] = (ijk[:, 3] == 0).astype(np.uint8)        # bottom layer of the base
+    return sc
+
+
 CONFIGS = {
     "cantilever": cantilever,
     "hetero_block": hetero_block,

@@ -94,6 +94,7 @@ SIGNATURES = {
     "vx_rollout_forward": (C.c_int, [_P, _i64, _i32, _pf, _P]),
     "vx_graph_capture": (C.c_int, [_P, _i64, _P]),
     "vx_audit": (C.c_int, [_P, _pd, _P]),
+    "vx_set_collision_scheme": (C.c_int, [_P, _i32, _i32]),
     "vx_relax": (C.c_int, [_P, _i64, C.c_double, _i32, _pi64, _pd, _pi32, _P]),
     "vx_graph_launch": (C.c_int, [_P, _P]),
     "vx_autotune_batching": (C.c_int, [_P, _i32, _pi32, _pi64, _pd, _P]),
@@ -418,6 +419,9 @@ class Sim:
         return tm.value, gv.value, r.value
 
     # -- collisions --------------------------------------------------------
+    def set_collision_scheme(self, all_voxels=False, every_step=False):
+        _check(self._L.vx_set_collision_scheme(self.h, int(bool(all_voxels)), int(bool(every_step))))
+
     def rebuild_collisions(self, stream=None):
         _check(self._L.vx_rebuild_collisions(self.h, _stream_ptr(stream)))
 

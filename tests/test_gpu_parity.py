@@ -572,3 +572,33 @@ def test_shared_world_collision_matches_oracle(vx):
     ref = {tuple(int(x) for x in p) for p in ora.pairs_from_offsets(off)}
     assert got == ref
     sim.close()
+
+
+def test_collision_schemes_on_the_clapper(vx):
+    """All four collision schemes (all / surface voxels x every step /
+    horizon) step the clapper through its contact to the same bits; the
+    trajectory follows the oracle; at the contact the candidate set of each
+    scheme equals the oracle's brute force on the same GPU offsets."""
+    sc = scenes.clapper()
+    ora = Oracle(sc)
+    ora.set_dt(f32_dt(ora))
+    ora.step(1200)
+    finals = []
+    for all_voxels, every in ((False, False), (True, True), (False, True), (True, False)):
+        sim = vx.Sim(sc)
+        sim.set_collision_scheme(all_voxels, every)
+        sim.step(1200)
+        g = sim.state()
+        finals.append(g)
+        off = sim.read_state()["offset"].astype(np.float64)
+        sim.rebuild_collisions()
+        got = {tuple(int(x) for x in p) for p in sim.collision_pairs()}
+        ref_o = Oracle(sc)
+        ref_o.set_collision_scheme(all_voxels, every)
+        ref = {tuple(int(x) for x in p) for p in ref_o.pairs_from_offsets(off)}
+        assert got == ref and len(got) > 0, (all_voxels, every)
+        sim.close()
+    for g in finals[1:]:
+        for k in ("pos", "quat", "vel", "angvel"):
+            assert np.array_equal(g[k], finals[0][k]), k
+    assert pos_error(sc, finals[0], ora.state()) < 1e-3
