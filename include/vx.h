@@ -227,6 +227,16 @@ VX_API int vx_set_environment(vx_sim* sim, float gravity_z, int32_t floor_on, in
  * is offset + amplitude * sin(2 pi n / period + phase_v) (period 0: offset
  * only).  Bond rest length l (1 + (cte1 dT1 + cte2 dT2) / 2). */
 VX_API int vx_set_actuation(vx_sim* sim, float amplitude_K, int64_t period_steps, float offset_K);
+/* Independent temperature signals per material (Sec 2.3: several separately
+ * controlled temperatures may drive different materials).  Material m then
+ * follows offset[m] + amplitude[m] * sin(2 pi n / period + phase_v + phase[m]),
+ * on the common period of vx_set_actuation (period 0: offset[m] only).  Each
+ * array is host memory of n_materials floats, copied; NULL amplitude or
+ * offset means the global value from vx_set_actuation, NULL phase means 0.
+ * All three NULL restores the single global signal.  Non-finite values return
+ * VX_ERR_ARG.  Invalidates a recorded rollout and a captured graph. */
+VX_API int vx_set_material_actuation(vx_sim* sim, const float* amplitude_K, const float* offset_K,
+                                     const float* phase_rad);
 /* Stable-timestep safety factor f in (0, 1]; recomputes dt. */
 VX_API int vx_set_dt_factor(vx_sim* sim, float f);
 /* dt of every body [n_bodies] (double on the host; the device steps in FP32). */

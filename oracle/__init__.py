@@ -73,6 +73,7 @@ def lib():
             "orc_linear_static": (C.c_int, [_P, _D, _D]),
             "orc_stiffness": (None, [_P, _D, _D]),
             "orc_set_collision_scheme": (None, [_P, C.c_int, C.c_int]),
+            "orc_set_material_actuation": (None, [_P, _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -109,6 +110,7 @@ class Oracle:
         if not self.h:
             raise ValueError("oracle: invalid scene")
         self.n_bodies = dims.shape[0]
+        self.n_materials = pal.shape[0]
         self.N = L.orc_n_voxels(self.h)
         self.n_bonds = L.orc_n_bonds(self.h)
         self.l = float(sc["voxel_size"])
@@ -137,6 +139,17 @@ class Oracle:
                                sc["gravity_z"], int(sc["floor"]), int(sc["collide"]),
                                sc["act_amplitude"], int(sc["act_period"]), sc["act_offset"],
                                sc["dt_factor"])
+        ks = ("mat_act_amplitude", "mat_act_offset", "mat_act_phase")
+        self.set_material_actuation(*[sc.get(k) for k in ks])
+
+    def set_material_actuation(self, amplitude=None, offset=None, phase=None):
+        """Per-material temperature signals on the common period (Sec 2.3);
+        None: the global amplitude / offset, a zero phase shift."""
+        arrs = [None if a is None else _f64(a) for a in (amplitude, offset, phase)]
+        for a in arrs:
+            if a is not None and a.size != self.n_materials:
+                raise ValueError("one value per material expected")
+        self._L.orc_set_material_actuation(self.h, *[_dp(a) for a in arrs])
 
     def set_voxel_params(self, log_E=None, phase=None):
         le = None if log_E is None else _f64(log_E)

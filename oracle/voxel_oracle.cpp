@@ -255,6 +255,9 @@ struct Params {
   int cand_all = 0, cand_every = 0;
   double act_A = 0.0, act_T0 = 0.0;
   long act_P = 0;
+  // several temperature signals (Sec 2.3): per material amplitude, offset and
+  // phase shift on the common period; empty = the single global signal
+  std::vector<double> mat_A, mat_T0, mat_ph;
   double dt_factor = 0.9;
 };
 
@@ -355,11 +358,20 @@ template <class R> static void compute_dt(Sim<R>& S) {
 }
 
 // Temperature offset of a voxel at step n (Sec 2.3): T_c - T_r.
+// Each material follows its own signal when one is set, else the global one.
+static void signal_of(const Params& p, int m, double* A, double* T0, double* ph) {
+  *A = p.mat_A.empty() ? p.act_A : p.mat_A[m];
+  *T0 = p.mat_T0.empty() ? p.act_T0 : p.mat_T0[m];
+  *ph = p.mat_ph.empty() ? 0.0 : p.mat_ph[m];
+}
+
 template <class R> static R delta_T(const Sim<R>& S, int v) {
   const Params& p = S.prm;
+  double A, T0, ph;
+  signal_of(p, S.T.mat[v], &A, &T0, &ph);
   if (p.act_P > 0)
-    return R(p.act_T0) + R(p.act_A) * sin(R(2.0 * M_PI * (double)S.n / (double)p.act_P) + S.phase[v]);
-  return R(p.act_T0);
+    return R(T0) + R(A) * sin(R(2.0 * M_PI * (double)S.n / (double)p.act_P) + S.phase[v] + R(ph));
+  return R(T0);
 }
 
 // Force and moment of one bond on its two voxels (Sec 2.1.2, 2.1.5, 2.3).
@@ -487,9 +499,14 @@ template <class R> static double horizon_threshold(const Sim<R>& S) {
   // Rebuild once the accumulated relative motion could close the gap between
   // the 2-voxel horizon and the largest possible contact distance (equal to
   // half the horizon, one voxel, without actuation).
-  double amax = 0.0;
-  for (int v = 0; v < S.T.N; ++v) amax = std::max(amax, std::fabs(S.cte[v]));
-  double cmax = S.T.l * (1.0 + amax * (std::fabs(S.prm.act_T0) + std::fabs(S.prm.act_A)));
+  double smax = 0.0;  // largest thermal strain any voxel can reach
+  for (int v = 0; v < S.T.N; ++v) {
+    double A, T0, ph;
+    signal_of(S.prm, S.T.mat[v], &A, &T0, &ph);
+    if (S.prm.act_P <= 0) A = 0.0;
+    smax = std::max(smax, std::fabs(S.cte[v]) * (std::fabs(T0) + std::fabs(A)));
+  }
+  double cmax = S.T.l * (1.0 + smax);
   return 2.0 * S.T.l - cmax;
 }
 
@@ -714,6 +731,14 @@ void orc_set_params(orc_sim* o, double zeta_bond, double zeta_ground, double zet
   p.gravity_z = gravity_z; p.floor_on = floor_on; p.collide_on = collide_on;
   p.act_A = act_A; p.act_P = act_P; p.act_T0 = act_T0; p.dt_factor = dt_factor;
   compute_dt(o->S);
+}
+
+void orc_set_material_actuation(orc_sim* o, const double* amplitude, const double* offset, const double* phase) {
+  Params& p = o->S.prm;
+  const int nm = o->S.n_mat;
+  if (amplitude) p.mat_A.assign(amplitude, amplitude + nm); else p.mat_A.clear();
+  if (offset) p.mat_T0.assign(offset, offset + nm); else p.mat_T0.clear();
+  if (phase) p.mat_ph.assign(phase, phase + nm); else p.mat_ph.clear();
 }
 
 void orc_set_collision_scheme(orc_sim* o, int all_voxels, int every_step) {

@@ -226,7 +226,7 @@ __global__ void __launch_bounds__(256) finish_adj(StepArgs A, AdjArgs J) {
   const DevMat& d = A.mats[mt.m];
   const float l = A.l, dt = mt.dt;
   const float Ev = voxel_E(A, v, mt.m);
-  const float adT = thermal_strain(A, v, d.cte);
+  const float adT = thermal_strain(A, v, d);
   const VoxS s = load_vox(A.st_in, P, v);
   V3f F = v3(J.fm[v], J.fm[P + v], J.fm[2 * P + v]);
   V3f M = v3(J.fm[3 * P + v], J.fm[4 * P + v], J.fm[5 * P + v]);
@@ -472,13 +472,7 @@ __device__ __forceinline__ VoxAdj read_slot(const AdjTile<TMAX>& S, int a, int k
 // E, G, thermal strain (Sec 2.3, the forward step's formula), material.
 __device__ __forceinline__ float4 adj_props_v(const StepArgs& A, const DevMat& d, int m, float le, float ph) {
   const float E = A.logE ? expf(le) : d.E;
-  float adT = 0.f;
-  if (A.act_on) {
-    float x = A.act_w + ph;
-    x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
-    adT = __fmul_rn(d.cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
-  }
-  return make_float4(E, E * d.g_ratio, adT, __int_as_float(m));
+  return make_float4(E, E * d.g_ratio, strain_of(A, d, ph), __int_as_float(m));
 }
 
 }  // namespace
@@ -570,9 +564,9 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 2 : 4))
   const float4 pr = S.props[i];
   J.grad_logE[v] = glE + (gdv.x + acc.E) * pr.x;
   if (A.act_on) {
-    const int m = __float_as_int(pr.w);
-    const float x = A.act_w + ph0;
-    J.grad_phase[v] = glP + (gdv.y + acc.eps) * S.mats[m].cte * A.actA * cosf(x);
+    const DevMat& d = S.mats[__float_as_int(pr.w)];
+    const float x = A.act_w + ph0 + d.act_phase;
+    J.grad_phase[v] = glP + (gdv.y + acc.eps) * d.cte * d.act_A * cosf(x);
   }
 }
 

@@ -81,6 +81,10 @@ struct vx_sim {
   int floor_on = 0, collide_on = 0;
   float actA = 0.f, actT0 = 0.f;
   int64_t actP = 0;
+  // per-material temperature signals (amplitude, offset, phase shift); an
+  // empty vector means the global value (phase shift 0)
+  std::vector<float> mactA, mactT0, mactPh;
+  bool act_any = false;    // some material has a non-zero temperature offset
   float dt_factor = 0.9f;
   std::vector<double> dt;
   std::vector<float> logE_h;
@@ -219,7 +223,7 @@ StepArgs step_args(vx_sim* s) {
   A.floor_on = s->floor_on;
   A.collide_on = s->collide_on;
   A.actA = s->actA; A.actT0 = s->actT0;
-  A.act_on = (s->actA != 0.f || s->actT0 != 0.f) ? 1 : 0;
+  A.act_on = s->act_any ? 1 : 0;
   A.act_w = 0.f;
   A.step = s->step;
   A.tile_a = s->tile_a;
@@ -281,6 +285,15 @@ CollideArgs collide_args(vx_sim* s) {
   return C;
 }
 
+// Temperature signal of material i (Sec 2.3): its own amplitude, offset and
+// phase shift where set, else the global ones; no period, no oscillation.
+void material_signal(const vx_sim* s, size_t i, float* a, float* t0, float* ph) {
+  *a = s->mactA.empty() ? s->actA : s->mactA[i];
+  *t0 = s->mactT0.empty() ? s->actT0 : s->mactT0[i];
+  *ph = s->mactPh.empty() ? 0.f : s->mactPh[i];
+  if (s->actP == 0) *a = 0.f;
+}
+
 int upload_materials(vx_sim* s) {
   std::vector<DevMat> m(s->L.palette.size());
   double l = s->L.l;
@@ -297,7 +310,12 @@ int upload_materials(vx_sim* s) {
     m[i].inv_m = (float)(1.0 / mass);
     m[i].I = (float)I;
     m[i].inv_I = (float)(1.0 / I);
+    float a, t0, ph;
+    material_signal(s, i, &a, &t0, &ph);
+    m[i].act_A = a; m[i].act_T0 = t0; m[i].act_phase = ph;
   }
+  s->act_any = false;
+  for (const DevMat& d : m) s->act_any = s->act_any || d.act_A != 0.f || d.act_T0 != 0.f;
   VX_CUDA(cudaMemcpy(s->mats, m.data(), m.size() * sizeof(DevMat), cudaMemcpyHostToDevice));
   return VX_OK;
 }
@@ -355,10 +373,15 @@ int recompute_dt(vx_sim* s) {
 }
 
 void update_threshold(vx_sim* s) {
-  double amax = 0.0;
-  for (const auto& p : s->L.palette) amax = std::max(amax, (double)std::fabs(p.cte));
+  double smax = 0.0;  // largest thermal strain any material can reach
+  for (size_t i = 0; i < s->L.palette.size(); ++i) {
+    float a, t0, ph;
+    material_signal(s, i, &a, &t0, &ph);
+    smax = std::max(smax, std::fabs((double)s->L.palette[i].cte) *
+                              (std::fabs((double)t0) + std::fabs((double)a)));
+  }
   double l = s->L.l;
-  double cmax = l * (1.0 + amax * (std::fabs((double)s->actT0) + std::fabs((double)s->actA)));
+  double cmax = l * (1.0 + smax);
   s->threshold = (float)(2.0 * l - cmax);
 }
 
@@ -963,7 +986,23 @@ int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
   if (period == 0) amplitude = 0.f;
   s->actA = amplitude; s->actP = period; s->actT0 = offset;
   update_threshold(s);
-  return VX_OK;
+  return upload_materials(s);
+}
+
+int vx_set_material_actuation(vx_sim* s, const float* amplitude, const float* offset, const float* phase) {
+  if (s) { ++s->gen; ++s->cfg; }  // invalidates a recorded rollout and a captured graph
+  int rc = check_sim(s);
+  if (rc) return rc;
+  const size_t nm = s->L.palette.size();
+  for (size_t i = 0; i < nm; ++i)
+    if ((amplitude && !std::isfinite(amplitude[i])) || (offset && !std::isfinite(offset[i])) ||
+        (phase && !std::isfinite(phase[i])))
+      return fail(VX_ERR_ARG, "material actuation values must be finite");
+  if (amplitude) s->mactA.assign(amplitude, amplitude + nm); else s->mactA.clear();
+  if (offset) s->mactT0.assign(offset, offset + nm); else s->mactT0.clear();
+  if (phase) s->mactPh.assign(phase, phase + nm); else s->mactPh.clear();
+  update_threshold(s);
+  return upload_materials(s);
 }
 
 int vx_set_dt_factor(vx_sim* s, float f) {

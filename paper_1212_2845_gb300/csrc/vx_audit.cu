@@ -73,7 +73,7 @@ __device__ double bond_energy(const AuditArgs& U, const StepArgs& A, int v, int 
   const double Ec = 2.0 * E1 * E2 / (E1 + E2), Gc = 2.0 * G1 * G2 / (G1 + G2);
   const double l = U.l;
   const double a1 = Ec * l, a2 = Gc * l * l * l / 6.0, b1 = a1, b2 = Ec * l * l / 2.0, b3 = Ec * l * l * l / 6.0;
-  const double eps = 0.5 * ((double)thermal_strain(A, v, d1.cte) + (double)thermal_strain(A, u, d2.cte));
+  const double eps = 0.5 * ((double)thermal_strain(A, v, d1) + (double)thermal_strain(A, u, d2));
   const D3v D1 = centre(U, A, v, s1), D2 = centre(U, A, u, s2);
   const D3v p = to_ax<a>(rot_inv(s1.q, dsub(D2, D1)));
   const D3v th = to_ax<a>(rel_rot(s1.q, s2.q));

@@ -30,7 +30,10 @@ struct DevMat {
   float mu_s, mu_k;
   float m, inv_m; // rho l^3 and its inverse
   float I, inv_I; // m l^2 / 6 (solid cube) and its inverse
-  float pad[3];
+  // this material's temperature signal (Sec 2.3: several independent
+  // "temperatures" may drive different materials): dT = act_T0 + act_A
+  // sin(2 pi n / P + phase_voxel + act_phase); the global signal by default
+  float act_A, act_T0, act_phase;
 };
 
 constexpr int kCandCap = 48;        // collision candidates per surface voxel
@@ -59,7 +62,7 @@ struct StepArgs {
   float zb, zg, zc, gz;
   int floor_on, collide_on;
   int act_on;              // temperature offset is non-zero somewhere
-  float actA, actT0, act_w;  // dT = T0 + A sin(act_w + phase), act_w = 2 pi (n mod P) / P
+  float actA, actT0, act_w;  // global signal (materials carry their own copy); act_w = 2 pi (n mod P) / P
   int64_t step;
   // two-pass form
   const int32_t* nbr;      // 6 planes (-x,+x,-y,+y,-z,+z), internal indices
@@ -243,15 +246,20 @@ __device__ __forceinline__ void store_vox(float* st, int64_t pitch, int64_t i, c
   StPtr(st, pitch).store(i, s);
 }
 
-// Thermal strain alpha_v dT_v of a voxel at the current step (Sec 2.3).  The
-// sine argument is reduced to [-pi, pi] for the hardware sine (absolute error
-// below 4e-7); the product is rounded explicitly so that every caller gets the
-// same bits whether it stores the value or uses it at once.
-__device__ __forceinline__ float thermal_strain(const StepArgs& A, int64_t g, float cte) {
+// Thermal strain alpha dT of a voxel of material d with actuation phase ph
+// at the current step (Sec 2.3), the material's own temperature signal.  The
+// sine argument is reduced to [-pi, pi] for the hardware sine (absolute
+// error below 4e-7); every product is rounded explicitly so that every
+// caller gets the same bits whether it stores the value or uses it at once.
+__device__ __forceinline__ float strain_of(const StepArgs& A, const DevMat& d, float ph) {
   if (!A.act_on) return 0.f;
-  float x = A.act_w + (A.phase ? A.phase[g] : 0.f);
+  float x = __fadd_rn(__fadd_rn(A.act_w, ph), d.act_phase);
   x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
-  return __fmul_rn(cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
+  return __fmul_rn(d.cte, __fmaf_rn(d.act_A, __sinf(x), d.act_T0));
+}
+
+__device__ __forceinline__ float thermal_strain(const StepArgs& A, int64_t g, const DevMat& d) {
+  return strain_of(A, d, A.phase ? A.phase[g] : 0.f);
 }
 
 __device__ __forceinline__ float voxel_E(const StepArgs& A, int64_t g, int m) {
@@ -455,7 +463,7 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
         float r2 = dot3(dd, dd);
         int mj = A.mat[j];
         const DevMat& dj = mats[mj];
-        float hj = fma_(hl, thermal_strain(A, j, dj.cte), hl);
+        float hj = fma_(hl, thermal_strain(A, j, dj), hl);
         float cdist = add_(h, hj);
         if (!(r2 < mul_(cdist, cdist))) continue;
         float ir = rsqrtf(r2);

@@ -132,13 +132,7 @@ __device__ __forceinline__ BondK pair_consts(const StepArgs& A, const float* lut
 
 __device__ __forceinline__ float4 voxel_props(const StepArgs& A, const DevMat& d, int m, float ph, float le) {
   float E = A.logE ? expf(le) : d.E;
-  float adT = 0.f;
-  if (A.act_on) {
-    float x = A.act_w + ph;
-    x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
-    adT = __fmul_rn(d.cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
-  }
-  return make_float4(E, __fmul_rn(E, d.g_ratio), adT, __int_as_float(m));
+  return make_float4(E, __fmul_rn(E, d.g_ratio), strain_of(A, d, ph), __int_as_float(m));
 }
 
 template <int TMAX, int a>

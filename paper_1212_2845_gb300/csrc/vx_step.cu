@@ -37,7 +37,7 @@ __device__ __forceinline__ void bond_pass_axis(const StepArgs& A, int v) {
     k = bond_consts(A.l, E1, E2, __fmul_rn(E1, d1.g_ratio), __fmul_rn(E2, d2.g_ratio), fminf(d1.m, d2.m),
                     fminf(d1.I, d2.I), A.zb);
   }
-  float eps = mul_(0.5f, add_(thermal_strain(A, v, d1.cte), thermal_strain(A, u, d2.cte)));
+  float eps = mul_(0.5f, add_(thermal_strain(A, v, d1), thermal_strain(A, u, d2)));
   BondOut o = bond_eval<a>(s1, qmat(s1.q), s2, A.l, k, eps, A.zb != 0.f);
   float* bf = A.bf + (int64_t)a * P + v;
   const int64_t C = 3 * P;
@@ -85,7 +85,7 @@ __global__ void __launch_bounds__(256) voxel_pass(StepArgs A) {
     }
     VoxS s = load_vox(A.st_in, P, v);
     store_bond_sums(A, v, F, M);
-    speed = voxel_finish(A, v, mt, s, F, M, thermal_strain(A, v, A.mats[mt.m].cte), voxel_E(A, v, mt.m), A.mats);
+    speed = voxel_finish(A, v, mt, s, F, M, thermal_strain(A, v, A.mats[mt.m]), voxel_E(A, v, mt.m), A.mats);
   }
   if (A.collide_on) horizon_max(A, body, active, speed);
 }
@@ -167,13 +167,7 @@ __device__ __forceinline__ void halo_bond(const StepArgs& A, const Smem<TMAX>& S
 // Material-dependent values of one staged voxel: E, G, thermal strain, material.
 __device__ __forceinline__ float4 slot_props(const StepArgs& A, const DevMat& d, int m, float ph, float le) {
   float E = A.logE ? expf(le) : d.E;
-  float adT = 0.f;
-  if (A.act_on) {
-    float x = A.act_w + ph;
-    x = __fmaf_rn(-6.28318530717958648f, rintf(__fmul_rn(x, 0.159154943091895336f)), x);
-    adT = __fmul_rn(d.cte, __fmaf_rn(A.actA, __sinf(x), A.actT0));
-  }
-  return make_float4(E, __fmul_rn(E, d.g_ratio), adT, __int_as_float(m));
+  return make_float4(E, __fmul_rn(E, d.g_ratio), strain_of(A, d, ph), __int_as_float(m));
 }
 
 template <int TMAX>

@@ -48,6 +48,9 @@ def _base(dims, grid, l, palette, **kw):
         zeta_bond=1.0, zeta_ground=0.0, zeta_collision=1.0,
         gravity_z=0.0, floor=False, collide=False,
         act_amplitude=0.0, act_period=0, act_offset=0.0,
+        # per-material temperature signals (amplitude, offset, phase shift per
+        # palette entry) or None for the global signal
+        mat_act_amplitude=None, mat_act_offset=None, mat_act_phase=None,
         v0=(0.0, 0.0, 0.0), dt_factor=0.9, steps=1,
         name="scene",
     )
@@ -65,7 +68,7 @@ def normalize(sc):
         sc[k] = float(f32(sc[k]))
     sc["v0"] = tuple(float(x) for x in f32(sc["v0"]))
     sc["origin"] = f32(sc["origin"])
-    for k in ("phase", "log_E", "force"):
+    for k in ("phase", "log_E", "force", "mat_act_amplitude", "mat_act_offset", "mat_act_phase"):
         if sc.get(k) is not None:
             sc[k] = f32(sc[k])
     return sc

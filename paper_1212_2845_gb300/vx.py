@@ -76,6 +76,7 @@ SIGNATURES = {
     "vx_set_damping": (C.c_int, [_P, _f32, _f32, _f32]),
     "vx_set_environment": (C.c_int, [_P, _f32, _i32, _i32]),
     "vx_set_actuation": (C.c_int, [_P, _f32, _i64, _f32]),
+    "vx_set_material_actuation": (C.c_int, [_P, _pf, _pf, _pf]),
     "vx_set_dt_factor": (C.c_int, [_P, _f32]),
     "vx_get_dt": (C.c_int, [_P, _pd]),
     "vx_set_dt": (C.c_int, [_P, _pd]),
@@ -219,6 +220,7 @@ class Sim:
         _check(L.vx_get_counts(self.h, *[C.byref(x) for x in n]))
         self.N, self.n_bonds, self.n_surface = (x.value for x in n)
         self.n_bodies = self._d.dims.shape[0]
+        self.n_materials = int(np.asarray(sc["palette"]).reshape(-1, 6).shape[0])
         self.l = float(np.float32(sc["voxel_size"]))
         if apply_scene:
             self.apply(sc)
@@ -238,6 +240,9 @@ class Sim:
     def apply(self, sc):
         self.set_damping(sc["zeta_bond"], sc["zeta_ground"], sc["zeta_collision"])
         self.set_actuation(sc["act_amplitude"], sc["act_period"], sc["act_offset"])
+        if any(sc.get(k) is not None for k in ("mat_act_amplitude", "mat_act_offset", "mat_act_phase")):
+            self.set_material_actuation(sc.get("mat_act_amplitude"), sc.get("mat_act_offset"),
+                                        sc.get("mat_act_phase"))
         if sc.get("log_E") is not None or sc.get("phase") is not None:
             self.set_voxel_params(sc.get("log_E"), sc.get("phase"))
         self.set_dt_factor(sc["dt_factor"])
@@ -257,6 +262,17 @@ class Sim:
 
     def set_actuation(self, amplitude, period, offset=0.0):
         _check(self._L.vx_set_actuation(self.h, float(amplitude), int(period), float(offset)))
+
+    def set_material_actuation(self, amplitude=None, offset=None, phase=None):
+        """Per-material temperature signals on the common period (Sec 2.3);
+        None keeps the global amplitude / offset, or a zero phase shift."""
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=np.float32).reshape(-1)
+                for a in (amplitude, offset, phase)]
+        for a in arrs:
+            if a is not None and a.size != self.n_materials:
+                raise ValueError("one value per material expected")
+        ptr = [None if a is None else a.ctypes.data_as(_pf) for a in arrs]
+        _check(self._L.vx_set_material_actuation(self.h, *ptr))
 
     def set_voxel_params(self, log_E=None, phase=None):
         le = None if log_E is None else np.ascontiguousarray(log_E, dtype=np.float32)

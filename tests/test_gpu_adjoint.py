@@ -75,11 +75,18 @@ def variant(name):
         sc = scenes.random_blob((5, 4, 4), seed=3, fill=0.85)
         sc.update(gravity_z=-9.81, floor=True, act_amplitude=20.0, act_period=60)
         return scenes.normalize(sc), 200
+    if name == "material_signals":     # every material on its own temperature signal
+        sc = scenes.random_blob((5, 4, 4), seed=3, fill=0.85)
+        sc["palette"] = sc["palette"].copy()
+        sc["palette"][:, 3] = scenes.f32([0.01, -0.015, 0.02])
+        sc.update(gravity_z=-9.81, floor=True, act_amplitude=20.0, act_period=60,
+                  mat_act_amplitude=[8.0, 3.0, -5.0], mat_act_offset=[1.0, -1.0, 0.5], mat_act_phase=[0.0, 2.1, -0.7])
+        return scenes.normalize(sc), 200
     raise KeyError(name)
 
 
 @pytest.mark.parametrize("name", ["floor_actuation", "ground_damping", "sliding", "fixed_face",
-                                  "hetero_materials"])
+                                  "hetero_materials", "material_signals"])
 def test_directional_derivative_matches_oracle_tangent(env, name):
     torch, vx = env
     sc, steps = variant(name)

@@ -93,9 +93,22 @@ def set_both(sim, ora, anchors, off, q, vel, w, flags=None):
                   angvel=w.astype(np.float64), static=st)
 
 
-@pytest.mark.parametrize("dims,seed", [((7, 5, 4), 0), ((9, 6, 5), 1), ((33, 3, 2), 2), ((1, 1, 13), 3)])
-def test_one_step_force_response(vx, dims, seed):
+def with_material_signals(sc):
+    """Three materials, each on its own temperature signal (Sec 2.3): own
+    expansion coefficient sign, amplitude, offset and phase shift."""
+    sc["palette"] = sc["palette"].copy()
+    sc["palette"][:, 3] = scenes.f32([0.01, -0.015, 0.02])
+    sc.update(mat_act_amplitude=scenes.f32([6.0, 3.0, -4.0]), mat_act_offset=scenes.f32([1.0, -1.0, 0.5]),
+              mat_act_phase=scenes.f32([0.0, 2.1, -0.7]))
+    return sc
+
+
+@pytest.mark.parametrize("dims,seed,signals", [((7, 5, 4), 0, False), ((9, 6, 5), 1, False), ((33, 3, 2), 2, False),
+                                               ((1, 1, 13), 3, False), ((9, 6, 5), 4, True), ((33, 3, 2), 5, True)])
+def test_one_step_force_response(vx, dims, seed, signals):
     sc = perturbed_scene(dims, seed)
+    if signals:
+        sc = with_material_signals(sc)
     sim, ora = pair(vx, sc)
     anchors = ora.anchors(sc)
     assert np.allclose(sim.anchors(), anchors, rtol=0, atol=1e-15)
@@ -151,6 +164,25 @@ def test_hetero_block_reduced(vx):
     flips = int(np.sum(g["static"] != o["static"]))
     print(f"hetero block: pos err/diag {err:.2e}, static flag mismatches {flips}/{sim.N}")
     assert err < 1e-3
+
+
+def test_material_signals_rollout_with_collisions(vx):
+    """Per-material temperature signals through 1,500 steps with floor,
+    friction and self-collision on (the collision sizes use each voxel's own
+    signal too); the same scene under one global signal moves differently."""
+    sc = with_material_signals(scenes.random_blob((10, 8, 6), seed=7, fill=0.8))
+    sc.update(gravity_z=-9.81, floor=True, collide=True, zeta_ground=0.05, act_period=400)
+    scenes.normalize(sc)
+    sim, ora = pair(vx, sc)
+    sim.step(1500)
+    ora.step(1500)
+    g, o = sim.state(), ora.state()
+    assert pos_error(sc, g, o) < 1e-3
+    sim.set_material_actuation(None, None, None)
+    sim.reset()
+    sim.step(1500)
+    assert pos_error(sc, sim.state(), o) > 5e-3
+    sim.close()
 
 
 def test_population_reduced(vx):

@@ -648,3 +648,96 @@ def test_collision_schemes_give_the_same_trajectory():
         for k in ("pos", "quat", "vel", "angvel"):
             assert np.array_equal(s[k], finals[0][k]), k
     assert npairs[0] > 0
+
+
+# ---------------------------------------------------------------------------
+# several temperature signals (Sec 2.3: separately controlled temperatures
+# driving different materials)
+# ---------------------------------------------------------------------------
+
+def test_material_offsets_rest_length_closed_form():
+    """Two materials held at their own offsets (no oscillation): the bond
+    between them relaxes to l (1 + (a1 dT1 + a2 dT2) / 2), whatever the two
+    stiffnesses (no force at the rest length)."""
+    a1, a2, T1, T2 = 0.01, -0.004, 6.0, 9.0
+    sc = two_voxel(0, mats=((1e6, 0.35, 1000.0, a1), (4e6, 0.3, 1500.0, a2)), grid=(1, 2), zeta_bond=1.0,
+                   zeta_ground=0.02, act_offset=3.0)
+    sc["mat_act_offset"] = scenes.f32([T1, T2])
+    o = Oracle(sc)
+    e = relax(o, lambda: o.state()["pos"][1, 0] - o.state()["pos"][0, 0], tol=1e-14)
+    l = sc["voxel_size"]
+    a1, a2 = sc["palette"][0, 3], sc["palette"][1, 3]
+    T1, T2 = sc["mat_act_offset"]
+    assert e == pytest.approx(l * (1 + 0.5 * (a1 * T1 + a2 * T2)), rel=1e-10)
+    # the global offset alone would give a different length
+    assert abs(e - l * (1 + 0.5 * (a1 + a2) * sc["act_offset"])) > 1e-3 * l * abs(a1 * T1)
+
+
+def two_bodies_two_materials():
+    pal = [scenes.material(1e6, 0.35, 1000.0, 0.01), scenes.material(3e6, 0.3, 1200.0, -0.02)]
+    dims = [(4, 3, 2), (3, 3, 3)]
+    grid = np.concatenate([np.full(24, 1, np.uint8), np.full(27, 2, np.uint8)])
+    sc = scenes._base(dims, grid, 1e-3, pal, gravity_z=-9.81, floor=True, zeta_ground=0.05,
+                      act_amplitude=5.0, act_period=300, act_offset=1.0)
+    sc["origin"] = scenes.f32([[0.0, 0.0, 0.0], [0.01, 0.0, 0.0]])
+    return sc
+
+
+def test_material_signals_drive_each_material_independently():
+    """Two bodies of one material each, every material on its own amplitude,
+    offset and phase shift: each body follows, bit for bit, the same body
+    simulated alone under the single global signal with those values (the
+    phase shift carried by every voxel's own phase)."""
+    sc = two_bodies_two_materials()
+    amp, off, ph = scenes.f32([12.0, 4.0]), scenes.f32([-2.0, 3.0]), scenes.f32([0.0, 1.3])
+    sc.update(mat_act_amplitude=amp, mat_act_offset=off, mat_act_phase=ph)
+    o = Oracle(sc)
+    o.step(900)
+    both = o.state()
+    n0 = 24
+    for b, sl in ((0, slice(0, n0)), (1, slice(n0, None))):
+        alone = scenes._base([sc["dims"][b]], sc["grid"][sl] * 0 + 1, 1e-3, [sc["palette"][b]],
+                             gravity_z=-9.81, floor=True, zeta_ground=0.05, act_amplitude=float(amp[b]),
+                             act_period=300, act_offset=float(off[b]))
+        alone["origin"] = sc["origin"][b:b + 1]
+        alone["phase"] = np.full(scenes.n_occupied(alone), ph[b], np.float32)
+        oa = Oracle(alone)
+        oa.step(900)
+        s = oa.state()
+        for k in ("pos", "quat", "vel", "angvel", "static"):
+            assert np.array_equal(s[k], both[k][sl]), (b, k)
+    # and the per-material signals matter: the global signal gives another motion
+    g = Oracle(two_bodies_two_materials())
+    g.step(900)
+    assert not np.allclose(g.state()["pos"], both["pos"], rtol=0, atol=1e-9)
+
+
+def test_material_signals_equal_to_global_change_nothing():
+    """Per-material values equal to the global amplitude and offset, zero
+    phase shifts: the same trajectory bit for bit; a phase shift of pi on a
+    material equals flipping the sign of its expansion coefficient."""
+    sc = two_bodies_two_materials()
+    o = Oracle(sc)
+    o.step(600)
+    ref = o.state()
+    sc2 = two_bodies_two_materials()
+    sc2.update(mat_act_amplitude=scenes.f32([5.0, 5.0]), mat_act_offset=scenes.f32([1.0, 1.0]),
+               mat_act_phase=scenes.f32([0.0, 0.0]))
+    o2 = Oracle(sc2)
+    o2.step(600)
+    for k in ("pos", "quat", "vel", "angvel"):
+        assert np.array_equal(o2.state()[k], ref[k]), k
+    # sin(x + pi) = -sin(x): with zero offsets, a pi shift on material 1 and
+    # its cte negated describe the same physics (equal up to sine rounding)
+    sc3 = two_bodies_two_materials()
+    sc3.update(act_offset=0.0, mat_act_phase=np.array([0.0, math.pi]))
+    sc4 = two_bodies_two_materials()
+    sc4.update(act_offset=0.0)
+    sc4["palette"] = sc4["palette"].copy()
+    sc4["palette"][1, 3] = -sc4["palette"][1, 3]
+    o3, o4 = Oracle(sc3), Oracle(sc4)
+    o3.step(600)
+    o4.step(600)
+    s3, s4 = o3.state(), o4.state()
+    span = np.ptp(s4["pos"], axis=0).max()
+    assert np.abs(s3["pos"] - s4["pos"]).max() <= 1e-9 * span
