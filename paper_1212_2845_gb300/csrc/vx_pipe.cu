@@ -24,7 +24,7 @@ __device__ __forceinline__ void cp4(void* d, const void* s) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sptr(d)), "l"(s) : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Descriptor of a tile held in registers (h0, h1: halo voxels of list
 // positions threadIdx.x and threadIdx.x + TMAX).
@@ -146,26 +146,37 @@ __device__ __forceinline__ void halo_bond_p(const StepArgs& A, const Stage<TMAX>
   minus_slot<TMAX, a>(F4, F2, s2, o);
 }
 
-// Everything after a tile's staging has landed: material properties of the
-// staged voxels, own and halo bonds, gather and the voxel update.
+// Material properties (E, G, thermal strain, material) of the slots this
+// thread staged itself (owned voxel i, halo list positions i and i + TMAX):
+// after its own copies have landed they need no barrier.
+template <int TMAX>
+__device__ __forceinline__ void tile_props(const StepArgs& A, const Stage<TMAX>& S, float4* props,
+                                           const DevMat* mats, const TileRegs& r) {
+  const int i = threadIdx.x;
+  if (i < r.T) {
+    const uint32_t w = S.vw[i];
+    props[i] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[i] : 0.f, S.le ? S.le[i] : 0.f);
+  }
+  for (int j = i; j < r.nh; j += TMAX) {
+    const int k = r.T + j;
+    const uint32_t w = S.vw[k];
+    props[k] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[k] : 0.f, S.le ? S.le[k] : 0.f);
+  }
+}
+
+// Everything after a tile's staging and properties are in place: own and
+// halo bonds, gather and the voxel update.  Between the bond results and the
+// gather (after the barrier that publishes the results, when nobody reads
+// the property slots any more) the thread waits for its copies of the next
+// tile and writes that tile's properties.
 template <int TMAX>
 __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX>& S, float4* props, float4* F4,
                                              float2* F2, const DevMat* mats, const float* lut, const TileRegs& cur,
-                                             uint8_t fl_cur) {
+                                             uint8_t fl_cur, const Stage<TMAX>& Sn, const TileRegs& nxt) {
   const int i = threadIdx.x;
   const int T = cur.T;
   const bool own = i < T;
-  if (own) {
-    uint32_t w = S.vw[i];
-    props[i] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[i] : 0.f, S.le ? S.le[i] : 0.f);
-  }
-  for (int j = i; j < cur.nh; j += TMAX) {
-    const int k = T + j;
-    uint32_t w = S.vw[k];
-    props[k] = voxel_props(A, mats[w & 255u], (int)(w & 255u), S.ph ? S.ph[k] : 0.f, S.le ? S.le[k] : 0.f);
-  }
-  __syncthreads();
-  // 4. own +x, +y, +z bonds; halo bonds
+  // own +x, +y, +z bonds; halo bonds
   V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
   VoxS s;
   float4 pr;
@@ -201,7 +212,11 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
     else halo_bond_p<TMAX, 2>(A, S, props, lut, mats, F4, F2, s1, s2);
   }
   __syncthreads();
-  // 5. gather the -x, -y, -z results and integrate
+  if (nxt.valid) {
+    cp_wait_all();
+    tile_props<TMAX>(A, Sn, props, mats, nxt);
+  }
+  // gather the -x, -y, -z results and integrate
   float speed = 0.f;
   int body = 0;
   if (own) {
@@ -230,6 +245,58 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
   if (A.collide_on) horizon_max(A, body, own, speed);
 }
 
+// One step over the tiles t, t + stride, ... < t_end (pipelined staging; two
+// CTA barriers per tile).  Each pass of the loop starts at a barrier that
+// publishes tile t (staged, properties written) and frees the other staging
+// buffer and the shared bond results of tile t - stride; the copies of the
+// next tile are issued right after it and land while tile t is computed.
+// Ends with no copy in flight; the caller separates two calls with a
+// barrier because the shared buffers are reused.
+template <int TMAX>
+__device__ __forceinline__ void pipe_tiles(const StepArgs& A, int t, int stride, int t_end, float* smem, int sf,
+                                           float4* props, float4* F4, float2* F2, const DevMat* mats,
+                                           const float* lut) {
+  const bool hph = A.phase != nullptr, hle = A.logE != nullptr, hbody = A.body != nullptr, hfx = A.fext != nullptr;
+  const bool hcol = A.collide_on != 0;
+  const int i = threadIdx.x;
+  const StPtr G(const_cast<float*>(A.st_in), A.pitch);
+  // prologue: stage the first tile and write its properties
+  TileRegs cur = load_tile<TMAX>(A, t, t_end);
+  {
+    Stage<TMAX> S0;
+    S0.carve(smem, hph, hle, hbody, hfx, hcol);
+    issue_tile<TMAX>(A, G, S0, cur);
+    cp_commit();
+    cp_wait_all();
+    tile_props<TMAX>(A, S0, props, mats, cur);
+  }
+  uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
+  TileRegs nxt = load_tile<TMAX>(A, t + stride, t_end);
+  int b = 0;
+  for (;;) {
+    Stage<TMAX> S, Sn;
+    S.carve(smem + b * sf, hph, hle, hbody, hfx, hcol);
+    Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx, hcol);
+    __syncthreads();
+    // stream the next tile into the other buffer, its flags into a register
+    uint8_t fl_nxt = 0;
+    if (nxt.valid) {
+      issue_tile<TMAX>(A, G, Sn, nxt);
+      cp_commit();
+      fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
+    }
+    // descriptor and halo indices of the tile after it
+    const TileRegs nn = load_tile<TMAX>(A, t + 2 * stride, t_end);
+    compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur, Sn, nxt);
+    if (!nxt.valid) break;  // uniform
+    cur = nxt;
+    nxt = nn;
+    fl_cur = fl_nxt;
+    t += stride;
+    b ^= 1;
+  }
+}
+
 }  // namespace
 
 template <int TMAX> struct PipeSmem {
@@ -239,57 +306,6 @@ template <int TMAX> struct PipeSmem {
     return f * sizeof(float) + (size_t)n_mats * sizeof(DevMat) + (lut ? (size_t)8 * n_mats * n_mats * 4 : 0);
   }
 };
-
-// One step over this CTA's tiles t = blockIdx.x, + gridDim.x, ... (pipelined
-// staging).  Ends with every copy landed; the caller separates two calls
-// with a barrier because the shared buffers are reused.
-template <int TMAX>
-__device__ __forceinline__ void pipe_tiles(const StepArgs& A, float* smem, int sf, float4* props, float4* F4,
-                                           float2* F2, const DevMat* mats, const float* lut) {
-  const bool hph = A.phase != nullptr, hle = A.logE != nullptr, hbody = A.body != nullptr, hfx = A.fext != nullptr;
-  const bool hcol = A.collide_on != 0;
-  const int i = threadIdx.x;
-  const int Gs = gridDim.x;
-  int t = blockIdx.x;
-  const StPtr G(const_cast<float*>(A.st_in), A.pitch);
-  // prologue: stage the first tile, fetch the next descriptor
-  TileRegs cur = load_tile<TMAX>(A, t, A.n_tiles);
-  {
-    Stage<TMAX> S0;
-    S0.carve(smem, hph, hle, hbody, hfx, hcol);
-    issue_tile<TMAX>(A, G, S0, cur);
-  }
-  cp_commit();
-  uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
-  TileRegs nxt = load_tile<TMAX>(A, t + Gs, A.n_tiles);
-  int b = 0;
-  for (;;) {
-    Stage<TMAX> S;
-    S.carve(smem + b * sf, hph, hle, hbody, hfx, hcol);
-    // 1. stream the next tile into the other buffer; its flags into a register
-    uint8_t fl_nxt = 0;
-    if (nxt.valid) {
-      Stage<TMAX> Sn;
-      Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx, hcol);
-      issue_tile<TMAX>(A, G, Sn, nxt);
-      fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
-    }
-    cp_commit();
-    // 2. descriptor and halo indices of the tile after it
-    const TileRegs nn = load_tile<TMAX>(A, t + 2 * Gs, A.n_tiles);
-    // 3. this tile has landed
-    cp_wait1();
-    __syncthreads();
-    compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur);
-    if (!nxt.valid) break;  // uniform
-    __syncthreads();        // buffer b and the shared results are reused
-    cur = nxt;
-    nxt = nn;
-    fl_cur = fl_nxt;
-    t += Gs;
-    b ^= 1;
-  }
-}
 
 template <int TMAX> struct PipeLayout {
   int sf;
@@ -321,7 +337,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
   if ((int)blockIdx.x >= A.n_tiles) return;  // uniform over the CTA
   const PipeLayout<TMAX> L(smem, A);
   L.load_tables(A);
-  pipe_tiles<TMAX>(A, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+  pipe_tiles<TMAX>(A, blockIdx.x, gridDim.x, A.n_tiles, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
 }
 
 // Multi-step form: one cooperative launch runs n steps of the whole lattice;
@@ -344,7 +360,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) multi_pipe(StepArgs
     A.step = step0 + k;
     if (A.act_on && M.act_P > 0)
       A.act_w = (float)(6.283185307179586 * (double)(A.step % M.act_P) / (double)M.act_P);
-    pipe_tiles<TMAX>(A, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+    pipe_tiles<TMAX>(A, blockIdx.x, gridDim.x, A.n_tiles, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
     if (k + 1 < M.n_steps && !grid_barrier(M.bar, gridDim.x + M.extra, M.spins, A0.status)) return;
   }
 }
@@ -387,39 +403,8 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
       A.step = step0 + k;
       if (A.act_on && Bt.act_P > 0)
         A.act_w = (float)(6.283185307179586 * (double)(A.step % Bt.act_P) / (double)Bt.act_P);
-      const StPtr G(const_cast<float*>(A.st_in), A.pitch);
-      TileRegs cur = load_tile<TMAX>(A, t0, t1);
-      {
-        Stage<TMAX> S0;
-        S0.carve(smem, hph, hle, hbody, hfx, hcol);
-        issue_tile<TMAX>(A, G, S0, cur);
-      }
-      cp_commit();
-      uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
-      TileRegs nxt = load_tile<TMAX>(A, t0 + 1, t1);
-      int b = 0;
-      for (int t = t0;; ++t) {
-        Stage<TMAX> S;
-        S.carve(smem + b * sf, hph, hle, hbody, hfx, hcol);
-        uint8_t fl_nxt = 0;
-        if (nxt.valid) {
-          Stage<TMAX> Sn;
-          Sn.carve(smem + (b ^ 1) * sf, hph, hle, hbody, hfx, hcol);
-          issue_tile<TMAX>(A, G, Sn, nxt);
-          fl_nxt = i < nxt.T ? A.flags[nxt.v0 + i] : 0;
-        }
-        cp_commit();
-        const TileRegs nn = load_tile<TMAX>(A, t + 2, t1);
-        cp_wait1();
-        __syncthreads();
-        compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur);
-        __syncthreads();  // buffers reused; at the last tile: the step's writes are complete
-        if (!nxt.valid) break;
-        cur = nxt;
-        nxt = nn;
-        fl_cur = fl_nxt;
-        b ^= 1;
-      }
+      pipe_tiles<TMAX>(A, t0, 1, t1, smem, sf, props, F4, F2, mats, lut);
+      __syncthreads();  // the buffers are reused; the next step reads what this one wrote
     }
   }
 }
