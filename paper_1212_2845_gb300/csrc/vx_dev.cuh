@@ -160,13 +160,13 @@ __device__ __forceinline__ V3f rel_rotvec(Qf a, Qf b) {
   float x = fma_(a.w, b.x, fma_(-a.x, b.w, fma_(-a.y, b.z, mul_(a.z, b.y))));
   float y = fma_(a.w, b.y, fma_(a.x, b.z, fma_(-a.y, b.w, -mul_(a.z, b.x))));
   float z = fma_(a.w, b.z, fma_(-a.x, b.y, fma_(a.y, b.x, -mul_(a.z, b.w))));
-  float sg = w < 0.f ? -1.f : 1.f;
-  w = mul_(w, sg);
+  // shortest arc: for w < 0 the factor below takes the sign of w, which is
+  // the rotation vector of -q (the same rotation)
   float s2 = fma_(x, x, fma_(y, y, mul_(z, z)));
   float f;
   if (s2 < mul_(0.04f, mul_(w, w))) {
-    // 2 atan(t) / (t w), t = s / w < 0.2: alternating series to t^10
-    // (remainder below t^12 / 13 < 4e-10)
+    // 2 atan(t) / (t |w|) sign(w), t = s / |w| < 0.2: alternating series to
+    // t^10 (remainder below t^12 / 13 < 4e-10); 1/w carries the sign
     float iw = __fdividef(1.f, w);
     float t2 = mul_(s2, mul_(iw, iw));
     float pz = fma_(t2, 1.f / 11.f, -1.f / 9.f);
@@ -176,9 +176,9 @@ __device__ __forceinline__ V3f rel_rotvec(Qf a, Qf b) {
     f = mul_(add_(iw, iw), fma_(-t2, pz, 1.f));
   } else {
     float sq = sqrtf(s2);
-    f = __fdividef(mul_(2.f, atan2f(sq, w)), sq);
+    f = __fdividef(mul_(2.f, atan2f(sq, fabsf(w))), sq);
+    if (w < 0.f) f = -f;
   }
-  f = mul_(f, sg);
   return v3(mul_(x, f), mul_(y, f), mul_(z, f));
 }
 

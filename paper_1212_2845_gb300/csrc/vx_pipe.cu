@@ -117,9 +117,11 @@ __device__ __forceinline__ void issue_tile(const StepArgs& A, const StPtr& G, co
   if (i + TMAX < r.nhb) cp4(&S.hb[i + TMAX], &A.hbonds[r.hb0 + i + TMAX]);
 }
 
+// Result of a bond for its voxel 2 (the owner's -a bond): F1 (voxel 2
+// receives -F1, subtracted at the gather) and M2.
 template <int TMAX, int a>
 __device__ __forceinline__ void minus_slot(float4* F4, float2* F2, int k, const BondOut& o) {
-  F4[a * TMAX + k] = make_float4(-o.F1.x, -o.F1.y, -o.F1.z, o.M2.x);
+  F4[a * TMAX + k] = make_float4(o.F1.x, o.F1.y, o.F1.z, o.M2.x);
   F2[a * TMAX + k] = make_float2(o.M2.y, o.M2.z);
 }
 
@@ -226,7 +228,7 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
       if (mask & (1u << (2 * a))) {
         const float4 f = F4[a * TMAX + i];
         const float2 g = F2[a * TMAX + i];
-        F = add(F, v3(f.x, f.y, f.z));
+        F = sub(F, v3(f.x, f.y, f.z));  // F - F1 is F + (-F1) exactly
         M = add(M, v3(f.w, g.x, g.y));
       }
     VoxMeta mt;
