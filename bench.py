@@ -80,7 +80,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.rows = []
+        self.times = []
         self.proc = None
+        self.w0, self.w1 = None, None
 
     def __enter__(self):
         try:
@@ -96,6 +98,18 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.rows.append([x.strip() for x in line.split(",")])
+            self.times.append(time.perf_counter())
+
+    def start_window(self, timeout=2.0):
+        """Waits (up to timeout s) for the sampler's first row, then opens the
+        window whose rows the summary keeps."""
+        t0 = time.perf_counter()
+        while self.proc and not self.rows and time.perf_counter() - t0 < timeout:
+            time.sleep(0.01)
+        self.w0 = time.perf_counter()
+
+    def end_window(self):
+        self.w1 = time.perf_counter()
 
     def __exit__(self, *a):
         if self.proc:
@@ -104,14 +118,17 @@ class ClockSampler:
             self.t.join(timeout=2)
 
     def summary(self):
-        if not self.rows:
+        rows = self.rows
+        if self.w0 is not None and self.w1 is not None:  # rows taken while the timed region ran
+            rows = [r for r, t in zip(self.rows, self.times) if self.w0 <= t <= self.w1 + 0.1]
+        if not rows:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
-        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
-        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({n for r in self.rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+                "reasons": reasons, "samples": len(rows)}
 
 
 def dist_env():
@@ -375,7 +392,7 @@ def multi_step_line(sim, stream, flush, steps=500):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=300)
@@ -432,10 +449,12 @@ def main():
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(local_rank) as clk:
+        clk.start_window()
         t_wall0 = time.perf_counter()
         times = time_steps(sim, stream, args.steps, args.warmup, flush)
         t_wall = time.perf_counter() - t_wall0
         torch.cuda.synchronize()
+        clk.end_window()
     t_steps = float(times.sum())
     if ws > 1:
         tt = torch.tensor([t_steps], dtype=torch.float64, device="cuda")
