@@ -475,9 +475,11 @@ def main():
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
         sim.write_state_from(**pin, stream=stream, on_device=False)
-        sim.step(1, stream)
+        sim.step_async(1, stream)              # the read below waits for it
         sim.read_state_into(**pin, stream=stream, on_device=False)
     t_e2e = time.perf_counter() - t0
+    if sim.status(stream)[0] != 0:
+        raise RuntimeError("end-to-end run reported an unstable state")
 
     if rank != 0:
         if ws > 1:

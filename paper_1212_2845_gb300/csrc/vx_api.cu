@@ -556,12 +556,38 @@ int build_schedule(vx_sim* s) {
 
 // Rebuild the tiles for the current tile size (with group boundaries when
 // the batched form is on) and upload them.
+//
+// Without batching the persistent grid (G CTAs) walks the tiles round robin,
+// so on a lattice of a few tiles per CTA the step lasts as long as the CTAs
+// that walk one tile more than the others.  There the runs are shortened to
+// about N / (k G) voxels (k = tiles per CTA at full length) so that every
+// CTA walks k tiles; never below half the tile size, and only while k <= 8
+// (beyond that the last round is a small part of the step).
 int retile(vx_sim* s, int tile_max) {
   Tiling T;
   std::vector<int64_t> starts;
   if (s->group_voxels > 0) starts = batch_group_starts(s->L, s->group_voxels);
-  int rc = build_tiling(s->L, tile_max, 2 * tile_max, T, g_err, s->group_voxels > 0 ? &starts : nullptr);
-  if (rc) return rc;
+  int run = tile_max;
+  int64_t G = 0, k = 0;
+  int dev = 0, n_sm = 0;
+  if (s->group_voxels == 0 && cudaGetDevice(&dev) == cudaSuccess &&
+      cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n_sm > 0) {
+    G = (int64_t)n_sm * (tile_max == 128 ? 4 : 2);  // resident CTAs of the pipelined kernels
+    k = (s->L.N + (int64_t)tile_max * G - 1) / ((int64_t)tile_max * G);
+    const int64_t r = (s->L.N + k * G - 1) / (k * G);
+    if (k <= 8 && 2 * r >= tile_max && r < tile_max) run = (int)r;
+  }
+  int rc;
+  for (int pass = 0;; ++pass) {
+    rc = build_tiling(s->L, run, 2 * tile_max, T, g_err, s->group_voxels > 0 ? &starts : nullptr);
+    if (rc) return rc;
+    // tiles shortened around large halos can leave a few more than k G:
+    // shorten the runs in proportion (at most two more passes)
+    if (run == tile_max || T.n_tiles() <= k * G || pass == 2) break;
+    const int r = (int)((int64_t)run * k * G / T.n_tiles());
+    if (2 * r < tile_max || r >= run) break;
+    run = r;
+  }
   s->T.tile_a.swap(T.tile_a); s->T.tile_b.swap(T.tile_b); s->T.halo.swap(T.halo); s->T.plus.swap(T.plus);
   s->T.halo_bonds.swap(T.halo_bonds); s->T.tile_desc.swap(T.tile_desc); s->T.halo_fixed.swap(T.halo_fixed);
   s->T.halo_stride = T.halo_stride;

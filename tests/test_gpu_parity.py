@@ -634,3 +634,62 @@ def test_collision_schemes_on_the_clapper(vx):
         for k in ("pos", "quat", "vel", "angvel"):
             assert np.array_equal(g[k], finals[0][k]), k
     assert pos_error(sc, finals[0], ora.state()) < 1e-3
+
+
+# ---------------------------------------------------------------------------
+# full-size population in the bench's batched launch configuration, sampled
+# ---------------------------------------------------------------------------
+
+def population_body(sc, b):
+    """Body b of a population scene as a scene of its own (same origin)."""
+    dims = sc["dims"]
+    sites = np.prod(dims, axis=1)
+    s0 = int(sites[:b].sum())
+    occ = np.array([np.count_nonzero(sc["grid"][int(sites[:k].sum()):int(sites[:k + 1].sum())])
+                    for k in range(b + 1)])
+    o0 = int(occ[:b].sum())
+    out = dict(sc)
+    out["dims"] = dims[b:b + 1].copy()
+    out["grid"] = sc["grid"][s0:s0 + int(sites[b])].copy()
+    out["origin"] = sc["origin"][b:b + 1].copy()
+    out["phase"] = sc["phase"][o0:o0 + int(occ[b])].copy()
+    return out, o0, int(occ[b])
+
+
+def _oracle_body_run(args):
+    sc, steps = args
+    o = Oracle(sc)
+    o.set_dt(f32_dt(o))
+    o.step(steps)
+    return o.state()["pos"]
+
+
+def test_full_population_batched_graph_sampled_bodies(vx):
+    """The batched workload at full size (4,096 bodies of edges U{4..24}, 8.9M
+    voxels), stepped as the bench times it (groups of whole bodies, one
+    captured graph replay of 200 steps); eight sampled bodies against the
+    oracle stepping each body alone (the bodies are separate worlds)."""
+    import multiprocessing as mp
+    sc = scenes.population(n_bodies=4096)
+    steps = 200
+    rng = np.random.default_rng(12)
+    picks = sorted(rng.choice(4096, size=8, replace=False).tolist())
+    jobs, spans = [], []
+    for b in picks:
+        sb, o0, n = population_body(sc, b)
+        jobs.append((sb, steps))
+        spans.append((sb, o0, n))
+    with mp.get_context("spawn").Pool(8) as pool:
+        pending = pool.map_async(_oracle_body_run, jobs)
+        sim = vx.Sim(sc)
+        sim.set_batching(4096)
+        sim.graph_capture(steps)
+        sim.graph_launch()
+        g = sim.state()
+        assert sim.status()[0] == 0
+        sim.close()
+        ora = pending.get()
+    for (sb, o0, n), o in zip(spans, ora):
+        gp = g["pos"][o0:o0 + n]
+        diag = np.linalg.norm(np.ptp(o, axis=0)) if n > 1 else sb["voxel_size"]
+        assert np.abs(gp - o).max() / diag < 1e-3, (o0, n)
