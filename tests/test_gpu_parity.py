@@ -693,3 +693,71 @@ def test_full_population_batched_graph_sampled_bodies(vx):
         gp = g["pos"][o0:o0 + n]
         diag = np.linalg.norm(np.ptp(o, axis=0)) if n > 1 else sb["voxel_size"]
         assert np.abs(gp - o).max() / diag < 1e-3, (o0, n)
+
+
+# ---------------------------------------------------------------------------
+# edge lattices: no bonds, the largest lattice coordinates, isolated voxels,
+# bodies of one voxel next to large ones, everything fixed, zero steps
+# ---------------------------------------------------------------------------
+
+def edge_scene(case):
+    pal = [scenes.material(1e6, cte=0.01), scenes.material(5e7, rho=1200.0)]
+    kw = dict(gravity_z=-9.81, floor=True, zeta_ground=0.05, act_amplitude=10.0, act_period=300)
+    if case == "single_voxel":
+        sc = scenes._base([(1, 1, 1)], [1], 1e-3, pal, **kw)
+        sc["v0"] = (0.02, -0.01, -0.05)
+        return scenes.normalize(sc), 3000
+    if case in ("line_x_2048", "line_y_2048", "column_z_1024"):
+        d = {"line_x_2048": (2048, 1, 1), "line_y_2048": (1, 2048, 1), "column_z_1024": (1, 1, 1024)}[case]
+        n = int(np.prod(d))
+        grid = 1 + (np.arange(n) % 7 == 3).astype(np.uint8)        # every 7th voxel stiff
+        sc = scenes._base([d], grid, 1e-3, pal, **kw)
+        sc["phase"] = scenes.f32(np.linspace(0.0, 2.0 * np.pi, n))
+        return scenes.normalize(sc), 200
+    if case == "sparse_blob":                                       # many isolated voxels and small clusters
+        sc = scenes.random_blob((12, 10, 8), seed=21, fill=0.3)
+        sc.update(collide=True, **kw)
+        return scenes.normalize(sc), 800
+    if case == "ragged_bodies":                                     # bodies of 1 to 5^3 sites, one world each
+        # without the population's 20 K step of actuation strain at the
+        # start, whose transient leaves a few dangling voxels spinning
+        # chaotically in such small bodies
+        sc = scenes.population(n_bodies=40, seed=9, lo=1, hi=5)
+        sc.update(act_amplitude=0.0, zeta_ground=0.05)
+        sc["v0"] = (0.01, 0.0, -0.02)
+        return scenes.normalize(sc), 600
+    raise KeyError(case)
+
+
+@pytest.mark.parametrize("case", ["single_voxel", "line_x_2048", "line_y_2048", "column_z_1024", "sparse_blob",
+                                  "ragged_bodies"])
+def test_edge_lattices_follow_the_oracle(vx, case):
+    sc, steps = edge_scene(case)
+    sim, ora = pair(vx, sc)
+    assert np.allclose(sim.anchors(), ora.anchors(sc), rtol=0, atol=1e-15)
+    sim.step(steps)
+    ora.step(steps)
+    g, o = sim.state(), ora.state()
+    assert pos_error(sc, g, o) < 1e-3, case
+    # the body diagonal of a 2 m line is a loose yardstick: also hold the
+    # error to a few percent of the largest displacement
+    disp = np.abs(o["pos"] - ora.anchors(sc)).max()
+    assert np.abs(g["pos"] - o["pos"]).max() <= 5e-2 * disp, case
+    assert quat_error(g, o) < 1e-3
+    sim.close()
+
+
+def test_all_fixed_and_zero_steps_leave_the_state_unchanged(vx):
+    sc = scenes.random_blob((7, 6, 5), seed=4, fill=0.8)
+    sc.update(gravity_z=-9.81, floor=True, act_amplitude=20.0, act_period=50)
+    scenes.normalize(sc)
+    sc["fixed"] = np.ones(scenes.n_occupied(sc), np.uint8)
+    sim = vx.Sim(sc)
+    s0 = sim.read_state()
+    sim.step(0)
+    sim.step(300)
+    s1 = sim.read_state()
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(s0[k], s1[k]), k
+    assert sim.step_count == 300
+    sim.close()
