@@ -118,12 +118,16 @@ __device__ __forceinline__ V3f cross3(V3f a, V3f b) {
   return v3(fma_(a.y, b.z, -mul_(a.z, b.y)), fma_(a.z, b.x, -mul_(a.x, b.z)), fma_(a.x, b.y, -mul_(a.y, b.x)));
 }
 // cyclic permutation taking lattice axis a to local x: local[i] = v[(i + a) % 3]
-template <int a> __device__ __forceinline__ V3f to_axis(V3f v) {
+// (a is a compile-time constant in the unrolled callers, a register value
+// where one code path serves all three axes)
+__device__ __forceinline__ V3f to_axis_r(V3f v, int a) {
   return a == 0 ? v : (a == 1 ? v3(v.y, v.z, v.x) : v3(v.z, v.x, v.y));
 }
-template <int a> __device__ __forceinline__ V3f from_axis(V3f u) {
+__device__ __forceinline__ V3f from_axis_r(V3f u, int a) {
   return a == 0 ? u : (a == 1 ? v3(u.z, u.x, u.y) : v3(u.y, u.z, u.x));
 }
+template <int a> __device__ __forceinline__ V3f to_axis(V3f v) { return to_axis_r(v, a); }
+template <int a> __device__ __forceinline__ V3f from_axis(V3f u) { return from_axis_r(u, a); }
 // sqrt(x) for x > 0 from the hardware reciprocal square root (2 ulp)
 __device__ __forceinline__ float fsqrt(float x) { return mul_(x, rsqrtf(x)); }
 
@@ -148,11 +152,12 @@ __device__ __forceinline__ V3f mulT(const M3f& m, V3f v) {
 }
 // (R^T e_a) - e_a: row a of R(q) minus the unit vector, diagonal entry formed
 // as -2 (sum of the other two squares) so that no cancellation occurs.
-template <int a> __device__ __forceinline__ V3f row_dev(const M3f& R, Qf q) {
+__device__ __forceinline__ V3f row_dev_r(const M3f& R, Qf q, int a) {
   if (a == 0) return v3(mul_(-2.f, fma_(q.y, q.y, mul_(q.z, q.z))), R.r0.y, R.r0.z);
   if (a == 1) return v3(R.r1.x, mul_(-2.f, fma_(q.x, q.x, mul_(q.z, q.z))), R.r1.z);
   return v3(R.r2.x, R.r2.y, mul_(-2.f, fma_(q.x, q.x, mul_(q.y, q.y))));
 }
+template <int a> __device__ __forceinline__ V3f row_dev(const M3f& R, Qf q) { return row_dev_r(R, q, a); }
 
 // Rotation vector of conj(q1) * q2 (shortest arc).
 __device__ __forceinline__ V3f rel_rotvec(Qf a, Qf b) {
@@ -302,25 +307,24 @@ __device__ __forceinline__ BondK lut_consts(const float* lut, int n_mats, int m1
 // One bond along lattice axis a from voxel 1 (negative side) to voxel 2:
 // co-rotational beam (Sec 2.1.2) in voxel 1's frame (R1 = R(q1)), local
 // damping (Sec 2.1.5), rest length scaled by the mean thermal strain (Sec 2.3).
-template <int a>
-__device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, const VoxS& s2, float l, const BondK& k,
-                                             float eps, bool damp) {
+__device__ __forceinline__ BondOut bond_eval_r(const VoxS& s1, const M3f& R1, const VoxS& s2, float l,
+                                               const BondK& k, float eps, bool damp, int a) {
   const float a1 = k.a1, a2 = k.a2, b1 = k.a1, b2 = k.b2, b3 = k.b3;
   // position of voxel 2 in voxel 1's frame minus its rest vector l e_a:
   // R1^T (l e_a + do) - l e_a = R1^T do + l (R1^T e_a - e_a)
   V3f dO = sub(s2.o, s1.o);
-  V3f p = to_axis<a>(axpy(mulT(R1, dO), l, row_dev<a>(R1, s1.q)));
+  V3f p = to_axis_r(axpy(mulT(R1, dO), l, row_dev_r(R1, s1.q, a)), a);
   float X = fma_(-l, eps, p.x), Y = p.y, Z = p.z;
-  V3f th = to_axis<a>(rel_rotvec(s1.q, s2.q));
+  V3f th = to_axis_r(rel_rotvec(s1.q, s2.q), a);
   // bond forces on the voxels: the negated rows of [K] u (reduced form)
   V3f F1 = v3(mul_(a1, X), fma_(b1, Y, -mul_(b2, th.z)), fma_(b1, Z, mul_(b2, th.y)));
   V3f M1 = v3(mul_(a2, th.x), fma_(-b2, Z, -mul_(b3, th.y)), fma_(b2, Y, -mul_(b3, th.z)));
   const float b3x2 = add_(b3, b3);
   V3f M2 = v3(-mul_(a2, th.x), fma_(-b2, Z, -mul_(b3x2, th.y)), fma_(b2, Y, -mul_(b3x2, th.z)));
   BondOut o;
-  o.F1 = mul(R1, from_axis<a>(F1));
-  o.M1 = mul(R1, from_axis<a>(M1));
-  o.M2 = mul(R1, from_axis<a>(M2));
+  o.F1 = mul(R1, from_axis_r(F1, a));
+  o.M1 = mul(R1, from_axis_r(M1, a));
+  o.M2 = mul(R1, from_axis_r(M2, a));
   if (damp) {
     // V_{2->1} = (v2 - Va) + (D2 - Da) x wa = (v2 - v1)/2 + (l e_a + do) x (w1 + w2)/4;
     // F1 += c V_{2->1};  M1 += cr (w2 - wa) = cr/2 (w2 - w1);  M2 -= the same
@@ -333,6 +337,12 @@ __device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, cons
     o.M2 = axpy(o.M2, -k.cr2, dw);
   }
   return o;
+}
+
+template <int a>
+__device__ __forceinline__ BondOut bond_eval(const VoxS& s1, const M3f& R1, const VoxS& s2, float l, const BondK& k,
+                                             float eps, bool damp) {
+  return bond_eval_r(s1, R1, s2, l, k, eps, damp, a);
 }
 
 // Stores the bond force and moment sums of voxel v when the caller asked for

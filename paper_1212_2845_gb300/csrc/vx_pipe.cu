@@ -119,10 +119,14 @@ __device__ __forceinline__ void issue_tile(const StepArgs& A, const StPtr& G, co
 
 // Result of a bond for its voxel 2 (the owner's -a bond): F1 (voxel 2
 // receives -F1, subtracted at the gather) and M2.
-template <int TMAX, int a>
-__device__ __forceinline__ void minus_slot(float4* F4, float2* F2, int k, const BondOut& o) {
+template <int TMAX>
+__device__ __forceinline__ void minus_slot_r(float4* F4, float2* F2, int k, int a, const BondOut& o) {
   F4[a * TMAX + k] = make_float4(o.F1.x, o.F1.y, o.F1.z, o.M2.x);
   F2[a * TMAX + k] = make_float2(o.M2.y, o.M2.z);
+}
+template <int TMAX, int a>
+__device__ __forceinline__ void minus_slot(float4* F4, float2* F2, int k, const BondOut& o) {
+  minus_slot_r<TMAX>(F4, F2, k, a, o);
 }
 
 __device__ __forceinline__ BondK pair_consts(const StepArgs& A, const float* lut, const DevMat* mats, float4 p1,
@@ -137,15 +141,17 @@ __device__ __forceinline__ float4 voxel_props(const StepArgs& A, const DevMat& d
   return make_float4(E, __fmul_rn(E, d.g_ratio), strain_of(A, d, ph), __int_as_float(m));
 }
 
-template <int TMAX, int a>
+// A bond entering the tile from its halo (voxel 1 in the halo, voxel 2
+// owned): one code path for the three axes, the axis a register value.
+template <int TMAX>
 __device__ __forceinline__ void halo_bond_p(const StepArgs& A, const Stage<TMAX>& S, const float4* props,
                                             const float* lut, const DevMat* mats, float4* F4, float2* F2, int s1,
-                                            int s2) {
+                                            int s2, int a) {
   VoxS v1 = S.vox(s1), v2 = S.vox(s2);
   float4 p1 = props[s1], p2 = props[s2];
   BondK k = pair_consts(A, lut, mats, p1, p2);
-  BondOut o = bond_eval<a>(v1, qmat(v1.q), v2, A.l, k, mul_(0.5f, add_(p1.z, p2.z)), A.zb != 0.f);
-  minus_slot<TMAX, a>(F4, F2, s2, o);
+  BondOut o = bond_eval_r(v1, qmat(v1.q), v2, A.l, k, mul_(0.5f, add_(p1.z, p2.z)), A.zb != 0.f, a);
+  minus_slot_r<TMAX>(F4, F2, s2, a, o);
 }
 
 // Material properties (E, G, thermal strain, material) of the slots this
@@ -209,9 +215,7 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
   for (int j = i; j < cur.nhb; j += TMAX) {
     const uint32_t pk = S.hb[j];
     const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
-    if (ax == 0) halo_bond_p<TMAX, 0>(A, S, props, lut, mats, F4, F2, s1, s2);
-    else if (ax == 1) halo_bond_p<TMAX, 1>(A, S, props, lut, mats, F4, F2, s1, s2);
-    else halo_bond_p<TMAX, 2>(A, S, props, lut, mats, F4, F2, s1, s2);
+    halo_bond_p<TMAX>(A, S, props, lut, mats, F4, F2, s1, s2, ax);
   }
   __syncthreads();
   if (nxt.valid) {
