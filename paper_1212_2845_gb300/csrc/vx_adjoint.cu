@@ -74,9 +74,8 @@ struct BondAdj { V3f dO, dv, w1, w2; Qf q1, q2; float E1, E2, G1, G2, eps; };
 // Reverse of bond_eval along lattice axis a: recomputes the forward values the
 // derivatives need, then applies the chain rule from (gF1, gM1, gM2), the
 // adjoints of the bond's force on voxel 1 and moments on voxels 1 and 2.
-template <int a>
 __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, float l, float zb, V3f gF1, V3f gM1,
-                         V3f gM2, BondAdj& g) {
+                         V3f gM2, BondAdj& g, int a) {
   // ---- forward values
   // (derivative-only values: hardware reciprocal, reciprocal square root and
   // fast division, a few ulp, are accurate enough)
@@ -89,7 +88,7 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   const V3f dO = S3(s2.o, s1.o);
   V3f rd = (a == 0) ? R.r0 : (a == 1 ? R.r1 : R.r2);  // R^T e_a - e_a
   if (a == 0) rd.x -= 1.f; else if (a == 1) rd.y -= 1.f; else rd.z -= 1.f;
-  const V3f p = to_axis<a>(A3(RTv(R, dO), M3(rd, l)));
+  const V3f p = to_axis_r(A3(RTv(R, dO), M3(rd, l)), a);
   const float X = p.x - l * bp.eps, Y = p.y, Z = p.z;
   // relative rotation (W, vq) = sign * conj(q1) q2 and theta = f(W, |vq|^2) vq
   const Qf A1 = s1.q, B2 = s2.q;
@@ -117,10 +116,10 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
     fW = -2.f * iden;
     fs2 = (W * iden - at * is) * is * is;
   }
-  const V3f th = to_axis<a>(M3(vq, f));
-  const V3f F1w = from_axis<a>(v3(a1 * X, b1 * Y - b2 * th.z, b1 * Z + b2 * th.y));
-  const V3f M1w = from_axis<a>(v3(a2 * th.x, -b2 * Z - b3 * th.y, b2 * Y - b3 * th.z));
-  const V3f M2w = from_axis<a>(v3(-a2 * th.x, -b2 * Z - 2.f * b3 * th.y, b2 * Y - 2.f * b3 * th.z));
+  const V3f th = to_axis_r(M3(vq, f), a);
+  const V3f F1w = from_axis_r(v3(a1 * X, b1 * Y - b2 * th.z, b1 * Z + b2 * th.y), a);
+  const V3f M1w = from_axis_r(v3(a2 * th.x, -b2 * Z - b3 * th.y, b2 * Y - b3 * th.z), a);
+  const V3f M2w = from_axis_r(v3(-a2 * th.x, -b2 * Z - 2.f * b3 * th.y, b2 * Y - 2.f * b3 * th.z), a);
 
   // ---- reverse
   V3f g_dO = v3(0.f, 0.f, 0.f);
@@ -154,7 +153,7 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   outer_add(gR, gF1, F1w);
   outer_add(gR, gM1, M1w);
   outer_add(gR, gM2, M2w);
-  const V3f gF = to_axis<a>(RTv(R, gF1)), gm1 = to_axis<a>(RTv(R, gM1)), gm2 = to_axis<a>(RTv(R, gM2));
+  const V3f gF = to_axis_r(RTv(R, gF1), a), gm1 = to_axis_r(RTv(R, gM1), a), gm2 = to_axis_r(RTv(R, gM2), a);
   // local forces and moments (the negated rows of [K] u, Sec 2.1.2)
   float g_X = 0.f, g_Y = 0.f, g_Z = 0.f;
   V3f g_th = v3(0.f, 0.f, 0.f);
@@ -169,7 +168,7 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   g_b3 -= (gm1.z + 2.f * gm2.z) * th.z; g_th.z -= b3 * (gm1.z + 2.f * gm2.z);
   // X = p.x - l eps, p = Pi_a (R^T dO + l (R^T e_a - e_a))
   g.eps = -l * g_X;
-  const V3f g_pw = from_axis<a>(v3(g_X, g_Y, g_Z));
+  const V3f g_pw = from_axis_r(v3(g_X, g_Y, g_Z), a);
   outer_add(gR, dO, g_pw);
   g_dO = A3(g_dO, Rv(R, g_pw));
   if (a == 0) gR.r0 = A3(gR.r0, M3(g_pw, l));
@@ -177,7 +176,7 @@ __device__ void bond_vjp(const VoxS& s1, const VoxS& s2, const BondPar& bp, floa
   else gR.r2 = A3(gR.r2, M3(g_pw, l));
   g.dO = g_dO;
   // theta = Pi_a (f vq)
-  const V3f g_thq = from_axis<a>(g_th);
+  const V3f g_thq = from_axis_r(g_th, a);
   const float g_f = D3(g_thq, vq);
   const V3f g_vq = A3(M3(g_thq, f), M3(vq, 2.f * fs2 * g_f));
   const float gw = sg * fW * g_f, gx = sg * g_vq.x, gy = sg * g_vq.y, gz = sg * g_vq.z;
@@ -424,8 +423,9 @@ __device__ __forceinline__ void voxadj_add(VoxAdj& r, const VoxAdj& b) {
 // Reverse of the bond between staged voxels k1 (negative side) and k2 along
 // axis a; returns the voxel-1 part, stores the voxel-2 part in slot (a, k2)
 // when k2 is owned.
-template <int TMAX, int a>
-__device__ __forceinline__ VoxAdj tile_bond(const StepArgs& A, const AdjTile<TMAX>& S, int k1, int k2, int T) {
+template <int TMAX>
+__device__ __forceinline__ VoxAdj tile_bond(const StepArgs& A, const AdjTile<TMAX>& S, int k1, int k2, int T,
+                                            int a) {
   const VoxS s1 = S.vox(k1), s2 = S.vox(k2);
   const float4 p1 = S.props[k1], p2 = S.props[k2];
   const DevMat& d1 = S.mats[__float_as_int(p1.w)];
@@ -436,7 +436,7 @@ __device__ __forceinline__ VoxAdj tile_bond(const StepArgs& A, const AdjTile<TMA
   bp.Imin = fminf(d1.I, d2.I);
   bp.eps = 0.5f * (p1.z + p2.z);
   BondAdj g;
-  bond_vjp<a>(s1, s2, bp, A.l, A.zb, S3(S.gF(k1), S.gF(k2)), S.gM(k1), S.gM(k2), g);
+  bond_vjp(s1, s2, bp, A.l, A.zb, S3(S.gF(k1), S.gF(k2)), S.gM(k1), S.gM(k2), g, a);
   if (k2 < T) {
     float4* sl = S.slot + a * TMAX + k2;
     sl[0] = make_float4(g.dO.x, g.dO.y, g.dO.z, g.dv.x);
@@ -534,9 +534,9 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 2 : 4))
   // ---- own +x, +y, +z bonds (voxel-1 part kept), halo bonds
   VoxAdj acc = voxadj_zero();
   if (own) {
-    if (px != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 0>(A, S, i, px, T));
-    if (py != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 1>(A, S, i, py, T));
-    if (pz != 0xFFFF) voxadj_add(acc, tile_bond<TMAX, 2>(A, S, i, pz, T));
+    if (px != 0xFFFF) voxadj_add(acc, tile_bond<TMAX>(A, S, i, px, T, 0));
+    if (py != 0xFFFF) voxadj_add(acc, tile_bond<TMAX>(A, S, i, py, T, 1));
+    if (pz != 0xFFFF) voxadj_add(acc, tile_bond<TMAX>(A, S, i, pz, T, 2));
   }
   // bonds entering from the halo (at most two per thread: the list fits 2 TMAX)
 #pragma unroll
@@ -544,9 +544,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? 2 : 4))
     const uint32_t pk = r == 0 ? hb0 : hb1;
     if (pk == 0xFFFFFFFFu) continue;
     const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
-    if (ax == 0) tile_bond<TMAX, 0>(A, S, s1, s2, T);
-    else if (ax == 1) tile_bond<TMAX, 1>(A, S, s1, s2, T);
-    else tile_bond<TMAX, 2>(A, S, s1, s2, T);
+    tile_bond<TMAX>(A, S, s1, s2, T, ax);  // one code path for the three axes (no divergence)
   }
   __syncthreads();
   if (!own) return;
