@@ -139,10 +139,13 @@ template <int TMAX> struct Smem {
   __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
 };
 
+__device__ __forceinline__ void store_minus_slot_r(float4* F4, float2* F2, int tmax, int k, int a, const BondOut& o) {
+  F4[a * tmax + k] = make_float4(-o.F1.x, -o.F1.y, -o.F1.z, o.M2.x);
+  F2[a * tmax + k] = make_float2(o.M2.y, o.M2.z);
+}
 template <int TMAX, int a>
 __device__ __forceinline__ void store_minus_slot(const Smem<TMAX>& S, int k, const BondOut& o) {
-  S.slotF4[a * TMAX + k] = make_float4(-o.F1.x, -o.F1.y, -o.F1.z, o.M2.x);
-  S.slotF2[a * TMAX + k] = make_float2(o.M2.y, o.M2.z);
+  store_minus_slot_r(S.slotF4, S.slotF2, TMAX, k, a, o);
 }
 
 // Constants of the bond between staged voxels k1 and k2.
@@ -155,13 +158,15 @@ __device__ __forceinline__ BondK staged_consts(const StepArgs& A, const Smem<TMA
   return bond_consts(A.l, p1.x, p2.x, p1.y, p2.y, fminf(d1.m, d2.m), fminf(d1.I, d2.I), A.zb);
 }
 
-template <int TMAX, int a>
-__device__ __forceinline__ void halo_bond(const StepArgs& A, const Smem<TMAX>& S, int s1, int s2) {
+// A bond entering the tile from its halo: one code path for the three axes
+// (lanes of a warp holding bonds of different axes do not diverge).
+template <int TMAX>
+__device__ __forceinline__ void halo_bond(const StepArgs& A, const Smem<TMAX>& S, int s1, int s2, int a) {
   VoxS v1 = S.vox(s1), v2 = S.vox(s2);
   float4 p1 = S.props[s1], p2 = S.props[s2];
   BondK k = staged_consts<TMAX>(A, S, p1, p2);
-  BondOut o = bond_eval<a>(v1, qmat(v1.q), v2, A.l, k, mul_(0.5f, add_(p1.z, p2.z)), A.zb != 0.f);
-  store_minus_slot<TMAX, a>(S, s2, o);
+  BondOut o = bond_eval_r(v1, qmat(v1.q), v2, A.l, k, mul_(0.5f, add_(p1.z, p2.z)), A.zb != 0.f, a);
+  store_minus_slot_r(S.slotF4, S.slotF2, TMAX, s2, a, o);
 }
 
 // Material-dependent values of one staged voxel: E, G, thermal strain, material.
@@ -239,9 +244,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 512 ? 1 : (TMAX == 256 ? VX_CTAS
   for (int j = i; j < nhb; j += TMAX) {
     uint32_t pk = S.hb[j];
     int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
-    if (ax == 0) halo_bond<TMAX, 0>(A, S, s1, s2);
-    else if (ax == 1) halo_bond<TMAX, 1>(A, S, s1, s2);
-    else halo_bond<TMAX, 2>(A, S, s1, s2);
+    halo_bond<TMAX>(A, S, s1, s2, ax);
   }
   __syncthreads();
   // ---- gather the -x, -y, -z results and integrate
