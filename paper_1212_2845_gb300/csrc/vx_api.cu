@@ -159,6 +159,7 @@ struct vx_sim {
   unsigned* vmax = nullptr;
   int* cflag = nullptr;
   int* any = nullptr;
+  unsigned* hdone = nullptr;  // CTAs of a step launch done (the step keeps the horizon)
   long long* nreb = nullptr;
   unsigned* cbar = nullptr;  // grid barrier words of the rebuild launch
   int64_t* qorg = nullptr;   // shared world: quantised body origins rint(origin 2^K), 3 per body
@@ -200,6 +201,12 @@ float* next_state(vx_sim* s) { return s->st + (size_t)(1 - s->cur) * NPLANE * s-
 
 StepArgs step_args(vx_sim* s) {
   StepArgs A;
+  A.h_done = nullptr;  // the horizon is kept by a separate launch unless the caller sets it
+  A.h_acc = nullptr;
+  A.h_flag = A.h_any = nullptr;
+  A.h_threshold = 0.f;
+  A.h_world = 0;
+  A.n_bodies = s->L.n_bodies;
   A.N = (int)s->L.N;
   A.pitch = s->pitch;
   A.l = s->L.l;
@@ -400,6 +407,7 @@ int alloc_collisions(vx_sim* s) {
       (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, kRebuildMaxGrid)) || (rc = dalloc(&s->cbar, 2)) ||
       (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
+      (rc = dalloc(&s->hdone, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
     return rc;
   // searched voxels (surface voxels, or all) in ascending internal order
@@ -414,6 +422,7 @@ int alloc_collisions(vx_sim* s) {
   VX_CUDA(cudaMemset(s->acc, 0, L.n_bodies * sizeof(float)));
   VX_CUDA(cudaMemset(s->cflag, 0, L.n_bodies * sizeof(int)));
   VX_CUDA(cudaMemset(s->any, 0, sizeof(int)));
+  VX_CUDA(cudaMemset(s->hdone, 0, sizeof(unsigned)));
   VX_CUDA(cudaMemset(s->nreb, 0, sizeof(long long)));
   VX_CUDA(cudaMemset(s->cbar, 0, 2 * sizeof(unsigned)));
   s->coll_alloc = true;
@@ -423,7 +432,7 @@ int alloc_collisions(vx_sim* s) {
 void free_collisions(vx_sim* s) {
   dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket); dfree(s->hcount); dfree(s->hcursor);
   dfree(s->hstart); dfree(s->bsum); dfree(s->cbar); dfree(s->sorted); dfree(s->ccount); dfree(s->cand);
-  dfree(s->acc); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
+  dfree(s->acc); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
   s->coll_alloc = false;
   s->coll_S = 0;
 }
@@ -807,7 +816,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->phase); dfree(s->logE); dfree(s->fext); dfree(s->mats); dfree(s->lut); dfree(s->dtb); dfree(s->origin);
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
-  dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb);
+  dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
   dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar); dfree(s->qorg);
@@ -1202,9 +1211,19 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     }
     cudaGetLastError();  // not co-resident on this device: fall back to one launch per step
   }
+  // the pipelined step keeps the collision horizon itself (one launch less per step)
+  const bool tail = s->collide_on && !s->coll_every && s->form == VX_FORM_PIPELINED;
   for (int64_t i = 0; i < n; ++i) {
     StepArgs A = step_args(s);
     if (s->actP > 0) A.act_w = (float)(2.0 * M_PI * (double)(s->step % s->actP) / (double)s->actP);
+    if (tail) {
+      A.h_done = s->hdone;
+      A.h_acc = s->acc;
+      A.h_flag = s->cflag;
+      A.h_any = s->any;
+      A.h_threshold = s->threshold;
+      A.h_world = s->collide_on == 2 ? 1 : 0;
+    }
     if (s->form == VX_FORM_PIPELINED) {
       if ((rc = ensure_pipe(s, A))) return rc;
       launch_pipe(A, s->tile_max, s->pipe_smem, s->pipe_grid, st);
@@ -1216,7 +1235,7 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     if (s->collide_on) {
       CollideArgs C = collide_args(s);
       if (s->coll_every) launch_flag_all(C, st);  // rebuild every step
-      else launch_horizon(C, st);
+      else if (!tail) launch_horizon(C, st);
       launch_rebuild(C, st);
     }
   }

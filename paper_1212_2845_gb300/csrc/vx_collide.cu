@@ -59,7 +59,7 @@ __global__ void horizon_update_world(CollideArgs C) {
     if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
     __syncthreads();
   }
-  const float acc = C.acc[0] + 2.f * red[0] * C.dt_body[0];
+  const float acc = horizon_acc(C.acc[0], red[0], C.dt_body[0]);
   const bool rebuild = acc >= C.threshold;
   __syncthreads();
   if (rebuild)
@@ -75,7 +75,7 @@ __global__ void horizon_update(CollideArgs C) {
   if (b >= C.n_bodies) return;
   float vmax = __uint_as_float(C.vmax_bits[b]);
   C.vmax_bits[b] = 0u;
-  float acc = C.acc[b] + 2.f * vmax * C.dt_body[b];
+  float acc = horizon_acc(C.acc[b], vmax, C.dt_body[b]);
   if (acc >= C.threshold) {
     acc = 0.f;
     C.flag[b] = 1;

@@ -88,6 +88,15 @@ struct StepArgs {
   unsigned* vmax_bits;     // per body, float bits of max |v|
   int* status;             // [0] bits, [1] first bad voxel (internal), [2..3] step
   float* fm_out;           // 6 planes: bond force and moment sum of every voxel, or nullptr
+  // collision horizon kept by the pipelined step itself (nullptr h_done: a
+  // separate launch keeps it): the last CTA to finish updates the per-body
+  // accumulators and flags the bodies to rebuild
+  unsigned* h_done;        // CTAs done in this launch (0 between launches)
+  float* h_acc;            // per body, or one for a shared world
+  int* h_flag;             // per body: rebuild
+  int* h_any;              // some body flagged
+  float h_threshold;
+  int h_world, n_bodies;
 };
 
 
@@ -524,6 +533,62 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
   float chk = s.o.x + s.o.y + s.o.z + s.v.x + s.v.y + s.v.z + s.w.x + s.w.y + s.w.z + s.q.w;
   if (!isfinite(chk)) record_bad(A, v);
   return fsqrt(fmaxf(dot3(s.v, s.v), 1e-30f));
+}
+
+// Collision horizon accumulator after a step (Sec 2.2.2, horizon reading):
+// acc + 2 max|v| dt, the largest relative closure two voxels can make.
+__device__ __forceinline__ float horizon_acc(float acc, float vmax, float dt) {
+  return fma_(mul_(2.f, vmax), dt, acc);
+}
+
+// The horizon bookkeeping at the end of a step launch: each CTA, its tiles
+// done, counts itself in; the last one adds each body's closure to its
+// accumulator (one accumulator with the largest speed of all bodies in a
+// shared world), flags the bodies whose accumulator reached the threshold,
+// zeroes the speeds and the counter.  red: blockDim.x floats of shared scratch.
+__device__ __forceinline__ void horizon_tail(const StepArgs& A, float* red) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned prev = atomicAdd(A.h_done, 1u);
+    reinterpret_cast<int*>(red)[0] = prev + 1 == gridDim.x;
+  }
+  __syncthreads();
+  const bool last = reinterpret_cast<int*>(red)[0] != 0;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (!A.h_world) {
+    for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) {
+      const float vmax = __uint_as_float(atomicExch(&A.vmax_bits[b], 0u));
+      float acc = horizon_acc(__ldcg(&A.h_acc[b]), vmax, A.dt_body[b]);
+      if (acc >= A.h_threshold) {
+        acc = 0.f;
+        A.h_flag[b] = 1;
+        atomicExch(A.h_any, 1);
+      }
+      A.h_acc[b] = acc;
+    }
+  } else {
+    float m = 0.f;
+    for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x)
+      m = fmaxf(m, __uint_as_float(atomicExch(&A.vmax_bits[b], 0u)));
+    red[threadIdx.x] = m;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+      __syncthreads();
+    }
+    const float acc = horizon_acc(__ldcg(&A.h_acc[0]), red[0], A.dt_body[0]);
+    const bool rebuild = acc >= A.h_threshold;
+    if (rebuild)
+      for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) A.h_flag[b] = 1;
+    if (threadIdx.x == 0) {
+      A.h_acc[0] = rebuild ? 0.f : acc;
+      if (rebuild) atomicExch(A.h_any, 1);
+    }
+  }
+  if (threadIdx.x == 0) *A.h_done = 0u;
 }
 
 // Per-body max |v| for the collision horizon (max is order-independent).

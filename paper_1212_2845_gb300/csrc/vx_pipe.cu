@@ -340,10 +340,12 @@ template <int TMAX> struct PipeLayout {
 template <int TMAX>
 __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs A) {
   extern __shared__ __align__(16) float smem[];
-  if ((int)blockIdx.x >= A.n_tiles) return;  // uniform over the CTA
   const PipeLayout<TMAX> L(smem, A);
-  L.load_tables(A);
-  pipe_tiles<TMAX>(A, blockIdx.x, gridDim.x, A.n_tiles, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+  if ((int)blockIdx.x < A.n_tiles) {  // uniform over the CTA
+    L.load_tables(A);
+    pipe_tiles<TMAX>(A, blockIdx.x, gridDim.x, A.n_tiles, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+  }
+  if (A.h_done) horizon_tail(A, reinterpret_cast<float*>(L.props));
 }
 
 // Multi-step form: one cooperative launch runs n steps of the whole lattice;
