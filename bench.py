@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -136,6 +137,20 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")), ws
 
 
+def host_cpu():
+    """Model name and online core count of the host (reported beside the oracle timing)."""
+    model = platform.machine()
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def cpu_baseline(sc, seconds=12.0):
     """The FP64 oracle (single thread) on a bounded sample of the same workload."""
     from oracle import Oracle
@@ -147,7 +162,28 @@ def cpu_baseline(sc, seconds=12.0):
         n += 5
     t = time.perf_counter() - t0
     return {"value": o.N * n / t, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{WORKLOAD}, first {n} steps from rest, FP64, 1 thread, {t:.1f} s"}
+            "sample": f"{WORKLOAD}, first {n} steps from rest, FP64, 1 thread, {t:.1f} s", "host": host_cpu()}
+
+
+def oracle_per_config(seconds=4.0):
+    """The oracle (single thread) on a bounded sample of each other
+    configuration: the cantilever, a scaled ball drop, a 64-body subset of the
+    population and one design body."""
+    from oracle import Oracle
+    out = {}
+    for name, sc in (("cantilever_10x10x10", scenes.cantilever()),
+                     ("hollow_ball_R20_t4", scenes.hollow_ball(R=20, t=4)),
+                     ("population_64", scenes.population(n_bodies=64)),
+                     ("design_population_1x12^3", scenes.design_population(n_bodies=1))):
+        o = Oracle(sc)
+        n = 0
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < seconds:
+            o.step(1)
+            n += 1
+        t = time.perf_counter() - t0
+        out[name] = {"voxels": o.N, "steps": n, "value": o.N * n / t, "unit": METRIC, "steps_per_s": n / t}
+    return out
 
 
 def run_reference(args, sc):
@@ -168,7 +204,8 @@ def run_reference(args, sc):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "voxels": o.N, "bonds": o.n_bonds},
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
-                             "sample": f"{args.steps} steps after {args.warmup} warm-up, 1 thread"},
+                             "sample": f"{args.steps} steps after {args.warmup} warm-up, 1 thread",
+                             "host": host_cpu()},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -512,6 +549,8 @@ def main():
                          "small_lattice": small_lattice(stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
+        if not args.no_forms:
+            line["cpu_baseline"]["other_configs"] = oracle_per_config()
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
