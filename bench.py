@@ -374,7 +374,6 @@ def collision_schemes(stream, steps=2000):
     for name, all_voxels, every in (("all+every", True, True), ("surf+every", False, True),
                                     ("all+horizon", True, False), ("surf+horizon", False, False)):
         sim = vx.Sim(sc)
-        sim.set_multistep(0)
         sim.set_collision_scheme(all_voxels, every)
         n0, _ = sim.collision_stats()
         t = _events_time(stream, lambda: sim.step_async(steps, stream))

@@ -1179,7 +1179,7 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     VX_CUDA(cudaGetLastError());
     return VX_OK;
   }
-  bool multi = s->multistep && s->form == VX_FORM_PIPELINED && !s->collide_on && n > 1;
+  bool multi = s->multistep && s->form == VX_FORM_PIPELINED && n > 1;
   if (multi) {
     StepArgs A = step_args(s);
     if ((rc = ensure_pipe(s, A))) return rc;
@@ -1204,6 +1204,21 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     M.bar = s->bar;
     M.spins = s->bar_spins;
     M.extra = (unsigned)s->bar_extra;
+    M.collide = 0;
+    M.every_step = 0;
+    if (s->collide_on) {
+      // horizon and rebuilds between the steps, on the launch's own grid and barrier
+      M.collide = 1;
+      M.every_step = s->coll_every ? 1 : 0;
+      M.coll = collide_args(s);
+      M.coll.bar = s->bar;
+      M.coll.spins = s->bar_spins;
+      A.h_acc = s->acc;
+      A.h_flag = s->cflag;
+      A.h_any = s->any;
+      A.h_threshold = s->threshold;
+      A.h_world = s->collide_on == 2 ? 1 : 0;
+    }
     if (launch_multi(A, M, s->tile_max, s->pipe_smem, s->multi_grid, st) == cudaSuccess) {
       s->cur ^= (int)(n & 1);
       s->step += n;

@@ -25,24 +25,11 @@
 //     query         27 neighbour cells per surface voxel of a flagged body;
 //                   candidates sorted ascending by canonical index
 //     finish        clears flags, counts the rebuild
-#include "vx_dev.cuh"
-#include "vx_kernels.h"
+#include "vx_collide.cuh"
 
 #include <algorithm>
 
 namespace vx {
-
-__device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {
-  int64_t q = a / b;
-  return (a % b != 0 && ((a < 0) != (b < 0))) ? q - 1 : q;
-}
-
-__device__ __forceinline__ uint32_t cell_hash(int64_t cx, int64_t cy, int64_t cz, uint32_t mask) {
-  uint64_t h = (uint64_t)cx * 0x9E3779B97F4A7C15ull ^ (uint64_t)cy * 0xC2B2AE3D27D4EB4Full ^
-               (uint64_t)cz * 0x165667B19E3779F9ull;
-  h ^= h >> 29;
-  return (uint32_t)h & mask;
-}
 
 // Shared world: one accumulator over all bodies (relative motion between
 // bodies counts), kept in slot 0; a rebuild flags every body.  One block.
@@ -84,157 +71,14 @@ __global__ void horizon_update(CollideArgs C) {
   C.acc[b] = acc;
 }
 
-__device__ __forceinline__ void quantise_one(const CollideArgs& C, int s) {
-  int v = C.surf[s];
-  uint32_t lp = C.lat[v];
-  int64_t ijk[3] = {(int64_t)(lp & 2047u), (int64_t)((lp >> 11) & 2047u), (int64_t)(lp >> 22)};
-  const int64_t* qo = C.qorg ? C.qorg + 3 * (C.body ? C.body[v] : 0) : nullptr;
-  int64_t xq[3];
-  for (int a = 0; a < 3; ++a) {
-    float o = C.st[(int64_t)v * C.ostride_v + a * C.ostride_a];
-    xq[a] = (qo ? qo[a] : 0) + ijk[a] * C.Q + llrintf(ldexpf(o, C.K));
-    C.xq[(int64_t)a * C.S + s] = xq[a];
-  }
-  int64_t cs = 2 * C.Q;
-  const int64_t cx = floordiv(xq[0], cs), cy = floordiv(xq[1], cs), cz = floordiv(xq[2], cs);
-  C.cell[s] = make_int4((int)cx, (int)cy, (int)cz, 0);  // cells of a world fit in 32 bits
-  uint32_t h = cell_hash(cx, cy, cz, C.H - 1);
-  C.bucket[s] = h;
-  atomicAdd(&C.hcount[h], 1u);
-}
-
-// Exclusive scan of x over the CTA (all threads call it); returns this
-// thread's prefix and the CTA total.
-__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* warp_tot, uint32_t* block_total) {
-  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t inc = x;
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  if (lane == 31) warp_tot[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t t = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0u;
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, t, o);
-      if (lane >= o) t += y;
-    }
-    warp_tot[lane] = t;
-  }
-  __syncthreads();
-  uint32_t pre = (w > 0 ? warp_tot[w - 1] : 0u) + inc - x;
-  *block_total = warp_tot[(blockDim.x >> 5) - 1];
-  __syncthreads();
-  return pre;
-}
-
-__device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
-  int v = C.surf[s];
-  int b = C.body ? C.body[v] : 0;
-  if (!C.flag[b]) return;
-  int64_t x0 = C.xq[s], y0 = C.xq[(int64_t)C.S + s], z0 = C.xq[2 * (int64_t)C.S + s];
-  int64_t cs = 2 * C.Q;
-  const int4 c0 = C.cell[s];
-  const int cx = c0.x, cy = c0.y, cz = c0.z;
-  uint32_t lp = C.lat[v];
-  int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);
-  int64_t r2max = cs * cs;  // (2 Q)^2
-  int list[kCandCap];
-  int n = 0;
-  bool overflow = false;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
-        uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
-        uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
-        for (uint32_t e = e0; e < e1; ++e) {
-          int t = C.sorted[e];
-          if (t == s) continue;
-          const int4 c1 = C.cell[t];
-          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
-          int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
-          int u = C.surf[t];
-          if (C.body && C.body[u] != b) {
-            if (!C.qorg) continue;  // bodies are separate worlds
-          } else {
-            uint32_t lq = C.lat[u];
-            int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
-            if (man <= 3) continue;
-          }
-          int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
-          if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
-          if (n < kCandCap) list[n++] = u; else overflow = true;
-        }
-      }
-  // insertion sort ascending (lists are short)
-  for (int i = 1; i < n; ++i) {
-    int x = list[i];
-    int k = i - 1;
-    while (k >= 0 && list[k] > x) { list[k + 1] = list[k]; --k; }
-    list[k + 1] = x;
-  }
-  int32_t* out = C.cand + (int64_t)s * kCandCap;
-  for (int i = 0; i < n; ++i) out[i] = list[i];
-  C.ccount[s] = n;
-  if (overflow) atomicOr(C.status, kStatusCapacity);
-}
-
 constexpr int kRebuildThreads = 256;
 
 // The whole rebuild in one cooperative launch (all CTAs co-resident; phases
 // separated by grid barriers, whose waits are bounded: on a timeout the
 // launch ends with the timeout status bit set).
 __global__ void __launch_bounds__(kRebuildThreads) rebuild_all(CollideArgs C) {
-  __shared__ uint32_t warp_tot[32];
-  __shared__ uint32_t offset;
   if (*C.any == 0) return;  // the same value for every CTA: set by an earlier launch
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
-  const unsigned G = gridDim.x;
-  // zero the bucket counters
-  for (int i = tid; i < C.H; i += nthr) { C.hcount[i] = 0u; C.hcursor[i] = 0u; }
-  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
-  for (int s = tid; s < C.S; s += nthr) quantise_one(C, s);
-  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
-  // scan: CTA c owns buckets [c chunk, (c + 1) chunk)
-  const int chunk = (C.H + (int)G - 1) / (int)G;
-  const int b0 = min(C.H, (int)blockIdx.x * chunk), b1 = min(C.H, b0 + chunk);
-  uint32_t carry = 0u;
-  for (int base = b0; base < b1; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const uint32_t x = i < b1 ? C.hcount[i] : 0u;
-    uint32_t tot;
-    const uint32_t pre = block_exclusive_scan(x, warp_tot, &tot);
-    if (i < b1) C.hstart[i] = carry + pre;
-    carry += tot;
-  }
-  if (threadIdx.x == 0) C.bsum[blockIdx.x] = carry;
-  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
-  {
-    // offset of this CTA's chunk: sum of the chunk totals before it (fixed order)
-    uint32_t part = 0u;
-    for (int c = threadIdx.x; c < (int)blockIdx.x; c += blockDim.x) part += C.bsum[c];
-    uint32_t tot;
-    block_exclusive_scan(part, warp_tot, &tot);
-    if (threadIdx.x == 0) offset = tot;
-    __syncthreads();
-    for (int i = b0 + threadIdx.x; i < b1; i += blockDim.x) C.hstart[i] += offset;
-    if (blockIdx.x == G - 1 && threadIdx.x == 0) C.hstart[C.H] = offset + carry;
-  }
-  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
-  for (int s = tid; s < C.S; s += nthr) {
-    const uint32_t h = C.bucket[s];
-    C.sorted[C.hstart[h] + atomicAdd(&C.hcursor[h], 1u)] = s;
-  }
-  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
-  for (int s = tid; s < C.S; s += nthr) query_one(C, s);
-  if (!grid_barrier(C.bar, G, C.spins, C.status)) return;
-  if (blockIdx.x == 0) {
-    for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) C.flag[b] = 0;
-    __syncthreads();
-    if (threadIdx.x == 0) { *C.any = 0; *C.n_rebuilds += 1; }
-  }
+  rebuild_phases(C, gridDim.x);
 }
 
 // Raise every body's rebuild flag (forced rebuild).

@@ -541,11 +541,47 @@ __device__ __forceinline__ float horizon_acc(float acc, float vmax, float dt) {
   return fma_(mul_(2.f, vmax), dt, acc);
 }
 
+// The horizon bookkeeping after a step, run by one CTA once every CTA's
+// speeds are in: adds each body's closure to its accumulator (one
+// accumulator with the largest speed of all bodies in a shared world), flags
+// the bodies whose accumulator reached the threshold and zeroes the speeds.
+// red: blockDim.x floats of shared scratch.
+__device__ __forceinline__ void horizon_account(const StepArgs& A, float* red) {
+  if (!A.h_world) {
+    for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) {
+      const float vmax = __uint_as_float(atomicExch(&A.vmax_bits[b], 0u));
+      float acc = horizon_acc(__ldcg(&A.h_acc[b]), vmax, A.dt_body[b]);
+      if (acc >= A.h_threshold) {
+        acc = 0.f;
+        A.h_flag[b] = 1;
+        atomicExch(A.h_any, 1);
+      }
+      A.h_acc[b] = acc;
+    }
+    return;
+  }
+  float m = 0.f;
+  for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x)
+    m = fmaxf(m, __uint_as_float(atomicExch(&A.vmax_bits[b], 0u)));
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const float acc = horizon_acc(__ldcg(&A.h_acc[0]), red[0], A.dt_body[0]);
+  const bool rebuild = acc >= A.h_threshold;
+  if (rebuild)
+    for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) A.h_flag[b] = 1;
+  if (threadIdx.x == 0) {
+    A.h_acc[0] = rebuild ? 0.f : acc;
+    if (rebuild) atomicExch(A.h_any, 1);
+  }
+}
+
 // The horizon bookkeeping at the end of a step launch: each CTA, its tiles
-// done, counts itself in; the last one adds each body's closure to its
-// accumulator (one accumulator with the largest speed of all bodies in a
-// shared world), flags the bodies whose accumulator reached the threshold,
-// zeroes the speeds and the counter.  red: blockDim.x floats of shared scratch.
+// done, counts itself in; the last one runs horizon_account and zeroes the
+// counter for the next launch.  red: blockDim.x floats of shared scratch.
 __device__ __forceinline__ void horizon_tail(const StepArgs& A, float* red) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -558,36 +594,7 @@ __device__ __forceinline__ void horizon_tail(const StepArgs& A, float* red) {
   __syncthreads();
   if (!last) return;
   __threadfence();
-  if (!A.h_world) {
-    for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) {
-      const float vmax = __uint_as_float(atomicExch(&A.vmax_bits[b], 0u));
-      float acc = horizon_acc(__ldcg(&A.h_acc[b]), vmax, A.dt_body[b]);
-      if (acc >= A.h_threshold) {
-        acc = 0.f;
-        A.h_flag[b] = 1;
-        atomicExch(A.h_any, 1);
-      }
-      A.h_acc[b] = acc;
-    }
-  } else {
-    float m = 0.f;
-    for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x)
-      m = fmaxf(m, __uint_as_float(atomicExch(&A.vmax_bits[b], 0u)));
-    red[threadIdx.x] = m;
-    __syncthreads();
-    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
-      if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
-      __syncthreads();
-    }
-    const float acc = horizon_acc(__ldcg(&A.h_acc[0]), red[0], A.dt_body[0]);
-    const bool rebuild = acc >= A.h_threshold;
-    if (rebuild)
-      for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) A.h_flag[b] = 1;
-    if (threadIdx.x == 0) {
-      A.h_acc[0] = rebuild ? 0.f : acc;
-      if (rebuild) atomicExch(A.h_any, 1);
-    }
-  }
+  horizon_account(A, red);
   if (threadIdx.x == 0) *A.h_done = 0u;
 }
 

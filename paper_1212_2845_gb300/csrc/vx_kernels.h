@@ -101,6 +101,11 @@ struct MultiArgs {
   unsigned* bar;               // barrier count and generation
   long long spins;             // wait budget of one barrier (units of 128 SM cycles)
   unsigned extra;              // CTAs the barrier waits for beyond the grid (fault injection; 0)
+  // collisions between the steps: after each step the horizon (or, with
+  // every_step, a forced rebuild) and, when a body is flagged, the rebuild
+  // phases on the same grid and barrier (coll.st is set per step)
+  int collide, every_step;
+  CollideArgs coll;
 };
 int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid);
 cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s);

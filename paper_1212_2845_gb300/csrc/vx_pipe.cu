@@ -7,8 +7,7 @@
 // with cp.async, and the descriptor and halo indices of the tile after it are
 // already on their way into registers.  Tile descriptors and halo index lists
 // live at fixed strides so that both arrive in one round trip.
-#include "vx_dev.cuh"
-#include "vx_kernels.h"
+#include "vx_collide.cuh"
 
 namespace vx {
 namespace {
@@ -369,6 +368,30 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) multi_pipe(StepArgs
     if (A.act_on && M.act_P > 0)
       A.act_w = (float)(6.283185307179586 * (double)(A.step % M.act_P) / (double)M.act_P);
     pipe_tiles<TMAX>(A, blockIdx.x, gridDim.x, A.n_tiles, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
+    if (M.collide) {
+      // every CTA's speeds and new state are in: horizon (or a forced
+      // rebuild), then the rebuild phases when a body is flagged
+      const unsigned G = gridDim.x + M.extra;
+      if (!grid_barrier(M.bar, G, M.spins, A0.status)) return;
+      if (blockIdx.x == 0) {
+        if (M.every_step) {
+          for (int b = threadIdx.x; b < A.n_bodies; b += blockDim.x) {
+            A.h_flag[b] = 1;
+            A.h_acc[b] = 0.f;
+            A.vmax_bits[b] = 0u;
+          }
+          if (threadIdx.x == 0) *A.h_any = 1;
+        } else {
+          horizon_account(A, reinterpret_cast<float*>(L.props));
+        }
+      }
+      if (!grid_barrier(M.bar, G, M.spins, A0.status)) return;
+      if (__ldcg(A.h_any)) {  // the same value for every CTA until the last phase clears it
+        CollideArgs C = M.coll;
+        C.st = A.st_out;
+        if (!rebuild_phases(C, G)) return;
+      }
+    }
     if (k + 1 < M.n_steps && !grid_barrier(M.bar, gridDim.x + M.extra, M.spins, A0.status)) return;
   }
 }

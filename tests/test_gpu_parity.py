@@ -487,6 +487,45 @@ def test_multistep_launch_bitwise_equals_per_step_launches(vx, which):
         assert np.array_equal(out[0][k].view(np.uint8), out[1][k].view(np.uint8)), k
 
 
+@pytest.mark.parametrize("which", ["clapper_horizon", "clapper_every_step", "ball_impact", "shared_world"])
+def test_multistep_launch_with_collisions_bitwise_equals_per_step_launches(vx, which):
+    """With collisions on, the cooperative multi-step launch keeps the horizon
+    and runs the candidate rebuilds between its steps on its own grid; states,
+    candidate sets and the rebuild count equal those of one launch per step
+    (followed by the separate rebuild launch)."""
+    every = False
+    if which.startswith("clapper"):
+        sc, steps = scenes.clapper(), 1500
+        every = which == "clapper_every_step"
+    elif which == "ball_impact":
+        sc, steps = scenes.hollow_ball(R=12, t=3), 900
+    else:
+        l = 1e-3
+        sc = scenes._base([(3, 3, 3), (3, 3, 3)], np.ones(54, np.uint8), l, [scenes.material(1e6)],
+                          collide=2, zeta_collision=0.0, zeta_bond=1.0)
+        sc["origin"] = scenes.f32([[0.0, 0.0, 0.0], [6 * l, 0.0, 0.0]])
+        steps = 2500
+    out = []
+    for multi in (0, 1):
+        sim = vx.Sim(sc, apply_scene=False)
+        sim.set_collision_scheme(False, every)
+        sim.apply(sc)
+        if which == "shared_world":
+            vel = np.zeros((sim.N, 3), np.float32)
+            vel[:27, 0], vel[27:, 0] = 0.2, -0.2
+            sim.write_state(vel=vel)
+        sim.set_multistep(multi)
+        sim.step(steps)
+        assert sim.status()[0] == 0
+        out.append((sim.read_state(), sim.collision_pairs(), sim.collision_stats()[0]))
+        sim.close()
+    (s0, p0, n0), (s1, p1, n1) = out
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(s0[k].view(np.uint8), s1[k].view(np.uint8)), k
+    assert np.array_equal(p0, p1)
+    assert n0 == n1 and n0 > 0
+
+
 def test_simulators_of_different_sizes_coexist(vx):
     """Kernel launch limits set for one simulator never break another one in
     the same process (every form, stepped in turn)."""
