@@ -110,6 +110,7 @@ struct vx_sim {
   // multi-step form (one cooperative launch for n steps)
   int multistep = 1;          // use it for vx_step(n > 1) in the pipelined form without collisions
   int multi_grid = 0;
+  int multi_co = 0;           // co-resident CTAs of the multi-step kernel
   unsigned* bar = nullptr;    // grid barrier words
   int64_t bar_spins = 1ll << 24;  // barrier wait budget in 128-cycle units: about one second
   int32_t bar_extra = 0;      // phantom CTAs (fault injection)
@@ -515,7 +516,7 @@ int ensure_pipe(vx_sim* s, const StepArgs& A) {
                               A.fext != nullptr, A.collide_on != 0, nm, nm <= kLutMaxMats);
   if (sm != s->pipe_smem) {
     if (prepare_pipe(s->tile_max, sm, &s->pipe_grid) != 0 || prepare_batched(s->tile_max, sm) != 0 ||
-        prepare_multi(s->tile_max, sm, (int)s->T.n_tiles(), &s->multi_grid) != 0)
+        prepare_multi(s->tile_max, sm, (int)s->T.n_tiles(), &s->multi_grid, &s->multi_co) != 0)
       return fail(VX_ERR_CUDA, "pipelined kernels need " + std::to_string(sm) + " bytes of shared memory");
     s->pipe_smem = sm;
   }
@@ -1219,7 +1220,11 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
       A.h_threshold = s->threshold;
       A.h_world = s->collide_on == 2 ? 1 : 0;
     }
-    if (launch_multi(A, M, s->tile_max, s->pipe_smem, s->multi_grid, st) == cudaSuccess) {
+    // with collisions, enough CTAs for one warp per searched voxel in a rebuild
+    // (CTAs beyond the tiles meet at the barriers and join the rebuilds)
+    int grid = s->multi_grid;
+    if (M.collide) grid = std::max(grid, std::min(s->multi_co, (int)((s->coll_S + 7) / 8)));
+    if (launch_multi(A, M, s->tile_max, s->pipe_smem, grid, st) == cudaSuccess) {
       s->cur ^= (int)(n & 1);
       s->step += n;
       return VX_OK;

@@ -107,7 +107,8 @@ int rebuild_grid_limit() {
 void launch_rebuild(const CollideArgs& C, cudaStream_t st) {
   if (C.S == 0) return;
   const int limit = rebuild_grid_limit();
-  const int want = (std::max(C.S, C.H) + kRebuildThreads - 1) / kRebuildThreads;
+  // one warp per searched voxel in the query, one thread per bucket in the scan
+  const int want = std::max((C.S + kRebuildWarps - 1) / kRebuildWarps, (C.H + kRebuildThreads - 1) / kRebuildThreads);
   int grid = std::min(std::min(want, limit), kRebuildMaxGrid);
   if (grid < 1) grid = 1;
   void* args[1] = {const_cast<CollideArgs*>(&C)};

@@ -64,6 +64,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
   return pre;
 }
 
+// Candidates of searched voxel s, found by one thread (27 neighbour cells in
+// a row): the query when there are many more searched voxels than warps.
 __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   int v = C.surf[s];
   int b = C.body ? C.body[v] : 0;
@@ -116,12 +118,86 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   if (overflow) atomicOr(C.status, kStatusCapacity);
 }
 
+// Candidates of searched voxel s, found by one warp: lane l < 27 scans the
+// hash bucket of neighbour cell l (dx, dy, dz = l mod 3, l / 3 mod 3, l / 9,
+// each minus 1), so a search costs one bucket's chain of loads instead of
+// 27 in a row.  The lanes' finds are gathered in the warp's shared buffer
+// (kCandCap ints), sorted ascending by canonical index and written out.
+constexpr int kLaneCap = 16;  // finds per neighbour cell (a cell holds about 8 voxels)
+
+__device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane, int* buf) {
+  const int v = C.surf[s];
+  const int b = C.body ? C.body[v] : 0;
+  if (!C.flag[b]) return;  // the same s for the whole warp
+  const int64_t x0 = C.xq[s], y0 = C.xq[(int64_t)C.S + s], z0 = C.xq[2 * (int64_t)C.S + s];
+  const int64_t cs = 2 * C.Q;
+  const int4 c0 = C.cell[s];
+  const uint32_t lp = C.lat[v];
+  const int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);
+  const int64_t r2max = cs * cs;  // (2 Q)^2
+  int mine[kLaneCap];
+  int n = 0;
+  bool overflow = false;
+  if (lane < 27) {
+    const int ncx = c0.x + lane % 3 - 1, ncy = c0.y + (lane / 3) % 3 - 1, ncz = c0.z + lane / 9 - 1;
+    const uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
+    const uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
+    for (uint32_t e = e0; e < e1; ++e) {
+      const int t = C.sorted[e];
+      if (t == s) continue;
+      const int4 c1 = C.cell[t];
+      if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
+      const int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
+      const int u = C.surf[t];
+      if (C.body && C.body[u] != b) {
+        if (!C.qorg) continue;  // bodies are separate worlds
+      } else {
+        const uint32_t lq = C.lat[u];
+        const int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
+        if (man <= 3) continue;
+      }
+      const int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
+      if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
+      if (n < kLaneCap) mine[n++] = u; else overflow = true;
+    }
+  }
+  // offsets of the lanes' finds in the buffer (prefix sum over the warp)
+  int inc = n;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  const int total = __shfl_sync(0xffffffffu, inc, 31);
+  const int off = inc - n;
+  for (int i = 0; i < n; ++i)
+    if (off + i < kCandCap) buf[off + i] = mine[i];
+  if (total > kCandCap) overflow = true;
+  __syncwarp();
+  const int m = total < kCandCap ? total : kCandCap;
+  if (lane == 0)
+    for (int i = 1; i < m; ++i) {  // insertion sort ascending (lists are short)
+      const int x = buf[i];
+      int k = i - 1;
+      while (k >= 0 && buf[k] > x) { buf[k + 1] = buf[k]; --k; }
+      buf[k + 1] = x;
+    }
+  __syncwarp();
+  int32_t* out = C.cand + (int64_t)s * kCandCap;
+  for (int i = lane; i < m; i += 32) out[i] = buf[i];
+  if (lane == 0) C.ccount[s] = m;
+  if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(C.status, kStatusCapacity);
+  __syncwarp();  // the buffer is reused for the warp's next voxel
+}
+
 // The rebuild phases, run by every CTA of a cooperative grid (any number of
-// CTAs up to kRebuildMaxGrid, blockDim a multiple of 32); G is the count the
-// grid barriers wait for.  Returns false if a barrier wait gave up.
+// CTAs up to kRebuildMaxGrid, blockDim a multiple of 32 up to 32 kRebuildWarps);
+// G is the count the grid barriers wait for.  Returns false if a barrier wait
+// gave up.
+constexpr int kRebuildWarps = 8;
 __device__ __forceinline__ bool rebuild_phases(const CollideArgs& C, unsigned G) {
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t offset;
+  __shared__ int qbuf[kRebuildWarps][kCandCap];  // query: one candidate buffer per warp
   const int tid = blockIdx.x * blockDim.x + threadIdx.x, nthr = gridDim.x * blockDim.x;
   // zero the bucket counters
   for (int i = tid; i < C.H; i += nthr) { C.hcount[i] = 0u; C.hcursor[i] = 0u; }
@@ -159,7 +235,19 @@ __device__ __forceinline__ bool rebuild_phases(const CollideArgs& C, unsigned G)
     C.sorted[C.hstart[h] + atomicAdd(&C.hcursor[h], 1u)] = s;
   }
   if (!grid_barrier(C.bar, G, C.spins, C.status)) return false;
-  for (int s = tid; s < C.S; s += nthr) query_one(C, s);
+  {
+    // one warp per searched voxel while that leaves at most 8 voxels to a
+    // warp (8 one-cell chains of dependent loads, against one 27-cell chain
+    // per thread); beyond, one thread per voxel.  Both give the same sorted
+    // lists.
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int nw = (int)(gridDim.x * (blockDim.x >> 5));
+    if (C.S <= 8 * nw) {
+      for (int q = (int)blockIdx.x * (int)(blockDim.x >> 5) + w; q < C.S; q += nw) query_warp(C, q, lane, qbuf[w]);
+    } else {
+      for (int q = tid; q < C.S; q += nthr) query_one(C, q);
+    }
+  }
   if (!grid_barrier(C.bar, G, C.spins, C.status)) return false;
   if (blockIdx.x == 0) {
     for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) C.flag[b] = 0;

@@ -107,7 +107,7 @@ struct MultiArgs {
   int collide, every_step;
   CollideArgs coll;
 };
-int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid);
+int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid, int* co_resident);
 cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);

@@ -474,7 +474,7 @@ void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t 
   else batched_pipe<256><<<grid, 256, smem, s>>>(A, B);
 }
 
-int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid) {
+int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid, int* co_resident) {
   int per_sm = 0, dev = 0, n_sm = 0;
   cudaError_t e;
   if (tile_max == 128) {
@@ -489,6 +489,7 @@ int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid) {
     return -1;
   const int co = per_sm * n_sm;
   *grid = n_tiles < co ? n_tiles : co;
+  *co_resident = co;
   return 0;
 }
 
