@@ -210,6 +210,19 @@ def run_reference(args, sc):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(x, device):
+    """The largest x over the ranks of the process group (x itself with one
+    rank): the job's time is its slowest replica's.  Ends with a barrier."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
 def time_steps(sim, stream, steps, warmup, flush=None):
     """Per-step CUDA-event times (s) of `steps` single-step launches."""
     import torch
@@ -491,12 +504,7 @@ def main():
         t_wall = time.perf_counter() - t_wall0
         torch.cuda.synchronize()
         clk.end_window()
-    t_steps = float(times.sum())
-    if ws > 1:
-        tt = torch.tensor([t_steps], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_steps = float(tt.item())
-        torch.distributed.barrier()
+    t_steps = max_over_ranks(float(times.sum()), "cuda")
     value = ws * sim.N * args.steps / t_steps
     avg = t_steps / args.steps
 
