@@ -518,8 +518,8 @@ def main():
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        sim.write_state_from(**pin, stream=stream, on_device=False)
-        sim.step_async(1, stream)              # the read below waits for it
+        sim.write_state_from(**pin, stream=stream, on_device=False, wait=False)
+        sim.step_async(1, stream)              # the read below waits for the upload and the step
         sim.read_state_into(**pin, stream=stream, on_device=False)
     t_e2e = time.perf_counter() - t0
     if sim.status(stream)[0] != 0:

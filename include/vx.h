@@ -254,6 +254,11 @@ VX_API int vx_reset(vx_sim* sim, const float v0[3]);
 VX_API int vx_read_state(vx_sim* sim, const vx_state_view* out, int32_t dst_on_device, void* stream);
 /* Overwrite the state from caller buffers (NULL fields unchanged). */
 VX_API int vx_write_state(vx_sim* sim, const vx_state_view* in, int32_t src_on_device, void* stream);
+/* Same, without waiting: the copies and the unpacking are enqueued on
+ * `stream` and the call returns at once; the caller keeps the source buffers
+ * unchanged (and alive) until that work is done (a later synchronising call
+ * on the stream, e.g. vx_read_state, or a stream synchronisation). */
+VX_API int vx_write_state_async(vx_sim* sim, const vx_state_view* in, int32_t src_on_device, void* stream);
 /* Step counter n (number of steps taken since the last reset). */
 VX_API int vx_get_step(vx_sim* sim, int64_t* step);
 VX_API int vx_set_step(vx_sim* sim, int64_t step);

@@ -1116,6 +1116,13 @@ int vx_read_state(vx_sim* s, const vx_state_view* out, int32_t dst_on_device, vo
 }
 
 int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, void* stream) {
+  int rc = vx_write_state_async(s, in, src_on_device, stream);
+  if (rc) return rc;
+  VX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return VX_OK;
+}
+
+int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_device, void* stream) {
   if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
@@ -1126,7 +1133,6 @@ int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, vo
     launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset, in->quat, in->vel, in->angvel,
                         in->flags, st);
     VX_CUDA(cudaGetLastError());
-    VX_CUDA(cudaStreamSynchronize(st));
     return VX_OK;
   }
   if ((rc = ensure_stage(s))) return rc;
@@ -1144,7 +1150,6 @@ int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, vo
                       in->quat ? quat : nullptr, in->vel ? vel : nullptr, in->angvel ? w : nullptr,
                       in->flags ? fl : nullptr, st);
   VX_CUDA(cudaGetLastError());
-  VX_CUDA(cudaStreamSynchronize(st));
   return VX_OK;
 }
 

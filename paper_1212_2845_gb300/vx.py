@@ -83,6 +83,7 @@ SIGNATURES = {
     "vx_reset": (C.c_int, [_P, _pf]),
     "vx_read_state": (C.c_int, [_P, C.POINTER(StateView), _i32, _P]),
     "vx_write_state": (C.c_int, [_P, C.POINTER(StateView), _i32, _P]),
+    "vx_write_state_async": (C.c_int, [_P, C.POINTER(StateView), _i32, _P]),
     "vx_get_step": (C.c_int, [_P, _pi64]),
     "vx_set_step": (C.c_int, [_P, _i64]),
     "vx_step": (C.c_int, [_P, _i64, _P]),
@@ -369,13 +370,16 @@ class Sim:
         _check(self._L.vx_read_state(self.h, C.byref(v), int(bool(on_device)), _stream_ptr(stream)))
 
     def write_state_from(self, offset=None, quat=None, vel=None, angvel=None, flags=None, stream=None,
-                         on_device=True):
+                         on_device=True, wait=True):
+        """Overwrite the state from caller buffers; wait=False returns once the
+        copies are enqueued (keep the buffers unchanged until the stream is done)."""
         def p(x):
             if x is None:
                 return None
             return x.data_ptr() if hasattr(x, "data_ptr") else x.ctypes.data
         v = StateView(p(offset), p(quat), p(vel), p(angvel), p(flags))
-        _check(self._L.vx_write_state(self.h, C.byref(v), int(bool(on_device)), _stream_ptr(stream)))
+        fn = self._L.vx_write_state if wait else self._L.vx_write_state_async
+        _check(fn(self.h, C.byref(v), int(bool(on_device)), _stream_ptr(stream)))
 
     def write_state(self, offset=None, quat=None, vel=None, angvel=None, flags=None, stream=None):
         arrs = [None if x is None else np.ascontiguousarray(x, dtype=np.float32) for x in (offset, quat, vel, angvel)]

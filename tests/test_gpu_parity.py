@@ -257,6 +257,16 @@ def test_state_roundtrip_and_reset(vx):
     assert not s["offset"].any() and not s["vel"].any()
     assert np.array_equal(s["quat"], np.tile([1, 0, 0, 0], (sim.N, 1)).astype(np.float32))
     assert sim.step_count == 0
+    # the asynchronous upload from pinned host buffers, then a read on the same stream
+    torch = pytest.importorskip("torch")
+    pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+           for k, a in (("offset", off), ("quat", q), ("vel", vel), ("angvel", w))}
+    stream = torch.cuda.Stream()
+    sim.write_state_from(**pin, stream=stream, on_device=False, wait=False)
+    out = {k: torch.empty_like(t).pin_memory() for k, t in pin.items()}
+    sim.read_state_into(**out, stream=stream, on_device=False)
+    for k in pin:
+        assert torch.equal(out[k], pin[k]), k
 
 
 def test_unstable_is_reported_not_trapped(vx):
