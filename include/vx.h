@@ -245,10 +245,17 @@ VX_API int vx_get_dt(vx_sim* sim, double* dt_per_body);
 VX_API int vx_set_dt(vx_sim* sim, const double* dt_per_body);
 
 /* ---- state -------------------------------------------------------------- */
-/* Rest state: zero offsets, identity orientations, velocity v0 (or zero if
- * NULL) for non-fixed voxels, zero angular velocity, static flags clear, step
- * counter 0, collision candidates rebuilt.  Synchronous. */
+/* Rest state: zero offsets, identity orientations, velocity v0 (if NULL,
+ * the one set by vx_set_initial_velocity, zero by default) for non-fixed
+ * voxels, zero angular velocity, static flags clear, step counter 0,
+ * collision candidates rebuilt.  Synchronous. */
 VX_API int vx_reset(vx_sim* sim, const float v0[3]);
+/* Initial velocity (App. B: the environment's initial velocity) [m/s]: sets
+ * the linear velocity of every non-fixed voxel to v now (positions,
+ * orientations and angular velocities unchanged) and makes v the velocity of
+ * later vx_reset(sim, NULL) calls.  v: 3 host floats; non-finite values or
+ * NULL return VX_ERR_ARG.  Synchronous. */
+VX_API int vx_set_initial_velocity(vx_sim* sim, const float v[3]);
 /* Copy the state to caller buffers (dst_on_device = 1: device pointers, else
  * host).  Synchronous with respect to work already queued on `stream`. */
 VX_API int vx_read_state(vx_sim* sim, const vx_state_view* out, int32_t dst_on_device, void* stream);

@@ -86,6 +86,7 @@ struct vx_sim {
   std::vector<float> mactA, mactT0, mactPh;
   bool act_any = false;    // some material has a non-zero temperature offset
   float dt_factor = 0.9f;
+  float v0[3] = {0.f, 0.f, 0.f};  // initial velocity of a reset without one
   std::vector<double> dt;
   std::vector<float> logE_h;
   std::vector<float> fext_h;   // canonical order, 3 per voxel
@@ -1071,14 +1072,27 @@ int vx_reset(vx_sim* s, const float v0[3]) {
   if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
-  launch_reset_state(cur_state(s), s->pitch, (int)s->L.N, s->flags, v0 ? v0[0] : 0.f, v0 ? v0[1] : 0.f,
-                     v0 ? v0[2] : 0.f, 0);
+  const float* v = v0 ? v0 : s->v0;
+  launch_reset_state(cur_state(s), s->pitch, (int)s->L.N, s->flags, v[0], v[1], v[2], 0);
   VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaMemset(s->status, 0, 16));
   VX_CUDA(cudaMemset(s->vmax, 0, 4 * s->L.n_bodies));
   if (s->cbar) VX_CUDA(cudaMemset(s->cbar, 0, 2 * sizeof(unsigned)));  // clean after a timed-out launch
   s->step = 0;
   if (s->collide_on && (rc = force_rebuild(s, 0))) return rc;
+  VX_CUDA(cudaDeviceSynchronize());
+  return VX_OK;
+}
+
+int vx_set_initial_velocity(vx_sim* s, const float v[3]) {
+  if (s) ++s->gen;  // invalidates a recorded rollout
+  int rc = check_sim(s);
+  if (rc) return rc;
+  if (!v || !std::isfinite(v[0]) || !std::isfinite(v[1]) || !std::isfinite(v[2]))
+    return fail(VX_ERR_ARG, "initial velocity must be three finite values");
+  for (int a = 0; a < 3; ++a) s->v0[a] = v[a];
+  launch_set_velocity(cur_state(s), s->pitch, (int)s->L.N, s->flags, v[0], v[1], v[2], 0);
+  VX_CUDA(cudaGetLastError());
   VX_CUDA(cudaDeviceSynchronize());
   return VX_OK;
 }

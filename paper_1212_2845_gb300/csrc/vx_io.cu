@@ -44,6 +44,17 @@ __global__ void reset_state(float* __restrict__ st, int64_t P, int N, uint8_t* _
   store_vox(st, P, v, s);
 }
 
+// Linear velocity of every non-fixed voxel set to (vx, vy, vz); the rest of
+// the state unchanged.
+__global__ void set_velocity(float* __restrict__ st, int64_t P, int N, const uint8_t* __restrict__ flags, float vx,
+                             float vy, float vz) {
+  int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= N || (flags[v] & 1u)) return;
+  VoxS s = load_vox(st, P, v);
+  s.v = v3(vx, vy, vz);
+  store_vox(st, P, v, s);
+}
+
 // Largest speed |v| over the voxels (the bits of a non-negative float order
 // like unsigned integers, so an atomic max is exact and order-independent).
 __global__ void max_speed(const float* __restrict__ st, int64_t P, int N, unsigned* __restrict__ out) {
@@ -70,6 +81,11 @@ void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, 
                          const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
                          cudaStream_t s) {
   unpack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, iperm, flags, off, quat, vel, angvel, fl);
+}
+
+void launch_set_velocity(float* st, int64_t pitch, int N, const uint8_t* flags, float vx, float vy, float vz,
+                         cudaStream_t s) {
+  set_velocity<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, flags, vx, vy, vz);
 }
 
 void launch_reset_state(float* st, int64_t pitch, int N, uint8_t* flags, float v0x, float v0y, float v0z,

@@ -170,5 +170,7 @@ void launch_max_speed(const float* st, int64_t pitch, int N, unsigned* out, cuda
 // rest state: zero offsets, identity quaternions, v0 for non-fixed voxels
 void launch_reset_state(float* st, int64_t pitch, int N, uint8_t* flags, float v0x, float v0y, float v0z,
                         cudaStream_t s);
+void launch_set_velocity(float* st, int64_t pitch, int N, const uint8_t* flags, float vx, float vy, float vz,
+                         cudaStream_t s);
 
 }  // namespace vx

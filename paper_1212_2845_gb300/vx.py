@@ -76,6 +76,7 @@ SIGNATURES = {
     "vx_set_damping": (C.c_int, [_P, _f32, _f32, _f32]),
     "vx_set_environment": (C.c_int, [_P, _f32, _i32, _i32]),
     "vx_set_actuation": (C.c_int, [_P, _f32, _i64, _f32]),
+    "vx_set_initial_velocity": (C.c_int, [_P, _pf]),
     "vx_set_material_actuation": (C.c_int, [_P, _pf, _pf, _pf]),
     "vx_set_dt_factor": (C.c_int, [_P, _f32]),
     "vx_get_dt": (C.c_int, [_P, _pd]),
@@ -338,6 +339,11 @@ class Sim:
         return out
 
     # -- state -------------------------------------------------------------
+    def set_initial_velocity(self, v):
+        """Linear velocity of every non-fixed voxel now, and of later resets without one."""
+        a = np.ascontiguousarray(v, dtype=np.float32).reshape(3)
+        _check(self._L.vx_set_initial_velocity(self.h, a.ctypes.data_as(_pf)))
+
     def reset(self, v0=None):
         v = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float32)
         _check(self._L.vx_reset(self.h, _ptr(v, C.c_float)))

@@ -269,6 +269,30 @@ def test_state_roundtrip_and_reset(vx):
         assert torch.equal(out[k], pin[k]), k
 
 
+def test_initial_velocity(vx):
+    """vx_set_initial_velocity moves every non-fixed voxel at v now and is the
+    velocity of a later reset without one; fixed voxels stay at rest."""
+    sc = scenes.random_blob((6, 5, 4), seed=3)
+    sc["fixed"] = (np.arange(scenes.n_occupied(sc)) % 5 == 0).astype(np.uint8)
+    sim = vx.Sim(sc)
+    sim.step(20)
+    before = sim.read_state()
+    v = np.array([0.01, -0.02, 0.03], np.float32)
+    sim.set_initial_velocity(v)
+    after = sim.read_state()
+    free = sc["fixed"] == 0
+    assert np.array_equal(after["vel"][free], np.tile(v, (free.sum(), 1)))
+    assert not after["vel"][~free].any()
+    for k in ("offset", "quat", "angvel"):
+        assert np.array_equal(after[k], before[k]), k
+    sim.reset()
+    s = sim.read_state()
+    assert np.array_equal(s["vel"][free], np.tile(v, (free.sum(), 1))) and not s["offset"].any()
+    with pytest.raises(vx.VxError):
+        sim.set_initial_velocity([np.nan, 0.0, 0.0])
+    sim.close()
+
+
 def test_unstable_is_reported_not_trapped(vx):
     sc = scenes.random_blob((4, 4, 4), seed=1)
     sc.update(zeta_bond=0.0)
