@@ -375,6 +375,26 @@ def collision_form(stream, steps=600):
     return out
 
 
+def rebuild_sizes(stream, reps=20):
+    """Forced candidate rebuilds (flag every body, rebuild, wait) on lattices
+    from the clapper to the R100 ball: the query runs one warp per searched
+    voxel while the grid has a warp for every 8 of them, else one thread."""
+    from paper_1212_2845_gb300 import vx
+    out = {}
+    for name, mk, all_v in (("clapper_surface", scenes.clapper, False), ("clapper_all_voxels", scenes.clapper, True),
+                            ("shell_R12_t3", lambda: scenes.hollow_ball(R=12, t=3), False),
+                            ("shell_R20_t4", lambda: scenes.hollow_ball(R=20, t=4), False),
+                            ("shell_R40_t4", lambda: scenes.hollow_ball(R=40, t=4), False),
+                            ("shell_R100_t8", lambda: scenes.hollow_ball(R=100, t=8), False)):
+        sim = vx.Sim(mk())
+        sim.set_collision_scheme(all_v, False)
+        sim.rebuild_collisions(stream)
+        t = _events_time(stream, lambda: [sim.rebuild_collisions(stream) for _ in range(reps)]) / reps
+        out[name] = {"searched_voxels": sim.N if all_v else sim.n_surface, "us_per_rebuild": 1e6 * t}
+        sim.close()
+    return out
+
+
 def collision_schemes(stream, steps=2000):
     """The paper's comparison of collision schemes on a synthetic clapper
     (880 voxels, arms closing and touching during the run): candidates among
@@ -479,7 +499,7 @@ def main():
     if args.only_collisions:
         st = torch.cuda.Stream()
         print(json.dumps({"ball": collision_form(st, steps=args.form_steps or 600),
-                          "schemes": collision_schemes(st)}))
+                          "schemes": collision_schemes(st), "rebuilds": rebuild_sizes(st)}))
         return
     if args.only_batched:
         peak, _ = load_peaks()
@@ -553,6 +573,7 @@ def main():
                          "batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
                          "collisions": collision_form(stream),
                          "collision_schemes": collision_schemes(stream),
+                         "collision_rebuilds": rebuild_sizes(stream),
                          "small_lattice": small_lattice(stream)}
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
