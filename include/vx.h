@@ -259,7 +259,10 @@ VX_API int vx_set_initial_velocity(vx_sim* sim, const float v[3]);
 /* Copy the state to caller buffers (dst_on_device = 1: device pointers, else
  * host).  Synchronous with respect to work already queued on `stream`. */
 VX_API int vx_read_state(vx_sim* sim, const vx_state_view* out, int32_t dst_on_device, void* stream);
-/* Overwrite the state from caller buffers (NULL fields unchanged). */
+/* Overwrite the state from caller buffers (NULL fields unchanged).  With
+ * collisions on, the candidate lists are rebuilt from the written state.
+ * Together with vx_read_state and the step counter (vx_get_step /
+ * vx_set_step) this is a bit-exact checkpoint and resume. */
 VX_API int vx_write_state(vx_sim* sim, const vx_state_view* in, int32_t src_on_device, void* stream);
 /* Same, without waiting: the copies and the unpacking are enqueued on
  * `stream` and the call returns at once; the caller keeps the source buffers

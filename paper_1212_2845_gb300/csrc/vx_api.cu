@@ -1,6 +1,7 @@
 // C ABI of the simulator (declared in include/vx.h): argument checking,
 // device memory ownership and the launch sequence of each step.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -21,6 +22,13 @@
 using namespace vx;
 
 namespace {
+
+// Named range on the profiler timeline (NVTX; free when no tool is attached).
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+};
+
 thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
@@ -764,6 +772,7 @@ int vx_region_mask(const vx_desc* desc, int32_t body, const float loc[3], const 
 }
 
 int vx_create(const vx_desc* desc, vx_sim** out) {
+  const Range range("vx_create");
   if (!out) return fail(VX_ERR_ARG, "out is NULL");
   *out = nullptr;
   vx_sim* s = new (std::nothrow) vx_sim();
@@ -1147,7 +1156,7 @@ int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_devi
     launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset, in->quat, in->vel, in->angvel,
                         in->flags, st);
     VX_CUDA(cudaGetLastError());
-    return VX_OK;
+    return s->collide_on ? force_rebuild(s, st) : VX_OK;
   }
   if ((rc = ensure_stage(s))) return rc;
   float* off = s->stage;
@@ -1164,7 +1173,8 @@ int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_devi
                       in->quat ? quat : nullptr, in->vel ? vel : nullptr, in->angvel ? w : nullptr,
                       in->flags ? fl : nullptr, st);
   VX_CUDA(cudaGetLastError());
-  return VX_OK;
+  // the candidate lists belong to the previous state: rebuild them from this one
+  return s->collide_on ? force_rebuild(s, st) : VX_OK;
 }
 
 int vx_get_step(vx_sim* s, int64_t* step) {
@@ -1181,6 +1191,7 @@ int vx_set_step(vx_sim* s, int64_t step) {
 }
 
 int vx_step_async(vx_sim* s, int64_t n, void* stream) {
+  const Range range("vx_step");
   if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
   if (rc) return rc;
@@ -1315,6 +1326,7 @@ int vx_step(vx_sim* s, int64_t n, void* stream) {
 }
 
 int vx_rebuild_collisions(vx_sim* s, void* stream) {
+  const Range range("vx_rebuild_collisions");
   int rc = check_sim(s);
   if (rc) return rc;
   if ((rc = force_rebuild(s, (cudaStream_t)stream))) return rc;
@@ -1363,6 +1375,7 @@ int vx_collision_stats(vx_sim* s, int64_t* n_rebuilds, double* accumulator) {
 }
 
 int vx_rollout_forward(vx_sim* s, int64_t n, int32_t K, float* loss_body, void* stream) {
+  const Range range("vx_rollout_forward");
   int rc = check_sim(s);
   if (rc) return rc;
   if (n < 1 || K < 1) return fail(VX_ERR_ARG, "n_steps and checkpoint_every must be >= 1");
@@ -1403,6 +1416,7 @@ int vx_rollout_forward(vx_sim* s, int64_t n, int32_t K, float* loss_body, void* 
 }
 
 int vx_rollout_backward(vx_sim* s, const float* w_body, float* grad_logE, float* grad_phase, void* stream) {
+  const Range range("vx_rollout_backward");
   int rc = check_sim(s);
   if (rc) return rc;
   if (s->ro_steps == 0 || s->ro_gen != s->gen)
