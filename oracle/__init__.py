@@ -14,7 +14,10 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "voxel_oracle.cpp")
-_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+# VX_HOST_SANITIZE=1: built with AddressSanitizer and UndefinedBehaviorSanitizer
+# into a separate file (load the runtimes with LD_PRELOAD)
+_SANITIZE = os.environ.get("VX_HOST_SANITIZE") == "1"
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle_san.so" if _SANITIZE else "liboracle.so")
 _lib = None
 
 _P = C.c_void_p
@@ -28,7 +31,8 @@ def build(force: bool = False) -> str:
     os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
-        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-o", tmp, _SRC])
+        san = ["-g", "-fsanitize=address,undefined", "-fno-omit-frame-pointer"] if _SANITIZE else []
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fPIC", "-shared", *san, "-o", tmp, _SRC])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 

@@ -13,7 +13,11 @@ import subprocess
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 SRC = os.path.join(HERE, "csrc")
-OUT = os.path.join(HERE, "_build")
+# VX_HOST_SANITIZE=1: host code built with AddressSanitizer and
+# UndefinedBehaviorSanitizer into a separate folder (load the runtimes with
+# LD_PRELOAD); device code is unchanged
+SANITIZE = os.environ.get("VX_HOST_SANITIZE") == "1"
+OUT = os.path.join(HERE, "_build_san" if SANITIZE else "_build")
 LIB = os.path.join(OUT, "libvx.so")
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -21,6 +25,8 @@ SOURCES = ["vx_host.cpp", "vx_api.cu", "vx_step.cu", "vx_collide.cu", "vx_io.cu"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          f"-I{INCLUDE}", f"-I{SRC}"]
+SAN_FLAGS = (["-Xcompiler", "-fsanitize=address", "-Xcompiler", "-fsanitize=undefined", "-Xcompiler", "-fno-omit-frame-pointer", "-g"]
+             if SANITIZE else [])  # one sanitizer per -Xcompiler: nvcc splits its argument on commas
 
 
 def nvcc() -> str:
@@ -50,7 +56,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [exe, *ARCH, *FLAGS, "-c", os.path.join(SRC, src), "-o", obj]
+        cmd = [exe, *ARCH, *FLAGS, *SAN_FLAGS, "-c", os.path.join(SRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -65,7 +71,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             if log:
                 print(log)
     tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [exe, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results]]
+    cmd = [exe, *ARCH, *SAN_FLAGS, "-shared", "-o", tmp, *[o for o, _ in results]]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")

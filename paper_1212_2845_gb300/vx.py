@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libvx.so")
+LIB_PATH = os.path.join(HERE, "_build_san" if os.environ.get("VX_HOST_SANITIZE") == "1" else "_build", "libvx.so")
 
 VX_OK = 0
 ERRORS = {-1: "VX_ERR_ARG", -2: "VX_ERR_CUDA", -3: "VX_ERR_OOM", -4: "VX_ERR_UNSTABLE",
