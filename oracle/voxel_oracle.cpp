@@ -27,6 +27,12 @@
 //   collision candidates (Sec 2.2.2)                   pinned: brute-force sets
 //   voxel-voxel contact force law                      parity unpinned (paper silent)
 //   volumetric actuation (Sec 2.3)                     pinned: free expansion
+//   several temperature signals (Sec 2.3)              pinned: two-material rest length,
+//                                                      solo runs of one-material bodies
+//   bodies in one world (Sec 2.2.2)                    pinned: antisymmetric cross-body
+//                                                      pairs (momentum), bounce
+//   collision schemes (all/surface, every/horizon)     pinned: identical trajectories
+//   assembled stiffness (modal check)                  pinned: beam-theory frequencies
 #include <algorithm>
 #include <array>
 #include <cmath>
