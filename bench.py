@@ -267,6 +267,7 @@ def large_lattice(stream, peak, steps=200, warmup=5, R=200):
     b_alg = 108  # state r/w 104, flags 2, material 1, bond mask 1
     out = {"workload": f"hollow_shell_R{R}_t8 (plain step, fused kernel, no self-collision)", "voxels": sim.N,
            "bonds": sim.n_bonds, "value": sim.N / avg, "unit": METRIC, "ms_per_step": avg * 1e3,
+           "bond_steps_per_s": sim.n_bonds / avg,
            "l2": "inputs larger than L2",
            "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg,
@@ -312,8 +313,10 @@ def batched_form(stream, peak, n_bodies=4096, steps=200, warmup=5):
     out = {"workload": f"population_{n_bodies} (edges U{{4..24}}, seed 4)", "voxels": N, "bonds": sim.n_bonds,
            "steps": steps, "l2": "inputs larger than L2", "bytes_per_voxel_step": b_alg,
            "per_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
+                        "bond_steps_per_s": sim.n_bonds * steps / t_plain,
                         "frac": b_alg * N * steps / t_plain / 1e9 / peak, "kernel": "fused_pipe<256>"},
            "batched": {"value": N * steps / t_graph, "unit": METRIC, "ms_per_step": 1e3 * t_graph / steps,
+                       "bond_steps_per_s": sim.n_bonds * steps / t_graph,
                        "frac": b_alg * N * steps / t_graph / 1e9 / peak, "kernel": f"batched_pipe<{sim.tiling()['tile_max']}>",
                        "launch": "one captured CUDA graph replay", "group_voxels": gv if gv else 4096},
            "autotune": {"tile_max": tm, "group_voxels": gv, "sample_voxel_steps_per_s": rate, "sample_steps": 20}}
@@ -345,9 +348,11 @@ def adjoint_form(stream, peak, n_bodies=1024, steps=2000, K=100):
     out = {"workload": f"design_population_{n_bodies}x12^3 (log E, phase per voxel, seed 5)", "voxels": N,
            "bonds": sim.n_bonds, "steps": steps, "checkpoint_every": K, "l2": "inputs larger than L2",
            "plain_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
+                          "bond_steps_per_s": sim.n_bonds * steps / t_plain,
                           "frac": b_fwd * N * steps / t_plain / 1e9 / peak},
            "rollout_forward": {"value": N * steps / t_fwd, "unit": METRIC, "s": t_fwd},
            "backward": {"value": N * steps / t_bwd, "unit": METRIC, "s": t_bwd,
+                        "bond_steps_per_s": sim.n_bonds * steps / t_bwd,
                         "bytes_per_voxel_step": b_bwd, "frac": b_bwd * N * steps / t_bwd / 1e9 / peak,
                         "kernels": "fused_pipe<256> (recompute) + finish_adj + adj_tile<256>"},
            "gradient": {"value": N * steps / (t_fwd + t_bwd), "unit": METRIC,
@@ -376,6 +381,7 @@ def collision_form(stream, steps=600):
     t_reb = _events_time(stream, lambda: sim.rebuild_collisions(stream))
     out = {"workload": "hollow_ball_R100_t8 drop (floor + self-collision)", "voxels": N, "bonds": sim.n_bonds,
            "surface_voxels": sim.n_surface, "steps": steps, "value": N * steps / t_run, "unit": METRIC,
+           "bond_steps_per_s": sim.n_bonds * steps / t_run,
            "us_per_step": 1e6 * t_run / steps, "rebuilds_in_run": n1 - n0,
            "us_per_forced_rebuild": 1e6 * t_reb, "candidate_pairs_at_end": pairs,
            "bytes_per_voxel_step": 108, "l2": "inputs larger than L2"}
