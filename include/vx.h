@@ -295,7 +295,11 @@ VX_API int vx_relax(vx_sim* sim, int64_t max_steps, double v_tol, int32_t check_
                     double* max_speed, int32_t* converged, void* stream);
 
 /* ---- collisions (Sec 2.2.2) ---------------------------------------------- */
-/* Rebuild the surface-voxel candidate list from the current positions now. */
+/* Rebuild the surface-voxel candidate list from the current positions now.
+ * Synchronous.  VX_ERR_CAPACITY when a voxel has more than 48 candidates;
+ * VX_ERR_TIMEOUT when a grid barrier of the rebuild gave up waiting (the
+ * candidate lists are then unspecified until the next vx_reset or
+ * vx_write_state). */
 VX_API int vx_rebuild_collisions(vx_sim* sim, void* stream);
 /* Collision scheme (the paper compares these, Sec 3 "Speedup of self
  * collision schemes"): all_voxels = 1 searches every voxel instead of the
@@ -397,8 +401,11 @@ VX_API int vx_rollout_backward(vx_sim* sim, const float* w_body, float* grad_log
  * Manhattan distance > 3, quantised centre distance below 2 voxel_size.
  *
  * Limits: n_surface <= VX_STATIC_MAX_SURFACE, n_bodies <= VX_STATIC_MAX_BODIES
- * (larger inputs return VX_ERR_ARG); more than 48 candidates for a voxel
- * returns VX_ERR_CAPACITY.  Scratch comes from one fixed device array of
+ * (larger inputs return VX_ERR_ARG); a body id outside [0, n_bodies) (read on
+ * the device before the search) returns VX_ERR_ARG naming the first such
+ * voxel; more than 48 candidates for a voxel returns VX_ERR_CAPACITY; a grid
+ * barrier of the search that waits longer than about a second returns
+ * VX_ERR_TIMEOUT.  On any error the outputs are unspecified.  Scratch comes from one fixed device array of
  * about 5 MiB that every GPU loading the library holds until exit.  The first
  * call on a device (with that device current) looks up the array's address;
  * make it before any stream capture.  Calls share the array: calls whose GPU

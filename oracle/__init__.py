@@ -77,6 +77,7 @@ def lib():
             "orc_linear_static": (C.c_int, [_P, _D, _D]),
             "orc_stiffness": (None, [_P, _D, _D]),
             "orc_set_collision_scheme": (None, [_P, C.c_int, C.c_int]),
+            "orc_set_brute_search": (None, [_P, C.c_int]),
             "orc_set_material_actuation": (None, [_P, _D, _D, _D]),
         }
         for name, (res, args) in sig.items():
@@ -165,6 +166,11 @@ class Oracle:
         voxels (not only surface voxels); rebuild every step (not on the
         horizon trigger)."""
         self._L.orc_set_collision_scheme(self.h, int(bool(all_voxels)), int(bool(every_step)))
+
+    def set_brute_search(self, on=True):
+        """Search candidate pairs by testing every pair of searched voxels
+        (the definition) instead of the x-sorted sweep; both give one set."""
+        self._L.orc_set_brute_search(self.h, int(bool(on)))
 
     def set_fixed(self, mask):
         m = np.ascontiguousarray(mask, dtype=np.uint8)

@@ -24,7 +24,8 @@
 //                                                      nothing: checks stability + value)
 //   bond damping (Sec 2.1.5)                           pinned: rigid motion undamped
 //   gravity/floor/friction (Sec 2.2.1)                 pinned: friction threshold/decel.
-//   collision candidates (Sec 2.2.2)                   pinned: brute-force sets
+//   collision candidates (Sec 2.2.2)                   pinned: brute-force sets; the
+//                                                      x-sorted sweep equals brute force
 //   voxel-voxel contact force law                      parity unpinned (paper silent)
 //   volumetric actuation (Sec 2.3)                     pinned: free expansion
 //   several temperature signals (Sec 2.3)              pinned: two-material rest length,
@@ -259,6 +260,8 @@ struct Params {
   // collision scheme (the paper's comparison): candidates among all voxels
   // instead of surface voxels; rebuild every step instead of on the horizon
   int cand_all = 0, cand_every = 0;
+  // test every pair of searched voxels instead of the sorted sweep (same set)
+  int brute_search = 0;
   double act_A = 0.0, act_T0 = 0.0;
   long act_P = 0;
   // several temperature signals (Sec 2.3): per material amplitude, offset and
@@ -467,19 +470,52 @@ template <class R> static std::vector<std::array<int64_t, 3>> quantise_positions
   return xq;
 }
 
-// Shared world: every body's candidates at once (pairs may cross bodies).
-template <class R> static void rebuild_world(Sim<R>& S) {
-  const Topo& T = S.T;
-  auto xq = quantise_positions(S);
-  for (int i = 0; i < T.N; ++i) S.partners[i].clear();
-  for (int i = 0; i < T.N; ++i) {
-    if (!S.prm.cand_all && !T.surface[i]) continue;
-    for (int j = i + 1; j < T.N; ++j) {
-      if (!S.prm.cand_all && !T.surface[j]) continue;
-      if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
+// The candidate pairs among the searched voxels `list` (Sec 2.2.2), written
+// into the partner lists of those voxels (cleared first, sorted ascending).
+// Brute force tests every pair.  The default search visits the voxels in
+// order of their quantised x coordinate and tests, for each, only the voxels
+// after it whose x differs by less than 2 Q: a pair with |dx| >= 2 Q has
+// dx^2 >= (2 Q)^2 and fails the strict distance test, so both searches find
+// the same set (checked against each other by the tests).
+template <class R> static void search_pairs(Sim<R>& S, const std::vector<int>& list,
+                                            const std::vector<std::array<int64_t, 3>>& xq) {
+  for (int i : list) S.partners[i].clear();
+  const size_t n = list.size();
+  if (S.prm.brute_search) {
+    for (size_t a = 0; a < n; ++a)
+      for (size_t b = a + 1; b < n; ++b) {
+        int i = list[a], j = list[b];
+        if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
+      }
+  } else {
+    std::vector<int> ord(list);
+    std::sort(ord.begin(), ord.end(), [&](int u, int v) { return xq[u][0] < xq[v][0] || (xq[u][0] == xq[v][0] && u < v); });
+    const int64_t two = 2 * S.qQ;
+    for (size_t a = 0; a < n; ++a) {
+      int i = ord[a];
+      for (size_t b = a + 1; b < n && xq[ord[b]][0] - xq[i][0] < two; ++b) {
+        int j = ord[b];
+        if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
+      }
     }
   }
-  for (int i = 0; i < T.N; ++i) std::sort(S.partners[i].begin(), S.partners[i].end());
+  for (int i : list) std::sort(S.partners[i].begin(), S.partners[i].end());
+}
+
+// Searched voxels of the voxel range [lo, hi): the surface voxels, or every
+// voxel in the "all voxels" scheme.
+template <class R> static std::vector<int> searched(const Sim<R>& S, int lo, int hi) {
+  std::vector<int> list;
+  for (int i = lo; i < hi; ++i)
+    if (S.prm.cand_all || S.T.surface[i]) list.push_back(i);
+  return list;
+}
+
+// Shared world: every body's candidates at once (pairs may cross bodies).
+template <class R> static void rebuild_world(Sim<R>& S) {
+  auto xq = quantise_positions(S);
+  for (int i = 0; i < S.T.N; ++i) S.partners[i].clear();
+  search_pairs(S, searched(S, 0, S.T.N), xq);
   S.n_rebuilds++;
 }
 
@@ -490,14 +526,7 @@ template <class R> static void rebuild_candidates(Sim<R>& S, int body) {
   auto xq = quantise_positions(S);
   int lo = T.body_first[body], hi = T.body_first[body + 1];
   for (int i = lo; i < hi; ++i) S.partners[i].clear();
-  for (int i = lo; i < hi; ++i) {
-    if (!S.prm.cand_all && !T.surface[i]) continue;
-    for (int j = i + 1; j < hi; ++j) {
-      if (!S.prm.cand_all && !T.surface[j]) continue;
-      if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
-    }
-  }
-  for (int i = lo; i < hi; ++i) std::sort(S.partners[i].begin(), S.partners[i].end());
+  search_pairs(S, searched(S, lo, hi), xq);
   S.n_rebuilds++;
 }
 
@@ -751,6 +780,8 @@ void orc_set_collision_scheme(orc_sim* o, int all_voxels, int every_step) {
   o->S.prm.cand_all = all_voxels ? 1 : 0;
   o->S.prm.cand_every = every_step ? 1 : 0;
 }
+
+void orc_set_brute_search(orc_sim* o, int on) { o->S.prm.brute_search = on ? 1 : 0; }
 
 void orc_set_voxel_params(orc_sim* o, const double* logE, const double* phase) {
   Sim<double>& S = o->S;

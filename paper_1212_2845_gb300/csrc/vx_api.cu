@@ -75,6 +75,14 @@ template <class T> void dfree(T*& p) {
 
 int vx::set_error(int code, const std::string& msg) { return fail(code, msg); }
 
+int vx::status_code(int bits) {
+  if (bits & kStatusUnstable) return VX_ERR_UNSTABLE;
+  if (bits & kStatusTimeout) return VX_ERR_TIMEOUT;
+  if (bits & kStatusCapacity) return VX_ERR_CAPACITY;
+  if (bits & kStatusArg) return VX_ERR_ARG;
+  return VX_OK;
+}
+
 struct vx_sim {
   Lattice L;
   Tiling T;
@@ -298,6 +306,7 @@ CollideArgs collide_args(vx_sim* s) {
   C.status = s->status;
   C.bar = s->cbar;
   C.spins = s->bar_spins;
+  C.extra = (unsigned)s->bar_extra;
   C.qorg = s->collide_on == 2 ? s->qorg : nullptr;
   return C;
 }
@@ -1299,10 +1308,7 @@ int vx_get_status(vx_sim* s, void* stream, int32_t* status, int64_t* bad_step, i
   int h[4] = {0, -1, 0, 0};
   VX_CUDA(cudaMemcpyAsync(h, s->status, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   VX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  int code = VX_OK;
-  if (h[0] & kStatusUnstable) code = VX_ERR_UNSTABLE;
-  else if (h[0] & kStatusTimeout) code = VX_ERR_TIMEOUT;
-  else if (h[0] & kStatusCapacity) code = VX_ERR_CAPACITY;
+  const int code = status_code(h[0]);
   long long bs;
   std::memcpy(&bs, &h[2], 8);
   if (status) *status = code;
@@ -1330,7 +1336,12 @@ int vx_rebuild_collisions(vx_sim* s, void* stream) {
   int rc = check_sim(s);
   if (rc) return rc;
   if ((rc = force_rebuild(s, (cudaStream_t)stream))) return rc;
+  int h[4] = {0, 0, 0, 0};
+  VX_CUDA(cudaMemcpyAsync(h, s->status, 16, cudaMemcpyDeviceToHost, (cudaStream_t)stream));
   VX_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  if (h[0] & kStatusTimeout) return fail(VX_ERR_TIMEOUT, "a grid barrier of the candidate rebuild gave up waiting");
+  if (h[0] & kStatusCapacity)
+    return fail(VX_ERR_CAPACITY, "collision candidate list overflow (more than " + std::to_string(kCandCap) + " per voxel)");
   return VX_OK;
 }
 

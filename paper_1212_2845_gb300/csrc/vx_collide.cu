@@ -78,7 +78,7 @@ constexpr int kRebuildThreads = 256;
 // launch ends with the timeout status bit set).
 __global__ void __launch_bounds__(kRebuildThreads) rebuild_all(CollideArgs C) {
   if (*C.any == 0) return;  // the same value for every CTA: set by an earlier launch
-  rebuild_phases(C, gridDim.x);
+  rebuild_phases(C, gridDim.x + C.extra);
 }
 
 // Raise every body's rebuild flag (forced rebuild).

@@ -40,6 +40,7 @@ constexpr int kCandCap = 48;        // collision candidates per surface voxel
 constexpr int kStatusUnstable = 1;  // status word bits
 constexpr int kStatusCapacity = 2;
 constexpr int kStatusTimeout = 4;   // a bounded device wait gave up
+constexpr int kStatusArg = 8;       // an input value checked on the device was out of range
 
 struct StepArgs {
   int N;

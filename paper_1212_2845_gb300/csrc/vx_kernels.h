@@ -56,7 +56,12 @@ struct CollideArgs {
   const int64_t* qorg;    // shared world: quantised body origins (3 per body), else nullptr
   unsigned* bar;          // grid barrier words of the rebuild launch (zero at setup)
   long long spins;        // barrier wait budget (units of 128 SM cycles)
+  unsigned extra = 0;     // CTAs the rebuild launch's barriers wait for beyond the grid (fault injection; 0)
 };
+
+// Error code of a device status word (the first set bit in the order
+// unstable, timeout, capacity, argument), VX_OK when none is set.
+int status_code(int bits);
 // the rebuild launch uses at most this many CTAs (bsum holds one entry per CTA)
 constexpr int kRebuildMaxGrid = 1024;
 

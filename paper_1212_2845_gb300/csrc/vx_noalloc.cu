@@ -75,9 +75,19 @@ int scratch_address(unsigned char** out) {
   return VX_OK;
 }
 
-__global__ void iota_kernel(int32_t* a, int n) {
+// Identity surface list; body ids outside [0, n_bodies) set the argument
+// status bit and record the first offending input index.
+__global__ void prepare_kernel(int32_t* a, int n, const int32_t* body, int n_bodies, int* status) {
   int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) a[i] = i;
+  if (i >= n) return;
+  a[i] = i;
+  if (body) {
+    const int b = body[i];
+    if (b < 0 || b >= n_bodies) {
+      atomicOr(status, kStatusArg);
+      atomicMin(status + 1, i);
+    }
+  }
 }
 
 }  // namespace
@@ -138,17 +148,29 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.bar = reinterpret_cast<unsigned*>(base + kOffMisc + 128);
   C.qorg = nullptr;
   C.spins = 1ll << 24;
+  // status words: bits, then the first out-of-range body index (starts at
+  // 0x7F7F7F7F, above any input index)
   cudaError_t e = cudaMemsetAsync(C.status, 0, 16, st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(C.status + 1, 0x7F, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
-  iota_kernel<<<(n_surface + 255) / 256, 256, 0, st>>>(const_cast<int32_t*>(C.surf), n_surface);
+  prepare_kernel<<<(n_surface + 255) / 256, 256, 0, st>>>(const_cast<int32_t*>(C.surf), n_surface, C.body,
+                                                          n_bodies, C.status);
+  int status[4] = {0, 0, 0, 0};
+  // the body ids are checked before the rebuild indexes per-body scratch with them
+  if (C.body && ((e = cudaGetLastError()) != cudaSuccess ||
+                 (e = cudaMemcpyAsync(status, C.status, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
+                 (e = cudaStreamSynchronize(st)) != cudaSuccess))
+    return fail(VX_ERR_CUDA, std::string("collision candidates: ") + cudaGetErrorString(e));
+  if (status[0] & kStatusArg)
+    return fail(VX_ERR_ARG, "body id out of [0, n_bodies) at surface voxel " + std::to_string(status[1]));
   launch_flag_all(C, st);
   launch_rebuild(C, st);
-  int status[4] = {0, 0, 0, 0};
   if ((e = cudaGetLastError()) != cudaSuccess ||
       (e = cudaMemcpyAsync(status, C.status, 16, cudaMemcpyDeviceToHost, st)) != cudaSuccess ||
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return fail(VX_ERR_CUDA, std::string("collision candidates: ") + cudaGetErrorString(e));
+  if (status[0] & kStatusTimeout) return fail(VX_ERR_TIMEOUT, "a grid barrier of the candidate search gave up waiting");
   if (status[0] & kStatusCapacity)
     return fail(VX_ERR_CAPACITY, "more than " + std::to_string(kCandCap) + " candidates for a surface voxel");
   return VX_OK;

@@ -39,6 +39,24 @@ def test_barrier_wait_runs_out_and_reports_timeout(vx):
     sim.close()
 
 
+def test_rebuild_barrier_wait_runs_out_and_reports_timeout(vx):
+    """A forced candidate rebuild whose grid barriers wait for a CTA that
+    does not exist gives up after the small budget and returns
+    VX_ERR_TIMEOUT; after a reset with normal limits it rebuilds again."""
+    sc = scenes.hollow_ball(R=12, t=3)
+    sim = vx.Sim(sc)
+    n_pairs = len(sim.collision_pairs())
+    sim.set_barrier_limits(max_spins=2000, phantom_ctas=1)
+    with pytest.raises(vx.VxError) as e:
+        sim.rebuild_collisions()
+    assert e.value.code == -5
+    sim.set_barrier_limits(0, 0)
+    sim.reset()
+    sim.rebuild_collisions()
+    assert len(sim.collision_pairs()) == n_pairs
+    sim.close()
+
+
 def test_nan_in_the_input_state_is_reported_as_unstable(vx):
     sc = scenes.random_blob((5, 4, 3), seed=4)
     sim = vx.Sim(sc)
