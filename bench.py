@@ -1,18 +1,24 @@
-"""Benchmark of one explicit lattice step on the heterogeneous actuated block
-(64 x 64 x 32 sites, 10 % empty, soft/stiff mix, sinusoidal actuation, floor
-contact with friction, gravity; seed 2).
+"""Benchmark of one explicit lattice step on the large hollow ball drop
+(spherical shell of outer radius 100 voxels and thickness 8: 926,584 voxels,
+E 0.5 MPa, rho 1100, nu 0.45, dropped at 2 m/s from 5 voxels above the floor,
+floor contact and surface-voxel self-collision on, anchor-offset FP32 state).
 
-One bench "step" is one simulation step of the whole lattice: one launch of
-the fused step kernel (bonds, gather, contacts, integration).  The state fits
-in L2, so the timed loop writes a 256 MB buffer between steps (L2 flush) and
-times every step with CUDA events on the simulator's stream; `value` is
-voxel-steps per second over the K timed steps.  The line also carries the same
-measurement on a lattice larger than L2 (hollow shell R 200, t 8), where HBM
-bandwidth bounds the step.
+One bench "step" is one simulation step of the whole lattice: the fused step
+kernel (bonds, gather, voxel contacts, floor, integration, collision horizon)
+and the candidate-rebuild launch (which rebuilds when the horizon says so and
+otherwise returns at once).  The drop is first advanced untimed to step 350,
+just before the impact (about step 370), so that the warm-up and timed steps
+cover the impact, the contacts and the rebuilds.  The state is close to the
+L2 size, so the timed loop writes a 256 MB buffer between steps (L2 flush)
+and times every step with CUDA events on the simulator's stream; `value` is
+voxel-steps per second over the K timed steps.  The line also carries the
+same kind of measurement on the heterogeneous actuated block and on a
+lattice larger than L2 (hollow shell R 200, t 8), and the step forms.
 
-Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on the
-same workload instead.  Under torchrun every rank runs an independent replica
-(the plain step of one lattice is not sharded across GPUs).
+Prints one JSON line.  `--impl reference` times the FP64 CPU oracle on a
+bounded sample of the same workload instead.  Under torchrun every rank runs
+an independent replica (the plain step of one lattice is not sharded across
+GPUs).
 """
 from __future__ import annotations
 
@@ -34,9 +40,10 @@ sys.path.insert(0, ROOT)
 from paper_1212_2845_gb300 import scenes  # noqa: E402
 
 METRIC = "voxel-steps/s"
-WORKLOAD = "hetero_block_64x64x32 (plain step, fused pipelined kernel)"
-B_ALG = 112  # algorithmic bytes per voxel-step for this workload (state r/w 104, flags 2, material 1,
-             # bond mask 1, phase 4); bond results are not algorithmic traffic
+WORKLOAD = "hollow_ball_R100_t8 drop (floor + self-collision, anchor-offset FP32 state)"
+B_ALG = 108  # algorithmic bytes per voxel-step for this workload (state r/w 104, flags 2, material 1,
+             # bond mask 1); bond results and candidate lists are not algorithmic traffic
+PRE_STEPS = 350  # untimed set-up: the drop advanced to just before the impact (about step 370)
 
 
 KERNEL_SOURCES = ("paper_1212_2845_gb300/csrc/vx_pipe.cu", "paper_1212_2845_gb300/csrc/vx_dev.cuh")
@@ -151,28 +158,28 @@ def host_cpu():
     return {"model": model, "nproc": os.cpu_count()}
 
 
-def cpu_baseline(sc, seconds=12.0):
-    """The FP64 oracle (single thread) on a bounded sample of the same workload."""
+def cpu_baseline(sc, steps=20):
+    """The FP64 oracle (single thread) on a bounded sample of the same
+    workload: the first `steps` steps of the full ball drop from rest."""
     from oracle import Oracle
     o = Oracle(sc)
-    n = 0
     t0 = time.perf_counter()
-    while time.perf_counter() - t0 < seconds:
-        o.step(5)
-        n += 5
+    o.step(steps)
     t = time.perf_counter() - t0
-    return {"value": o.N * n / t, "unit": METRIC, "cores": 1, "kind": "oracle",
-            "sample": f"{WORKLOAD}, first {n} steps from rest, FP64, 1 thread, {t:.1f} s", "host": host_cpu()}
+    return {"value": o.N * steps / t, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{WORKLOAD}: the first {steps} steps from rest of the full {o.N}-voxel ball, FP64, "
+                      f"1 thread, {t:.1f} s (creation and the initial candidate search not timed)",
+            "host": host_cpu()}
 
 
 def oracle_per_config(seconds=4.0):
     """The oracle (single thread) on a bounded sample of each other
-    configuration: the cantilever, a scaled ball drop, a 64-body subset of the
-    population and one design body."""
+    configuration: the cantilever, the heterogeneous block, a 64-body subset
+    of the population and one design body."""
     from oracle import Oracle
     out = {}
     for name, sc in (("cantilever_10x10x10", scenes.cantilever()),
-                     ("hollow_ball_R20_t4", scenes.hollow_ball(R=20, t=4)),
+                     ("hetero_block_64x64x32", scenes.hetero_block()),
                      ("population_64", scenes.population(n_bodies=64)),
                      ("design_population_1x12^3", scenes.design_population(n_bodies=1))):
         o = Oracle(sc)
@@ -187,18 +194,19 @@ def oracle_per_config(seconds=4.0):
 
 
 # Each step of the reference arm: one oracle step of a bounded sample of the
-# workload, a 16 x 16 x 8 block built by the same recipe (material mix,
-# phases, actuation, floor), so that the requested steps end within seconds
-# to a few minutes at the oracle's rate (which does not depend on the size).
-REF_SAMPLE_DIMS = (16, 16, 8)
+# workload, a hollow ball of outer radius 8 and thickness 4 built by the same
+# recipe (material, drop height and speed, floor, self-collision), so that the
+# requested steps end within seconds to a few minutes at the oracle's rate
+# (which hardly depends on the size).
+REF_SAMPLE = {"R": 8, "t": 4}
 
 
-def run_reference(args, sc):
+def run_reference(args):
     rank, _, ws = dist_env()
     if rank != 0:
         return
     from oracle import Oracle
-    o = Oracle(scenes.hetero_block(dims=REF_SAMPLE_DIMS, seed=2))
+    o = Oracle(scenes.hollow_ball(**REF_SAMPLE))
     for _ in range(args.warmup):
         o.step(1)
     t0 = time.perf_counter()
@@ -206,8 +214,8 @@ def run_reference(args, sc):
         o.step(1)
     t = time.perf_counter() - t0
     v = o.N * args.steps / t
-    sample = (f"each step: one FP64 oracle step of a {REF_SAMPLE_DIMS[0]}x{REF_SAMPLE_DIMS[1]}x{REF_SAMPLE_DIMS[2]} "
-              f"block of the same recipe ({o.N} voxels); {args.steps} steps after {args.warmup} warm-up, 1 thread")
+    sample = (f"each step: one FP64 oracle step of a hollow ball R{REF_SAMPLE['R']} t{REF_SAMPLE['t']} of the same "
+              f"recipe ({o.N} voxels, floor + self-collision); {args.steps} steps after {args.warmup} warm-up, 1 thread")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -472,13 +480,33 @@ def multi_step_line(sim, stream, flush, steps=500):
             "l2": "flushed before each call; the lattice stays in L2 across the steps of a call"}
 
 
+def hetero_block_line(stream, peak, flush, steps=2000, warmup=10):
+    """The heterogeneous actuated block (64 x 64 x 32 sites, seed 2; 117,907
+    voxels, about 13 MB of state): per-step launches with the L2 flushed
+    between steps, then the same lattice stepped by one call of 500 steps."""
+    from paper_1212_2845_gb300 import vx
+    sim = vx.Sim(scenes.hetero_block())
+    t = time_steps(sim, stream, steps, warmup, flush)
+    avg = float(t.mean())
+    b_alg = 112  # state r/w 104, flags 2, material 1, bond mask 1, phase 4
+    out = {"workload": "hetero_block_64x64x32 (plain step, floor, actuation)", "voxels": sim.N,
+           "bonds": sim.n_bonds, "value": sim.N / avg, "unit": METRIC, "ms_per_step": avg * 1e3,
+           "bond_steps_per_s": sim.n_bonds / avg, "l2": "flushed between steps",
+           "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg,
+                        "kernel": "fused_pipe<256>", "traffic": measured_traffic("hetero_block_64x64x32")},
+           "multi_step_call": multi_step_line(sim, stream, flush)}
+    sim.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10000)
     ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--e2e-steps", type=int, default=300)
+    ap.add_argument("--e2e-steps", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-large", action="store_true")
     ap.add_argument("--only-large", action="store_true",
@@ -487,14 +515,14 @@ def main():
     ap.add_argument("--only-adjoint", action="store_true", help="time only the adjoint form (profiling aid)")
     ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
     ap.add_argument("--only-collisions", action="store_true", help="time only the ball drop with collisions")
+    ap.add_argument("--only-small", action="store_true", help="time only the small-lattice forms")
     ap.add_argument("--bodies", type=int, default=0, help="bodies for --only-adjoint / --only-batched")
     ap.add_argument("--shell-radius", type=int, default=200, help="outer radius of the --only-large shell")
     ap.add_argument("--form-steps", type=int, default=0, help="steps for --only-adjoint / --only-batched")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    sc = scenes.hetero_block()
     if args.impl == "reference":
-        run_reference(args, sc)
+        run_reference(args)
         return
 
     import torch
@@ -520,14 +548,20 @@ def main():
         print(json.dumps(batched_form(torch.cuda.Stream(), peak, n_bodies=args.bodies or 4096,
                                       steps=args.form_steps or 200)))
         return
+    if args.only_small:
+        print(json.dumps(small_lattice(torch.cuda.Stream())))
+        return
     if ws > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
     from paper_1212_2845_gb300 import vx
 
+    sc = scenes.hollow_ball()
     sim = vx.Sim(sc)
     stream = torch.cuda.Stream()
+    sim.step(PRE_STEPS, stream)               # untimed set-up: the drop to just before the impact
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    reb0 = sim.collision_stats()[0]
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
@@ -538,6 +572,7 @@ def main():
         t_wall = time.perf_counter() - t_wall0
         torch.cuda.synchronize()
         clk.end_window()
+    rebuilds = sim.collision_stats()[0] - reb0
     t_steps = max_over_ranks(float(times.sum()), "cuda")
     value = ws * sim.N * args.steps / t_steps
     avg = t_steps / args.steps
@@ -565,30 +600,36 @@ def main():
         return
     peak, peak_kind = load_peaks()
     achieved = B_ALG * N / avg / 1e9
+    window = (f"steps {PRE_STEPS + args.warmup}..{PRE_STEPS + args.warmup + args.steps} of the 20,000-step drop "
+              f"(steps 0..{PRE_STEPS} untimed set-up, then {args.warmup} warm-up; impact near step 370)")
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": avg * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "voxels": N, "bonds": sim.n_bonds, "l2": "flushed between steps",
-                   "parallelism": "replicas" if ws > 1 else "single", "bond_steps_per_s": ws * sim.n_bonds * args.steps / t_steps,
-                   "wall_s": t_wall},
+        "config": {"workload": WORKLOAD, "voxels": N, "bonds": sim.n_bonds, "surface_voxels": sim.n_surface,
+                   "window": window, "candidate_rebuilds_in_window": rebuilds, "l2": "flushed between steps",
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "bond_steps_per_s": ws * sim.n_bonds * args.steps / t_steps, "wall_s": t_wall},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "traffic": measured_traffic("hetero_block_64x64x32"), "kernel": "fused_pipe<256>",
+                     "traffic": measured_traffic("hollow_ball_R100_t8"),
+                     "traffic_source": "stored ncu capture of the same kernel source (null when it changed)",
+                     "kernel": "fused_pipe<256> + rebuild_all (every launch of a step, rebuilds included)",
                      "bytes_per_voxel_step": B_ALG, "peak_kind": peak_kind},
         "e2e": {"value": N * args.e2e_steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": nb,
-                "d2h_bytes_per_step": nb},
-        "gpu_launches": args.steps,
+                "d2h_bytes_per_step": nb, "steps": args.e2e_steps},
+        "gpu_launches": 2 * (args.steps + args.warmup),
         "clocks": clk.summary(),
     }
     if not args.no_large:
         line["large_lattice"] = large_lattice(stream, peak)
     if not args.no_forms:
-        line["forms"] = {"multi_step_call": multi_step_line(sim, stream, flush),
+        line["forms"] = {"hetero_block": hetero_block_line(stream, peak, flush),
                          "batched": batched_form(stream, peak), "adjoint": adjoint_form(stream, peak),
                          "collisions": collision_form(stream),
                          "collision_schemes": collision_schemes(stream),
                          "collision_rebuilds": rebuild_sizes(stream),
                          "small_lattice": small_lattice(stream)}
+    sim.close()
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(sc)
         if not args.no_forms:

@@ -470,34 +470,41 @@ template <class R> static std::vector<std::array<int64_t, 3>> quantise_positions
   return xq;
 }
 
-// The candidate pairs among the searched voxels `list` (Sec 2.2.2), written
-// into the partner lists of those voxels (cleared first, sorted ascending).
-// Brute force tests every pair.  The default search visits the voxels in
-// order of their quantised x coordinate and tests, for each, only the voxels
-// after it whose x differs by less than 2 Q: a pair with |dx| >= 2 Q has
-// dx^2 >= (2 Q)^2 and fails the strict distance test, so both searches find
-// the same set (checked against each other by the tests).
+// The candidate pairs (i < j) among the searched voxels `list` (Sec 2.2.2)
+// for the quantised centres xq, in no particular order.  Brute force tests
+// every pair.  The default search visits the voxels in order of their
+// quantised x coordinate and tests, for each, only the voxels after it whose
+// x differs by less than 2 Q: a pair with |dx| >= 2 Q has dx^2 >= (2 Q)^2 and
+// fails the strict distance test, so both searches find the same set
+// (checked against each other by the tests).
+template <class R> static std::vector<std::pair<int, int>> find_pairs(const Sim<R>& S, const std::vector<int>& list,
+                                                                     const std::vector<std::array<int64_t, 3>>& xq) {
+  std::vector<std::pair<int, int>> out;
+  const size_t n = list.size();
+  auto test = [&](int i, int j) {
+    if (cand_pred(S, i, j, xq)) out.push_back(i < j ? std::make_pair(i, j) : std::make_pair(j, i));
+  };
+  if (S.prm.brute_search) {
+    for (size_t a = 0; a < n; ++a)
+      for (size_t b = a + 1; b < n; ++b) test(list[a], list[b]);
+    return out;
+  }
+  std::vector<int> ord(list);
+  std::sort(ord.begin(), ord.end(), [&](int u, int v) { return xq[u][0] < xq[v][0] || (xq[u][0] == xq[v][0] && u < v); });
+  const int64_t two = 2 * S.qQ;
+  for (size_t a = 0; a < n; ++a)
+    for (size_t b = a + 1; b < n && xq[ord[b]][0] - xq[ord[a]][0] < two; ++b) test(ord[a], ord[b]);
+  return out;
+}
+
+// The pairs of `list` written into the partner lists of its voxels (cleared
+// first, sorted ascending).
 template <class R> static void search_pairs(Sim<R>& S, const std::vector<int>& list,
                                             const std::vector<std::array<int64_t, 3>>& xq) {
   for (int i : list) S.partners[i].clear();
-  const size_t n = list.size();
-  if (S.prm.brute_search) {
-    for (size_t a = 0; a < n; ++a)
-      for (size_t b = a + 1; b < n; ++b) {
-        int i = list[a], j = list[b];
-        if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
-      }
-  } else {
-    std::vector<int> ord(list);
-    std::sort(ord.begin(), ord.end(), [&](int u, int v) { return xq[u][0] < xq[v][0] || (xq[u][0] == xq[v][0] && u < v); });
-    const int64_t two = 2 * S.qQ;
-    for (size_t a = 0; a < n; ++a) {
-      int i = ord[a];
-      for (size_t b = a + 1; b < n && xq[ord[b]][0] - xq[i][0] < two; ++b) {
-        int j = ord[b];
-        if (cand_pred(S, i, j, xq)) { S.partners[i].push_back(j); S.partners[j].push_back(i); }
-      }
-    }
+  for (const auto& p : find_pairs(S, list, xq)) {
+    S.partners[p.first].push_back(p.second);
+    S.partners[p.second].push_back(p.first);
   }
   for (int i : list) std::sort(S.partners[i].begin(), S.partners[i].end());
 }
@@ -907,9 +914,10 @@ long orc_candidate_pairs(orc_sim* o, int32_t* pairs, long cap) {
 long orc_n_rebuilds(orc_sim* o) { return o->S.n_rebuilds; }
 double orc_accumulator(orc_sim* o, int body) { return o->S.acc[body]; }
 
-// Brute-force candidate pairs (i<j) for given anchor offsets o (N x 3 doubles,
-// typically FP32 values widened exactly): every surface pair is tested with
-// the quantised predicate.
+// Candidate pairs (i<j, sorted) for given anchor offsets o (N x 3 doubles,
+// typically FP32 values widened exactly), searched body by body (all bodies
+// at once in a shared world) with the search the simulator uses (the sweep,
+// or brute force when set).
 long orc_pairs_from_offsets(orc_sim* o, const double* off, int32_t* pairs, long cap) {
   Sim<double>& S = o->S;
   const Topo& T = S.T;
@@ -920,13 +928,20 @@ long orc_pairs_from_offsets(orc_sim* o, const double* off, int32_t* pairs, long 
       xq[v][a] = (S.prm.collide_on == 2 ? (int64_t)std::nearbyint(std::ldexp(S.origin[T.body[v]][a], S.qK)) : 0) +
                  (int64_t)c[a] * S.qQ + (int64_t)std::nearbyint(std::ldexp(off[3 * v + a], S.qK));
   }
-  long n = 0;
-  for (int i = 0; i < T.N; ++i) {
-    if (!S.prm.cand_all && !T.surface[i]) continue;
-    for (int j = i + 1; j < T.N; ++j) {
-      if (!S.prm.cand_all && !T.surface[j]) continue;
-      if (cand_pred(S, i, j, xq)) { if (n < cap) { pairs[2 * n] = i; pairs[2 * n + 1] = j; } ++n; }
+  std::vector<std::pair<int, int>> all;
+  if (S.prm.collide_on == 2) {
+    all = find_pairs(S, searched(S, 0, T.N), xq);
+  } else {
+    for (int b = 0; b < T.n_bodies; ++b) {
+      auto p = find_pairs(S, searched(S, T.body_first[b], T.body_first[b + 1]), xq);
+      all.insert(all.end(), p.begin(), p.end());
     }
+  }
+  std::sort(all.begin(), all.end());
+  long n = 0;
+  for (const auto& p : all) {
+    if (n < cap) { pairs[2 * n] = p.first; pairs[2 * n + 1] = p.second; }
+    ++n;
   }
   return n;
 }

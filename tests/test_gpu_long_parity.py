@@ -11,6 +11,9 @@ kernels run every case in full and are compared at those voxels:
   hollow ball R40 t4, 2,000 steps (through the impact and bounce)
   hollow ball R20 t4, 20,000 steps (a scaled shell for the whole drop)
   16 population bodies, 20,000 steps
+  hollow ball R100 t8 (the full 926,584-voxel ball), 1,000 steps: the fall,
+  the impact near step 370 and the first compression, with its candidate
+  rebuilds
 """
 import importlib.util
 import os
@@ -46,12 +49,16 @@ def test_long_run_matches_the_stored_oracle_state(vx, name):
     sim.step(steps)
     assert sim.status()[0] == 0
     s = sim.state()
+    rebuilds = sim.collision_stats()[0]
     sim.close()
     idx = g[f"{name}/idx"]
     err = np.linalg.norm(s["pos"][idx] - g[f"{name}/pos"], axis=1) / g[f"{name}/diag"]
     flips = int(np.count_nonzero(s["static"][idx] != g[f"{name}/static"]))
+    msg = ""
+    if f"{name}/n_rebuilds" in g:
+        msg = f", candidate rebuilds gpu {rebuilds} oracle {int(g[f'{name}/n_rebuilds'])}"
     print(f"{name}: {steps} steps, max position error / diagonal {err.max():.2e}, "
-          f"static-flag flips {flips}/{len(idx)}, largest displacement {float(g[f'{name}/max_disp']):.3e} m")
+          f"static-flag flips {flips}/{len(idx)}, largest displacement {float(g[f'{name}/max_disp']):.3e} m{msg}")
     assert err.max() < 1e-3
 
 

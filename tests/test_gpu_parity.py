@@ -380,24 +380,28 @@ def test_collision_threshold_exact(vx):
         assert ((0, 1) in gp) == expect
 
 
-def test_collision_sets_full_ball_sampled(vx):
-    """Config 3 size: full 200^3 shell, scrambled state; sampled surface voxels'
-    partner lists against the oracle's brute force."""
-    sc = scenes.hollow_ball()
+@pytest.mark.parametrize("R", [60, 100])
+def test_collision_sets_complete_on_the_thread_query_path(vx, R):
+    """Shells with more than 8 surface voxels per warp of the rebuild grid
+    (R60 t8: 65,792 surface voxels, the smallest such shell; R100 t8: the
+    full ball, 192,848), where the query searches one voxel per thread: the
+    complete candidate set of a scrambled state against the oracle's search
+    on the same FP32 offsets."""
+    sc = scenes.hollow_ball(R=R, t=8)
     sim = vx.Sim(sc, apply_scene=False)
     sim.set_environment(0.0, False, True)
     ora = Oracle(sc, apply_scene=False)
+    assert sim.n_surface > 65536
     off = scrambled_offsets(sim.N, sc["voxel_size"], 5, amp=0.4)
     sim.write_state(offset=off)
     sim.rebuild_collisions()
-    pairs = sim.collision_pairs()
-    _, _, surf = ora.topology()
-    rng = np.random.default_rng(6)
-    sample = rng.choice(np.nonzero(surf)[0], size=150, replace=False)
-    off64 = off.astype(np.float64)
-    for i in sample:
-        mine = np.sort(np.concatenate([pairs[pairs[:, 0] == i, 1], pairs[pairs[:, 1] == i, 0]]))
-        assert np.array_equal(mine, ora.partners_of(off64, i)), i
+    gp = sim.collision_pairs()
+    op = ora.pairs_from_offsets(off.astype(np.float64))
+    gp = gp[np.lexsort((gp[:, 1], gp[:, 0]))]
+    print(f"R{R}: {sim.n_surface} surface voxels, {len(op)} pairs")
+    assert len(op) > sim.n_surface
+    assert np.array_equal(gp, op)
+    sim.close()
 
 
 def test_ball_drop_with_self_collision(vx):

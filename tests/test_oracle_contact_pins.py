@@ -230,7 +230,7 @@ def test_sweep_search_equals_brute_force(which):
     else:
         sc = scenes.clapper()
     for seed in (1, 2, 3):
-        sets = []
+        sets, from_off = [], []
         for brute in (True, False):
             o = Oracle(sc, apply_scene=False)
             if which == "clapper_all":
@@ -240,5 +240,8 @@ def test_sweep_search_equals_brute_force(which):
             scrambled_state(o, seed)
             o.reset_candidates()
             sets.append({tuple(p) for p in o.candidate_pairs()})
-        assert len(sets[0]) > 30
+            off = np.random.default_rng(seed + 10).uniform(-0.45, 0.45, size=(o.N, 3)) * o.l
+            from_off.append([tuple(p) for p in o.pairs_from_offsets(off)])
+        assert len(sets[0]) > 30 and len(from_off[0]) > 30
         assert sets[0] == sets[1]
+        assert from_off[0] == from_off[1] == sorted(set(from_off[0]))
