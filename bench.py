@@ -516,6 +516,8 @@ def main():
     ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
     ap.add_argument("--only-collisions", action="store_true", help="time only the ball drop with collisions")
     ap.add_argument("--only-small", action="store_true", help="time only the small-lattice forms")
+    ap.add_argument("--pre-steps", type=int, default=PRE_STEPS,
+                    help="untimed steps of the drop before the warm-up (profiling aid: 0 starts in the free fall)")
     ap.add_argument("--bodies", type=int, default=0, help="bodies for --only-adjoint / --only-batched")
     ap.add_argument("--shell-radius", type=int, default=200, help="outer radius of the --only-large shell")
     ap.add_argument("--form-steps", type=int, default=0, help="steps for --only-adjoint / --only-batched")
@@ -559,7 +561,7 @@ def main():
     sc = scenes.hollow_ball()
     sim = vx.Sim(sc)
     stream = torch.cuda.Stream()
-    sim.step(PRE_STEPS, stream)               # untimed set-up: the drop to just before the impact
+    sim.step(args.pre_steps, stream)          # untimed set-up: the drop to just before the impact
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
     reb0 = sim.collision_stats()[0]
     if ws > 1:
@@ -600,8 +602,9 @@ def main():
         return
     peak, peak_kind = load_peaks()
     achieved = B_ALG * N / avg / 1e9
-    window = (f"steps {PRE_STEPS + args.warmup}..{PRE_STEPS + args.warmup + args.steps} of the 20,000-step drop "
-              f"(steps 0..{PRE_STEPS} untimed set-up, then {args.warmup} warm-up; impact near step 370)")
+    p0 = args.pre_steps
+    window = (f"steps {p0 + args.warmup}..{p0 + args.warmup + args.steps} of the 20,000-step drop "
+              f"(steps 0..{p0} untimed set-up, then {args.warmup} warm-up; impact near step 370)")
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": avg * 1e3, "higher_is_better": True, "scaling": "weak",
