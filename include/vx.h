@@ -171,7 +171,20 @@ VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
  * run all n steps in ONE launch, each CTA stepping one group at a time with
  * a barrier between steps so the group's state stays in L2.  Same arithmetic
  * and bits as the per-step forms.  Ignored while self-collision is on.
- * 0 turns it off.  Needs a fused form with tiles of 128 or 256. */
+ * 0 turns it off.  Needs a fused form with tiles of 128 or 256.
+ *
+ * group_voxels = VX_GROUPS_RESIDENT: the shared-memory-resident form.
+ * Consecutive whole bodies are grouped so that a group fits the shared memory
+ * of one cluster of up to 16 CTAs (about 1,000 voxels per CTA; the cluster
+ * size is the smallest power of two that holds the largest body, widened to
+ * up to 8 CTAs when there are few groups).  vx_step / vx_step_async run all n
+ * steps in ONE launch: each cluster loads a group's state into shared memory
+ * once, steps it n times with cluster barriers between the bond and voxel
+ * phases (partners in another CTA of the cluster are read through
+ * distributed shared memory) and writes it back once.  Same arithmetic and
+ * bits as the per-step forms.  VX_ERR_STATE if a body does not fit 16 CTAs;
+ * ignored while self-collision is on. */
+#define VX_GROUPS_RESIDENT (-1)
 VX_API int vx_set_batching(vx_sim* sim, int64_t group_voxels);
 /* Multi-step launches (on by default): in the pipelined form without
  * batching or collisions, on lattices of at most 4 tiles per persistent CTA
@@ -340,12 +353,14 @@ VX_API int vx_audit(vx_sim* sim, double* out, void* stream);
  * by vx_get_status as after vx_step_async).
  *
  * vx_autotune_batching: time tile sizes {128, 256} x group sizes {per-step
- * launches, 1024, 4096, 16384, 65536 voxels} on sample_steps steps from the
- * current state (restored afterwards), keep the fastest for the lattice's
- * size class (log2 voxels, log2 mean body size, per-voxel arrays in use) in
- * a process-wide cache, and apply it.  A cached class is applied without
- * timing.  Outputs (any may be NULL): tile size, group size (0 = per-step
- * launches) and the sampled voxel-steps/s.  Synchronous. */
+ * launches, 1024, 4096, 16384, 65536 voxels} and the resident form (where
+ * the lattice fits it) on sample_steps steps from the current state
+ * (restored afterwards), keep the fastest for the lattice's size class (log2
+ * voxels, log2 mean body size, per-voxel arrays in use) in a process-wide
+ * cache, and apply it.  A cached class is applied without timing.  Outputs
+ * (any may be NULL): tile size, group size (0 = per-step launches,
+ * VX_GROUPS_RESIDENT = the resident form) and the sampled voxel-steps/s.
+ * Synchronous. */
 VX_API int vx_graph_capture(vx_sim* sim, int64_t n_steps, void* stream);
 VX_API int vx_graph_launch(vx_sim* sim, void* stream);
 VX_API int vx_autotune_batching(vx_sim* sim, int32_t sample_steps, int32_t* tile_max, int64_t* group_voxels,

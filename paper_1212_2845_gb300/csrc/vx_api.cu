@@ -132,7 +132,16 @@ struct vx_sim {
   int64_t bar_spins = 1ll << 24;  // barrier wait budget in 128-cycle units: about one second
   int32_t bar_extra = 0;      // phantom CTAs (fault injection)
   // batched form
-  int64_t group_voxels = 0;   // 0: off
+  int64_t group_voxels = 0;   // 0: off; VX_GROUPS_RESIDENT: the shared-memory-resident form
+  // resident form: groups of whole bodies kept in the shared memory of a CTA
+  // cluster for all steps of a launch (planned per model configuration)
+  int res_ok = -1;            // -1 not planned for res_cfg, 0 not possible, 1 planned
+  uint64_t res_cfg = ~0ull;
+  int res_C = 0, res_cap = 0, res_grid = 0;
+  size_t res_smem = 0;
+  int32_t* r_grp = nullptr;
+  int32_t* r_cls = nullptr;
+  int32_t* r_clg = nullptr;
   Batch B;
   int32_t* b_cta_start = nullptr;
   int32_t* b_cta_groups = nullptr;
@@ -556,6 +565,90 @@ int ensure_nbr(vx_sim* s) {
   return VX_OK;
 }
 
+// Plans the resident form for the current model: the slice capacity from
+// the device's shared memory, the cluster size from the largest body (a
+// power of two up to 16; wider when there are few groups, so a small lattice
+// spreads over up to 8 SMs), the groups and their clusters.  Sets res_ok.
+int ensure_resident(vx_sim* s) {
+  if (s->res_cfg == s->cfg && s->res_ok >= 0) return VX_OK;
+  s->res_cfg = s->cfg;
+  s->res_ok = 0;
+  int rc;
+  if ((rc = ensure_nbr(s))) return rc;
+  const Lattice& L = s->L;
+  const int nm = (int)L.palette.size();
+  const bool fext = s->has_fext, lut = s->lut && s->logE_h.empty();
+  int dev = 0, optin = 0, n_sm = 0;
+  VX_CUDA(cudaGetDevice(&dev));
+  VX_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  VX_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  int cap = 1024;
+  while (cap > 64 && res_smem_bytes(cap, fext, nm, lut) > (size_t)optin) cap -= 32;
+  const size_t smem = res_smem_bytes(cap, fext, nm, lut);
+  if (smem > (size_t)optin) return VX_OK;
+  // bodies' internal voxel ranges (bodies are contiguous in the internal order)
+  std::vector<int64_t> bs(L.n_bodies + 1, L.N);
+  {
+    int prev = -1;
+    for (int64_t v = 0; v < L.N; ++v) {
+      const int b = L.body[s->T.perm[v]];
+      for (int k = prev + 1; k <= b; ++k) bs[k] = v;
+      prev = b;
+    }
+  }
+  int64_t max_body = 0;
+  for (int b = 0; b < L.n_bodies; ++b) max_body = std::max(max_body, bs[b + 1] - bs[b]);
+  int C = 1;
+  while ((int64_t)C * cap < max_body) C *= 2;
+  if (C > 16) return VX_OK;
+  ResPlan P;
+  if (!plan_resident(bs, (int64_t)C * cap, 1, P)) return VX_OK;
+  while (C < 8 && (int64_t)(P.grp_start.size() - 1) * C * 2 <= n_sm) {
+    C *= 2;
+    plan_resident(bs, (int64_t)C * cap, 1, P);
+  }
+  int max_cl = 0;
+  for (;;) {
+    max_cl = 0;
+    if (prepare_resident(C, smem, fext, &max_cl) == 0 || C == 1 || (int64_t)(C / 2) * cap < max_body) break;
+    C /= 2;
+  }
+  if (max_cl < 1) return VX_OK;
+  plan_resident(bs, (int64_t)C * cap, 1, P);
+  const int ng = (int)P.grp_start.size() - 1;
+  const int n_cl = std::min(ng, max_cl);
+  plan_resident(bs, (int64_t)C * cap, n_cl, P);
+  dfree(s->r_grp); dfree(s->r_cls); dfree(s->r_clg);
+  if ((rc = dalloc(&s->r_grp, P.grp_start.size())) || (rc = dalloc(&s->r_cls, P.cl_start.size())) ||
+      (rc = dalloc(&s->r_clg, P.cl_groups.size())))
+    return rc;
+  VX_CUDA(cudaMemcpy(s->r_grp, P.grp_start.data(), P.grp_start.size() * 4, cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemcpy(s->r_cls, P.cl_start.data(), P.cl_start.size() * 4, cudaMemcpyHostToDevice));
+  VX_CUDA(cudaMemcpy(s->r_clg, P.cl_groups.data(), P.cl_groups.size() * 4, cudaMemcpyHostToDevice));
+  s->res_C = C;
+  s->res_cap = cap;
+  s->res_grid = n_cl * C;
+  s->res_smem = smem;
+  s->res_ok = 1;
+  return VX_OK;
+}
+
+ResArgs res_args(vx_sim* s, int64_t n) {
+  ResArgs R;
+  R.grp_start = s->r_grp;
+  R.cl_start = s->r_cls;
+  R.cl_groups = s->r_clg;
+  R.buf0 = s->st;
+  R.buf1 = s->st + (size_t)NPLANE * s->pitch;
+  R.cur0 = s->cur;
+  R.n_steps = (int)n;
+  R.step0 = s->step;
+  R.act_P = s->actP;
+  R.ctr = nullptr;
+  R.cap = s->res_cap;
+  return R;
+}
+
 int ensure_two_pass(vx_sim* s) {
   int rc;
   if ((rc = ensure_nbr(s))) return rc;
@@ -840,6 +933,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
   dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar); dfree(s->qorg);
+  dfree(s->r_grp); dfree(s->r_cls); dfree(s->r_clg);
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
   delete s;
 }
@@ -887,7 +981,15 @@ int vx_set_batching(vx_sim* s, int64_t group_voxels) {
   if (s) ++s->cfg;  // invalidates a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
-  if (group_voxels < 0) return fail(VX_ERR_ARG, "group_voxels must be >= 0");
+  if (group_voxels == VX_GROUPS_RESIDENT) {
+    if (s->form == VX_FORM_TWO_PASS) return fail(VX_ERR_STATE, "the resident form needs a fused form");
+    if ((rc = ensure_resident(s))) return rc;
+    if (s->res_ok != 1)
+      return fail(VX_ERR_STATE, "the resident form does not fit this lattice (a body above 16 CTAs' shared memory)");
+    s->group_voxels = group_voxels;
+    return retile(s, s->tile_max);
+  }
+  if (group_voxels < 0) return fail(VX_ERR_ARG, "group_voxels must be >= 0 or VX_GROUPS_RESIDENT");
   if (group_voxels > 0 && s->form == VX_FORM_TWO_PASS) return fail(VX_ERR_STATE, "batching needs a fused form");
   if (s->tile_max == 512 && group_voxels > 0) return fail(VX_ERR_ARG, "batching takes tiles of 128 or 256 voxels");
   s->group_voxels = group_voxels;
@@ -1207,6 +1309,18 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   if (n < 0) return fail(VX_ERR_ARG, "n_steps must be >= 0");
   if (n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps too large for one call");
   cudaStream_t st = (cudaStream_t)stream;
+  if (s->group_voxels == VX_GROUPS_RESIDENT && !s->collide_on && n > 0) {
+    // resident form: all n steps in one launch, state in cluster shared memory
+    if ((rc = ensure_resident(s))) return rc;
+    if (s->res_ok != 1) return fail(VX_ERR_STATE, "the resident form does not fit this lattice");
+    StepArgs A = step_args(s);
+    ResArgs R = res_args(s, n);
+    const cudaError_t e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, st);
+    if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
+    s->cur ^= (int)(n & 1);
+    s->step += n;
+    return VX_OK;
+  }
   if (s->group_voxels > 0 && !s->collide_on && n > 0) {
     // batched form: all n steps in one launch
     StepArgs A = step_args(s);
@@ -1503,22 +1617,33 @@ int vx_graph_capture(vx_sim* s, int64_t n, void* stream) {
   int rc = check_sim(s);
   if (rc) return rc;
   if (n < 1 || n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps must be in [1, 2^31)");
-  if (s->group_voxels <= 0) return fail(VX_ERR_STATE, "graph capture takes the batched form (vx_set_batching)");
+  if (s->group_voxels == 0) return fail(VX_ERR_STATE, "graph capture takes the batched form (vx_set_batching)");
   if (s->collide_on) return fail(VX_ERR_STATE, "the batched form has no voxel-voxel collisions");
+  const bool res = s->group_voxels == VX_GROUPS_RESIDENT;
+  if (res) {
+    if ((rc = ensure_resident(s))) return rc;  // before step_args: it may allocate the neighbour planes
+    if (s->res_ok != 1) return fail(VX_ERR_STATE, "the resident form does not fit this lattice");
+  }
   StepArgs A = step_args(s);
-  if ((rc = ensure_pipe(s, A))) return rc;
-  if ((int64_t)s->B.cta_start.size() != (int64_t)s->pipe_grid + 1 && (rc = build_schedule(s))) return rc;
+  if (!res) {
+    if ((rc = ensure_pipe(s, A))) return rc;
+    if ((int64_t)s->B.cta_start.size() != (int64_t)s->pipe_grid + 1 && (rc = build_schedule(s))) return rc;
+  }
   if (!s->ctr_d && (rc = dalloc(&s->ctr_d, 2))) return rc;
   BatchArgs Bt = batch_args(s, n);
   Bt.ctr = s->ctr_d;
+  ResArgs R = res_args(s, n);
+  R.ctr = s->ctr_d;
   cudaStream_t cs;
   VX_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ge = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, cs);
-    e = cudaStreamEndCapture(cs, &g);
+    if (res) e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, cs);
+    else launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, cs);
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
+    if (e == cudaSuccess) e = e2;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
   if (g) cudaGraphDestroy(g);
@@ -1555,13 +1680,14 @@ int vx_autotune_batching(vx_sim* s, int32_t sample_steps, int32_t* tile_max_out,
   if (s->collide_on) return fail(VX_ERR_STATE, "the batched form has no voxel-voxel collisions");
   cudaStream_t st = (cudaStream_t)stream;
   const TuneKey key = tune_key(s);
-  TuneVal best{0, -1, 0.0};
+  TuneVal best{0, 0, 0.0};
+  bool cached = false;
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) best = it->second;
+    if (it != g_tune.end()) { best = it->second; cached = true; }
   }
-  if (best.group_voxels < 0) {
+  if (!cached) {
     // time every candidate from the same state, then put the state back
     const int64_t N = s->L.N, P = s->pitch;
     const size_t sb = (size_t)NPLANE * P;
@@ -1584,10 +1710,13 @@ int vx_autotune_batching(vx_sim* s, int32_t sample_steps, int32_t* tile_max_out,
       VX_CUDA(cudaMemcpyAsync(save, cur_state(s), 4 * sb, cudaMemcpyDeviceToDevice, st));
       VX_CUDA(cudaMemcpyAsync(save_fl, s->flags, N, cudaMemcpyDeviceToDevice, st));
       const int tiles[2] = {128, 256};
-      const int64_t groups[5] = {0, 1024, 4096, 16384, 65536};
+      const int64_t groups[6] = {0, 1024, 4096, 16384, 65536, VX_GROUPS_RESIDENT};
+      int r;
+      if ((r = ensure_resident(s))) return r;
+      const bool res_possible = s->res_ok == 1;
       for (int tm : tiles)
         for (int64_t gv : groups) {
-          int r;
+          if (gv == VX_GROUPS_RESIDENT && (!res_possible || tm != 256)) continue;  // no tiles in that form
           if ((r = vx_set_step_form(s, VX_FORM_PIPELINED, tm)) || (r = vx_set_batching(s, gv))) return r;
           if ((r = vx_step_async(s, 2, st)) || (r = restore())) return r;  // warm-up (prepares kernels)
           VX_CUDA(cudaEventRecord(e0, st));

@@ -437,16 +437,13 @@ __device__ __forceinline__ VoxMeta load_meta(const StepArgs& A, int v) {
 
 // Everything a voxel does after its bond forces are summed (Sec 2.2.1,
 // Sec 2.2.2, Sec 2.1.3): external force, gravity, ground damping, voxel
-// contacts, floor contact with Coulomb friction, then integration.  Writes
-// the new state to st_out; returns |v| for the collision horizon.
-__device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const VoxMeta& mt, VoxS s, V3f F, V3f M,
-                                              float adT, float Ev, const DevMat* mats) {
+// contacts, floor contact with Coulomb friction, then integration.  Updates
+// s and fl (the caller stores them); returns |v| for the collision horizon.
+__device__ __forceinline__ float voxel_update(const StepArgs& A, int v, const VoxMeta& mt, VoxS& s, uint8_t& fl,
+                                              V3f F, V3f M, float adT, float Ev, const DevMat* mats) {
   const int64_t P = A.pitch;
-  uint8_t fl = mt.fl;
-  if (fl & 1u) {  // fixed: immobile, state carried over
-    store_vox(A.st_out, P, v, s);
-    return 0.f;
-  }
+  fl = mt.fl;
+  if (fl & 1u) return 0.f;  // fixed: immobile, state carried over
   const DevMat& d = mats[mt.m];
   const float dt = mt.dt;
   const float l = A.l;
@@ -529,11 +526,19 @@ __device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const Vo
   s.o = axpy(s.o, dt, s.v);
   s.w = axpy(s.w, mul_(dt, d.inv_I), M);
   s.q = integrate_rot(s.q, s.w, dt);
-  store_vox(A.st_out, P, v, s);
-  if (fl != mt.fl) A.flags[v] = fl;
   float chk = s.o.x + s.o.y + s.o.z + s.v.x + s.v.y + s.v.z + s.w.x + s.w.y + s.w.z + s.q.w;
   if (!isfinite(chk)) record_bad(A, v);
   return fsqrt(fmaxf(dot3(s.v, s.v), 1e-30f));
+}
+
+// voxel_update, then the new state to st_out and changed flags in place.
+__device__ __forceinline__ float voxel_finish(const StepArgs& A, int v, const VoxMeta& mt, VoxS s, V3f F, V3f M,
+                                              float adT, float Ev, const DevMat* mats) {
+  uint8_t fl;
+  const float speed = voxel_update(A, v, mt, s, fl, F, M, adT, Ev, mats);
+  store_vox(A.st_out, A.pitch, v, s);
+  if (fl != mt.fl) A.flags[v] = fl;
+  return speed;
 }
 
 // Collision horizon accumulator after a step (Sec 2.2.2, horizon reading):

@@ -297,6 +297,43 @@ void build_batch(const Tiling& T, const std::vector<int64_t>& starts, int64_t N,
   B.max_cta_voxels = *std::max_element(load.begin(), load.end());
 }
 
+bool plan_resident(const std::vector<int64_t>& body_start, int64_t max_group, int n_clusters, ResPlan& P) {
+  P = ResPlan();
+  const size_t nb = body_start.size() - 1;
+  P.grp_start.push_back((int32_t)body_start[0]);
+  int64_t cur = 0;
+  for (size_t b = 0; b < nb; ++b) {
+    const int64_t sz = body_start[b + 1] - body_start[b];
+    if (sz > max_group) return false;
+    if (cur > 0 && cur + sz > max_group) {
+      P.grp_start.push_back((int32_t)body_start[b]);
+      cur = 0;
+    }
+    cur += sz;
+  }
+  P.grp_start.push_back((int32_t)body_start[nb]);
+  const size_t ng = P.grp_start.size() - 1;
+  // longest processing time first onto the least loaded cluster
+  std::vector<int32_t> order(ng);
+  for (size_t g = 0; g < ng; ++g) order[g] = (int32_t)g;
+  auto size_of = [&](int32_t g) { return (int64_t)P.grp_start[g + 1] - P.grp_start[g]; };
+  std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return size_of(a) > size_of(b); });
+  std::vector<int64_t> load(n_clusters, 0);
+  std::vector<std::vector<int32_t>> lists(n_clusters);
+  for (int32_t g : order) {
+    const int c = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    load[c] += size_of(g);
+    lists[c].push_back(g);
+  }
+  P.cl_start.push_back(0);
+  for (int c = 0; c < n_clusters; ++c) {
+    P.cl_groups.insert(P.cl_groups.end(), lists[c].begin(), lists[c].end());
+    P.cl_start.push_back((int32_t)P.cl_groups.size());
+  }
+  P.max_cluster_voxels = *std::max_element(load.begin(), load.end());
+  return true;
+}
+
 int64_t Tiling::n_tile_bonds() const {
   int64_t n = (int64_t)halo_bonds.size();
   for (uint16_t p : plus) n += p != 0xFFFFu;

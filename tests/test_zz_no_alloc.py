@@ -122,7 +122,7 @@ def test_static_candidates_report_overflow_and_bad_body_ids(env):
     i = 4 * np.arange(n, dtype=np.uint32)
     lat = torch.from_numpy(i.view(np.int32).copy()).cuda()
     off = np.zeros((3, n), np.float32)
-    off[0] = (-i * np.float32(l)).astype(np.float32)
+    off[0] = (-i.astype(np.float64) * l).astype(np.float32)
     t_off = torch.from_numpy(off).cuda()
     cnt = torch.zeros(n, dtype=torch.int32, device="cuda")
     cand = torch.zeros((n, vx.CAND_CAP), dtype=torch.int32, device="cuda")
