@@ -185,6 +185,13 @@ VX_API int vx_set_step_form(vx_sim* sim, int32_t form, int32_t tile_max);
  * bits as the per-step forms.  VX_ERR_STATE if a body does not fit 16 CTAs;
  * ignored while self-collision is on. */
 #define VX_GROUPS_RESIDENT (-1)
+/* The same form with its bond phase split one way: one thread per bond
+ * (shortest phases: the automatic choice when every group has a cluster of
+ * its own) or one thread per voxel evaluating its +x, +y, +z bonds with one
+ * rotation matrix (the automatic choice when clusters take several groups
+ * each).  Both give the same bits. */
+#define VX_GROUPS_RESIDENT_BOND (-2)
+#define VX_GROUPS_RESIDENT_VOXEL (-3)
 VX_API int vx_set_batching(vx_sim* sim, int64_t group_voxels);
 /* Multi-step launches (on by default): in the pipelined form without
  * batching or collisions, on lattices of at most 4 tiles per persistent CTA

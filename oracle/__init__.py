@@ -69,6 +69,7 @@ def lib():
             "orc_momentum": (None, [_P, _D]),
             "orc_candidate_pairs": (C.c_long, [_P, _I32, C.c_long]),
             "orc_n_rebuilds": (C.c_long, [_P]),
+            "orc_event_signature": (C.c_uint64, [_P]),
             "orc_accumulator": (C.c_double, [_P, C.c_int]),
             "orc_pairs_from_offsets": (C.c_long, [_P, _D, _I32, C.c_long]),
             "orc_partners_of": (C.c_long, [_P, _D, C.c_int, _I32, C.c_long]),
@@ -267,6 +268,12 @@ class Oracle:
         p = np.zeros((max(n, 1), 2), dtype=np.int32)
         self._L.orc_candidate_pairs(self.h, p.ctypes.data_as(_I32), n)
         return p[:n]
+
+    def event_signature(self):
+        """Hash of every discrete decision since the last reset (floor contact
+        and its stick/slip branch per voxel and step, voxel-voxel contacts):
+        equal for two runs that take the same branches."""
+        return self._L.orc_event_signature(self.h)
 
     def n_rebuilds(self):
         return self._L.orc_n_rebuilds(self.h)

@@ -293,6 +293,11 @@ template <class R> struct Sim {
   std::vector<std::vector<int>> partners;  // per voxel, ascending
   long n_rebuilds = 0;
   int qK = 0; int64_t qQ = 0;
+  // signature of the run's discrete decisions (floor contact and its
+  // stick/slip branch, voxel-voxel contacts): two runs that take the same
+  // branches everywhere have the same signature (test aid for finite
+  // differences, which are only meaningful when no decision flips inside +-h)
+  uint64_t events = 1469598103934665603ull;
   // per-step scratch
   struct BondOut { V3<R> F1, M1, F2, M2; };
   std::vector<BondOut> bo;
@@ -557,6 +562,13 @@ template <class R> static void rebuild_all_candidates(Sim<R>& S) {
   else for (int b = 0; b < S.T.n_bodies; ++b) rebuild_candidates(S, b);
 }
 
+// Folds one decision (step, voxel or pair, branch code) into the signature.
+inline uint64_t fold_event(uint64_t h, long n, long a, long b, int code) {
+  const uint64_t w[4] = {(uint64_t)n, (uint64_t)a, (uint64_t)b, (uint64_t)code};
+  for (uint64_t x : w) { h ^= x; h *= 1099511628211ull; }
+  return h;
+}
+
 // One synchronous step of every voxel (Sec 2.1: all forces, then all positions).
 template <class R> static int step(Sim<R>& S) {
   const Topo& T = S.T;
@@ -597,6 +609,7 @@ template <class R> static int step(Sim<R>& S) {
         R hj = R(0.5 * l) * (R(1.0) + R(S.cte[j]) * dT[j]);
         R c = h + hj;
         if (!(r < c)) continue;
+        S.events = fold_event(S.events, S.n, v, j, 1);
         V3<R> nh = d * (R(1.0) / r);
         R kc = R(2.0) * S.E[v] * S.E[j] / (S.E[v] + S.E[j]) * R(l);
         // READING (force law not given): penalty spring on the overlap plus
@@ -618,14 +631,16 @@ template <class R> static int step(Sim<R>& S) {
         R vl = sqrt(vel.x * vel.x + vel.y * vel.y);
         R mus = R(S.mus[v]) * Fn, mud = R(S.muk[v]) * Fn;
         bool zero_l = false;
+        int branch;
         if (statn[v]) {
-          if (Fl <= mus) zero_l = true;                 // held by static friction
-          else { statn[v] = 0; F.x -= mud * Flx / Fl; F.y -= mud * Fly / Fl; }
+          if (Fl <= mus) { zero_l = true; branch = 2; }   // held by static friction
+          else { statn[v] = 0; F.x -= mud * Flx / Fl; F.y -= mud * Fly / Fl; branch = 3; }
         } else {
-          if (vl <= mud * R(dt / m) && Fl <= mus) { zero_l = true; statn[v] = 1; }  // halt
-          else if (vl > R(0.0)) { F.x -= mud * vel.x / vl; F.y -= mud * vel.y / vl; }
-          else { F.x -= mud * Flx / Fl; F.y -= mud * Fly / Fl; }
+          if (vl <= mud * R(dt / m) && Fl <= mus) { zero_l = true; statn[v] = 1; branch = 4; }  // halt
+          else if (vl > R(0.0)) { F.x -= mud * vel.x / vl; F.y -= mud * vel.y / vl; branch = 5; }
+          else { F.x -= mud * Flx / Fl; F.y -= mud * Fly / Fl; branch = 6; }
         }
+        S.events = fold_event(S.events, S.n, v, -1, branch);
         if (zero_l) { F.x = R(0.0); F.y = R(0.0); Pv.x = R(0.0); Pv.y = R(0.0); }
       } else {
         statn[v] = 0;
@@ -680,6 +695,7 @@ template <class R> static void reset_state(Sim<R>& S, const double* v0) {
   S.n = 0;
   S.acc.assign(S.T.n_bodies, 0.0);
   S.partners.assign(N, {});
+  S.events = 1469598103934665603ull;
 }
 
 // Elastic energy of the bonds: 1/2 u^T K u in each bond's reduced frame.
@@ -912,6 +928,8 @@ long orc_candidate_pairs(orc_sim* o, int32_t* pairs, long cap) {
 }
 
 long orc_n_rebuilds(orc_sim* o) { return o->S.n_rebuilds; }
+// Signature of the discrete decisions since the last reset (see Sim::events).
+uint64_t orc_event_signature(orc_sim* o) { return o->S.events; }
 double orc_accumulator(orc_sim* o, int body) { return o->S.acc[body]; }
 
 // Candidate pairs (i<j, sorted) for given anchor offsets o (N x 3 doubles,

@@ -138,6 +138,7 @@ struct vx_sim {
   int res_ok = -1;            // -1 not planned for res_cfg, 0 not possible, 1 planned
   uint64_t res_cfg = ~0ull;
   int res_C = 0, res_cap = 0, res_grid = 0;
+  bool res_per_voxel = false;  // bond phase split: thread per voxel (many groups) or per bond (one wave)
   size_t res_smem = 0;
   int32_t* r_grp = nullptr;
   int32_t* r_cls = nullptr;
@@ -565,6 +566,10 @@ int ensure_nbr(vx_sim* s) {
   return VX_OK;
 }
 
+bool is_resident(int64_t g) {
+  return g == VX_GROUPS_RESIDENT || g == VX_GROUPS_RESIDENT_BOND || g == VX_GROUPS_RESIDENT_VOXEL;
+}
+
 // Plans the resident form for the current model: the slice capacity from
 // the device's shared memory, the cluster size from the largest body (a
 // power of two up to 16; wider when there are few groups, so a small lattice
@@ -628,6 +633,11 @@ int ensure_resident(vx_sim* s) {
   s->res_C = C;
   s->res_cap = cap;
   s->res_grid = n_cl * C;
+  // one wave of groups is latency-bound: a thread per bond shortens the
+  // chain of each phase; with more groups than clusters a thread per voxel
+  // evaluates the rotation once for three bonds
+  s->res_per_voxel = s->group_voxels == VX_GROUPS_RESIDENT_VOXEL ||
+                     (s->group_voxels != VX_GROUPS_RESIDENT_BOND && ng > n_cl);
   s->res_smem = smem;
   s->res_ok = 1;
   return VX_OK;
@@ -981,15 +991,19 @@ int vx_set_batching(vx_sim* s, int64_t group_voxels) {
   if (s) ++s->cfg;  // invalidates a captured graph
   int rc = check_sim(s);
   if (rc) return rc;
-  if (group_voxels == VX_GROUPS_RESIDENT) {
+  if (is_resident(group_voxels)) {
     if (s->form == VX_FORM_TWO_PASS) return fail(VX_ERR_STATE, "the resident form needs a fused form");
-    if ((rc = ensure_resident(s))) return rc;
-    if (s->res_ok != 1)
+    const int64_t prev = s->group_voxels;
+    s->group_voxels = group_voxels;  // the plan reads the requested split
+    s->res_ok = -1;
+    if ((rc = ensure_resident(s))) { s->group_voxels = prev; return rc; }
+    if (s->res_ok != 1) {
+      s->group_voxels = prev;
       return fail(VX_ERR_STATE, "the resident form does not fit this lattice (a body above 16 CTAs' shared memory)");
-    s->group_voxels = group_voxels;
+    }
     return retile(s, s->tile_max);
   }
-  if (group_voxels < 0) return fail(VX_ERR_ARG, "group_voxels must be >= 0 or VX_GROUPS_RESIDENT");
+  if (group_voxels < 0) return fail(VX_ERR_ARG, "group_voxels must be >= 0 or one of VX_GROUPS_RESIDENT*");
   if (group_voxels > 0 && s->form == VX_FORM_TWO_PASS) return fail(VX_ERR_STATE, "batching needs a fused form");
   if (s->tile_max == 512 && group_voxels > 0) return fail(VX_ERR_ARG, "batching takes tiles of 128 or 256 voxels");
   s->group_voxels = group_voxels;
@@ -1309,13 +1323,13 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   if (n < 0) return fail(VX_ERR_ARG, "n_steps must be >= 0");
   if (n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps too large for one call");
   cudaStream_t st = (cudaStream_t)stream;
-  if (s->group_voxels == VX_GROUPS_RESIDENT && !s->collide_on && n > 0) {
+  if (is_resident(s->group_voxels) && !s->collide_on && n > 0) {
     // resident form: all n steps in one launch, state in cluster shared memory
     if ((rc = ensure_resident(s))) return rc;
     if (s->res_ok != 1) return fail(VX_ERR_STATE, "the resident form does not fit this lattice");
     StepArgs A = step_args(s);
     ResArgs R = res_args(s, n);
-    const cudaError_t e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, st);
+    const cudaError_t e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, s->res_per_voxel, st);
     if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
     s->cur ^= (int)(n & 1);
     s->step += n;
@@ -1619,7 +1633,7 @@ int vx_graph_capture(vx_sim* s, int64_t n, void* stream) {
   if (n < 1 || n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps must be in [1, 2^31)");
   if (s->group_voxels == 0) return fail(VX_ERR_STATE, "graph capture takes the batched form (vx_set_batching)");
   if (s->collide_on) return fail(VX_ERR_STATE, "the batched form has no voxel-voxel collisions");
-  const bool res = s->group_voxels == VX_GROUPS_RESIDENT;
+  const bool res = is_resident(s->group_voxels);
   if (res) {
     if ((rc = ensure_resident(s))) return rc;  // before step_args: it may allocate the neighbour planes
     if (s->res_ok != 1) return fail(VX_ERR_STATE, "the resident form does not fit this lattice");
@@ -1640,7 +1654,7 @@ int vx_graph_capture(vx_sim* s, int64_t n, void* stream) {
   cudaGraphExec_t ge = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    if (res) e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, cs);
+    if (res) e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, s->res_per_voxel, cs);
     else launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, cs);
     const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;

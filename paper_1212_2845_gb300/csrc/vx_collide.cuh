@@ -122,8 +122,12 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
 // hash bucket of neighbour cell l (dx, dy, dz = l mod 3, l / 3 mod 3, l / 9,
 // each minus 1), so a search costs one bucket's chain of loads instead of
 // 27 in a row.  The lanes' finds are gathered in the warp's shared buffer
-// (kCandCap ints), sorted ascending by canonical index and written out.
-constexpr int kLaneCap = 16;  // finds per neighbour cell (a cell holds about 8 voxels)
+// (kCandCap ints), sorted ascending by canonical index and written out.  A
+// lane holds at most kLaneCap finds (a cell of non-overlapping voxels holds
+// at most 8); if a cell yields more, lane 0 searches the voxel again alone
+// (query_one), so the lists and the overflow report are those of the
+// 48-candidate limit either way.
+constexpr int kLaneCap = 16;
 
 __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane, int* buf) {
   const int v = C.surf[s];
@@ -160,6 +164,11 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
       if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
       if (n < kLaneCap) mine[n++] = u; else overflow = true;
     }
+  }
+  if (__any_sync(0xffffffffu, overflow)) {  // a crowded cell: the one-thread search
+    if (lane == 0) query_one(C, s);
+    __syncwarp();
+    return;
   }
   // offsets of the lanes' finds in the buffer (prefix sum over the warp)
   int inc = n;

@@ -5,22 +5,32 @@
 // all n steps of a launch: each CTA of the cluster holds a contiguous slice
 // of the group's voxels (state, bond results, material properties, the
 // neighbour table), loaded once at the start and written back once at the
-// end.  A step is two phases separated by cluster barriers:
+// end.  A step is two phases separated by cluster barriers, in one of two
+// work splits:
 //
-//   bonds   one thread per bond (voxel u, lattice axis a, u on the negative
-//           side) evaluates the co-rotational beam with the partner's state
-//           read from whichever CTA of the cluster holds it (distributed
-//           shared memory) and stores F1, M1, M2 in u's slot for axis a;
-//   voxels  one thread per voxel sums its +x, +y, +z slots and the -x, -y, -z
-//           slots of its neighbours in the order of the per-step kernels,
-//           runs the voxel update and writes the new state in place, then
-//           the voxel's thermal strain for the next step.
+//   BOND (latency: a small lattice spread over a cluster)
+//     bonds   one thread per bond (voxel u, lattice axis a, u on the
+//             negative side) evaluates the co-rotational beam with the
+//             partner's state read from whichever CTA of the cluster holds it
+//             (distributed shared memory) and stores F1, M1, M2 in u's slot;
+//     voxels  one thread per voxel sums its +x, +y, +z slots and the -x, -y,
+//             -z slots of its neighbours in the order of the per-step kernels
+//             and runs the voxel update;
+//   VOXEL (throughput: many groups)
+//     bonds   one thread per voxel evaluates its own +x, +y, +z bonds with its
+//             rotation matrix computed once, keeps the sums of F1 and M1 in
+//             its own slot and stores F1, M2 for the partners;
+//     voxels  the same voxel adds its neighbours' -x, -y, -z results and runs
+//             the voxel update.
 //
-// No bond result, state or property touches global memory between the two
-// loads, and no grid-wide barrier or launch separates the steps.  Clusters
-// take their groups one after the other (longest first onto the least loaded
-// cluster, planned on the host); there are no voxel-voxel collisions in this
-// form (bodies are independent worlds; the floor is fine).
+// Either way every bond is evaluated once (no halo copies), the state is
+// updated in place, and the voxel's thermal strain for the next step is
+// written at the end of the voxel phase.  No bond result, state or property
+// touches global memory between the two loads, and no grid-wide barrier or
+// launch separates the steps.  Clusters take their groups one after the
+// other (longest first onto the least loaded cluster, planned on the host);
+// there are no voxel-voxel collisions in this form (bodies are independent
+// worlds; the floor is fine).
 #include <cooperative_groups.h>
 
 #include "vx_dev.cuh"
@@ -34,9 +44,12 @@ constexpr int kLocBits = 11;                 // neighbour entry: rank << 11 | lo
 constexpr uint16_t kNoNb = 0xFFFF;
 
 // One CTA's slice of a group in shared memory (capacity V voxels).  Bond
-// slots are [3][V] per array, axis-major: (F1.x, F1.y, F1.z, M2.x),
-// (M2.y, M2.z, M1.x, M1.y), M1.z, so a neighbour's -a gather (F1 and M2)
-// reads one float4 and one float2.
+// slots are [3][V] per array, axis-major: sa (F1.x, F1.y, F1.z, M2.x),
+// sb (M2.y, M2.z, M1.x, M1.y), sc M1.z, so a neighbour's -a gather (F1 and
+// M2) reads one float4 and one float2.  The VOXEL split stores no M1 per
+// bond; there the voxel's own sums F and M of its +x, +y, +z bonds take the
+// freed places: F.x, F.y in the last two floats of sb[2V + u], F.z in
+// sc[u], M.x in sc[V + u], M.y in sc[2V + u], M.z in sb[V + u].z.
 struct ResSmem {
   float4 *A, *B, *C;   // state planes (as in global memory)
   float* D;
@@ -88,7 +101,43 @@ __device__ __forceinline__ float act_phase_of(int64_t step, int64_t P) {
   return P > 0 ? (float)(6.283185307179586 * (double)(step % P) / (double)P) : 0.f;
 }
 
-template <bool FX>
+// State and properties of slot k2 of cluster rank r2: shared-memory loads
+// when it is this CTA, distributed shared memory otherwise.
+__device__ __forceinline__ void partner(const cg::cluster_group& cl, const ResSmem& S, int rank, int r2, int k2,
+                                        VoxS& s2, float4& p2) {
+  if (r2 == rank) {
+    s2 = S.vox(k2);
+    p2 = S.pr[k2];
+    return;
+  }
+  const float4* A2 = cl.map_shared_rank(S.A, r2);
+  const float4* B2 = cl.map_shared_rank(S.B, r2);
+  const float4* C2 = cl.map_shared_rank(S.C, r2);
+  const float* D2 = cl.map_shared_rank(S.D, r2);
+  s2 = unpack_vox(A2[k2], B2[k2], C2[k2], D2[k2]);
+  p2 = cl.map_shared_rank(S.pr, r2)[k2];
+}
+
+// F1 and M2 of the -a bond of a voxel, stored by its neighbour (slot k2 of rank r2).
+__device__ __forceinline__ void minus_result(const cg::cluster_group& cl, const ResSmem& S, int rank, int r2, int k2,
+                                             int a, int V, float4& f, float2& h) {
+  if (r2 == rank) {
+    f = S.sa[a * V + k2];
+    h = *reinterpret_cast<const float2*>(S.sb + a * V + k2);
+    return;
+  }
+  f = cl.map_shared_rank(S.sa, r2)[a * V + k2];
+  h = *reinterpret_cast<const float2*>(cl.map_shared_rank(S.sb, r2) + a * V + k2);
+}
+
+__device__ __forceinline__ BondK res_consts(const StepArgs& A, const ResSmem& S, float4 p1, float4 p2) {
+  const int m1 = __float_as_int(p1.w), m2 = __float_as_int(p2.w);
+  if (A.lut) return lut_consts(S.lut, A.n_mats, m1, m2);
+  return bond_consts(A.l, p1.x, p2.x, p1.y, p2.y, fminf(S.mats[m1].m, S.mats[m2].m), fminf(S.mats[m1].I, S.mats[m2].I),
+                     A.zb);
+}
+
+template <bool FX, bool PER_VOXEL>
 __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs R) {
   extern __shared__ __align__(16) float smem[];
   cg::cluster_group cl = cg::this_cluster();
@@ -157,50 +206,87 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
     for (int k = 0; k < R.n_steps; ++k) {
       StepArgs A = A0;
       A.step = step0 + k;
-      // ---- bonds: thread per (axis, voxel) with the voxel on the negative side
-      for (int bi = tid; bi < 3 * ns; bi += T) {
-        const int a = (bi >= ns) + (bi >= 2 * ns);
-        const int u = bi - a * ns;
-        const uint16_t e = S.nb[(2 * a + 1) * V + u];
-        if (e == kNoNb) continue;
-        const int r2 = e >> kLocBits, k2 = e & ((1 << kLocBits) - 1);
-        const float4* A2 = cl.map_shared_rank(S.A, r2);
-        const float4* B2 = cl.map_shared_rank(S.B, r2);
-        const float4* C2 = cl.map_shared_rank(S.C, r2);
-        const float* D2 = cl.map_shared_rank(S.D, r2);
-        const float4* P2 = cl.map_shared_rank(S.pr, r2);
-        const VoxS s1 = S.vox(u);
-        const VoxS s2 = unpack_vox(A2[k2], B2[k2], C2[k2], D2[k2]);
-        const float4 p1 = S.pr[u], p2 = P2[k2];
-        const int m1 = __float_as_int(p1.w), m2 = __float_as_int(p2.w);
-        const BondK bk = A.lut ? lut_consts(S.lut, A.n_mats, m1, m2)
-                               : bond_consts(A.l, p1.x, p2.x, p1.y, p2.y, fminf(S.mats[m1].m, S.mats[m2].m),
-                                             fminf(S.mats[m1].I, S.mats[m2].I), A.zb);
-        const BondOut o = bond_eval_r(s1, qmat(s1.q), s2, A.l, bk, mul_(0.5f, add_(p1.z, p2.z)), damp, a);
-        S.sa[a * V + u] = make_float4(o.F1.x, o.F1.y, o.F1.z, o.M2.x);
-        S.sb[a * V + u] = make_float4(o.M2.y, o.M2.z, o.M1.x, o.M1.y);
-        S.sc[a * V + u] = o.M1.z;
+      if (!PER_VOXEL) {
+        // ---- bonds: thread per (axis, voxel) with the voxel on the negative side
+        for (int bi = tid; bi < 3 * ns; bi += T) {
+          const int a = (bi >= ns) + (bi >= 2 * ns);
+          const int u = bi - a * ns;
+          const uint16_t e = S.nb[(2 * a + 1) * V + u];
+          if (e == kNoNb) continue;
+          VoxS s2;
+          float4 p2;
+          partner(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);
+          const VoxS s1 = S.vox(u);
+          const float4 p1 = S.pr[u];
+          const BondOut o = bond_eval_r(s1, qmat(s1.q), s2, A.l, res_consts(A, S, p1, p2),
+                                        mul_(0.5f, add_(p1.z, p2.z)), damp, a);
+          S.sa[a * V + u] = make_float4(o.F1.x, o.F1.y, o.F1.z, o.M2.x);
+          S.sb[a * V + u] = make_float4(o.M2.y, o.M2.z, o.M1.x, o.M1.y);
+          S.sc[a * V + u] = o.M1.z;
+        }
+      } else {
+        // ---- bonds: thread per voxel, its own +x, +y, +z bonds
+        for (int u = tid; u < ns; u += T) {
+          const VoxS s1 = S.vox(u);
+          const float4 p1 = S.pr[u];
+          const M3f R1 = qmat(s1.q);
+          V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
+#define VX_RES_BOND(AX)                                                                                     \
+          {                                                                                                 \
+            const uint16_t e = S.nb[(2 * AX + 1) * V + u];                                                  \
+            if (e != kNoNb) {                                                                               \
+              VoxS s2;                                                                                      \
+              float4 p2;                                                                                    \
+              partner(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);                       \
+              const BondOut o = bond_eval<AX>(s1, R1, s2, A.l, res_consts(A, S, p1, p2),                    \
+                                              mul_(0.5f, add_(p1.z, p2.z)), damp);                           \
+              F = add(F, o.F1);                                                                             \
+              M = add(M, o.M1);                                                                             \
+              S.sa[AX * V + u] = make_float4(o.F1.x, o.F1.y, o.F1.z, o.M2.x);                               \
+              *reinterpret_cast<float2*>(S.sb + AX * V + u) = make_float2(o.M2.y, o.M2.z);                  \
+            }                                                                                               \
+          }
+          VX_RES_BOND(0)
+          VX_RES_BOND(1)
+          VX_RES_BOND(2)
+#undef VX_RES_BOND
+          // own sums in the unused halves of the z-axis plane of sb and in sc
+          reinterpret_cast<float2*>(S.sb + 2 * V + u)[1] = make_float2(F.x, F.y);
+          S.sc[u] = F.z;
+          S.sc[V + u] = M.x;
+          S.sc[2 * V + u] = M.y;
+          reinterpret_cast<float2*>(S.sb + V + u)[1] = make_float2(M.z, 0.f);
+        }
       }
       cl.sync();
       // ---- voxels: the per-step kernels' summation order (+x, +y, +z own
       // bonds, then the -x, -y, -z bonds of the neighbours), then the update
       const float w_next = act_phase_of(step0 + k + 1, R.act_P);
       for (int u = tid; u < ns; u += T) {
-        V3f F = v3(0.f, 0.f, 0.f), M = v3(0.f, 0.f, 0.f);
+        V3f F, M;
+        if (!PER_VOXEL) {
+          F = v3(0.f, 0.f, 0.f);
+          M = v3(0.f, 0.f, 0.f);
 #pragma unroll
-        for (int a = 0; a < 3; ++a)
-          if (S.nb[(2 * a + 1) * V + u] != kNoNb) {
-            const float4 f = S.sa[a * V + u], h = S.sb[a * V + u];
-            F = add(F, v3(f.x, f.y, f.z));
-            M = add(M, v3(h.z, h.w, S.sc[a * V + u]));
-          }
+          for (int a = 0; a < 3; ++a)
+            if (S.nb[(2 * a + 1) * V + u] != kNoNb) {
+              const float4 f = S.sa[a * V + u], h = S.sb[a * V + u];
+              F = add(F, v3(f.x, f.y, f.z));
+              M = add(M, v3(h.z, h.w, S.sc[a * V + u]));
+            }
+        } else {
+          const float2 fxy = reinterpret_cast<const float2*>(S.sb + 2 * V + u)[1];
+          const float2 mz = reinterpret_cast<const float2*>(S.sb + V + u)[1];
+          F = v3(fxy.x, fxy.y, S.sc[u]);
+          M = v3(S.sc[V + u], S.sc[2 * V + u], mz.x);
+        }
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const uint16_t e = S.nb[2 * a * V + u];
           if (e != kNoNb) {
-            const int r2 = e >> kLocBits, k2 = e & ((1 << kLocBits) - 1);
-            const float4 f = cl.map_shared_rank(S.sa, r2)[a * V + k2];
-            const float2 h = *reinterpret_cast<const float2*>(cl.map_shared_rank(S.sb, r2) + a * V + k2);
+            float4 f;
+            float2 h;
+            minus_result(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), a, V, f, h);
             F = sub(F, v3(f.x, f.y, f.z));  // F - F1 is F + (-F1) exactly
             M = add(M, v3(f.w, h.x, h.y));
           }
@@ -241,7 +327,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
   }
 }
 
-template <bool FX> cudaLaunchConfig_t res_config(int grid, int C, size_t smem, cudaStream_t s, cudaLaunchAttribute* at) {
+cudaLaunchConfig_t res_config(int grid, int C, size_t smem, cudaStream_t s, cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kResThreads);
@@ -256,13 +342,13 @@ template <bool FX> cudaLaunchConfig_t res_config(int grid, int C, size_t smem, c
   return cfg;
 }
 
-template <bool FX> int prepare_res_t(int C, size_t smem, int* max_clusters) {
-  auto* k = res_pipe<FX>;
+template <bool FX, bool PV> int prepare_res_t(int C, size_t smem, int* max_clusters) {
+  auto* k = res_pipe<FX, PV>;
   cudaError_t e = allow_smem(k, smem);
   if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) { cudaGetLastError(); return -1; }
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = res_config<FX>(C, C, smem, 0, at);
+  cudaLaunchConfig_t cfg = res_config(C, C, smem, 0, at);
   int n = 0;
   e = cudaOccupancyMaxActiveClusters(&n, (const void*)k, &cfg);
   if (e != cudaSuccess) { cudaGetLastError(); return -1; }
@@ -270,22 +356,28 @@ template <bool FX> int prepare_res_t(int C, size_t smem, int* max_clusters) {
   return n > 0 ? 0 : -1;
 }
 
+template <bool FX> int prepare_res_both(int C, size_t smem, int* max_clusters) {
+  int a = 0, b = 0;
+  if (prepare_res_t<FX, false>(C, smem, &a) != 0 || prepare_res_t<FX, true>(C, smem, &b) != 0) return -1;
+  *max_clusters = a < b ? a : b;
+  return 0;
+}
+
 }  // namespace
 
 size_t res_smem_bytes(int cap, bool fext, int n_mats, bool lut) { return ResSmem::bytes(cap, fext, n_mats, lut); }
 
 int prepare_resident(int C, size_t smem, bool fext, int* max_clusters) {
-  return fext ? prepare_res_t<true>(C, smem, max_clusters) : prepare_res_t<false>(C, smem, max_clusters);
+  return fext ? prepare_res_both<true>(C, smem, max_clusters) : prepare_res_both<false>(C, smem, max_clusters);
 }
 
-cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, size_t smem, cudaStream_t s) {
+cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, size_t smem, bool per_voxel,
+                            cudaStream_t s) {
   cudaLaunchAttribute at[1];
-  if (A.fext) {
-    cudaLaunchConfig_t cfg = res_config<true>(grid, C, smem, s, at);
-    return cudaLaunchKernelEx(&cfg, res_pipe<true>, A, R);
-  }
-  cudaLaunchConfig_t cfg = res_config<false>(grid, C, smem, s, at);
-  return cudaLaunchKernelEx(&cfg, res_pipe<false>, A, R);
+  cudaLaunchConfig_t cfg = res_config(grid, C, smem, s, at);
+  if (A.fext)
+    return per_voxel ? cudaLaunchKernelEx(&cfg, res_pipe<true, true>, A, R) : cudaLaunchKernelEx(&cfg, res_pipe<true, false>, A, R);
+  return per_voxel ? cudaLaunchKernelEx(&cfg, res_pipe<false, true>, A, R) : cudaLaunchKernelEx(&cfg, res_pipe<false, false>, A, R);
 }
 
 }  // namespace vx

@@ -19,7 +19,9 @@ ERRORS = {-1: "VX_ERR_ARG", -2: "VX_ERR_CUDA", -3: "VX_ERR_OOM", -4: "VX_ERR_UNS
           -5: "VX_ERR_TIMEOUT", -6: "VX_ERR_STATE", -7: "VX_ERR_CAPACITY"}
 FLAG_FIXED = 1
 FLAG_STATIC = 2
-GROUPS_RESIDENT = -1    # vx_set_batching: the shared-memory-resident form
+GROUPS_RESIDENT = -1    # vx_set_batching: the shared-memory-resident form (split chosen automatically)
+GROUPS_RESIDENT_BOND = -2   # ... with one thread per bond in the bond phase
+GROUPS_RESIDENT_VOXEL = -3  # ... with one thread per voxel in the bond phase
 
 
 class VxError(RuntimeError):

@@ -6,7 +6,8 @@ lattice spread over a cluster of 8 CTAs (the cantilever), on a population
 of uneven bodies (several groups per cluster), on design bodies with
 per-voxel stiffness (one body across a cluster of two CTAs), on one large
 body across a wider cluster, with external forces, through captured graph
-replays, and on the FP64 oracle's trajectory within the stated tolerance."""
+replays, and on the FP64 oracle's trajectory within the stated tolerance, with the
+bond phase split either way (a thread per bond or a thread per voxel)."""
 import numpy as np
 import pytest
 
@@ -53,13 +54,15 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("split", ["auto", "bond", "voxel"])
 @pytest.mark.parametrize("which", list(CASES))
-def test_resident_form_bitwise_equals_per_step_launches(vx, which):
+def test_resident_form_bitwise_equals_per_step_launches(vx, which, split):
     mk, steps = CASES[which]
     sc = mk()
     ref = per_step(vx, sc, steps)
     sim = vx.Sim(sc)
-    sim.set_batching(vx.GROUPS_RESIDENT)
+    sim.set_batching({"auto": vx.GROUPS_RESIDENT, "bond": vx.GROUPS_RESIDENT_BOND,
+                      "voxel": vx.GROUPS_RESIDENT_VOXEL}[split])
     sim.step(steps // 3)                       # two launches (odd and even step counts)
     sim.step(steps - steps // 3)
     assert sim.status()[0] == 0
