@@ -137,7 +137,7 @@ struct vx_sim {
   // cluster for all steps of a launch (planned per model configuration)
   int res_ok = -1;            // -1 not planned for res_cfg, 0 not possible, 1 planned
   uint64_t res_cfg = ~0ull;
-  int res_C = 0, res_cap = 0, res_grid = 0;
+  int res_C = 0, res_cap = 0, res_grid = 0, res_threads = 0;
   bool res_per_voxel = false;  // bond phase split: thread per voxel (many groups) or per bond (one wave)
   size_t res_smem = 0;
   int32_t* r_grp = nullptr;
@@ -570,10 +570,15 @@ bool is_resident(int64_t g) {
   return g == VX_GROUPS_RESIDENT || g == VX_GROUPS_RESIDENT_BOND || g == VX_GROUPS_RESIDENT_VOXEL;
 }
 
-// Plans the resident form for the current model: the slice capacity from
-// the device's shared memory, the cluster size from the largest body (a
-// power of two up to 16; wider when there are few groups, so a small lattice
-// spreads over up to 8 SMs), the groups and their clusters.  Sets res_ok.
+// Plans the resident form for the current model.  Split: a thread per bond
+// when every group gets a cluster of its own (one wave: the phases' chains
+// set the time), else a thread per voxel.  Slice capacity: 1,024 voxels per
+// CTA for the per-bond split (a small lattice spread over up to 8 CTAs);
+// 512 for the per-voxel split where the largest body allows it, so that two
+// CTAs share an SM and one computes while the other waits at its cluster
+// barrier, with as many threads as half the largest slice (two voxels per
+// thread).  Cluster size: the smallest power of two that holds the largest
+// body (at most 16).  Sets res_ok.
 int ensure_resident(vx_sim* s) {
   if (s->res_cfg == s->cfg && s->res_ok >= 0) return VX_OK;
   s->res_cfg = s->cfg;
@@ -587,10 +592,6 @@ int ensure_resident(vx_sim* s) {
   VX_CUDA(cudaGetDevice(&dev));
   VX_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
   VX_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  int cap = 1024;
-  while (cap > 64 && res_smem_bytes(cap, fext, nm, lut) > (size_t)optin) cap -= 32;
-  const size_t smem = res_smem_bytes(cap, fext, nm, lut);
-  if (smem > (size_t)optin) return VX_OK;
   // bodies' internal voxel ranges (bodies are contiguous in the internal order)
   std::vector<int64_t> bs(L.n_bodies + 1, L.N);
   {
@@ -603,19 +604,38 @@ int ensure_resident(vx_sim* s) {
   }
   int64_t max_body = 0;
   for (int b = 0; b < L.n_bodies; ++b) max_body = std::max(max_body, bs[b + 1] - bs[b]);
-  int C = 1;
-  while ((int64_t)C * cap < max_body) C *= 2;
+  auto cluster_for = [&](int cap) { int C = 1; while ((int64_t)C * cap < max_body) C *= 2; return C; };
+  int cap = 1024;
+  while (cap > 64 && res_smem_bytes(cap, fext, nm, lut) > (size_t)optin) cap -= 32;
+  if (res_smem_bytes(cap, fext, nm, lut) > (size_t)optin) return VX_OK;
+  int C = cluster_for(cap);
   if (C > 16) return VX_OK;
   ResPlan P;
-  if (!plan_resident(bs, (int64_t)C * cap, 1, P)) return VX_OK;
-  while (C < 8 && (int64_t)(P.grp_start.size() - 1) * C * 2 <= n_sm) {
-    C *= 2;
+  plan_resident(bs, (int64_t)C * cap, 1, P);
+  const int64_t ng1 = (int64_t)P.grp_start.size() - 1;
+  bool per_voxel;
+  if (s->group_voxels == VX_GROUPS_RESIDENT_VOXEL) per_voxel = true;
+  else if (s->group_voxels == VX_GROUPS_RESIDENT_BOND) per_voxel = false;
+  else per_voxel = ng1 * C > n_sm;  // more groups than one wave of clusters
+  int threads = kResThreads;
+  if (per_voxel) {
+    if (cluster_for(512) <= 16) { cap = 512; C = cluster_for(cap); }
+    plan_resident(bs, (int64_t)C * cap, 1, P);
+    int64_t max_slice = 0;
+    for (size_t g = 0; g + 1 < P.grp_start.size(); ++g)
+      max_slice = std::max<int64_t>(max_slice, (P.grp_start[g + 1] - P.grp_start[g] + C - 1) / C);
+    threads = (int)std::min<int64_t>(kResThreads, std::max<int64_t>(32, ((max_slice + 1) / 2 + 31) / 32 * 32));
+  } else {
+    while (C < 8 && ng1 * C * 2 <= n_sm) C *= 2;  // spread a small lattice over more SMs
     plan_resident(bs, (int64_t)C * cap, 1, P);
   }
+  const size_t smem = res_smem_bytes(cap, fext, nm, lut);
   int max_cl = 0;
   for (;;) {
     max_cl = 0;
-    if (prepare_resident(C, smem, fext, &max_cl) == 0 || C == 1 || (int64_t)(C / 2) * cap < max_body) break;
+    if (prepare_resident(C, threads, smem, fext, per_voxel, &max_cl) == 0 || C == 1 ||
+        (int64_t)(C / 2) * cap < max_body)
+      break;
     C /= 2;
   }
   if (max_cl < 1) return VX_OK;
@@ -632,13 +652,10 @@ int ensure_resident(vx_sim* s) {
   VX_CUDA(cudaMemcpy(s->r_clg, P.cl_groups.data(), P.cl_groups.size() * 4, cudaMemcpyHostToDevice));
   s->res_C = C;
   s->res_cap = cap;
+  s->res_threads = threads;
   s->res_grid = n_cl * C;
-  // one wave of groups is latency-bound: a thread per bond shortens the
-  // chain of each phase; with more groups than clusters a thread per voxel
-  // evaluates the rotation once for three bonds
-  s->res_per_voxel = s->group_voxels == VX_GROUPS_RESIDENT_VOXEL ||
-                     (s->group_voxels != VX_GROUPS_RESIDENT_BOND && ng > n_cl);
   s->res_smem = smem;
+  s->res_per_voxel = per_voxel;
   s->res_ok = 1;
   return VX_OK;
 }
@@ -1329,7 +1346,7 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     if (s->res_ok != 1) return fail(VX_ERR_STATE, "the resident form does not fit this lattice");
     StepArgs A = step_args(s);
     ResArgs R = res_args(s, n);
-    const cudaError_t e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, s->res_per_voxel, st);
+    const cudaError_t e = launch_resident(A, R, s->res_grid, s->res_C, s->res_threads, s->res_smem, s->res_per_voxel, st);
     if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("resident launch: ") + cudaGetErrorString(e));
     s->cur ^= (int)(n & 1);
     s->step += n;
@@ -1654,7 +1671,7 @@ int vx_graph_capture(vx_sim* s, int64_t n, void* stream) {
   cudaGraphExec_t ge = nullptr;
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    if (res) e = launch_resident(A, R, s->res_grid, s->res_C, s->res_smem, s->res_per_voxel, cs);
+    if (res) e = launch_resident(A, R, s->res_grid, s->res_C, s->res_threads, s->res_smem, s->res_per_voxel, cs);
     else launch_batched(A, Bt, s->tile_max, s->pipe_smem, s->pipe_grid, cs);
     const cudaError_t e2 = cudaStreamEndCapture(cs, &g);
     if (e == cudaSuccess) e = e2;

@@ -132,14 +132,14 @@ struct ResArgs {
   int cap;                     // voxels per CTA slice (shared memory layout)
 };
 size_t res_smem_bytes(int cap, bool fext, int n_mats, bool lut);
-// Raises the kernel's limits for clusters of C CTAs and returns how many
-// such clusters can be resident at once; 0 on success.
-int prepare_resident(int C, size_t smem, bool fext, int* max_clusters);
+// Raises the kernel's limits for clusters of C CTAs of `threads` threads
+// (at most kResThreads) and returns how many such clusters can be resident
+// at once; 0 on success.  per_voxel: one thread per voxel in the bond phase
+// (its own +x, +y, +z bonds, rotation matrix once), else one thread per bond.
+int prepare_resident(int C, int threads, size_t smem, bool fext, bool per_voxel, int* max_clusters);
 // Needs A.nbr (internal neighbour planes); grid is a multiple of C.
-// per_voxel: one thread per voxel in the bond phase (its own +x, +y, +z
-// bonds, rotation matrix once), else one thread per bond.
-cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, size_t smem, bool per_voxel,
-                            cudaStream_t s);
+cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, int threads, size_t smem,
+                            bool per_voxel, cudaStream_t s);
 cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s);
 void launch_horizon(const CollideArgs& C, cudaStream_t s);

@@ -101,11 +101,13 @@ __device__ __forceinline__ float act_phase_of(int64_t step, int64_t P) {
   return P > 0 ? (float)(6.283185307179586 * (double)(step % P) / (double)P) : 0.f;
 }
 
-// State and properties of slot k2 of cluster rank r2: shared-memory loads
-// when it is this CTA, distributed shared memory otherwise.
+// State and properties of slot k2 of cluster rank r2 through distributed
+// shared memory; with LOCAL, plain shared-memory loads when it is this CTA
+// (a branch that pays where most partners are local: large slices).
+template <bool LOCAL>
 __device__ __forceinline__ void partner(const cg::cluster_group& cl, const ResSmem& S, int rank, int r2, int k2,
                                         VoxS& s2, float4& p2) {
-  if (r2 == rank) {
+  if (LOCAL && r2 == rank) {
     s2 = S.vox(k2);
     p2 = S.pr[k2];
     return;
@@ -119,9 +121,10 @@ __device__ __forceinline__ void partner(const cg::cluster_group& cl, const ResSm
 }
 
 // F1 and M2 of the -a bond of a voxel, stored by its neighbour (slot k2 of rank r2).
+template <bool LOCAL>
 __device__ __forceinline__ void minus_result(const cg::cluster_group& cl, const ResSmem& S, int rank, int r2, int k2,
                                              int a, int V, float4& f, float2& h) {
-  if (r2 == rank) {
+  if (LOCAL && r2 == rank) {
     f = S.sa[a * V + k2];
     h = *reinterpret_cast<const float2*>(S.sb + a * V + k2);
     return;
@@ -215,7 +218,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
           if (e == kNoNb) continue;
           VoxS s2;
           float4 p2;
-          partner(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);
+          partner<false>(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);
           const VoxS s1 = S.vox(u);
           const float4 p1 = S.pr[u];
           const BondOut o = bond_eval_r(s1, qmat(s1.q), s2, A.l, res_consts(A, S, p1, p2),
@@ -237,7 +240,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
             if (e != kNoNb) {                                                                               \
               VoxS s2;                                                                                      \
               float4 p2;                                                                                    \
-              partner(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);                       \
+              partner<true>(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);                 \
               const BondOut o = bond_eval<AX>(s1, R1, s2, A.l, res_consts(A, S, p1, p2),                    \
                                               mul_(0.5f, add_(p1.z, p2.z)), damp);                           \
               F = add(F, o.F1);                                                                             \
@@ -286,7 +289,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
           if (e != kNoNb) {
             float4 f;
             float2 h;
-            minus_result(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), a, V, f, h);
+            minus_result<PER_VOXEL>(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), a, V, f, h);
             F = sub(F, v3(f.x, f.y, f.z));  // F - F1 is F + (-F1) exactly
             M = add(M, v3(f.w, h.x, h.y));
           }
@@ -327,10 +330,10 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
   }
 }
 
-cudaLaunchConfig_t res_config(int grid, int C, size_t smem, cudaStream_t s, cudaLaunchAttribute* at) {
+cudaLaunchConfig_t res_config(int grid, int C, int threads, size_t smem, cudaStream_t s, cudaLaunchAttribute* at) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
-  cfg.blockDim = dim3(kResThreads);
+  cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -342,13 +345,13 @@ cudaLaunchConfig_t res_config(int grid, int C, size_t smem, cudaStream_t s, cuda
   return cfg;
 }
 
-template <bool FX, bool PV> int prepare_res_t(int C, size_t smem, int* max_clusters) {
+template <bool FX, bool PV> int prepare_res_t(int C, int threads, size_t smem, int* max_clusters) {
   auto* k = res_pipe<FX, PV>;
   cudaError_t e = allow_smem(k, smem);
   if (e == cudaSuccess && C > 8) e = cudaFuncSetAttribute((const void*)k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
   if (e != cudaSuccess) { cudaGetLastError(); return -1; }
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = res_config(C, C, smem, 0, at);
+  cudaLaunchConfig_t cfg = res_config(C, C, threads, smem, 0, at);
   int n = 0;
   e = cudaOccupancyMaxActiveClusters(&n, (const void*)k, &cfg);
   if (e != cudaSuccess) { cudaGetLastError(); return -1; }
@@ -356,25 +359,21 @@ template <bool FX, bool PV> int prepare_res_t(int C, size_t smem, int* max_clust
   return n > 0 ? 0 : -1;
 }
 
-template <bool FX> int prepare_res_both(int C, size_t smem, int* max_clusters) {
-  int a = 0, b = 0;
-  if (prepare_res_t<FX, false>(C, smem, &a) != 0 || prepare_res_t<FX, true>(C, smem, &b) != 0) return -1;
-  *max_clusters = a < b ? a : b;
-  return 0;
-}
-
 }  // namespace
 
 size_t res_smem_bytes(int cap, bool fext, int n_mats, bool lut) { return ResSmem::bytes(cap, fext, n_mats, lut); }
 
-int prepare_resident(int C, size_t smem, bool fext, int* max_clusters) {
-  return fext ? prepare_res_both<true>(C, smem, max_clusters) : prepare_res_both<false>(C, smem, max_clusters);
+int prepare_resident(int C, int threads, size_t smem, bool fext, bool per_voxel, int* max_clusters) {
+  if (fext) return per_voxel ? prepare_res_t<true, true>(C, threads, smem, max_clusters)
+                             : prepare_res_t<true, false>(C, threads, smem, max_clusters);
+  return per_voxel ? prepare_res_t<false, true>(C, threads, smem, max_clusters)
+                   : prepare_res_t<false, false>(C, threads, smem, max_clusters);
 }
 
-cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, size_t smem, bool per_voxel,
-                            cudaStream_t s) {
+cudaError_t launch_resident(const StepArgs& A, const ResArgs& R, int grid, int C, int threads, size_t smem,
+                            bool per_voxel, cudaStream_t s) {
   cudaLaunchAttribute at[1];
-  cudaLaunchConfig_t cfg = res_config(grid, C, smem, s, at);
+  cudaLaunchConfig_t cfg = res_config(grid, C, threads, smem, s, at);
   if (A.fext)
     return per_voxel ? cudaLaunchKernelEx(&cfg, res_pipe<true, true>, A, R) : cudaLaunchKernelEx(&cfg, res_pipe<true, false>, A, R);
   return per_voxel ? cudaLaunchKernelEx(&cfg, res_pipe<false, true>, A, R) : cudaLaunchKernelEx(&cfg, res_pipe<false, false>, A, R);
