@@ -187,59 +187,107 @@ def _oracle_final_pos(args):
     return o.state()["pos"]
 
 
+def _oracle_loss_sig(args):
+    """FP64 loss of a one-body scene and the signature of the run's discrete
+    decisions (floor contact, stick/slip branch, voxel contacts)."""
+    sc, logE, phase, dt, steps = args
+    o = Oracle(sc)
+    o.set_voxel_params(logE, phase)
+    o.set_dt(dt)
+    o.reset(sc["v0"])
+    x0 = o.state()["pos"][:, 0].copy()
+    o.step(steps)
+    return float(np.mean(o.state()["pos"][:, 0] - x0)), o.event_signature()
+
+
+def _fd_jobs(cand, h):
+    bsc, le, ph, bdt, steps, which, i = cand
+    out = []
+    for sgn in (+1, -1):
+        a, b = le.copy(), ph.copy()
+        (a if which == "logE" else b)[i] += sgn * h
+        out.append((bsc, a, b, bdt, steps))
+    return out
+
+
 def test_design_population_sampled_central_differences(env):
-    """1,024 bodies of 12^3 voxels, 2,000 steps, checkpoints every 100; 64
-    gradient entries sampled over 32 bodies, each against its body's own FP64
-    oracle rollout (bodies are independent):
-      * FP64 central differences (h = 1e-5) pin the FP64 tangent (forward
-        mode) on at least 90 % of the samples; the rest straddle a friction
-        or contact event inside +-h;
-      * the GPU entry equals the FP64 tangent within 1e-3 on every body whose
-        FP32 trajectory follows the FP64 one (final positions within 1e-8 m,
-        ten times the rounding-level difference); a body where a stick/slip
-        decision fell the other way at a near-tie follows another branch and
-        is held only to 5e-2; such bodies must stay rare (at most 10 %)."""
+    """1,024 bodies of 12^3 voxels, 2,000 steps, checkpoints every 100; one
+    gradient entry in each of 64 sampled bodies, against the body's own FP64
+    oracle rollout (bodies are independent).
+
+    A central difference is the derivative only if its two runs at +-h take
+    the same discrete decisions (floor contact and its stick/slip branch per
+    voxel and step, voxel contacts).  Where the runs' event signatures differ
+    the sample is rerun at h/10; if they still differ it is replaced by the
+    next candidate.  A body whose FP32 trajectory took another branch than the
+    FP64 one at a near-tie (final positions more than 1e-8 m apart, ten times
+    the rounding-level difference) is replaced too: its adjoint is the
+    derivative of the other branch.  Every reported entry then meets, with no
+    floor on the denominators:
+      |FD - tangent| <= 1e-4 |tangent|   (finite differences pin the FP64
+                                          forward-mode tangent)
+      |GPU - tangent| <= 1e-3 |tangent|  (the FP32 adjoint)
+    The rerun and replacement counts are printed."""
     torch, vx = env
-    n, nb, steps, K = 12, 1024, 2000, 100
+    n, nb, steps, K, h, want = 12, 1024, 2000, 100, 1e-5, 64
     sc = scenes.design_population(n_bodies=nb, n=n, steps=steps)
+    sim = vx.Sim(sc)
+    dt = sim.dt()
+    _, gE, gP = gpu_grads(torch, sim, steps, K)
+    pos = sim.state()["pos"]
+    sim.close()
+    rng = np.random.default_rng(64)
+    order = [int(b) for b in rng.permutation(nb)]
+    cands = []
+    for k, b in enumerate(order):
+        bsc = body_scene(sc, b, n)
+        w = "logE" if k % 2 == 0 else "phase"
+        i = int(rng.integers(n ** 3))
+        cands.append((b, w, i, (bsc, bsc["log_E"].astype(np.float64), bsc["phase"].astype(np.float64),
+                                np.array([np.float32(dt[b])], np.float64), steps, w, i)))
+    accepted, n_branch, n_rerun, n_straddle, nxt = [], 0, 0, 0, 0
     ctx = mp.get_context("spawn")
     with ctx.Pool(min(16, mp.cpu_count())) as pool:
-        sim = vx.Sim(sc)
-        dt = sim.dt()
-        loss, gE, gP = gpu_grads(torch, sim, steps, K)
-        pos = sim.state()["pos"]
-        sim.close()
-        rng = np.random.default_rng(64)
-        bodies = [int(b) for b in rng.choice(nb, size=32, replace=False)]
-        jobs, tang, picks, finals = [], [], [], []
-        for b in bodies:
-            bsc = body_scene(sc, b, n)
-            le = bsc["log_E"].astype(np.float64)
-            ph = bsc["phase"].astype(np.float64)
-            bdt = np.array([np.float32(dt[b])], np.float64)
-            finals.append((bsc, le, ph, bdt, steps))
-            for w in ("logE", "phase"):
-                i = int(rng.integers(n ** 3))
-                jobs.append((bsc, le, ph, bdt, steps, w, i, 1e-5))
-                tang.append((bsc, le, ph, bdt, steps, w, i))
-                picks.append((b, b * n ** 3 + i, w))
-        fd = np.array(central_fd(jobs, pool))
-        jv = np.array(pool.map(_oracle_tangent, tang))
-        fpos = pool.map(_oracle_final_pos, finals)
-    g = np.array([(gE if w == "logE" else gP)[c] for _, c, w in picks])
-    scale = np.abs(jv).max()
-    den = np.maximum(np.abs(jv), 0.01 * scale)
-    fd_ok = np.abs(fd - jv) / den <= 1e-4
-    assert fd_ok.mean() >= 0.9, (fd_ok.mean(), fd[~fd_ok], jv[~fd_ok])
-    follows = {}
-    for b, fp in zip(bodies, fpos):
-        gp = pos[b * n ** 3:(b + 1) * n ** 3] - sc["origin"][b].astype(np.float64)
-        follows[b] = np.abs(gp - fp).max() <= 1e-8
-    same = np.array([follows[b] for b, _, _ in picks])
-    err = np.abs(g - jv) / den
-    assert same.mean() >= 0.9, same.mean()
-    assert err[same].max() <= REL, (err[same].max(), picks[int(np.argmax(np.where(same, err, 0)))])
-    assert err.max() <= 5e-2, err.max()
+        while len(accepted) < want:
+            batch = cands[nxt:nxt + (want - len(accepted)) + 4]
+            nxt += len(batch)
+            assert batch, "ran out of candidate bodies"
+            fin = pool.map(_oracle_final_pos, [c[3][:5] for c in batch])
+            fd1 = pool.map(_oracle_loss_sig, [j for c in batch for j in _fd_jobs(c[3], h)])
+            tan = pool.map(_oracle_tangent, [c[3] for c in batch])
+            rerun = []
+            for k, (b, w, i, cand) in enumerate(batch):
+                gp = pos[b * n ** 3:(b + 1) * n ** 3] - sc["origin"][b].astype(np.float64)
+                if np.abs(gp - fin[k]).max() > 1e-8:
+                    n_branch += 1
+                    continue
+                (lp, sp), (lm, sm) = fd1[2 * k], fd1[2 * k + 1]
+                if sp == sm:
+                    accepted.append((b, w, i, (lp - lm) / (2 * h), tan[k]))
+                else:
+                    rerun.append((k, b, w, i, cand))
+            if rerun:
+                n_rerun += len(rerun)
+                fd2 = pool.map(_oracle_loss_sig, [j for r in rerun for j in _fd_jobs(r[4], h / 10)])
+                for q, (k, b, w, i, cand) in enumerate(rerun):
+                    (lp, sp), (lm, sm) = fd2[2 * q], fd2[2 * q + 1]
+                    if sp == sm:
+                        accepted.append((b, w, i, (lp - lm) / (2 * h / 10), tan[k]))
+                    else:
+                        n_straddle += 1
+    accepted = accepted[:want]
+    fd = np.array([a[3] for a in accepted])
+    jv = np.array([a[4] for a in accepted])
+    g = np.array([(gE if w == "logE" else gP)[b * n ** 3 + i] for b, w, i, _, _ in accepted])
+    fd_err = np.abs(fd - jv) / np.abs(jv)
+    err = np.abs(g - jv) / np.abs(jv)
+    print(f"{len(accepted)} entries from {nxt} candidate bodies: {n_branch} replaced (FP32 took another "
+          f"branch), {n_rerun} rerun at h/10 (event signatures differed at h), {n_straddle} replaced (still "
+          f"differed at h/10); |tangent| from {np.abs(jv).min():.2e} to {np.abs(jv).max():.2e}; largest "
+          f"|FD - tangent| / |tangent| {fd_err.max():.2e}; largest |GPU - tangent| / |tangent| {err.max():.2e}")
+    assert n_branch + n_straddle <= 16
+    assert fd_err.max() <= 1e-4, accepted[int(np.argmax(fd_err))][:3]
+    assert err.max() <= REL, accepted[int(np.argmax(err))][:3]
 
 
 def test_checkpoint_interval_does_not_change_bits(env):
