@@ -51,6 +51,8 @@ extern "C" {
 #define VX_ERR_TIMEOUT (-5)   /* a bounded device wait ran out                     */
 #define VX_ERR_STATE (-6)     /* call not valid in the current state               */
 #define VX_ERR_CAPACITY (-7)  /* a fixed-size buffer (collision pairs) overflowed  */
+#define VX_ERR_BOUNDS (-8)    /* bounds-checked debug builds only: an index read from a device
+                                 table was out of range (the access was skipped) */
 
 typedef struct vx_sim vx_sim;
 

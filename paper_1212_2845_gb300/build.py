@@ -17,7 +17,11 @@ SRC = os.path.join(HERE, "csrc")
 # UndefinedBehaviorSanitizer into a separate folder (load the runtimes with
 # LD_PRELOAD); device code is unchanged
 SANITIZE = os.environ.get("VX_HOST_SANITIZE") == "1"
-OUT = os.path.join(HERE, "_build_san" if SANITIZE else "_build")
+# VX_BOUNDS_CHECK=1: kernels built with bounds checks on the indices they read
+# from device tables (a failed check sets a status bit and skips the access;
+# vx_step returns VX_ERR_BOUNDS) into a separate folder
+BOUNDS = os.environ.get("VX_BOUNDS_CHECK") == "1"
+OUT = os.path.join(HERE, "_build_san" if SANITIZE else ("_build_bc" if BOUNDS else "_build"))
 LIB = os.path.join(OUT, "libvx.so")
 INCLUDE = os.path.join(ROOT, "include")
 
@@ -56,7 +60,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     def compile_one(src):
         obj = os.path.join(OUT, os.path.splitext(src)[0] + ".o")
-        cmd = [exe, *ARCH, *FLAGS, *SAN_FLAGS, "-c", os.path.join(SRC, src), "-o", obj]
+        cmd = [exe, *ARCH, *FLAGS, *SAN_FLAGS, *(["-DVX_BOUNDS_CHECK"] if BOUNDS else []), "-c",
+               os.path.join(SRC, src), "-o", obj]
         if src.endswith(".cu"):
             cmd[1:1] = ["-Xptxas", "-v"] if verbose else []
         r = subprocess.run(cmd, capture_output=True, text=True)

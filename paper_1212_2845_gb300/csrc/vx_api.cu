@@ -80,6 +80,7 @@ int vx::status_code(int bits) {
   if (bits & kStatusTimeout) return VX_ERR_TIMEOUT;
   if (bits & kStatusCapacity) return VX_ERR_CAPACITY;
   if (bits & kStatusArg) return VX_ERR_ARG;
+  if (bits & kStatusBounds) return VX_ERR_BOUNDS;
   return VX_OK;
 }
 
@@ -916,7 +917,7 @@ int vx_create(const vx_desc* desc, vx_sim** out) {
   if ((rc = dalloc(&s->st, 2 * NPLANE * s->pitch)) || (rc = dalloc(&s->flags, N)) || (rc = dalloc(&s->mat, N)) ||
       (rc = dalloc(&s->lat, N)) || (rc = dalloc(&s->iperm, N)) || (rc = dalloc(&s->mask, N)) ||
       (rc = dalloc(&s->mats, L.palette.size())) || (rc = dalloc(&s->dtb, L.n_bodies)) ||
-      (rc = dalloc(&s->origin, 3 * L.n_bodies)) || (rc = dalloc(&s->status, 4)) ||
+      (rc = dalloc(&s->origin, 3 * L.n_bodies)) || (rc = dalloc(&s->status, 8)) ||
       (rc = dalloc(&s->vmax, L.n_bodies)) || (L.n_bodies > 1 && (rc = dalloc(&s->body, N)))) {
     vx_destroy(s);
     return rc;
@@ -932,7 +933,7 @@ int vx_create(const vx_desc* desc, vx_sim** out) {
   if (up(s->mat, mat.data(), N) || up(s->lat, lat.data(), N * 4) || up(s->iperm, s->T.iperm.data(), N * 4) ||
       up(s->mask, s->T.mask.data(), N) || up(s->origin, L.origin.data(), 3 * L.n_bodies * 4) ||
       (s->body && up(s->body, body.data(), N * 4)) || cudaMemset(s->flags, 0, N) ||
-      cudaMemset(s->status, 0, 16) || cudaMemset(s->vmax, 0, 4 * L.n_bodies) ||
+      cudaMemset(s->status, 0, 32) || cudaMemset(s->vmax, 0, 4 * L.n_bodies) ||
       cudaMemset(s->st, 0, sizeof(float) * 2 * NPLANE * s->pitch)) {
     vx_destroy(s);
     return fail(VX_ERR_CUDA, "upload failed");
@@ -1226,7 +1227,7 @@ int vx_reset(vx_sim* s, const float v0[3]) {
   const float* v = v0 ? v0 : s->v0;
   launch_reset_state(cur_state(s), s->pitch, (int)s->L.N, s->flags, v[0], v[1], v[2], 0);
   VX_CUDA(cudaGetLastError());
-  VX_CUDA(cudaMemset(s->status, 0, 16));
+  VX_CUDA(cudaMemset(s->status, 0, 32));
   VX_CUDA(cudaMemset(s->vmax, 0, 4 * s->L.n_bodies));
   if (s->cbar) VX_CUDA(cudaMemset(s->cbar, 0, 2 * sizeof(unsigned)));  // clean after a timed-out launch
   s->step = 0;
@@ -1473,6 +1474,12 @@ int vx_step(vx_sim* s, int64_t n, void* stream) {
   if (code == VX_ERR_CAPACITY)
     return fail(code, "collision candidate list overflow (more than " + std::to_string(kCandCap) + " per voxel)");
   if (code == VX_ERR_TIMEOUT) return fail(code, "a grid barrier of the multi-step launch gave up waiting");
+  if (code == VX_ERR_BOUNDS) {
+    int h[8] = {0};
+    VX_CUDA(cudaMemcpy(h, s->status, 32, cudaMemcpyDeviceToHost));
+    return fail(code, "an index failed its bounds check at site " + std::to_string(h[4]) + " (index " +
+                          std::to_string(h[5]) + ")");
+  }
   return VX_OK;
 }
 

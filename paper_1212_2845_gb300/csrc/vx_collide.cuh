@@ -35,7 +35,7 @@ __device__ __forceinline__ void quantise_one(const CollideArgs& C, int s) {
   C.cell[s] = make_int4((int)cx, (int)cy, (int)cz, 0);  // cells of a world fit in 32 bits
   uint32_t h = cell_hash(cx, cy, cz, C.H - 1);
   C.bucket[s] = h;
-  atomicAdd(&C.hcount[h], 1u);
+  if (VX_IN_BOUNDS(C.status, h, C.H, kSiteBucket)) atomicAdd(&C.hcount[h], 1u);
 }
 
 // Exclusive scan of x over the CTA (all threads call it); returns this
@@ -94,8 +94,9 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
     for (int q = 0; q < 9; ++q) {
       const int ncx = cx + q % 3 - 1, ncy = cy + q / 3 - 1, ncz = cz + dz;
       for (uint32_t e = e0[q]; e < e1[q]; ++e) {
+        if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
         int t = C.sorted[e];
-        if (t == s) continue;
+        if (t == s || !VX_IN_BOUNDS(C.status, t, C.S, kSiteSorted)) continue;
         const int4 c1 = C.cell[t];
         if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
         int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
@@ -155,8 +156,9 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
     const uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
     const uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
     for (uint32_t e = e0; e < e1; ++e) {
+      if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
       const int t = C.sorted[e];
-      if (t == s) continue;
+      if (t == s || !VX_IN_BOUNDS(C.status, t, C.S, kSiteSorted)) continue;
       const int4 c1 = C.cell[t];
       if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
       const int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
@@ -249,7 +251,9 @@ __device__ __forceinline__ bool rebuild_phases(const CollideArgs& C, unsigned G)
   if (!grid_barrier(C.bar, G, C.spins, C.status)) return false;
   for (int s = tid; s < C.S; s += nthr) {
     const uint32_t h = C.bucket[s];
-    C.sorted[C.hstart[h] + atomicAdd(&C.hcursor[h], 1u)] = s;
+    if (!VX_IN_BOUNDS(C.status, h, C.H, kSiteBucket)) continue;
+    const uint32_t at = C.hstart[h] + atomicAdd(&C.hcursor[h], 1u);
+    if (VX_IN_BOUNDS(C.status, at, C.S, kSiteSorted)) C.sorted[at] = s;
   }
   if (!grid_barrier(C.bar, G, C.spins, C.status)) return false;
   {

@@ -41,6 +41,29 @@ constexpr int kStatusUnstable = 1;  // status word bits
 constexpr int kStatusCapacity = 2;
 constexpr int kStatusTimeout = 4;   // a bounded device wait gave up
 constexpr int kStatusArg = 8;       // an input value checked on the device was out of range
+constexpr int kStatusBounds = 16;   // debug builds: an index failed its bounds check
+
+// Bounds-checked debug builds (VX_BOUNDS_CHECK defined at compile time) test
+// the indices that come from device tables before they are used: halo and
+// bond staging slots, neighbour and candidate lists, hash buckets, cluster
+// slices.  A failed check sets kStatusBounds, records the check site and the
+// index in status[4] and status[5] (first failure only), and the caller skips
+// the access; nothing traps.  Normal builds compile the checks away.
+enum BoundsSite { kSiteHalo = 1, kSitePlusSlot, kSiteHaloBond, kSiteContact, kSiteBucket, kSiteSorted,
+                  kSiteCluster };
+#ifdef VX_BOUNDS_CHECK
+__device__ __forceinline__ bool vx_in_bounds(int* status, long long i, long long n, int site) {
+  if (i >= 0 && i < n) return true;
+  if (!(atomicOr(status, kStatusBounds) & kStatusBounds)) {
+    status[4] = site;
+    status[5] = (int)i;
+  }
+  return false;
+}
+#define VX_IN_BOUNDS(status, i, n, site) ::vx::vx_in_bounds((status), (long long)(i), (long long)(n), (site))
+#else
+#define VX_IN_BOUNDS(status, i, n, site) true
+#endif
 
 struct StepArgs {
   int N;
@@ -87,7 +110,7 @@ struct StepArgs {
   const int32_t* ccount;   // per surface voxel
   const int32_t* cand;     // per surface voxel, kCandCap slots (internal indices, ascending)
   unsigned* vmax_bits;     // per body, float bits of max |v|
-  int* status;             // [0] bits, [1] first bad voxel (internal), [2..3] step
+  int* status;             // [0] bits, [1] first bad voxel (internal), [2..3] step, [4..5] bounds site, index
   float* fm_out;           // 6 planes: bond force and moment sum of every voxel, or nullptr
   // collision horizon kept by the pipelined step itself (nullptr h_done: a
   // separate launch keeps it): the last CTA to finish updates the per-body
@@ -465,6 +488,7 @@ __device__ __forceinline__ float voxel_update(const StepArgs& A, int v, const Vo
       const int32_t* cl = A.cand + (int64_t)si * kCandCap;
       for (int c = 0; c < nc; ++c) {
         int j = cl[c];
+        if (!VX_IN_BOUNDS(A.status, j, A.N, kSiteContact)) continue;
         uint32_t lq = A.lat[j];
         const StPtr sp(const_cast<float*>(A.st_in), P);
         const float4 ja = sp.A[j], jb = sp.B[j], jc = sp.C[j];

@@ -46,7 +46,7 @@ constexpr size_t kOffSorted = kOffBsum + align256(kRebuildMaxGrid * sizeof(uint3
 constexpr size_t kOffIota = kOffSorted + align256(kMaxSurface * sizeof(int32_t));
 constexpr size_t kOffAcc = kOffIota + align256(kMaxSurface * sizeof(int32_t));
 constexpr size_t kOffFlag = kOffAcc + align256(kMaxBodies * sizeof(float));
-constexpr size_t kOffMisc = kOffFlag + align256(kMaxBodies * sizeof(int));  // any, status[4], n_rebuilds, barrier
+constexpr size_t kOffMisc = kOffFlag + align256(kMaxBodies * sizeof(int));  // any, status[8], n_rebuilds, barrier
 constexpr size_t kScratchBytes = kOffMisc + 256;
 
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
@@ -150,7 +150,7 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.spins = 1ll << 24;
   // status words: bits, then the first out-of-range body index (starts at
   // 0x7F7F7F7F, above any input index)
-  cudaError_t e = cudaMemsetAsync(C.status, 0, 16, st);
+  cudaError_t e = cudaMemsetAsync(C.status, 0, 32, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(C.status + 1, 0x7F, 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(C.bar, 0, 2 * sizeof(unsigned), st);
   if (e != cudaSuccess) return fail(VX_ERR_CUDA, std::string("cudaMemsetAsync: ") + cudaGetErrorString(e));
@@ -171,6 +171,7 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
       (e = cudaStreamSynchronize(st)) != cudaSuccess)
     return fail(VX_ERR_CUDA, std::string("collision candidates: ") + cudaGetErrorString(e));
   if (status[0] & kStatusTimeout) return fail(VX_ERR_TIMEOUT, "a grid barrier of the candidate search gave up waiting");
+  if (status[0] & kStatusBounds) return fail(VX_ERR_BOUNDS, "an index failed its bounds check (debug build)");
   if (status[0] & kStatusCapacity)
     return fail(VX_ERR_CAPACITY, "more than " + std::to_string(kCandCap) + " candidates for a surface voxel");
   return VX_OK;

@@ -110,8 +110,8 @@ __device__ __forceinline__ void issue_tile(const StepArgs& A, const StPtr& G, co
       cp4(&S.fx[2 * TMAX + i], &A.fext[2 * A.pitch + g]);
     }
   }
-  if (i < r.nh) stage_voxel<TMAX>(A, G, S, r.T + i, r.h0);
-  if (i + TMAX < r.nh) stage_voxel<TMAX>(A, G, S, r.T + i + TMAX, r.h1);
+  if (i < r.nh && VX_IN_BOUNDS(A.status, r.h0, A.N, kSiteHalo)) stage_voxel<TMAX>(A, G, S, r.T + i, r.h0);
+  if (i + TMAX < r.nh && VX_IN_BOUNDS(A.status, r.h1, A.N, kSiteHalo)) stage_voxel<TMAX>(A, G, S, r.T + i + TMAX, r.h1);
   if (i < r.nhb) cp4(&S.hb[i], &A.hbonds[r.hb0 + i]);
   if (i + TMAX < r.nhb) cp4(&S.hb[i + TMAX], &A.hbonds[r.hb0 + i + TMAX]);
 }
@@ -197,7 +197,7 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
     const M3f R1 = qmat(s.q);
     const bool damp = A.zb != 0.f;
 #define VX_PLUS_BOND(AX, P2)                                                                               \
-    if (P2 != 0xFFFF) {                                                                                  \
+    if (P2 != 0xFFFF && VX_IN_BOUNDS(A.status, P2, T + cur.nh, kSitePlusSlot)) {                         \
       const VoxS v2 = S.vox(P2);                                                                         \
       const float4 q2 = props[P2];                                                                       \
       const BondK k = pair_consts(A, lut, mats, pr, q2);                                                 \
@@ -214,6 +214,9 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
   for (int j = i; j < cur.nhb; j += TMAX) {
     const uint32_t pk = S.hb[j];
     const int s1 = (int)(pk & 4095u), s2 = (int)((pk >> 12) & 4095u), ax = (int)(pk >> 24);
+    if (!VX_IN_BOUNDS(A.status, s1, T + cur.nh, kSiteHaloBond) || !VX_IN_BOUNDS(A.status, s2, T, kSiteHaloBond) ||
+        !VX_IN_BOUNDS(A.status, ax, 3, kSiteHaloBond))
+      continue;
     halo_bond_p<TMAX>(A, S, props, lut, mats, F4, F2, s1, s2, ax);
   }
   __syncthreads();

@@ -215,7 +215,9 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
           const int a = (bi >= ns) + (bi >= 2 * ns);
           const int u = bi - a * ns;
           const uint16_t e = S.nb[(2 * a + 1) * V + u];
-          if (e == kNoNb) continue;
+          if (e == kNoNb || !VX_IN_BOUNDS(A.status, e >> kLocBits, C, kSiteCluster) ||
+              !VX_IN_BOUNDS(A.status, e & ((1 << kLocBits) - 1), slice, kSiteCluster))
+            continue;
           VoxS s2;
           float4 p2;
           partner<false>(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);
@@ -237,7 +239,8 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
 #define VX_RES_BOND(AX)                                                                                     \
           {                                                                                                 \
             const uint16_t e = S.nb[(2 * AX + 1) * V + u];                                                  \
-            if (e != kNoNb) {                                                                               \
+            if (e != kNoNb && VX_IN_BOUNDS(A.status, e >> kLocBits, C, kSiteCluster) &&                      \
+                VX_IN_BOUNDS(A.status, e & ((1 << kLocBits) - 1), slice, kSiteCluster)) {                   \
               VoxS s2;                                                                                      \
               float4 p2;                                                                                    \
               partner<true>(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), s2, p2);                 \
@@ -286,7 +289,8 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
           const uint16_t e = S.nb[2 * a * V + u];
-          if (e != kNoNb) {
+          if (e != kNoNb && VX_IN_BOUNDS(A.status, e >> kLocBits, C, kSiteCluster) &&
+              VX_IN_BOUNDS(A.status, e & ((1 << kLocBits) - 1), slice, kSiteCluster)) {
             float4 f;
             float2 h;
             minus_result<PER_VOXEL>(cl, S, rank, e >> kLocBits, e & ((1 << kLocBits) - 1), a, V, f, h);

@@ -12,11 +12,12 @@ import os
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build_san" if os.environ.get("VX_HOST_SANITIZE") == "1" else "_build", "libvx.so")
+LIB_PATH = os.path.join(HERE, "_build_san" if os.environ.get("VX_HOST_SANITIZE") == "1" else
+                        ("_build_bc" if os.environ.get("VX_BOUNDS_CHECK") == "1" else "_build"), "libvx.so")
 
 VX_OK = 0
 ERRORS = {-1: "VX_ERR_ARG", -2: "VX_ERR_CUDA", -3: "VX_ERR_OOM", -4: "VX_ERR_UNSTABLE",
-          -5: "VX_ERR_TIMEOUT", -6: "VX_ERR_STATE", -7: "VX_ERR_CAPACITY"}
+          -5: "VX_ERR_TIMEOUT", -6: "VX_ERR_STATE", -7: "VX_ERR_CAPACITY", -8: "VX_ERR_BOUNDS"}
 FLAG_FIXED = 1
 FLAG_STATIC = 2
 GROUPS_RESIDENT = -1    # vx_set_batching: the shared-memory-resident form (split chosen automatically)
