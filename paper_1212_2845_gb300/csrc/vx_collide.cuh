@@ -64,10 +64,8 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t x, uint32_t* w
   return pre;
 }
 
-// Candidates of searched voxel s, found by one thread: the query when there
-// are many more searched voxels than warps.  The 27 neighbour cells are taken
-// a layer of nine at a time, the nine bucket ranges loaded together before
-// any is walked, so a layer costs one round trip to memory for its ranges.
+// Candidates of searched voxel s, found by one thread (27 neighbour cells in
+// a row): the query when there are many more searched voxels than warps.
 __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   int v = C.surf[s];
   int b = C.body ? C.body[v] : 0;
@@ -82,38 +80,32 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   int list[kCandCap];
   int n = 0;
   bool overflow = false;
-  for (int dz = -1; dz <= 1; ++dz) {
-    uint32_t e0[9], e1[9];
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const uint32_t h = cell_hash(cx + q % 3 - 1, cy + q / 3 - 1, cz + dz, C.H - 1);
-      e0[q] = C.hstart[h];
-      e1[q] = C.hstart[h + 1];
-    }
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      const int ncx = cx + q % 3 - 1, ncy = cy + q / 3 - 1, ncz = cz + dz;
-      for (uint32_t e = e0[q]; e < e1[q]; ++e) {
-        if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
-        int t = C.sorted[e];
-        if (t == s || !VX_IN_BOUNDS(C.status, t, C.S, kSiteSorted)) continue;
-        const int4 c1 = C.cell[t];
-        if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
-        int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
-        int u = C.surf[t];
-        if (C.body && C.body[u] != b) {
-          if (!C.qorg) continue;  // bodies are separate worlds
-        } else {
-          uint32_t lq = C.lat[u];
-          int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
-          if (man <= 3) continue;
+  for (int dz = -1; dz <= 1; ++dz)
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
+        uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
+        uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
+        for (uint32_t e = e0; e < e1; ++e) {
+          if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
+          int t = C.sorted[e];
+          if (t == s || !VX_IN_BOUNDS(C.status, t, C.S, kSiteSorted)) continue;
+          const int4 c1 = C.cell[t];
+          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
+          int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
+          int u = C.surf[t];
+          if (C.body && C.body[u] != b) {
+            if (!C.qorg) continue;  // bodies are separate worlds
+          } else {
+            uint32_t lq = C.lat[u];
+            int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
+            if (man <= 3) continue;
+          }
+          int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
+          if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
+          if (n < kCandCap) list[n++] = u; else overflow = true;
         }
-        int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
-        if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
-        if (n < kCandCap) list[n++] = u; else overflow = true;
       }
-    }
-  }
   // insertion sort ascending (lists are short)
   for (int i = 1; i < n; ++i) {
     int x = list[i];
