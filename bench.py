@@ -264,12 +264,14 @@ def time_steps(sim, stream, steps, warmup, flush=None):
     return np.array([a.elapsed_time(b) for a, b in ev]) * 1e-3
 
 
-def large_lattice(stream, peak, steps=200, warmup=5, R=200):
+def large_lattice(stream, peak, steps=200, warmup=5, R=200, tile=0):
     """Plain step on a hollow shell of outer radius R (200: 3.86M voxels, state
     ~400 MB per step, larger than L2) and thickness 8 voxels, on the floor."""
     from paper_1212_2845_gb300 import vx
     sc = scenes.hollow_ball(R=R, t=8, collide=False)
     sim = vx.Sim(sc)
+    if tile:
+        sim.set_step_form(vx.FORM_PIPELINED, tile)
     t = time_steps(sim, stream, steps, warmup)
     avg = float(t.mean())
     b_alg = 108  # state r/w 104, flags 2, material 1, bond mask 1
@@ -516,6 +518,7 @@ def main():
     ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
     ap.add_argument("--only-collisions", action="store_true", help="time only the ball drop with collisions")
     ap.add_argument("--only-small", action="store_true", help="time only the small-lattice forms")
+    ap.add_argument("--tile", type=int, default=0, help="tile size of the pipelined step (profiling aid; 0: default)")
     ap.add_argument("--pre-steps", type=int, default=PRE_STEPS,
                     help="untimed steps of the drop before the warm-up (profiling aid: 0 starts in the free fall)")
     ap.add_argument("--bodies", type=int, default=0, help="bodies for --only-adjoint / --only-batched")
@@ -533,7 +536,7 @@ def main():
     if args.only_large:
         peak, _ = load_peaks()
         print(json.dumps(large_lattice(torch.cuda.Stream(), peak, steps=args.steps, warmup=args.warmup,
-                                       R=args.shell_radius)))
+                                       R=args.shell_radius, tile=args.tile)))
         return
     if args.only_adjoint:
         peak, _ = load_peaks()
@@ -560,6 +563,8 @@ def main():
 
     sc = scenes.hollow_ball()
     sim = vx.Sim(sc)
+    if args.tile:
+        sim.set_step_form(vx.FORM_PIPELINED, args.tile)
     stream = torch.cuda.Stream()
     sim.step(args.pre_steps, stream)          # untimed set-up: the drop to just before the impact
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")

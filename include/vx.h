@@ -160,7 +160,7 @@ VX_API int vx_get_anchors(vx_sim* sim, double* anchors);
  * CTAs that stream the next tile into shared memory (cp.async) while
  * computing the current one.  All forms compute the same arithmetic and give
  * bitwise-identical states.  tile_max (fused forms): 128, 256 or 512 voxels
- * per tile (pipelined: 128 or 256), 0 keeps the current size (256 at create).
+ * per tile (any form), 0 keeps the current size (256 at create).
  * The state is kept. */
 #define VX_FORM_FUSED 0
 #define VX_FORM_TWO_PASS 1
@@ -430,7 +430,7 @@ VX_API int vx_rollout_backward(vx_sim* sim, const float* w_body, float* grad_log
  * voxel; more than 48 candidates for a voxel returns VX_ERR_CAPACITY; a grid
  * barrier of the search that waits longer than about a second returns
  * VX_ERR_TIMEOUT.  On any error the outputs are unspecified.  Scratch comes from one fixed device array of
- * about 5 MiB that every GPU loading the library holds until exit.  The first
+ * about 8.3 MiB that every GPU loading the library holds until exit.  The first
  * call on a device (with that device current) looks up the array's address;
  * make it before any stream capture.  Calls share the array: calls whose GPU
  * work overlaps race and must be serialised by the caller.  Work is enqueued

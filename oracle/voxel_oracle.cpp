@@ -26,7 +26,10 @@
 //   gravity/floor/friction (Sec 2.2.1)                 pinned: friction threshold/decel.
 //   collision candidates (Sec 2.2.2)                   pinned: brute-force sets; the
 //                                                      x-sorted sweep equals brute force
-//   voxel-voxel contact force law                      parity unpinned (paper silent)
+//   voxel-voxel contact force law (paper silent)       pinned: one-step force, rest
+//                                                      overlap m g / k_c, restitution
+//                                                      and contact time of a head-on
+//                                                      damped collision
 //   volumetric actuation (Sec 2.3)                     pinned: free expansion
 //   several temperature signals (Sec 2.3)              pinned: two-material rest length,
 //                                                      solo runs of one-material bodies

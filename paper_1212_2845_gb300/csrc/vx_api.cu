@@ -182,6 +182,9 @@ struct vx_sim {
   uint32_t* hstart = nullptr;
   uint32_t* bsum = nullptr;
   int32_t* sorted = nullptr;
+  int4* scell = nullptr;     // searched voxels in bucket order: cell and index
+  int64_t* sxq = nullptr;    // quantised coordinates (3 planes)
+  int4* sinf = nullptr;      // voxel, lattice word, body
   int32_t* ccount = nullptr;
   int32_t* cand = nullptr;
   float* acc = nullptr;
@@ -307,6 +310,9 @@ CollideArgs collide_args(vx_sim* s) {
   C.hstart = s->hstart;
   C.bsum = s->bsum;
   C.sorted = s->sorted;
+  C.scell = s->scell;
+  C.sxq = s->sxq;
+  C.sinf = s->sinf;
   C.ccount = s->ccount;
   C.cand = s->cand;
   C.acc = s->acc;
@@ -435,7 +441,8 @@ int alloc_collisions(vx_sim* s) {
       (rc = dalloc(&s->cell, S)) ||
       (rc = dalloc(&s->bucket, S)) || (rc = dalloc(&s->hcount, H)) || (rc = dalloc(&s->hcursor, H)) ||
       (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, kRebuildMaxGrid)) || (rc = dalloc(&s->cbar, 2)) ||
-      (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
+      (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->scell, S)) || (rc = dalloc(&s->sxq, 3 * S)) ||
+      (rc = dalloc(&s->sinf, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
       (rc = dalloc(&s->hdone, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
@@ -462,6 +469,7 @@ int alloc_collisions(vx_sim* s) {
 void free_collisions(vx_sim* s) {
   dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket); dfree(s->hcount); dfree(s->hcursor);
   dfree(s->hstart); dfree(s->bsum); dfree(s->cbar); dfree(s->sorted); dfree(s->ccount); dfree(s->cand);
+  dfree(s->scell); dfree(s->sxq); dfree(s->sinf);
   dfree(s->acc); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
   s->coll_alloc = false;
   s->coll_S = 0;
@@ -721,7 +729,7 @@ int retile(vx_sim* s, int tile_max) {
   int dev = 0, n_sm = 0;
   if (s->group_voxels == 0 && cudaGetDevice(&dev) == cudaSuccess &&
       cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && n_sm > 0) {
-    G = (int64_t)n_sm * (tile_max == 128 ? 4 : 2);  // resident CTAs of the pipelined kernels
+    G = (int64_t)n_sm * (tile_max == 128 ? 4 : (tile_max == 256 ? 2 : 1));  // resident CTAs of the pipelined kernels
     k = (s->L.N + (int64_t)tile_max * G - 1) / ((int64_t)tile_max * G);
     const int64_t r = (s->L.N + k * G - 1) / (k * G);
     if (k <= 8 && 2 * r >= tile_max && r < tile_max) run = (int)r;
@@ -994,8 +1002,6 @@ int vx_set_step_form(vx_sim* s, int32_t form, int32_t tile_max) {
   if (form != VX_FORM_FUSED && form != VX_FORM_TWO_PASS && form != VX_FORM_PIPELINED)
     return fail(VX_ERR_ARG, "unknown step form");
   if (form == VX_FORM_TWO_PASS && (rc = ensure_two_pass(s))) return rc;
-  if (form == VX_FORM_PIPELINED && (tile_max == 512 || (tile_max == 0 && s->tile_max == 512)))
-    return fail(VX_ERR_ARG, "the pipelined form takes tiles of 128 or 256 voxels");
   if (form != VX_FORM_TWO_PASS && tile_max != 0 && tile_max != s->tile_max) {
     if (tile_max != 128 && tile_max != 256 && tile_max != 512) return fail(VX_ERR_ARG, "tile_max must be 128, 256 or 512");
     // the voxel order depends only on the lattice, so the state stays valid

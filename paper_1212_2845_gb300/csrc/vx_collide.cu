@@ -71,7 +71,7 @@ __global__ void horizon_update(CollideArgs C) {
   C.acc[b] = acc;
 }
 
-constexpr int kRebuildThreads = 256;
+constexpr int kRebuildThreads = 1024;  // few CTAs: each grid barrier counts few arrivals
 
 // The whole rebuild in one cooperative launch (all CTAs co-resident; phases
 // separated by grid barriers, whose waits are bounded: on a timeout the
@@ -108,7 +108,8 @@ void launch_rebuild(const CollideArgs& C, cudaStream_t st) {
   if (C.S == 0) return;
   const int limit = rebuild_grid_limit();
   // one warp per searched voxel in the query, one thread per bucket in the scan
-  const int want = std::max((C.S + kRebuildWarps - 1) / kRebuildWarps, (C.H + kRebuildThreads - 1) / kRebuildThreads);
+  const int warps_per_cta = kRebuildThreads / 32;
+  const int want = std::max((C.S + warps_per_cta - 1) / warps_per_cta, (C.H + kRebuildThreads - 1) / kRebuildThreads);
   int grid = std::min(std::min(want, limit), kRebuildMaxGrid);
   if (grid < 1) grid = 1;
   void* args[1] = {const_cast<CollideArgs*>(&C)};

@@ -88,16 +88,16 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
         uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
         for (uint32_t e = e0; e < e1; ++e) {
           if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
-          int t = C.sorted[e];
-          if (t == s || !VX_IN_BOUNDS(C.status, t, C.S, kSiteSorted)) continue;
-          const int4 c1 = C.cell[t];
+          const int4 c1 = C.scell[e];
+          if (c1.w == s) continue;
           if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
-          int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
-          int u = C.surf[t];
-          if (C.body && C.body[u] != b) {
+          const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
+          const int4 f = C.sinf[e];  // voxel, lattice word, body
+          const int u = f.x;
+          if (C.body && f.z != b) {
             if (!C.qorg) continue;  // bodies are separate worlds
           } else {
-            uint32_t lq = C.lat[u];
+            const uint32_t lq = (uint32_t)f.y;
             int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
             if (man <= 3) continue;
           }
@@ -149,16 +149,16 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
     const uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
     for (uint32_t e = e0; e < e1; ++e) {
       if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
-      const int t = C.sorted[e];
-      if (t == s || !VX_IN_BOUNDS(C.status, t, C.S, kSiteSorted)) continue;
-      const int4 c1 = C.cell[t];
+      const int4 c1 = C.scell[e];
+      if (c1.w == s) continue;
       if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
-      const int64_t x1 = C.xq[t], y1 = C.xq[(int64_t)C.S + t], z1 = C.xq[2 * (int64_t)C.S + t];
-      const int u = C.surf[t];
-      if (C.body && C.body[u] != b) {
+      const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
+      const int4 f = C.sinf[e];  // voxel, lattice word, body
+      const int u = f.x;
+      if (C.body && f.z != b) {
         if (!C.qorg) continue;  // bodies are separate worlds
       } else {
-        const uint32_t lq = C.lat[u];
+        const uint32_t lq = (uint32_t)f.y;
         const int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
         if (man <= 3) continue;
       }
@@ -201,10 +201,10 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
 }
 
 // The rebuild phases, run by every CTA of a cooperative grid (any number of
-// CTAs up to kRebuildMaxGrid, blockDim a multiple of 32 up to 32 kRebuildWarps);
-// G is the count the grid barriers wait for.  Returns false if a barrier wait
-// gave up.
-constexpr int kRebuildWarps = 8;
+// CTAs up to kRebuildMaxGrid, blockDim a multiple of 32 up to 32 kRebuildWarps
+// warps); G is the count the grid barriers wait for.  Returns false if a
+// barrier wait gave up.
+constexpr int kRebuildWarps = 32;
 __device__ __forceinline__ bool rebuild_phases(const CollideArgs& C, unsigned G) {
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t offset;
@@ -245,7 +245,14 @@ __device__ __forceinline__ bool rebuild_phases(const CollideArgs& C, unsigned G)
     const uint32_t h = C.bucket[s];
     if (!VX_IN_BOUNDS(C.status, h, C.H, kSiteBucket)) continue;
     const uint32_t at = C.hstart[h] + atomicAdd(&C.hcursor[h], 1u);
-    if (VX_IN_BOUNDS(C.status, at, C.S, kSiteSorted)) C.sorted[at] = s;
+    if (!VX_IN_BOUNDS(C.status, at, C.S, kSiteSorted)) continue;
+    C.sorted[at] = s;
+    // the query reads each bucket's entries as one contiguous run
+    const int4 c = C.cell[s];
+    C.scell[at] = make_int4(c.x, c.y, c.z, s);
+    for (int a = 0; a < 3; ++a) C.sxq[(int64_t)a * C.S + at] = C.xq[(int64_t)a * C.S + s];
+    const int u = C.surf[s];
+    C.sinf[at] = make_int4(u, (int)C.lat[u], C.body ? C.body[u] : 0, 0);
   }
   if (!grid_barrier(C.bar, G, C.spins, C.status)) return false;
   {

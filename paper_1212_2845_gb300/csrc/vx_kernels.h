@@ -45,6 +45,12 @@ struct CollideArgs {
   uint32_t* hstart;       // H + 1
   uint32_t* bsum;         // ceil(H / 1024)
   int32_t* sorted;        // S
+  // the searched voxels in bucket order (written by the scatter, read by the
+  // query as contiguous runs): cell and searched index (x, y, z, t), the
+  // quantised coordinates (3 planes of S) and (voxel, lattice word, body, 0)
+  int4* scell;
+  int64_t* sxq;
+  int4* sinf;
   int32_t* ccount;        // S
   int32_t* cand;          // S x kCandCap
   float* acc;             // per body

@@ -9,7 +9,7 @@
 // the hash grid and sort buffers come from one fixed array in this file.
 //
 // The array is a file-scope __device__ variable: every GPU that loads the
-// library holds it (kScratchBytes, about 5 MiB) until the process exits.  Host
+// library holds it (kScratchBytes, about 8.3 MiB) until the process exits.  Host
 // code cannot use the array's name as a device address, so the first call on
 // each device, with that device current, looks up the address with
 // cudaGetSymbolAddress and keeps it for later calls.  Make that first call
@@ -43,7 +43,10 @@ constexpr size_t kOffCursor = kOffCount + align256(kMaxBuckets * sizeof(uint32_t
 constexpr size_t kOffStart = kOffCursor + align256(kMaxBuckets * sizeof(uint32_t));
 constexpr size_t kOffBsum = kOffStart + align256((kMaxBuckets + 1) * sizeof(uint32_t));
 constexpr size_t kOffSorted = kOffBsum + align256(kRebuildMaxGrid * sizeof(uint32_t));
-constexpr size_t kOffIota = kOffSorted + align256(kMaxSurface * sizeof(int32_t));
+constexpr size_t kOffScell = kOffSorted + align256(kMaxSurface * sizeof(int32_t));
+constexpr size_t kOffSxq = kOffScell + align256(kMaxSurface * sizeof(int4));
+constexpr size_t kOffSinf = kOffSxq + align256(3 * kMaxSurface * sizeof(int64_t));
+constexpr size_t kOffIota = kOffSinf + align256(kMaxSurface * sizeof(int4));
 constexpr size_t kOffAcc = kOffIota + align256(kMaxSurface * sizeof(int32_t));
 constexpr size_t kOffFlag = kOffAcc + align256(kMaxBodies * sizeof(float));
 constexpr size_t kOffMisc = kOffFlag + align256(kMaxBodies * sizeof(int));  // any, status[8], n_rebuilds, barrier
@@ -137,6 +140,9 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.hstart = reinterpret_cast<uint32_t*>(base + kOffStart);
   C.bsum = reinterpret_cast<uint32_t*>(base + kOffBsum);
   C.sorted = reinterpret_cast<int32_t*>(base + kOffSorted);
+  C.scell = reinterpret_cast<int4*>(base + kOffScell);
+  C.sxq = reinterpret_cast<int64_t*>(base + kOffSxq);
+  C.sinf = reinterpret_cast<int4*>(base + kOffSinf);
   C.ccount = cand_count;
   C.cand = cand;
   C.acc = reinterpret_cast<float*>(base + kOffAcc);

@@ -340,7 +340,7 @@ template <int TMAX> struct PipeLayout {
 };
 
 template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs A) {
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) fused_pipe(StepArgs A) {
   extern __shared__ __align__(16) float smem[];
   const PipeLayout<TMAX> L(smem, A);
   if ((int)blockIdx.x < A.n_tiles) {  // uniform over the CTA
@@ -355,7 +355,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) fused_pipe(StepArgs
 // a grid barrier before the next step reads what this one wrote.  The
 // lattice stays in L2 between steps and no launch separates them.
 template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) multi_pipe(StepArgs A0, MultiArgs M) {
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) multi_pipe(StepArgs A0, MultiArgs M) {
   extern __shared__ __align__(16) float smem[];
   const PipeLayout<TMAX> L(smem, A0);
   L.load_tables(A0);
@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) multi_pipe(StepArgs
 // pipeline restarts after each barrier because the next step reads what this
 // one wrote.
 template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepArgs A0, BatchArgs Bt) {
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) batched_pipe(StepArgs A0, BatchArgs Bt) {
   constexpr int ML = 2 * TMAX;
   extern __shared__ __align__(16) float smem[];
   const bool hph = A0.phase != nullptr, hle = A0.logE != nullptr, hbody = A0.body != nullptr,
@@ -445,67 +445,75 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : 2) batched_pipe(StepAr
 
 size_t pipe_smem_bytes(int tile_max, bool ph, bool le, bool body, bool fext, bool col, int n_mats, bool lut) {
   if (tile_max == 128) return PipeSmem<128>::bytes(ph, le, body, fext, col, n_mats, lut);
+  if (tile_max == 512) return PipeSmem<512>::bytes(ph, le, body, fext, col, n_mats, lut);
   return PipeSmem<256>::bytes(ph, le, body, fext, col, n_mats, lut);
 }
 
-int prepare_pipe(int tile_max, size_t smem, int* grid) {
+namespace {
+
+// CTAs of `kernel` (TMAX threads, smem bytes) resident on the whole device.
+template <int TMAX, class K> int resident_ctas(K* kernel, size_t smem, int* n) {
   int per_sm = 0, dev = 0, n_sm = 0;
-  cudaError_t e;
-  if (tile_max == 128) {
-    e = allow_smem(fused_pipe<128>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pipe<128>, 128, smem);
-  } else {
-    e = allow_smem(fused_pipe<256>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fused_pipe<256>, 256, smem);
-  }
+  cudaError_t e = allow_smem(kernel, smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, TMAX, smem);
   if (e != cudaSuccess || per_sm < 1) return -1;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     return -1;
-  *grid = per_sm * n_sm;
+  *n = per_sm * n_sm;
   return 0;
+}
+
+template <int TMAX> int prepare_pipe_t(size_t smem, int* grid) { return resident_ctas<TMAX>(fused_pipe<TMAX>, smem, grid); }
+
+template <int TMAX> int prepare_multi_t(size_t smem, int n_tiles, int* grid, int* co_resident) {
+  int co = 0;
+  if (resident_ctas<TMAX>(multi_pipe<TMAX>, smem, &co) != 0) return -1;
+  *grid = n_tiles < co ? n_tiles : co;
+  *co_resident = co;
+  return 0;
+}
+
+}  // namespace
+
+int prepare_pipe(int tile_max, size_t smem, int* grid) {
+  if (tile_max == 128) return prepare_pipe_t<128>(smem, grid);
+  if (tile_max == 512) return prepare_pipe_t<512>(smem, grid);
+  return prepare_pipe_t<256>(smem, grid);
 }
 
 int prepare_batched(int tile_max, size_t smem) {
   cudaError_t e;
   if (tile_max == 128) e = allow_smem(batched_pipe<128>, smem);
+  else if (tile_max == 512) e = allow_smem(batched_pipe<512>, smem);
   else e = allow_smem(batched_pipe<256>, smem);
   return e == cudaSuccess ? 0 : -1;
 }
 
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s) {
   if (tile_max == 128) batched_pipe<128><<<grid, 128, smem, s>>>(A, B);
+  else if (tile_max == 512) batched_pipe<512><<<grid, 512, smem, s>>>(A, B);
   else batched_pipe<256><<<grid, 256, smem, s>>>(A, B);
 }
 
 int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid, int* co_resident) {
-  int per_sm = 0, dev = 0, n_sm = 0;
-  cudaError_t e;
-  if (tile_max == 128) {
-    e = allow_smem(multi_pipe<128>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_pipe<128>, 128, smem);
-  } else {
-    e = allow_smem(multi_pipe<256>, smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, multi_pipe<256>, 256, smem);
-  }
-  if (e != cudaSuccess || per_sm < 1) return -1;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return -1;
-  const int co = per_sm * n_sm;
-  *grid = n_tiles < co ? n_tiles : co;
-  *co_resident = co;
-  return 0;
+  if (tile_max == 128) return prepare_multi_t<128>(smem, n_tiles, grid, co_resident);
+  if (tile_max == 512) return prepare_multi_t<512>(smem, n_tiles, grid, co_resident);
+  return prepare_multi_t<256>(smem, n_tiles, grid, co_resident);
 }
 
 cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, size_t smem, int grid, cudaStream_t s) {
   void* args[2] = {const_cast<StepArgs*>(&A), const_cast<MultiArgs*>(&M)};
   if (tile_max == 128)
     return cudaLaunchCooperativeKernel((const void*)multi_pipe<128>, dim3(grid), dim3(128), args, smem, s);
+  if (tile_max == 512)
+    return cudaLaunchCooperativeKernel((const void*)multi_pipe<512>, dim3(grid), dim3(512), args, smem, s);
   return cudaLaunchCooperativeKernel((const void*)multi_pipe<256>, dim3(grid), dim3(256), args, smem, s);
 }
 
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {
   int g = grid < A.n_tiles ? grid : A.n_tiles;
   if (tile_max == 128) fused_pipe<128><<<g, 128, smem, s>>>(A);
+  else if (tile_max == 512) fused_pipe<512><<<g, 512, smem, s>>>(A);
   else fused_pipe<256><<<g, 256, smem, s>>>(A);
 }
 
