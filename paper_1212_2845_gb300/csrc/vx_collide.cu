@@ -77,8 +77,9 @@ constexpr int kRebuildThreads = 1024;  // few CTAs: each grid barrier counts few
 // separated by grid barriers, whose waits are bounded: on a timeout the
 // launch ends with the timeout status bit set).
 __global__ void __launch_bounds__(kRebuildThreads) rebuild_all(CollideArgs C) {
+  extern __shared__ int ws[];  // kWarpWs ints per warp
   if (*C.any == 0) return;  // the same value for every CTA: set by an earlier launch
-  rebuild_phases(C, gridDim.x + C.extra);
+  rebuild_phases(C, gridDim.x + C.extra, ws);
 }
 
 // Raise every body's rebuild flag (forced rebuild).
@@ -96,7 +97,9 @@ int rebuild_grid_limit() {
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
   if (!cached[dev]) {
     int per_sm = 0, n_sm = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rebuild_all, kRebuildThreads, 0) != cudaSuccess ||
+    const size_t ws = (size_t)(kRebuildThreads / 32) * kWarpWs * sizeof(int);
+    if (cudaFuncSetAttribute((const void*)rebuild_all, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, rebuild_all, kRebuildThreads, ws) != cudaSuccess ||
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || per_sm < 1)
       return 0;
     cached[dev] = per_sm * n_sm;
@@ -113,7 +116,8 @@ void launch_rebuild(const CollideArgs& C, cudaStream_t st) {
   int grid = std::min(std::min(want, limit), kRebuildMaxGrid);
   if (grid < 1) grid = 1;
   void* args[1] = {const_cast<CollideArgs*>(&C)};
-  cudaLaunchCooperativeKernel((const void*)rebuild_all, dim3(grid), dim3(kRebuildThreads), args, 0, st);
+  const size_t ws = (size_t)(kRebuildThreads / 32) * kWarpWs * sizeof(int);
+  cudaLaunchCooperativeKernel((const void*)rebuild_all, dim3(grid), dim3(kRebuildThreads), args, ws, st);
 }
 
 void launch_flag_all(const CollideArgs& C, cudaStream_t st) {

@@ -392,7 +392,8 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1))
       if (__ldcg(A.h_any)) {  // the same value for every CTA until the last phase clears it
         CollideArgs C = M.coll;
         C.st = A.st_out;
-        if (!rebuild_phases(C, G)) return;
+        // the staging buffers are free between steps: the query's workspace
+        if (!rebuild_phases(C, G, reinterpret_cast<int*>(smem))) return;
       }
     }
     if (k + 1 < M.n_steps && !grid_barrier(M.bar, gridDim.x + M.extra, M.spins, A0.status)) return;
