@@ -312,12 +312,21 @@ def batched_form(stream, peak, n_bodies=4096, steps=200, warmup=5):
     t_plain = _events_time(stream, lambda: sim.step_async(steps, stream))
     st0 = sim.status(stream)[0]
     tm, gv, rate = sim.autotune_batching(20, stream)
-    if gv == 0:                      # per-step launches won the sample: still time a batched launch
+    if gv <= 0:                      # per-step launches or the resident form won: time the batched launch too
         sim.set_batching(4096)
     sim.graph_capture(steps, stream)
     sim.graph_launch(stream)         # warm-up replay
     t_graph = _events_time(stream, lambda: sim.graph_launch(stream))
     st1 = sim.status(stream)[0]
+    t_res = None
+    try:
+        sim.set_batching(vx.GROUPS_RESIDENT)
+        sim.graph_capture(steps, stream)
+        sim.graph_launch(stream)
+        t_res = _events_time(stream, lambda: sim.graph_launch(stream))
+        st1 = st1 or sim.status(stream)[0]
+    except vx.VxError:
+        pass
     if st0 or st1:
         raise RuntimeError("population became unstable")
     out = {"workload": f"population_{n_bodies} (edges U{{4..24}}, seed 4)", "voxels": N, "bonds": sim.n_bonds,
@@ -330,6 +339,10 @@ def batched_form(stream, peak, n_bodies=4096, steps=200, warmup=5):
                        "frac": b_alg * N * steps / t_graph / 1e9 / peak, "kernel": f"batched_pipe<{sim.tiling()['tile_max']}>",
                        "launch": "one captured CUDA graph replay", "group_voxels": gv if gv else 4096},
            "autotune": {"tile_max": tm, "group_voxels": gv, "sample_voxel_steps_per_s": rate, "sample_steps": 20}}
+    if t_res is not None:
+        out["resident"] = {"value": N * steps / t_res, "unit": METRIC, "ms_per_step": 1e3 * t_res / steps,
+                           "frac": b_alg * N * steps / t_res / 1e9 / peak, "kernel": "res_pipe (thread per voxel)",
+                           "launch": "one captured CUDA graph replay"}
     sim.close()
     return out
 
@@ -345,6 +358,10 @@ def adjoint_form(stream, peak, n_bodies=1024, steps=2000, K=100):
     N = sim.N
     sim.step(5)
     t_plain = _events_time(stream, lambda: sim.step_async(200, stream)) / 200 * steps
+    sim.set_batching(vx.GROUPS_RESIDENT)
+    sim.step_async(200, stream)
+    t_res = _events_time(stream, lambda: sim.step_async(200, stream)) / 200 * steps
+    sim.set_batching(0)
     sim.reset(sc["v0"])
     gE = torch.empty(N, device="cuda")
     gP = torch.empty(N, device="cuda")
@@ -360,6 +377,9 @@ def adjoint_form(stream, peak, n_bodies=1024, steps=2000, K=100):
            "plain_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
                           "bond_steps_per_s": sim.n_bonds * steps / t_plain,
                           "frac": b_fwd * N * steps / t_plain / 1e9 / peak},
+           "resident_step": {"value": N * steps / t_res, "unit": METRIC, "ms_per_step": 1e3 * t_res / steps,
+                             "frac": b_fwd * N * steps / t_res / 1e9 / peak,
+                             "kernel": "res_pipe (thread per voxel, 200 steps per launch)"},
            "rollout_forward": {"value": N * steps / t_fwd, "unit": METRIC, "s": t_fwd},
            "backward": {"value": N * steps / t_bwd, "unit": METRIC, "s": t_bwd,
                         "bond_steps_per_s": sim.n_bonds * steps / t_bwd,
@@ -445,16 +465,21 @@ def collision_schemes(stream, steps=2000):
 def small_lattice(stream, steps=1000):
     """Cantilever 10x10x10 (1,000 voxels, 4 tiles): latency-bound.  Per-step
     launches, one cooperative multi-step launch (grid barrier between steps),
-    and one captured persistent batched launch (the body in one CTA)."""
+    the resident form (the lattice in the shared memory of a cluster of 8
+    CTAs for all steps of the launch; the default for vx_step(n > 1) at this
+    size) and one captured persistent batched launch (the body in one CTA)."""
     from paper_1212_2845_gb300 import vx
     sc = scenes.cantilever()
     sim = vx.Sim(sc)
     sim.step(10)
     sim.set_multistep(0)
     t_plain = _events_time(stream, lambda: sim.step_async(steps, stream))
-    sim.set_multistep(1)
+    sim.set_multistep(2)
     sim.step_async(steps, stream)
     t_multi = _events_time(stream, lambda: sim.step_async(steps, stream))
+    sim.set_multistep(1)
+    sim.step_async(steps, stream)
+    t_res = _events_time(stream, lambda: sim.step_async(steps, stream))
     sim.set_batching(1 << 20)
     sim.graph_capture(steps, stream)
     sim.graph_launch(stream)
@@ -464,6 +489,8 @@ def small_lattice(stream, steps=1000):
     out = {"workload": "cantilever_10x10x10", "voxels": sim.N, "steps": steps,
            "per_step_launches": {"steps_per_s": steps / t_plain, "us_per_step": 1e6 * t_plain / steps},
            "multi_step_launch": {"steps_per_s": steps / t_multi, "us_per_step": 1e6 * t_multi / steps},
+           "resident_launch": {"steps_per_s": steps / t_res, "us_per_step": 1e6 * t_res / steps,
+                               "kernel": "res_pipe (cluster of 8 CTAs, thread per bond)"},
            "captured_batched_launch": {"steps_per_s": steps / t_graph, "us_per_step": 1e6 * t_graph / steps}}
     sim.close()
     return out
@@ -472,7 +499,7 @@ def small_lattice(stream, steps=1000):
 def multi_step_line(sim, stream, flush, steps=500):
     """The same lattice stepped by one call of `steps` steps (one cooperative
     launch on this size), L2 flushed before the call."""
-    sim.set_multistep(1)
+    sim.set_multistep(2)
     sim.step_async(steps, stream)
     flush.fill_(3.0)
     t = _events_time(stream, lambda: sim.step_async(steps, stream))

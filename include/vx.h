@@ -200,11 +200,14 @@ VX_API int vx_set_batching(vx_sim* sim, int64_t group_voxels);
  * (about 300,000 voxels), vx_step / vx_step_async with n_steps > 1 run all
  * steps in ONE cooperative launch of co-resident persistent CTAs that meet
  * at a grid barrier between steps, so the lattice stays in L2 and no launch
- * separates the steps.  Same arithmetic and bits as one launch per step.
- * The barrier waits are bounded (about a second); if one gives up, the
- * launch ends and vx_get_status / vx_step report VX_ERR_TIMEOUT.  If the
- * device cannot hold the grid at once the call falls back to one launch per
- * step.  on = 0 always launches once per step. */
+ * separates the steps.  Lattices of at most 8,192 voxels without collisions
+ * take the resident form instead (see vx_set_batching: the lattice stays in
+ * the shared memory of one cluster of CTAs).  Same arithmetic and bits as
+ * one launch per step.  The barrier waits are bounded (about a second); if
+ * one gives up, the launch ends and vx_get_status / vx_step report
+ * VX_ERR_TIMEOUT.  If the device cannot hold the grid at once the call falls
+ * back to one launch per step.  on = 0 always launches once per step; on = 2
+ * uses the cooperative grid launch on small lattices too. */
 VX_API int vx_set_multistep(vx_sim* sim, int32_t on);
 /* Fault-injection aid for tests of the bounded waits: the budget of one grid
  * barrier wait in units of 128 SM clock cycles (0 restores the default of

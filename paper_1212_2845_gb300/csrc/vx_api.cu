@@ -126,7 +126,8 @@ struct vx_sim {
   size_t pipe_smem = 0;
   int pipe_grid = 0;
   // multi-step form (one cooperative launch for n steps)
-  int multistep = 1;          // use it for vx_step(n > 1) in the pipelined form without collisions
+  int multistep = 1;          // 1: multi-step launches for vx_step(n > 1) (resident form on small
+                              // lattices, else the cooperative grid launch); 2: grid launch only
   int multi_grid = 0;
   int multi_co = 0;           // co-resident CTAs of the multi-step kernel
   unsigned* bar = nullptr;    // grid barrier words
@@ -574,6 +575,10 @@ int ensure_nbr(vx_sim* s) {
   VX_CUDA(cudaMemcpy(s->nbr, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice));
   return VX_OK;
 }
+
+// lattices up to this size step n > 1 in the resident form by default (one
+// cluster of up to 8 CTAs holds them)
+constexpr int64_t kResidentAutoVoxels = 8192;
 
 bool is_resident(int64_t g) {
   return g == VX_GROUPS_RESIDENT || g == VX_GROUPS_RESIDENT_BOND || g == VX_GROUPS_RESIDENT_VOXEL;
@@ -1347,7 +1352,14 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   if (n < 0) return fail(VX_ERR_ARG, "n_steps must be >= 0");
   if (n > INT32_MAX) return fail(VX_ERR_ARG, "n_steps too large for one call");
   cudaStream_t st = (cudaStream_t)stream;
-  if (is_resident(s->group_voxels) && !s->collide_on && n > 0) {
+  // a small lattice without collisions steps n > 1 in the resident form by
+  // default: one cluster holds it for all n steps
+  const bool res_auto = s->group_voxels == 0 && s->multistep == 1 && n > 1 && !s->collide_on &&
+                        s->form != VX_FORM_TWO_PASS && s->L.N <= kResidentAutoVoxels;
+  if (res_auto) {
+    if ((rc = ensure_resident(s))) return rc;
+  }
+  if ((is_resident(s->group_voxels) || (res_auto && s->res_ok == 1)) && !s->collide_on && n > 0) {
     // resident form: all n steps in one launch, state in cluster shared memory
     if ((rc = ensure_resident(s))) return rc;
     if (s->res_ok != 1) return fail(VX_ERR_STATE, "the resident form does not fit this lattice");
@@ -1847,7 +1859,8 @@ int vx_set_multistep(vx_sim* s, int32_t on) {
   if (s) ++s->cfg;
   int rc = check_sim(s);
   if (rc) return rc;
-  s->multistep = on ? 1 : 0;
+  if (on < 0 || on > 2) return fail(VX_ERR_ARG, "multistep must be 0, 1 or 2");
+  s->multistep = on;
   return VX_OK;
 }
 

@@ -71,7 +71,7 @@ __global__ void horizon_update(CollideArgs C) {
   C.acc[b] = acc;
 }
 
-constexpr int kRebuildThreads = 1024;  // few CTAs: each grid barrier counts few arrivals
+constexpr int kRebuildThreads = 256;
 
 // The whole rebuild in one cooperative launch (all CTAs co-resident; phases
 // separated by grid barriers, whose waits are bounded: on a timeout the

@@ -80,12 +80,11 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   int list[kCandCap];
   int n = 0;
   bool overflow = false;
-  for (int dz = -1; dz <= 1; ++dz)
-    for (int dy = -1; dy <= 1; ++dy)
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
-        uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
-        uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
+  for (int dz = -1; dz <= 1; ++dz) {
+    for (int q = 0; q < 9; ++q) {
+        const int ncx = cx + q % 3 - 1, ncy = cy + q / 3 - 1, ncz = cz + dz;
+        const uint32_t hq = cell_hash(ncx, ncy, ncz, C.H - 1);
+        const uint32_t e0 = C.hstart[hq], e1 = C.hstart[hq + 1];
         for (uint32_t e = e0; e < e1; ++e) {
           if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
           const int4 c1 = C.scell[e];
@@ -105,7 +104,8 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
           if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
           if (n < kCandCap) list[n++] = u; else overflow = true;
         }
-      }
+    }
+  }
   // insertion sort ascending (lists are short)
   for (int i = 1; i < n; ++i) {
     int x = list[i];
@@ -200,108 +200,7 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
   __syncwarp();  // the buffer is reused for the warp's next voxel
 }
 
-// Candidates of the searched voxels of one occupied hash bucket h, found by
-// one warp.  Lanes 0..26 load the bucket ranges of the 27 cells around the
-// cell c0 of the bucket's first voxel (a bucket reached from several of them
-// is taken once), the warp gathers the positions of those buckets' entries
-// in ebuf, and each voxel of the bucket that lies in c0 tests them 32 at a
-// time; the finds are compacted in cbuf, sorted and written out.  Entries
-// whose cell is not within one cell of c0 (hash collisions) are skipped, so
-// every voxel of the 27 cells is tested exactly once: the set query_one
-// finds.  Voxels of the bucket in another cell, and neighbourhoods with more
-// than kCellCap entries, go to query_one.
-constexpr int kCellCap = 256;
-constexpr int kWarpWs = kCellCap + kCandCap;  // ints of workspace per warp (ebuf, cbuf)
-
-__device__ __forceinline__ void query_bucket(const CollideArgs& C, uint32_t h, int lane, int* ebuf, int* cbuf) {
-  const uint32_t e0 = C.hstart[h];
-  const int n = (int)(C.hstart[h + 1] - e0);
-  const int4 c0 = C.scell[e0];
-  uint32_t r0 = 0u, cnt = 0u, nh = 0xFFFFFFFFu;
-  if (lane < 27) {
-    nh = cell_hash(c0.x + lane % 3 - 1, c0.y + (lane / 3) % 3 - 1, c0.z + lane / 9 - 1, C.H - 1);
-    r0 = C.hstart[nh];
-    cnt = C.hstart[nh + 1] - r0;
-  }
-  const unsigned same = __match_any_sync(0xffffffffu, nh);
-  if (lane >= 27 || __ffs(same) - 1 != lane) cnt = 0u;
-  uint32_t inc = cnt;
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
-    if (lane >= o) inc += y;
-  }
-  const int total = (int)__shfl_sync(0xffffffffu, inc, 31);
-  if (total > kCellCap) {  // crowded: one thread per voxel
-    for (int j = lane; j < n; j += 32) query_one(C, C.scell[e0 + j].w);
-    __syncwarp();
-    return;
-  }
-  const uint32_t off = inc - cnt;
-  for (uint32_t j = 0; j < cnt; ++j) ebuf[off + j] = (int)(r0 + j);
-  __syncwarp();
-  const int64_t r2max = 4 * C.Q * C.Q;  // (2 Q)^2
-  for (int m = 0; m < n; ++m) {
-    const int4 cm = C.scell[e0 + m];
-    const int s = cm.w;
-    if (cm.x != c0.x || cm.y != c0.y || cm.z != c0.z) {  // another cell in this bucket
-      if (lane == 0) query_one(C, s);
-      __syncwarp();
-      continue;
-    }
-    const int4 fm = C.sinf[e0 + m];  // voxel, lattice word, body
-    const int b = C.body ? fm.z : 0;
-    if (!C.flag[b]) continue;
-    const int64_t x0 = C.sxq[e0 + m], y0 = C.sxq[(int64_t)C.S + e0 + m], z0 = C.sxq[2 * (int64_t)C.S + e0 + m];
-    const uint32_t lp = (uint32_t)fm.y;
-    const int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);
-    int found = 0;
-    for (int j0 = 0; j0 < total; j0 += 32) {
-      const int j = j0 + lane;
-      bool hit = false;
-      int u = 0;
-      if (j < total) {
-        const int e = ebuf[j];
-        const int4 c1 = C.scell[e];
-        if (c1.w != s && abs(c1.x - c0.x) <= 1 && abs(c1.y - c0.y) <= 1 && abs(c1.z - c0.z) <= 1) {
-          const int4 f = C.sinf[e];
-          u = f.x;
-          bool ok;
-          if (C.body && f.z != b) {
-            ok = C.qorg != nullptr;  // bodies are separate worlds unless they share one
-          } else {
-            const uint32_t lq = (uint32_t)f.y;
-            ok = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk) > 3;
-          }
-          if (ok) {
-            const int64_t ddx = C.sxq[e] - x0, ddy = C.sxq[(int64_t)C.S + e] - y0, ddz = C.sxq[2 * (int64_t)C.S + e] - z0;
-            hit = ddx * ddx + ddy * ddy + ddz * ddz < r2max;
-          }
-        }
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, hit);
-      const int k = found + __popc(bal & ((1u << lane) - 1u));
-      if (hit && k < kCandCap) cbuf[k] = u;
-      found += __popc(bal);
-    }
-    __syncwarp();
-    const int mm = found < kCandCap ? found : kCandCap;
-    if (lane == 0)
-      for (int i = 1; i < mm; ++i) {  // insertion sort ascending (lists are short)
-        const int x = cbuf[i];
-        int k = i - 1;
-        while (k >= 0 && cbuf[k] > x) { cbuf[k + 1] = cbuf[k]; --k; }
-        cbuf[k + 1] = x;
-      }
-    __syncwarp();
-    int32_t* out = C.cand + (int64_t)s * kCandCap;
-    for (int i = lane; i < mm; i += 32) out[i] = cbuf[i];
-    if (lane == 0) {
-      C.ccount[s] = mm;
-      if (found > kCandCap) atomicOr(C.status, kStatusCapacity);
-    }
-    __syncwarp();  // cbuf is reused for the next voxel
-  }
-}
+constexpr int kWarpWs = kCandCap;  // ints of query workspace per warp
 
 // The rebuild phases, run by every CTA of a cooperative grid (any number of
 // CTAs up to kRebuildMaxGrid, blockDim a multiple of 32 up to 1024); G is
@@ -359,25 +258,15 @@ __device__ __forceinline__ bool rebuild_phases(const CollideArgs& C, unsigned G,
   {
     // one warp per searched voxel while that leaves at most 8 voxels to a
     // warp (8 one-cell chains of dependent loads, against one 27-cell chain
-    // per thread); beyond, one warp per occupied bucket, its 27 neighbour
-    // cells loaded once for all its voxels.  All give the same sorted lists.
+    // per thread); beyond, one thread per voxel (the search is bound by the
+    // latency of its chains, so the most independent chains win).  Both
+    // give the same sorted lists.
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int nw = (int)(gridDim.x * (blockDim.x >> 5));
-    const int gw = (int)blockIdx.x * (int)(blockDim.x >> 5) + w;
-    int* ebuf = ws + w * kWarpWs;
-    int* cbuf = ebuf + kCellCap;
     if (C.S <= 8 * nw) {
-      for (int q = gw; q < C.S; q += nw) query_warp(C, q, lane, cbuf);
+      for (int q = (int)blockIdx.x * (int)(blockDim.x >> 5) + w; q < C.S; q += nw) query_warp(C, q, lane, ws + w * kWarpWs);
     } else {
-      for (int base = gw * 32; base < C.H; base += nw * 32) {
-        const uint32_t hh = (uint32_t)(base + lane);
-        unsigned occ = __ballot_sync(0xffffffffu, (int)hh < C.H && C.hcount[hh] > 0u);
-        while (occ) {
-          const int l = __ffs(occ) - 1;
-          occ &= occ - 1u;
-          query_bucket(C, (uint32_t)(base + l), lane, ebuf, cbuf);
-        }
-      }
+      for (int q = tid; q < C.S; q += nthr) query_one(C, q);
     }
   }
   if (!grid_barrier(C.bar, G, C.spins, C.status)) return false;

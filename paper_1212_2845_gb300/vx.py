@@ -314,7 +314,9 @@ class Sim:
         _check(self._L.vx_set_batching(self.h, int(group_voxels)))
 
     def set_multistep(self, on):
-        _check(self._L.vx_set_multistep(self.h, int(bool(on))))
+        """0: one launch per step; 1 (default): multi-step launches (the
+        resident form on small lattices); 2: the cooperative grid launch."""
+        _check(self._L.vx_set_multistep(self.h, int(on)))
 
     def set_barrier_limits(self, max_spins=0, phantom_ctas=0):
         _check(self._L.vx_set_barrier_limits(self.h, int(max_spins), int(phantom_ctas)))

@@ -26,6 +26,7 @@ def test_barrier_wait_runs_out_and_reports_timeout(vx):
     sc = scenes.hetero_block(dims=(20, 18, 12), seed=9)
     sim = vx.Sim(sc)
     assert sim.tiling()["n_tiles"] > 1                 # several CTAs meet at the barrier
+    sim.set_multistep(2)                               # the cooperative grid launch (not the resident form)
     sim.set_barrier_limits(max_spins=2000, phantom_ctas=1)
     with pytest.raises(vx.VxError) as e:
         sim.step(5)

@@ -539,15 +539,16 @@ def test_multistep_launch_bitwise_equals_per_step_launches(vx, which):
     else:
         sc = scenes.population(n_bodies=30, seed=8, lo=3, hi=14)
     out = []
-    for multi in (0, 1):
+    for multi in (0, 1, 2):           # per-step launches, default (resident on small lattices), grid launch
         sim = vx.Sim(sc)
         sim.set_multistep(multi)
         sim.step(301)
         out.append(sim.read_state())
         assert sim.step_count == 301
         sim.close()
-    for k in ("offset", "quat", "vel", "angvel", "flags"):
-        assert np.array_equal(out[0][k].view(np.uint8), out[1][k].view(np.uint8)), k
+    for o in out[1:]:
+        for k in ("offset", "quat", "vel", "angvel", "flags"):
+            assert np.array_equal(out[0][k].view(np.uint8), o[k].view(np.uint8)), k
 
 
 @pytest.mark.parametrize("which", ["clapper_horizon", "clapper_every_step", "ball_impact", "shared_world"])
