@@ -545,6 +545,7 @@ def main():
     ap.add_argument("--only-batched", action="store_true", help="time only the batched form (profiling aid)")
     ap.add_argument("--only-collisions", action="store_true", help="time only the ball drop with collisions")
     ap.add_argument("--only-small", action="store_true", help="time only the small-lattice forms")
+    ap.add_argument("--only-hetero", action="store_true", help="time only the heterogeneous block (profiling aid)")
     ap.add_argument("--tile", type=int, default=0, help="tile size of the pipelined step (profiling aid; 0: default)")
     ap.add_argument("--pre-steps", type=int, default=PRE_STEPS,
                     help="untimed steps of the drop before the warm-up (profiling aid: 0 starts in the free fall)")
@@ -582,6 +583,11 @@ def main():
         return
     if args.only_small:
         print(json.dumps(small_lattice(torch.cuda.Stream())))
+        return
+    if args.only_hetero:
+        peak, _ = load_peaks()
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps(hetero_block_line(torch.cuda.Stream(), peak, flush, steps=args.steps, warmup=args.warmup)))
         return
     if ws > 1:
         import torch.distributed as dist
