@@ -87,11 +87,12 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
         const uint32_t e0 = C.hstart[hq], e1 = C.hstart[hq + 1];
         for (uint32_t e = e0; e < e1; ++e) {
           if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
+          // every field of the entry requested at once (one round trip)
           const int4 c1 = C.scell[e];
-          if (c1.w == s) continue;
-          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
           const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
           const int4 f = C.sinf[e];  // voxel, lattice word, body
+          if (c1.w == s) continue;
+          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
           const int u = f.x;
           if (C.body && f.z != b) {
             if (!C.qorg) continue;  // bodies are separate worlds
@@ -150,10 +151,10 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
     for (uint32_t e = e0; e < e1; ++e) {
       if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
       const int4 c1 = C.scell[e];
-      if (c1.w == s) continue;
-      if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
       const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
       const int4 f = C.sinf[e];  // voxel, lattice word, body
+      if (c1.w == s) continue;
+      if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
       const int u = f.x;
       if (C.body && f.z != b) {
         if (!C.qorg) continue;  // bodies are separate worlds
