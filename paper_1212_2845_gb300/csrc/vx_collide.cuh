@@ -87,9 +87,9 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
         const uint32_t e0 = C.hstart[hq], e1 = C.hstart[hq + 1];
         for (uint32_t e = e0; e < e1; ++e) {
           if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
-          // every field of the entry requested at once (one round trip)
+          // cell and lattice word together; the position only for the few
+          // entries the lattice-distance exclusion lets through
           const int4 c1 = C.scell[e];
-          const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
           const int4 f = C.sinf[e];  // voxel, lattice word, body
           if (c1.w == s) continue;
           if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
@@ -101,6 +101,7 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
             int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
             if (man <= 3) continue;
           }
+          const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
           int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
           if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
           if (n < kCandCap) list[n++] = u; else overflow = true;
@@ -151,7 +152,6 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
     for (uint32_t e = e0; e < e1; ++e) {
       if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
       const int4 c1 = C.scell[e];
-      const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
       const int4 f = C.sinf[e];  // voxel, lattice word, body
       if (c1.w == s) continue;
       if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
@@ -163,6 +163,7 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
         const int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
         if (man <= 3) continue;
       }
+      const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
       const int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
       if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
       if (n < kLaneCap) mine[n++] = u; else overflow = true;
