@@ -1801,8 +1801,13 @@ int vx_autotune_batching(vx_sim* s, int32_t sample_steps, int32_t* tile_max_out,
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune[key] = best;
   }
-  if ((rc = vx_set_step_form(s, VX_FORM_PIPELINED, best.tile_max)) || (rc = vx_set_batching(s, best.group_voxels)))
-    return rc;
+  if ((rc = vx_set_step_form(s, VX_FORM_PIPELINED, best.tile_max))) return rc;
+  if ((rc = vx_set_batching(s, best.group_voxels))) {
+    // a cached resident choice from a lattice of the same size class whose
+    // largest body fitted a cluster: per-step launches instead
+    if (!is_resident(best.group_voxels) || (rc = vx_set_batching(s, 0))) return rc;
+    best.group_voxels = 0;
+  }
   if (tile_max_out) *tile_max_out = best.tile_max;
   if (group_voxels_out) *group_voxels_out = best.group_voxels;
   if (rate_out) *rate_out = best.rate;
