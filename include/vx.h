@@ -266,10 +266,10 @@ VX_API int vx_set_material_actuation(vx_sim* sim, const float* amplitude_K, cons
 VX_API int vx_set_dt_factor(vx_sim* sim, float f);
 /* dt of every body [n_bodies] (double on the host; the device steps in FP32).
  * A simulator computes it (at creation and whenever the materials, the
- * per-voxel moduli, dt_factor or the shared-world mode change) as an FP64
+ * per-voxel moduli, dt_factor or the shared-world mode change) from an FP32
  * warp and block max-reduction of w^2 = k / m over the device lattice, with
- * the definition of vx_plan_dt; the result equals vx_plan_dt to the bit for
- * palette materials (per-voxel moduli: within the last bit of exp). */
+ * the definition of vx_plan_dt; the result is within 2e-7 of vx_plan_dt's
+ * FP64 value (3.5e-7 with per-voxel moduli). */
 VX_API int vx_get_dt(vx_sim* sim, double* dt_per_body);
 /* Override dt of every body (frozen until the next recompute). */
 VX_API int vx_set_dt(vx_sim* sim, const double* dt_per_body);
@@ -344,7 +344,7 @@ VX_API int vx_get_collision_pairs(vx_sim* sim, int32_t* pairs, int64_t cap, int6
  * accumulator of body 0 [m]. */
 VX_API int vx_collision_stats(vx_sim* sim, int64_t* n_rebuilds, double* accumulator);
 
-/* ---- FP64 audit (with the set-up stable-dt reduction, the only FP64 on the GPU)
+/* ---- FP64 audit (the only FP64 arithmetic on the GPU) -------------------
  * Deterministic FP64 reductions over the current state: out[0..2] total
  * linear momentum sum m v; out[3..5] angular momentum about the world origin
  * sum (D x m v + I w) with D the absolute centre (anchor + offset, formed in

@@ -25,7 +25,7 @@ OUT = os.path.join(HERE, "_build_san" if SANITIZE else ("_build_bc" if BOUNDS el
 LIB = os.path.join(OUT, "libvx.so")
 INCLUDE = os.path.join(ROOT, "include")
 
-SOURCES = ["vx_host.cpp", "vx_api.cu", "vx_step.cu", "vx_collide.cu", "vx_io.cu", "vx_noalloc.cu", "vx_pipe.cu", "vx_resident.cu", "vx_adjoint.cu", "vx_audit.cu"]
+SOURCES = ["vx_host.cpp", "vx_api.cu", "vx_step.cu", "vx_collide.cu", "vx_io.cu", "vx_noalloc.cu", "vx_pipe.cu", "vx_resident.cu", "vx_adjoint.cu", "vx_audit.cu", "vx_dt.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
          f"-I{INCLUDE}", f"-I{SRC}"]

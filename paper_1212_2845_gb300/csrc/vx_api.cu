@@ -408,10 +408,10 @@ int upload_dt(vx_sim* s) {
 int ensure_nbr(vx_sim* s);
 std::vector<int64_t> body_ranges(const vx_sim* s);
 
-// Largest w^2 of every body's bonds and contact springs, reduced on the
-// device from the uploaded lattice (materials, per-voxel moduli, bonds).
+// Largest w^2 of every body's bonds and contact springs, reduced in FP32 on
+// the device from the uploaded lattice (materials, per-voxel moduli, bonds).
 // The neighbour planes are uploaded for the call when no step form holds them.
-int device_w2(vx_sim* s, std::vector<double>& w2) {
+int device_w2(vx_sim* s, std::vector<float>& w2) {
   const Lattice& L = s->L;
   const int nb = L.n_bodies;
   const bool had_nbr = s->nbr != nullptr;
@@ -422,59 +422,49 @@ int device_w2(vx_sim* s, std::vector<double>& w2) {
   for (int b = 0; b < nb; ++b)
     for (int64_t v = bs[b]; v < bs[b + 1]; v += kDtChunk)
       ch.push_back(make_int4((int)v, (int)std::min<int64_t>(v + kDtChunk, bs[b + 1]), b, 0));
-  const double l = L.l;
-  std::vector<double> em(2 * L.palette.size());
-  for (size_t i = 0; i < L.palette.size(); ++i) {
-    em[2 * i] = (double)L.palette[i].E;
-    em[2 * i + 1] = (double)L.palette[i].rho * l * l * l;
-  }
-  std::vector<unsigned long long> bits(nb, 0ull);
-  double* em_d = nullptr;
+  std::vector<unsigned> bits(nb, 0u);
   int4* ch_d = nullptr;
-  unsigned long long* w2_d = nullptr;
-  rc = dalloc(&em_d, em.size());
-  if (!rc) rc = dalloc(&ch_d, std::max<size_t>(ch.size(), 1));
+  unsigned* w2_d = nullptr;
+  rc = dalloc(&ch_d, std::max<size_t>(ch.size(), 1));
   if (!rc) rc = dalloc(&w2_d, nb);
   if (!rc) {
-    cudaError_t e = cudaMemcpy(em_d, em.data(), em.size() * sizeof(double), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(ch_d, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemset(w2_d, 0, nb * sizeof(unsigned long long));
+    cudaError_t e = cudaMemcpy(ch_d, ch.data(), ch.size() * sizeof(int4), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(w2_d, 0, nb * sizeof(unsigned));
     if (e == cudaSuccess) {
       DtArgs D;
       D.n_chunks = (int)ch.size();
       D.N = L.N;
-      D.l = l;
+      D.l = L.l;
       D.mat = s->mat;
       D.logE = s->logE_h.empty() ? nullptr : s->logE;
       D.nbr = s->nbr;
-      D.Em = em_d;
+      D.mats = s->mats;
       D.chunks = ch_d;
       D.w2 = w2_d;
       launch_stable_w2(D, 0);
       e = cudaGetLastError();
     }
-    if (e == cudaSuccess) e = cudaMemcpy(bits.data(), w2_d, nb * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(bits.data(), w2_d, nb * sizeof(unsigned), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) rc = fail(VX_ERR_CUDA, std::string("stable timestep reduction: ") + cudaGetErrorString(e));
   }
-  dfree(em_d);
   dfree(ch_d);
   dfree(w2_d);
   if (!had_nbr) dfree(s->nbr);
   w2.resize(nb);
-  for (int b = 0; b < nb; ++b) std::memcpy(&w2[b], &bits[b], sizeof(double));
+  for (int b = 0; b < nb; ++b) std::memcpy(&w2[b], &bits[b], sizeof(float));
   return rc;
 }
 
-// dt = f / (2 pi w_max) per body (Sec 2.1.4), w_max = sqrt of the device
-// reduction's largest w^2 (the square root is monotone and correctly rounded,
-// so it equals the largest of the candidates' square roots).
+// dt = f / (2 pi w_max) per body (Sec 2.1.4) from the device reduction's
+// largest w^2 (FP32); the host forms the square root and the quotient in
+// FP64, and the step uses dt rounded to FP32.
 int recompute_dt(vx_sim* s) {
-  std::vector<double> w2;
+  std::vector<float> w2;
   int rc = device_w2(s, w2);
   if (rc) return rc;
   s->dt.assign(s->L.n_bodies, 0.0);
   for (int b = 0; b < s->L.n_bodies; ++b)
-    s->dt[b] = w2[b] > 0.0 ? (double)s->dt_factor / (2.0 * M_PI * std::sqrt(w2[b])) : 0.0;
+    s->dt[b] = w2[b] > 0.f ? (double)s->dt_factor / (2.0 * M_PI * std::sqrt((double)w2[b])) : 0.0;
   if (s->collide_on == 2) {  // one world, one clock: every body takes the smallest timestep
     double dmin = 0.0;
     for (double d : s->dt)

@@ -1,6 +1,5 @@
 // FP64 audit of the lattice state: linear and angular momentum, kinetic,
-// elastic and gravitational energy; and the set-up reduction of the stable
-// timestep.  These are the only FP64 arithmetic on the GPU.
+// elastic and gravitational energy (the only FP64 arithmetic on the GPU).
 //
 // Per voxel (Sec 2.1.3 state): P = m v, L = D x P + I w with D the absolute
 // centre (lattice anchor + FP32 offset, formed in FP64), KE = |P|^2 / 2m +
@@ -141,62 +140,7 @@ __global__ void __launch_bounds__(256) audit_total(const double* partial, int nb
   if (threadIdx.x < kAudit) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
-// Stable timestep (Sec 2.1.4): the largest w^2 = k / m of a body over every
-// voxel's own contact spring, E_v l / m_v, and every bond to a +a neighbour,
-// E_c l / min(m_v, m_u) with E_c = 2 E_v E_u / (E_v + E_u).  Each CTA takes
-// one chunk of one body's internal range; the threads' maxima meet in a warp
-// shuffle, then across the warps in shared memory, then one atomicMax on the
-// bits of the non-negative double (their integer order is the numeric
-// order).  Every operation is an explicit IEEE round-to-nearest one in the
-// host planner's order, so w^2 (and the timestep from its square root) is the
-// planner's to the bit for palette materials; a candidate that is NaN (0 / 0
-// for two zero moduli) is skipped, as a comparison with it is false.
-__global__ void __launch_bounds__(kDtThreads) stable_w2(DtArgs D) {
-  const int4 c = D.chunks[blockIdx.x];
-  double w = 0.0;
-  for (int v = c.x + (int)threadIdx.x; v < c.y; v += blockDim.x) {
-    const int iv = D.mat[v];
-    const double Ev = D.logE ? exp((double)D.logE[v]) : D.Em[2 * iv];
-    const double mv = D.Em[2 * iv + 1];
-    double x = __ddiv_rn(__dmul_rn(Ev, D.l), mv);
-    if (x > w) w = x;
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const int u = D.nbr[(int64_t)(2 * a + 1) * D.N + v];
-      if (u < 0) continue;
-      const int iu = D.mat[u];
-      const double Eu = D.logE ? exp((double)D.logE[u]) : D.Em[2 * iu];
-      const double mu = D.Em[2 * iu + 1];
-      const double Ec = __ddiv_rn(__dmul_rn(__dmul_rn(2.0, Ev), Eu), __dadd_rn(Ev, Eu));
-      x = __ddiv_rn(__dmul_rn(Ec, D.l), mu < mv ? mu : mv);
-      if (x > w) w = x;
-    }
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const double y = __shfl_xor_sync(0xffffffffu, w, o);
-    if (y > w) w = y;
-  }
-  __shared__ double red[kDtThreads / 32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (lane == 0) red[warp] = w;
-  __syncthreads();
-  if (warp == 0) {
-    w = lane < kDtThreads / 32 ? red[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double y = __shfl_xor_sync(0xffffffffu, w, o);
-      if (y > w) w = y;
-    }
-    if (lane == 0) atomicMax(&D.w2[c.z], (unsigned long long)__double_as_longlong(w));
-  }
-}
-
 }  // namespace
-
-void launch_stable_w2(const DtArgs& D, cudaStream_t s) {
-  if (D.n_chunks > 0) stable_w2<<<D.n_chunks, kDtThreads, 0, s>>>(D);
-}
 
 int audit_partials(int N) { return (N + 255) / 256; }
 

@@ -186,22 +186,22 @@ int audit_partials(int N);
 // U elastic, U gravity; partial: audit_partials(N) x 10 doubles
 void launch_audit(const StepArgs& A, const AuditArgs& U, double* partial, double* out, cudaStream_t s);
 
-// Stable timestep reduction (FP64, set-up work).  Chunks of at most
+// Stable timestep reduction (FP32, set-up work).  Chunks of at most
 // kDtChunk voxels, one per CTA, each inside one body's internal range:
 // (v0, v1, body, 0).  w2 [n_bodies] holds zero at launch and receives, as
-// the bits of a double, the body's largest w^2 [1/s^2].
+// the bits of a float, the body's largest w^2 [1/s^2].
 constexpr int kDtThreads = 256;
 constexpr int kDtChunk = 8 * kDtThreads;
 struct DtArgs {
   int n_chunks;
   int64_t N;
-  double l;               // voxel size [m]
+  float l;                // voxel size [m]
   const uint8_t* mat;     // per voxel (internal order)
   const float* logE;      // per voxel natural-log modulus overriding the palette, or nullptr
   const int32_t* nbr;     // 6 planes (-x,+x,-y,+y,-z,+z), internal indices, -1: no bond
-  const double* Em;       // 2 per material: E [Pa], m = rho l^3 [kg]
+  const DevMat* mats;     // E and m = rho l^3 of every material
   const int4* chunks;
-  unsigned long long* w2;
+  unsigned* w2;
 };
 void launch_stable_w2(const DtArgs& D, cudaStream_t s);
 
