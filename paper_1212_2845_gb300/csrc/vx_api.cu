@@ -187,6 +187,7 @@ struct vx_sim {
   int64_t* sxq = nullptr;    // quantised coordinates (3 planes)
   int4* sinf = nullptr;      // voxel, lattice word, body
   int32_t* ccount = nullptr;
+  int32_t* vcnt = nullptr;   // per voxel: candidate count (staged by the step)
   int32_t* cand = nullptr;
   float* acc = nullptr;
   unsigned* vmax = nullptr;
@@ -281,6 +282,7 @@ StepArgs step_args(vx_sim* s) {
   A.max_local = s->T.max_local;
   A.sidx = s->sidx;
   A.ccount = s->ccount;
+  A.vcnt = s->vcnt;
   A.cand = s->cand;
   A.vmax_bits = s->vmax;
   A.status = s->status;
@@ -315,6 +317,7 @@ CollideArgs collide_args(vx_sim* s) {
   C.sxq = s->sxq;
   C.sinf = s->sinf;
   C.ccount = s->ccount;
+  C.vcnt = s->vcnt;
   C.cand = s->cand;
   C.acc = s->acc;
   C.vmax_bits = s->vmax;
@@ -502,6 +505,7 @@ int alloc_collisions(vx_sim* s) {
       (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, kRebuildMaxGrid)) || (rc = dalloc(&s->cbar, 2)) ||
       (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->scell, S)) || (rc = dalloc(&s->sxq, 3 * S)) ||
       (rc = dalloc(&s->sinf, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
+      (rc = dalloc(&s->vcnt, L.N)) ||
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
       (rc = dalloc(&s->hdone, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
@@ -515,6 +519,7 @@ int alloc_collisions(vx_sim* s) {
   VX_CUDA(cudaMemcpy(s->surf, surf.data(), S * sizeof(int32_t), cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemcpy(s->sidx, sidx.data(), L.N * sizeof(int32_t), cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemset(s->ccount, 0, std::max<int64_t>(S, 1) * sizeof(int32_t)));
+  VX_CUDA(cudaMemset(s->vcnt, 0, L.N * sizeof(int32_t)));
   VX_CUDA(cudaMemset(s->acc, 0, L.n_bodies * sizeof(float)));
   VX_CUDA(cudaMemset(s->cflag, 0, L.n_bodies * sizeof(int)));
   VX_CUDA(cudaMemset(s->any, 0, sizeof(int)));
@@ -528,7 +533,7 @@ int alloc_collisions(vx_sim* s) {
 void free_collisions(vx_sim* s) {
   dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket); dfree(s->hcount); dfree(s->hcursor);
   dfree(s->hstart); dfree(s->bsum); dfree(s->cbar); dfree(s->sorted); dfree(s->ccount); dfree(s->cand);
-  dfree(s->scell); dfree(s->sxq); dfree(s->sinf);
+  dfree(s->scell); dfree(s->sxq); dfree(s->sinf); dfree(s->vcnt);
   dfree(s->acc); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
   s->coll_alloc = false;
   s->coll_S = 0;
@@ -1034,6 +1039,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
+  dfree(s->scell); dfree(s->sxq); dfree(s->sinf); dfree(s->vcnt);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
   dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar); dfree(s->qorg);

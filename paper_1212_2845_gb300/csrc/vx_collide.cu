@@ -75,8 +75,10 @@ constexpr int kRebuildThreads = 256;
 
 // The whole rebuild in one cooperative launch (all CTAs co-resident; phases
 // separated by grid barriers, whose waits are bounded: on a timeout the
-// launch ends with the timeout status bit set).
-__global__ void __launch_bounds__(kRebuildThreads) rebuild_all(CollideArgs C) {
+// launch ends with the timeout status bit set).  Five CTAs per SM (at most 48
+// registers) give 194,560 threads, one per searched voxel of a 192,848-voxel
+// ball surface in a single pass of the query; at four the query needs two.
+__global__ void __launch_bounds__(kRebuildThreads, 5) rebuild_all(CollideArgs C) {
   extern __shared__ int ws[];  // kWarpWs ints per warp
   if (*C.any == 0) return;  // the same value for every CTA: set by an earlier launch
   rebuild_phases(C, gridDim.x + C.extra, ws);

@@ -118,6 +118,7 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
   int32_t* out = C.cand + (int64_t)s * kCandCap;
   for (int i = 0; i < n; ++i) out[i] = list[i];
   C.ccount[s] = n;
+  if (C.vcnt) C.vcnt[v] = n;
   if (overflow) atomicOr(C.status, kStatusCapacity);
 }
 
@@ -197,7 +198,10 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
   __syncwarp();
   int32_t* out = C.cand + (int64_t)s * kCandCap;
   for (int i = lane; i < m; i += 32) out[i] = buf[i];
-  if (lane == 0) C.ccount[s] = m;
+  if (lane == 0) {
+    C.ccount[s] = m;
+    if (C.vcnt) C.vcnt[v] = m;
+  }
   if (__any_sync(0xffffffffu, overflow) && lane == 0) atomicOr(C.status, kStatusCapacity);
   __syncwarp();  // the buffer is reused for the warp's next voxel
 }

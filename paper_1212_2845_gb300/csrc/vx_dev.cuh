@@ -108,6 +108,7 @@ struct StepArgs {
   // collisions
   const int32_t* sidx;     // per voxel: surface index or -1
   const int32_t* ccount;   // per surface voxel
+  const int32_t* vcnt;     // per voxel: candidate count (0 for voxels outside the search)
   const int32_t* cand;     // per surface voxel, kCandCap slots (internal indices, ascending)
   unsigned* vmax_bits;     // per body, float bits of max |v|
   int* status;             // [0] bits, [1] first bad voxel (internal), [2..3] step, [4..5] bounds site, index
@@ -441,7 +442,7 @@ struct VoxMeta {
   uint8_t fl;     // flags
   float dt, z0;   // body timestep, anchor height of the voxel centre
   V3f fext;
-  int si;         // surface index (collisions on) or -1
+  int nc;         // collision candidates of the voxel (0 with collisions off)
 };
 
 __device__ __forceinline__ VoxMeta load_meta(const StepArgs& A, int v) {
@@ -454,7 +455,7 @@ __device__ __forceinline__ VoxMeta load_meta(const StepArgs& A, int v) {
   mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
   const int64_t P = A.pitch;
   mt.fext = A.fext ? v3(A.fext[v], A.fext[P + v], A.fext[2 * P + v]) : v3(0.f, 0.f, 0.f);
-  mt.si = A.collide_on ? A.sidx[v] : -1;
+  mt.nc = A.collide_on ? A.vcnt[v] : 0;
   return mt;
 }
 
@@ -479,12 +480,13 @@ __device__ __forceinline__ float voxel_update(const StepArgs& A, int v, const Vo
   }
   const float hl = mul_(0.5f, l);
   float h = fma_(hl, adT, hl);  // current half size l (1 + adT) / 2
-  if (A.collide_on) {
-    int si = mt.si;
+  if (A.collide_on && mt.nc > 0) {
+    // the list is read only for a voxel that has candidates (most have none)
+    const int si = A.sidx[v];
     if (si >= 0) {
       const uint32_t lp = mt.lat;
       int vi = (int)(lp & 2047u), vj = (int)((lp >> 11) & 2047u), vk = (int)(lp >> 22);
-      int nc = A.ccount[si];
+      const int nc = mt.nc;
       const int32_t* cl = A.cand + (int64_t)si * kCandCap;
       for (int c = 0; c < nc; ++c) {
         int j = cl[c];

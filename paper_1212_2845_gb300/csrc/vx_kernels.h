@@ -52,6 +52,7 @@ struct CollideArgs {
   int64_t* sxq;
   int4* sinf;
   int32_t* ccount;        // S
+  int32_t* vcnt;          // per voxel (internal order): the same counts for the step, or nullptr
   int32_t* cand;          // S x kCandCap
   float* acc;             // per body
   unsigned* vmax_bits;    // per body

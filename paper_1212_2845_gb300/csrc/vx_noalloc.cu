@@ -144,6 +144,7 @@ extern "C" VX_API int vx_collision_candidates_static(const uint32_t* lat, const 
   C.sxq = reinterpret_cast<int64_t*>(base + kOffSxq);
   C.sinf = reinterpret_cast<int4*>(base + kOffSinf);
   C.ccount = cand_count;
+  C.vcnt = nullptr;
   C.cand = cand;
   C.acc = reinterpret_cast<float*>(base + kOffAcc);
   C.vmax_bits = nullptr;

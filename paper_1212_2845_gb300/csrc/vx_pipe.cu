@@ -57,7 +57,7 @@ template <int TMAX> struct Stage {
   uint32_t* lat;
   int32_t* body;   // null for one body
   float* fx;       // 3 x TMAX external force (null when unused)
-  int32_t* si;     // surface index of owned voxels (null without collisions)
+  int32_t* nc;     // collision candidates of owned voxels (null without collisions)
   uint32_t* hb;    // halo bonds
   // floats this layout needs
   static __host__ __device__ int floats(bool ph, bool le, bool body, bool fext, bool col) {
@@ -78,7 +78,7 @@ template <int TMAX> struct Stage {
     le = hle ? p : nullptr; p += hle ? ML : 0;
     body = hbody ? reinterpret_cast<int32_t*>(p) : nullptr; p += hbody ? TMAX : 0;
     fx = hfext ? p : nullptr; p += hfext ? 3 * TMAX : 0;
-    si = hcol ? reinterpret_cast<int32_t*>(p) : nullptr;
+    nc = hcol ? reinterpret_cast<int32_t*>(p) : nullptr;
   }
   __device__ __forceinline__ VoxS vox(int k) const { return unpack_vox(A[k], B[k], C[k], D[k]); }
 };
@@ -103,7 +103,7 @@ __device__ __forceinline__ void issue_tile(const StepArgs& A, const StPtr& G, co
     cp8(&S.pl[i], &A.plus2[g]);
     cp4(&S.lat[i], &A.lat[g]);
     if (S.body) cp4(&S.body[i], &A.body[g]);
-    if (S.si) cp4(&S.si[i], &A.sidx[g]);
+    if (S.nc) cp4(&S.nc[i], &A.vcnt[g]);
     if (S.fx) {
       cp4(&S.fx[i], &A.fext[g]);
       cp4(&S.fx[TMAX + i], &A.fext[A.pitch + g]);
@@ -179,7 +179,8 @@ __device__ __forceinline__ void tile_props(const StepArgs& A, const Stage<TMAX>&
 template <int TMAX>
 __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX>& S, float4* props, float4* F4,
                                              float2* F2, const DevMat* mats, const float* lut, const TileRegs& cur,
-                                             uint8_t fl_cur, const Stage<TMAX>& Sn, const TileRegs& nxt) {
+                                             uint8_t fl_cur, const Stage<TMAX>& Sn, const TileRegs& nxt,
+                                             float& vrun) {
   const int i = threadIdx.x;
   const int T = cur.T;
   const bool own = i < T;
@@ -245,12 +246,17 @@ __device__ __forceinline__ void compute_tile(const StepArgs& A, const Stage<TMAX
     mt.dt = A.dt_body[mt.b];
     mt.z0 = fma_(add_((float)(int)(mt.lat >> 22), 0.5f), A.l, A.origin[3 * mt.b + 2]);
     mt.fext = S.fx ? v3(S.fx[i], S.fx[TMAX + i], S.fx[2 * TMAX + i]) : v3(0.f, 0.f, 0.f);
-    mt.si = S.si ? S.si[i] : -1;
+    mt.nc = S.nc ? S.nc[i] : 0;
     body = mt.b;
     store_bond_sums(A, cur.v0 + i, F, M);
     speed = voxel_finish(A, cur.v0 + i, mt, s, F, M, pr.z, pr.x, mats);
   }
-  if (A.collide_on) horizon_max(A, body, own, speed);
+  // the collision horizon's largest speed: per tile when the tiles of a CTA
+  // may belong to several bodies, else kept in a register over all tiles
+  if (A.collide_on) {
+    if (A.body) horizon_max(A, body, own, speed);
+    else if (own) vrun = fmaxf(vrun, speed);
+  }
 }
 
 // One step over the tiles t, t + stride, ... < t_end (pipelined staging; two
@@ -281,6 +287,7 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& A, int t, int stride,
   uint8_t fl_cur = i < cur.T ? A.flags[cur.v0 + i] : 0;
   TileRegs nxt = load_tile<TMAX>(A, t + stride, t_end);
   int b = 0;
+  float vrun = 0.f;  // largest speed of this thread's voxels (one body)
   for (;;) {
     Stage<TMAX> S, Sn;
     S.carve(smem + b * sf, hph, hle, hbody, hfx, hcol);
@@ -295,7 +302,7 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& A, int t, int stride,
     }
     // descriptor and halo indices of the tile after it
     const TileRegs nn = load_tile<TMAX>(A, t + 2 * stride, t_end);
-    compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur, Sn, nxt);
+    compute_tile<TMAX>(A, S, props, F4, F2, mats, lut, cur, fl_cur, Sn, nxt, vrun);
     if (!nxt.valid) break;  // uniform
     cur = nxt;
     nxt = nn;
@@ -303,6 +310,7 @@ __device__ __forceinline__ void pipe_tiles(const StepArgs& A, int t, int stride,
     t += stride;
     b ^= 1;
   }
+  if (hcol && !hbody) horizon_max(A, 0, true, vrun);  // one atomic per warp for all its tiles
 }
 
 }  // namespace

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
         mt.dt = S.dt[u];
         mt.z0 = S.z0[u];
         mt.fext = FX ? v3(S.fx[u], S.fx[V + u], S.fx[2 * V + u]) : v3(0.f, 0.f, 0.f);
-        mt.si = -1;
+        mt.nc = 0;
         VoxS s = S.vox(u);
         uint8_t fl;
         voxel_update(A, u0 + u, mt, s, fl, F, M, p.z, p.x, S.mats);
