@@ -290,7 +290,13 @@ VX_API int vx_set_initial_velocity(vx_sim* sim, const float v[3]);
  * host).  Synchronous with respect to work already queued on `stream`. */
 VX_API int vx_read_state(vx_sim* sim, const vx_state_view* out, int32_t dst_on_device, void* stream);
 /* Overwrite the state from caller buffers (NULL fields unchanged).  With
- * collisions on, the candidate lists are rebuilt from the written state.
+ * collisions on, the write counts as motion for the collision horizon: each
+ * body's accumulator grows by twice the largest distance the write moves one
+ * of its voxels, and the candidate lists of the bodies that reach the
+ * threshold (every body after a rebuild that timed out or overflowed) are
+ * rebuilt from the written state; lists kept hold every pair that can touch
+ * before the next rebuild, so a write that moves nothing (velocities, flags,
+ * or the state just read) costs no rebuild and changes no result.
  * Together with vx_read_state and the step counter (vx_get_step /
  * vx_set_step) this is a bit-exact checkpoint and resume. */
 VX_API int vx_write_state(vx_sim* sim, const vx_state_view* in, int32_t src_on_device, void* stream);
@@ -328,8 +334,8 @@ VX_API int vx_relax(vx_sim* sim, int64_t max_steps, double v_tol, int32_t check_
 /* Rebuild the surface-voxel candidate list from the current positions now.
  * Synchronous.  VX_ERR_CAPACITY when a voxel has more than 48 candidates;
  * VX_ERR_TIMEOUT when a grid barrier of the rebuild gave up waiting (the
- * candidate lists are then unspecified until the next vx_reset or
- * vx_write_state). */
+ * candidate lists are then unspecified until the next rebuild: vx_reset, a
+ * vx_write_state, which then rebuilds every body, or this call). */
 VX_API int vx_rebuild_collisions(vx_sim* sim, void* stream);
 /* Collision scheme (the paper compares these, Sec 3 "Speedup of self
  * collision schemes"): all_voxels = 1 searches every voxel instead of the

@@ -188,6 +188,7 @@ struct vx_sim {
   int4* sinf = nullptr;      // voxel, lattice word, body
   int32_t* ccount = nullptr;
   int32_t* vcnt = nullptr;   // per voxel: candidate count (staged by the step)
+  unsigned* dmax = nullptr;  // per body: largest displacement of a state write (float bits)
   int32_t* cand = nullptr;
   float* acc = nullptr;
   unsigned* vmax = nullptr;
@@ -505,7 +506,7 @@ int alloc_collisions(vx_sim* s) {
       (rc = dalloc(&s->hstart, H + 1)) || (rc = dalloc(&s->bsum, kRebuildMaxGrid)) || (rc = dalloc(&s->cbar, 2)) ||
       (rc = dalloc(&s->sorted, S)) || (rc = dalloc(&s->scell, S)) || (rc = dalloc(&s->sxq, 3 * S)) ||
       (rc = dalloc(&s->sinf, S)) || (rc = dalloc(&s->ccount, S)) || (rc = dalloc(&s->cand, S * kCandCap)) ||
-      (rc = dalloc(&s->vcnt, L.N)) ||
+      (rc = dalloc(&s->vcnt, L.N)) || (rc = dalloc(&s->dmax, L.n_bodies)) ||
       (rc = dalloc(&s->acc, L.n_bodies)) || (rc = dalloc(&s->cflag, L.n_bodies)) || (rc = dalloc(&s->any, 1)) ||
       (rc = dalloc(&s->hdone, 1)) ||
       (rc = dalloc(&s->nreb, 1)))
@@ -520,6 +521,7 @@ int alloc_collisions(vx_sim* s) {
   VX_CUDA(cudaMemcpy(s->sidx, sidx.data(), L.N * sizeof(int32_t), cudaMemcpyHostToDevice));
   VX_CUDA(cudaMemset(s->ccount, 0, std::max<int64_t>(S, 1) * sizeof(int32_t)));
   VX_CUDA(cudaMemset(s->vcnt, 0, L.N * sizeof(int32_t)));
+  VX_CUDA(cudaMemset(s->dmax, 0, L.n_bodies * sizeof(unsigned)));
   VX_CUDA(cudaMemset(s->acc, 0, L.n_bodies * sizeof(float)));
   VX_CUDA(cudaMemset(s->cflag, 0, L.n_bodies * sizeof(int)));
   VX_CUDA(cudaMemset(s->any, 0, sizeof(int)));
@@ -533,7 +535,7 @@ int alloc_collisions(vx_sim* s) {
 void free_collisions(vx_sim* s) {
   dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket); dfree(s->hcount); dfree(s->hcursor);
   dfree(s->hstart); dfree(s->bsum); dfree(s->cbar); dfree(s->sorted); dfree(s->ccount); dfree(s->cand);
-  dfree(s->scell); dfree(s->sxq); dfree(s->sinf); dfree(s->vcnt);
+  dfree(s->scell); dfree(s->sxq); dfree(s->sinf); dfree(s->vcnt); dfree(s->dmax);
   dfree(s->acc); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
   s->coll_alloc = false;
   s->coll_S = 0;
@@ -1039,7 +1041,7 @@ void vx_destroy(vx_sim* s) {
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket);
   dfree(s->hcount); dfree(s->hcursor); dfree(s->hstart); dfree(s->bsum); dfree(s->sorted); dfree(s->ccount);
   dfree(s->cand); dfree(s->acc); dfree(s->vmax); dfree(s->cflag); dfree(s->any); dfree(s->nreb); dfree(s->hdone);
-  dfree(s->scell); dfree(s->sxq); dfree(s->sinf); dfree(s->vcnt);
+  dfree(s->scell); dfree(s->sxq); dfree(s->sinf); dfree(s->vcnt); dfree(s->dmax);
   dfree(s->ro_ckpt); dfree(s->ro_cfl); dfree(s->ro_seg); dfree(s->ro_sfl); dfree(s->ro_sfm); dfree(s->adj);
   dfree(s->cw);
   dfree(s->bstart); dfree(s->loss_d); dfree(s->wb_d); dfree(s->ctr_d); dfree(s->aud); dfree(s->bar); dfree(s->vmax_d); dfree(s->cbar); dfree(s->qorg);
@@ -1368,6 +1370,22 @@ int vx_write_state(vx_sim* s, const vx_state_view* in, int32_t src_on_device, vo
   return VX_OK;
 }
 
+// With collisions on, a write is motion for the collision horizon: the
+// unpack records each body's largest displacement, the accumulators grow by
+// twice that, and only bodies that reach the threshold (every body after a
+// rebuild that timed out or overflowed) are rebuilt.  A write that moves no
+// voxel (velocities, flags, or the state just read) keeps the lists.
+int write_collisions(vx_sim* s, cudaStream_t st) {
+  const int rc = alloc_collisions(s);
+  if (rc) return rc;
+  update_threshold(s);
+  const CollideArgs C = collide_args(s);
+  launch_write_horizon(C, s->dmax, s->collide_on == 2, st);
+  launch_rebuild(C, st);
+  VX_CUDA(cudaGetLastError());
+  return VX_OK;
+}
+
 int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_device, void* stream) {
   if (s) ++s->gen;  // invalidates a recorded rollout
   int rc = check_sim(s);
@@ -1375,11 +1393,13 @@ int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_devi
   if (!in) return fail(VX_ERR_ARG, "view is NULL");
   cudaStream_t st = (cudaStream_t)stream;
   int N = (int)s->L.N;
+  if (s->collide_on && (rc = alloc_collisions(s))) return rc;
+  unsigned* dmax = s->collide_on ? s->dmax : nullptr;
   if (src_on_device) {
     launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset, in->quat, in->vel, in->angvel,
-                        in->flags, st);
+                        in->flags, st, s->body, dmax);
     VX_CUDA(cudaGetLastError());
-    return s->collide_on ? force_rebuild(s, st) : VX_OK;
+    return s->collide_on ? write_collisions(s, st) : VX_OK;
   }
   if ((rc = ensure_stage(s))) return rc;
   float* off = s->stage;
@@ -1394,10 +1414,9 @@ int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_devi
   if (in->flags) VX_CUDA(cudaMemcpyAsync(fl, in->flags, (size_t)N, cudaMemcpyHostToDevice, st));
   launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset ? off : nullptr,
                       in->quat ? quat : nullptr, in->vel ? vel : nullptr, in->angvel ? w : nullptr,
-                      in->flags ? fl : nullptr, st);
+                      in->flags ? fl : nullptr, st, s->body, dmax);
   VX_CUDA(cudaGetLastError());
-  // the candidate lists belong to the previous state: rebuild them from this one
-  return s->collide_on ? force_rebuild(s, st) : VX_OK;
+  return s->collide_on ? write_collisions(s, st) : VX_OK;
 }
 
 int vx_get_step(vx_sim* s, int64_t* step) {

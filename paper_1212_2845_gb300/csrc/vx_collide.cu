@@ -84,6 +84,49 @@ __global__ void __launch_bounds__(kRebuildThreads, 5) rebuild_all(CollideArgs C)
   rebuild_phases(C, gridDim.x + C.extra, ws);
 }
 
+// The largest written displacement d of a body moves any two of its voxels
+// relative to each other by at most 2 d, as a step's 2 max|v| dt does; the
+// relative margin 2^-16 covers the rounding of d.  One block.
+__global__ void write_horizon(CollideArgs C, unsigned* dmax, int world) {
+  __shared__ float red[256];
+  const bool all = (C.status[0] & (kStatusTimeout | kStatusCapacity)) != 0;
+  float m = 0.f;
+  for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) {
+    const float d = __uint_as_float(dmax[b]);
+    dmax[b] = 0u;
+    if (world) {
+      m = fmaxf(m, d);
+    } else {
+      float acc = __fmaf_rn(2.f * d, 1.f + 0x1p-16f, C.acc[b]);
+      if (all || acc >= C.threshold) {
+        acc = 0.f;
+        C.flag[b] = 1;
+        atomicExch(C.any, 1);
+      }
+      C.acc[b] = acc;
+    }
+  }
+  if (!world) return;  // uniform
+  red[threadIdx.x] = m;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) red[threadIdx.x] = fmaxf(red[threadIdx.x], red[threadIdx.x + o]);
+    __syncthreads();
+  }
+  const float acc = __fmaf_rn(2.f * red[0], 1.f + 0x1p-16f, C.acc[0]);
+  const bool rebuild = all || acc >= C.threshold;
+  if (rebuild)
+    for (int b = threadIdx.x; b < C.n_bodies; b += blockDim.x) C.flag[b] = 1;
+  if (threadIdx.x == 0) {
+    C.acc[0] = rebuild ? 0.f : acc;
+    if (rebuild) atomicExch(C.any, 1);
+  }
+}
+
+void launch_write_horizon(const CollideArgs& C, unsigned* dmax, int world, cudaStream_t st) {
+  write_horizon<<<1, 256, 0, st>>>(C, dmax, world);
+}
+
 // Raise every body's rebuild flag (forced rebuild).
 __global__ void flag_all(CollideArgs C) {
   for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < C.n_bodies; b += gridDim.x * blockDim.x) {

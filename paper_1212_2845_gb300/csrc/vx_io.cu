@@ -17,17 +17,52 @@ __global__ void pack_state(const float* __restrict__ st, int64_t P, int N, const
   if (fl) fl[c] = flags[v];
 }
 
-__global__ void unpack_state(float* __restrict__ st, int64_t P, int N, const int32_t* __restrict__ iperm,
-                             uint8_t* __restrict__ flags, const float* off, const float* quat, const float* vel,
-                             const float* angvel, const uint8_t* fl) {
-  int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= N) return;
-  int64_t v = iperm[c];
-  if (off) for (int a = 0; a < 3; ++a) st[state_index(OX + a, v, P)] = off[3 * (int64_t)c + a];
-  if (quat) for (int a = 0; a < 4; ++a) st[state_index(QW + a, v, P)] = quat[4 * (int64_t)c + a];
-  if (vel) for (int a = 0; a < 3; ++a) st[state_index(VX + a, v, P)] = vel[3 * (int64_t)c + a];
-  if (angvel) for (int a = 0; a < 3; ++a) st[state_index(WX + a, v, P)] = angvel[3 * (int64_t)c + a];
-  if (fl) flags[v] = fl[c];
+// With dmax set (collisions on), the largest distance between a voxel's
+// written and current offsets is recorded per body (float bits, atomicMax:
+// the maximum does not depend on the order): one atomic per CTA when all its
+// voxels belong to one body, else per warp or per voxel.
+__global__ void __launch_bounds__(256) unpack_state(float* __restrict__ st, int64_t P, int N,
+                                                    const int32_t* __restrict__ iperm, uint8_t* __restrict__ flags,
+                                                    const float* off, const float* quat, const float* vel,
+                                                    const float* angvel, const uint8_t* fl, const int32_t* body,
+                                                    unsigned* dmax) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = c < N;
+  float d2 = 0.f;
+  int b = 0;
+  if (active) {
+    const int64_t v = iperm[c];
+    if (off)
+      for (int a = 0; a < 3; ++a) {
+        const float o1 = off[3 * (int64_t)c + a];
+        if (dmax) {
+          const float dd = __fsub_rn(o1, st[state_index(OX + a, v, P)]);
+          d2 = __fmaf_rn(dd, dd, d2);
+        }
+        st[state_index(OX + a, v, P)] = o1;
+      }
+    if (quat) for (int a = 0; a < 4; ++a) st[state_index(QW + a, v, P)] = quat[4 * (int64_t)c + a];
+    if (vel) for (int a = 0; a < 3; ++a) st[state_index(VX + a, v, P)] = vel[3 * (int64_t)c + a];
+    if (angvel) for (int a = 0; a < 3; ++a) st[state_index(WX + a, v, P)] = angvel[3 * (int64_t)c + a];
+    if (fl) flags[v] = fl[c];
+    if (body) b = body[v];
+  }
+  if (!dmax || !off) return;  // uniform over the grid
+  const float d = sqrtf(d2);
+  const int b_first = body ? body[iperm[blockIdx.x * blockDim.x]] : 0;  // the CTA's first voxel exists
+  float m = d;
+  if (__syncthreads_and(!active || b == b_first)) {
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float red[8];
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, red[w]);
+      if (m > 0.f) atomicMax(&dmax[b_first], __float_as_uint(m));
+    }
+  } else if (active && d > 0.f) {
+    atomicMax(&dmax[b], __float_as_uint(d));
+  }
 }
 
 __global__ void reset_state(float* __restrict__ st, int64_t P, int N, uint8_t* __restrict__ flags, float vx,
@@ -79,8 +114,9 @@ void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* ipe
 
 void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, uint8_t* flags, const float* off,
                          const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
-                         cudaStream_t s) {
-  unpack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, iperm, flags, off, quat, vel, angvel, fl);
+                         cudaStream_t s, const int32_t* body, unsigned* dmax) {
+  if (N > 0)
+    unpack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, iperm, flags, off, quat, vel, angvel, fl, body, dmax);
 }
 
 void launch_set_velocity(float* st, int64_t pitch, int N, const uint8_t* flags, float vx, float vy, float vz,

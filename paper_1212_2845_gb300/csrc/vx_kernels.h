@@ -213,6 +213,12 @@ void launch_com_travel(const float* st1, const float* st0, int64_t pitch, const 
                        int n_bodies, float* loss, cudaStream_t s);
 void launch_to_canonical(const float* g, const int32_t* iperm, int N, float* out, cudaStream_t s);
 void launch_rebuild(const CollideArgs& C, cudaStream_t s);
+// A write of the state as motion for the collision horizon: every body's
+// accumulator grows by twice its largest written displacement dmax (float
+// bits, zeroed here); bodies at the threshold are flagged (world: one
+// accumulator, every body flagged), and so is every body when the status
+// word holds a timed-out or overflowed rebuild.
+void launch_write_horizon(const CollideArgs& C, unsigned* dmax, int world, cudaStream_t s);
 void launch_flag_all(const CollideArgs& C, cudaStream_t s);
 
 // internal-order device state <-> interleaved canonical-order caller layout
@@ -220,9 +226,12 @@ void launch_flag_all(const CollideArgs& C, cudaStream_t s);
 // canonical to internal indices; any destination/source pointer may be null
 void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* iperm, const uint8_t* flags,
                        float* off, float* quat, float* vel, float* angvel, uint8_t* fl, cudaStream_t s);
+// With dmax (per body, float bits, zero at launch) the largest distance
+// between written and current offsets is recorded per body (body: per voxel,
+// internal order, or nullptr for one body).
 void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, uint8_t* flags, const float* off,
                          const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
-                         cudaStream_t s);
+                         cudaStream_t s, const int32_t* body = nullptr, unsigned* dmax = nullptr);
 // atomic max of |v| over the voxels into *out (float bits; zero it first)
 void launch_max_speed(const float* st, int64_t pitch, int N, unsigned* out, cudaStream_t s);
 // rest state: zero offsets, identity quaternions, v0 for non-fixed voxels

@@ -298,8 +298,9 @@ def test_checkpoint_resume_is_bit_exact_with_collisions(vx):
     angular velocities, flags) and step counter, load them into a new
     simulator and continue: the continuation equals the uninterrupted run bit
     for bit, through the shell's impact with self-collision.  Writing a
-    state rebuilds the candidate lists from it; only overlapping candidates
-    act, so the horizon history does not matter."""
+    state counts as motion for the horizon (here far past its threshold, so
+    the lists are rebuilt from it); only overlapping candidates act, so the
+    horizon history does not matter."""
     sc = scenes.hollow_ball(R=12, t=3)
     a = vx.Sim(sc)
     a.step(300)
