@@ -257,16 +257,30 @@ def test_state_roundtrip_and_reset(vx):
     assert not s["offset"].any() and not s["vel"].any()
     assert np.array_equal(s["quat"], np.tile([1, 0, 0, 0], (sim.N, 1)).astype(np.float32))
     assert sim.step_count == 0
-    # the asynchronous upload from pinned host buffers, then a read on the same stream
+    # the asynchronous upload from pinned host buffers, then a read on the
+    # same stream into pinned buffers
     torch = pytest.importorskip("torch")
+    fl2 = (np.arange(sim.N) % 3 == 0).astype(np.uint8) * 2
     pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
-           for k, a in (("offset", off), ("quat", q), ("vel", vel), ("angvel", w))}
+           for k, a in (("offset", off), ("quat", q), ("vel", vel), ("angvel", w), ("flags", fl2))}
     stream = torch.cuda.Stream()
     sim.write_state_from(**pin, stream=stream, on_device=False, wait=False)
     out = {k: torch.empty_like(t).pin_memory() for k, t in pin.items()}
     sim.read_state_into(**out, stream=stream, on_device=False)
     for k in pin:
         assert torch.equal(out[k], pin[k]), k
+    s = sim.read_state()  # pageable buffers: the staging copies
+    for k in pin:
+        assert np.array_equal(s[k], pin[k].numpy()), k
+    # a view mixing pinned and pageable buffers
+    off2 = off + np.float32(1e-6)
+    sim.write_state_from(offset=torch.from_numpy(off2).pin_memory(), quat=np.ascontiguousarray(q[::-1]),
+                         stream=stream, on_device=False)
+    s = sim.read_state()
+    assert np.array_equal(s["offset"], off2) and np.array_equal(s["quat"], q[::-1])
+    part = {"vel": torch.empty_like(pin["vel"]).pin_memory()}
+    sim.read_state_into(**part, stream=stream, on_device=False)  # one field, pinned
+    assert torch.equal(part["vel"], pin["vel"])
 
 
 def test_initial_velocity(vx):
