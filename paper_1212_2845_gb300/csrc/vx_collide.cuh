@@ -85,26 +85,31 @@ __device__ __forceinline__ void query_one(const CollideArgs& C, int s) {
         const int ncx = cx + q % 3 - 1, ncy = cy + q / 3 - 1, ncz = cz + dz;
         const uint32_t hq = cell_hash(ncx, ncy, ncz, C.H - 1);
         const uint32_t e0 = C.hstart[hq], e1 = C.hstart[hq + 1];
-        for (uint32_t e = e0; e < e1; ++e) {
-          if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
-          // cell and lattice word together; the position only for the few
-          // entries the lattice-distance exclusion lets through
-          const int4 c1 = C.scell[e];
-          const int4 f = C.sinf[e];  // voxel, lattice word, body
-          if (c1.w == s) continue;
-          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
+        auto take = [&](uint32_t e, int4 c1, int4 f) {
+          if (c1.w == s) return;
+          if (c1.x != ncx || c1.y != ncy || c1.z != ncz) return;  // another cell in the same bucket
           const int u = f.x;
           if (C.body && f.z != b) {
-            if (!C.qorg) continue;  // bodies are separate worlds
+            if (!C.qorg) return;  // bodies are separate worlds
           } else {
             const uint32_t lq = (uint32_t)f.y;
             int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
-            if (man <= 3) continue;
+            if (man <= 3) return;
           }
           const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
           int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
-          if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
+          if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) return;
           if (n < kCandCap) list[n++] = u; else overflow = true;
+        };
+        // two entries requested at once: their loads overlap
+        for (uint32_t e = e0; e < e1; e += 2) {
+          if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
+          const bool two = e + 1 < e1 && VX_IN_BOUNDS(C.status, e + 1, C.S, kSiteSorted);
+          const int4 ca = C.scell[e], fa = C.sinf[e];
+          int4 cb = ca, fb = fa;
+          if (two) { cb = C.scell[e + 1]; fb = C.sinf[e + 1]; }
+          take(e, ca, fa);
+          if (two) take(e + 1, cb, fb);
         }
     }
   }
@@ -150,24 +155,30 @@ __device__ __forceinline__ void query_warp(const CollideArgs& C, int s, int lane
     const int ncx = c0.x + lane % 3 - 1, ncy = c0.y + (lane / 3) % 3 - 1, ncz = c0.z + lane / 9 - 1;
     const uint32_t h = cell_hash(ncx, ncy, ncz, C.H - 1);
     const uint32_t e0 = C.hstart[h], e1 = C.hstart[h + 1];
-    for (uint32_t e = e0; e < e1; ++e) {
-      if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
-      const int4 c1 = C.scell[e];
-      const int4 f = C.sinf[e];  // voxel, lattice word, body
-      if (c1.w == s) continue;
-      if (c1.x != ncx || c1.y != ncy || c1.z != ncz) continue;  // another cell in the same bucket
+    auto take = [&](uint32_t e, int4 c1, int4 f) {
+      if (c1.w == s) return;
+      if (c1.x != ncx || c1.y != ncy || c1.z != ncz) return;  // another cell in the same bucket
       const int u = f.x;
       if (C.body && f.z != b) {
-        if (!C.qorg) continue;  // bodies are separate worlds
+        if (!C.qorg) return;  // bodies are separate worlds
       } else {
         const uint32_t lq = (uint32_t)f.y;
         const int man = abs((int)(lq & 2047u) - vi) + abs((int)((lq >> 11) & 2047u) - vj) + abs((int)(lq >> 22) - vk);
-        if (man <= 3) continue;
+        if (man <= 3) return;
       }
       const int64_t x1 = C.sxq[e], y1 = C.sxq[(int64_t)C.S + e], z1 = C.sxq[2 * (int64_t)C.S + e];
       const int64_t ddx = x1 - x0, ddy = y1 - y0, ddz = z1 - z0;
-      if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) continue;
+      if (ddx * ddx + ddy * ddy + ddz * ddz >= r2max) return;
       if (n < kLaneCap) mine[n++] = u; else overflow = true;
+    };
+    for (uint32_t e = e0; e < e1; e += 2) {  // two entries requested at once
+      if (!VX_IN_BOUNDS(C.status, e, C.S, kSiteSorted)) break;
+      const bool two = e + 1 < e1 && VX_IN_BOUNDS(C.status, e + 1, C.S, kSiteSorted);
+      const int4 ca = C.scell[e], fa = C.sinf[e];
+      int4 cb = ca, fb = fa;
+      if (two) { cb = C.scell[e + 1]; fb = C.sinf[e + 1]; }
+      take(e, ca, fa);
+      if (two) take(e + 1, cb, fb);
     }
   }
   if (__any_sync(0xffffffffu, overflow)) {  // a crowded cell: the one-thread search
