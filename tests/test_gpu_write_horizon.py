@@ -111,3 +111,39 @@ def test_population_write_rebuilds_only_the_moved_body(vx):
     op = {tuple(p) for p in ora.pairs_from_offsets(off.astype(np.float64))}
     assert gp == op
     sim.close()
+
+
+def test_large_state_round_trip(vx):
+    """A state of more than 2^18 voxels: the round trip is exact through
+    pageable and through pinned buffers, and a write's largest displacement
+    is found wherever it lies (the last voxel of the canonical order too)."""
+    torch = pytest.importorskip("torch")
+    sim = vx.Sim(scenes.hollow_ball(R=60, t=8))
+    assert sim.N >= 1 << 18
+    sim.step(5)
+    st = sim.read_state()
+    rng = np.random.default_rng(2)
+    off = (st["offset"] + rng.normal(scale=1e-7, size=st["offset"].shape)).astype(np.float32)
+    vel = rng.normal(size=(sim.N, 3)).astype(np.float32)
+    w = rng.normal(size=(sim.N, 3)).astype(np.float32)
+    n0, acc0 = sim.collision_stats()
+    sim.write_state(offset=off, quat=st["quat"], vel=vel, angvel=w, flags=st["flags"])
+    back = sim.read_state()
+    for k, a in (("offset", off), ("quat", st["quat"]), ("vel", vel), ("angvel", w), ("flags", st["flags"])):
+        assert np.array_equal(back[k], a), k
+    n1, acc1 = sim.collision_stats()
+    d = np.sqrt(np.max(np.sum((off - st["offset"]).astype(np.float32) ** 2, axis=1)))
+    assert n1 == n0 and acc1 - acc0 == pytest.approx(2 * d, rel=1e-3)
+    pin = {k: torch.from_numpy(np.ascontiguousarray(a)).pin_memory() for k, a in back.items()}
+    stream = torch.cuda.Stream()
+    sim.write_state_from(**pin, stream=stream, on_device=False, wait=False)
+    out = {k: torch.empty_like(t).pin_memory() for k, t in pin.items()}
+    sim.read_state_into(**out, stream=stream, on_device=False)
+    for k in pin:
+        assert torch.equal(out[k], pin[k]), k
+    assert sim.collision_stats()[0] == n1
+    off2 = back["offset"].copy()
+    off2[sim.N - 1, 2] += np.float32(0.9 * sim.l)  # the last voxel
+    sim.write_state(offset=off2)
+    assert sim.collision_stats()[0] == n1 + 1
+    sim.close()
