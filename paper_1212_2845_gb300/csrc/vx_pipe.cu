@@ -347,8 +347,30 @@ template <int TMAX> struct PipeLayout {
   }
 };
 
-template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) fused_pipe(StepArgs A) {
+// LEAN > 0: a lattice without actuation, per-voxel moduli or phases,
+// external forces or recorded bond sums; LEAN - 1 has bit 0 set for voxel
+// contacts and bit 1 for several bodies.  Those features are then
+// compile-time constants, which takes their tests and the registers they
+// hold out of the per-voxel path; the arithmetic and its bits are the
+// generic kernel's.
+template <int TMAX, int LEAN>
+__device__ __forceinline__ StepArgs lean_args(const StepArgs& A_in) {
+  StepArgs A = A_in;
+  if (LEAN) {
+    A.act_on = 0;
+    A.logE = nullptr;
+    A.phase = nullptr;
+    A.fext = nullptr;
+    A.fm_out = nullptr;
+    if (!((LEAN - 1) & 2)) A.body = nullptr;
+    A.collide_on = ((LEAN - 1) & 1) ? 1 : 0;
+  }
+  return A;
+}
+
+template <int TMAX, int LEAN = 0>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) fused_pipe(StepArgs A_in) {
+  const StepArgs A = lean_args<TMAX, LEAN>(A_in);
   extern __shared__ __align__(16) float smem[];
   const PipeLayout<TMAX> L(smem, A);
   if ((int)blockIdx.x < A.n_tiles) {  // uniform over the CTA
@@ -472,7 +494,13 @@ template <int TMAX, class K> int resident_ctas(K* kernel, size_t smem, int* n) {
   return 0;
 }
 
-template <int TMAX> int prepare_pipe_t(size_t smem, int* grid) { return resident_ctas<TMAX>(fused_pipe<TMAX>, smem, grid); }
+template <int TMAX> int prepare_pipe_t(size_t smem, int* grid) {
+  if (TMAX == 256)  // the lean variants share the generic kernel's shared memory and grid
+    if (allow_smem(fused_pipe<256, 1>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 2>, smem) != cudaSuccess ||
+        allow_smem(fused_pipe<256, 3>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 4>, smem) != cudaSuccess)
+      return -1;
+  return resident_ctas<TMAX>(fused_pipe<TMAX>, smem, grid);
+}
 
 template <int TMAX> int prepare_multi_t(size_t smem, int n_tiles, int* grid, int* co_resident) {
   int co = 0;
@@ -519,11 +547,24 @@ cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, si
   return cudaLaunchCooperativeKernel((const void*)multi_pipe<256>, dim3(grid), dim3(256), args, smem, s);
 }
 
+// The lean variant of the 256-voxel kernel where the lattice's features
+// allow it (0: the generic kernel).
+static int lean_mode(const StepArgs& A) {
+  if (A.act_on || A.logE || A.phase || A.fext || A.fm_out) return 0;
+  return 1 + (A.collide_on ? 1 : 0) + (A.body ? 2 : 0);
+}
+
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {
   int g = grid < A.n_tiles ? grid : A.n_tiles;
   if (tile_max == 128) fused_pipe<128><<<g, 128, smem, s>>>(A);
   else if (tile_max == 512) fused_pipe<512><<<g, 512, smem, s>>>(A);
-  else fused_pipe<256><<<g, 256, smem, s>>>(A);
+  else switch (lean_mode(A)) {
+    case 1: fused_pipe<256, 1><<<g, 256, smem, s>>>(A); break;
+    case 2: fused_pipe<256, 2><<<g, 256, smem, s>>>(A); break;
+    case 3: fused_pipe<256, 3><<<g, 256, smem, s>>>(A); break;
+    case 4: fused_pipe<256, 4><<<g, 256, smem, s>>>(A); break;
+    default: fused_pipe<256><<<g, 256, smem, s>>>(A);
+  }
 }
 
 }  // namespace vx
