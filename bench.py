@@ -281,7 +281,7 @@ def large_lattice(stream, peak, steps=200, warmup=5, R=200, tile=0):
            "l2": "inputs larger than L2",
            "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg,
-                        "kernel": "fused_pipe<256>",
+                        "kernel": "fused_pipe<256, 1> (lean: one body, no contacts)",
                         "traffic": measured_traffic("hollow_shell_R200_t8") if R == 200 else None}}
     sim.close()
     return out
@@ -333,7 +333,7 @@ def batched_form(stream, peak, n_bodies=4096, steps=200, warmup=5):
            "steps": steps, "l2": "inputs larger than L2", "bytes_per_voxel_step": b_alg,
            "per_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
                         "bond_steps_per_s": sim.n_bonds * steps / t_plain,
-                        "frac": b_alg * N * steps / t_plain / 1e9 / peak, "kernel": "fused_pipe<256>"},
+                        "frac": b_alg * N * steps / t_plain / 1e9 / peak, "kernel": "fused_pipe<256, 0> (generic: actuated)"},
            "batched": {"value": N * steps / t_graph, "unit": METRIC, "ms_per_step": 1e3 * t_graph / steps,
                        "bond_steps_per_s": sim.n_bonds * steps / t_graph,
                        "frac": b_alg * N * steps / t_graph / 1e9 / peak, "kernel": f"batched_pipe<{sim.tiling()['tile_max']}>",
@@ -523,7 +523,7 @@ def hetero_block_line(stream, peak, flush, steps=2000, warmup=10):
            "bond_steps_per_s": sim.n_bonds / avg, "l2": "flushed between steps",
            "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg,
-                        "kernel": "fused_pipe<256>", "traffic": measured_traffic("hetero_block_64x64x32")},
+                        "kernel": "fused_pipe<256, 0> (generic: actuated)", "traffic": measured_traffic("hetero_block_64x64x32")},
            "multi_step_call": multi_step_line(sim, stream, flush)}
     sim.close()
     return out
@@ -654,7 +654,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "traffic": measured_traffic("hollow_ball_R100_t8"),
                      "traffic_source": "stored ncu capture of the same kernel source (null when it changed)",
-                     "kernel": "fused_pipe<256> + rebuild_all (every launch of a step, rebuilds included)",
+                     "kernel": "fused_pipe<256, 2> (lean: contacts, one body) + rebuild_all (every launch of a step, rebuilds included)",
                      "bytes_per_voxel_step": B_ALG, "peak_kind": peak_kind},
         "e2e": {"value": N * args.e2e_steps / t_e2e, "unit": METRIC, "h2d_bytes_per_step": nb,
                 "d2h_bytes_per_step": nb, "steps": args.e2e_steps},
