@@ -348,7 +348,8 @@ template <int TMAX> struct PipeLayout {
 };
 
 // LEAN > 0: a lattice without actuation, per-voxel moduli or phases,
-// external forces or recorded bond sums; LEAN - 1 has bit 0 set for voxel
+// external forces or recorded bond sums, whose material-pair constants come
+// from the table (at most 16 materials); LEAN - 1 has bit 0 set for voxel
 // contacts and bit 1 for several bodies.  Those features are then
 // compile-time constants, which takes their tests and the registers they
 // hold out of the per-voxel path; the arithmetic and its bits are the
@@ -371,6 +372,7 @@ __device__ __forceinline__ StepArgs lean_args(const StepArgs& A_in) {
 template <int TMAX, int LEAN = 0>
 __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) fused_pipe(StepArgs A_in) {
   const StepArgs A = lean_args<TMAX, LEAN>(A_in);
+  if (LEAN) __builtin_assume(A.lut != nullptr);  // lean launches carry the material-pair table
   extern __shared__ __align__(16) float smem[];
   const PipeLayout<TMAX> L(smem, A);
   if ((int)blockIdx.x < A.n_tiles) {  // uniform over the CTA
@@ -550,7 +552,7 @@ cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, si
 // The lean variant of the 256-voxel kernel where the lattice's features
 // allow it (0: the generic kernel).
 static int lean_mode(const StepArgs& A) {
-  if (A.act_on || A.logE || A.phase || A.fext || A.fm_out) return 0;
+  if (A.act_on || A.logE || A.phase || A.fext || A.fm_out || !A.lut) return 0;
   return 1 + (A.collide_on ? 1 : 0) + (A.body ? 2 : 0);
 }
 
