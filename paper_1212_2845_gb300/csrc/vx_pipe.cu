@@ -347,10 +347,11 @@ template <int TMAX> struct PipeLayout {
   }
 };
 
-// LEAN > 0: a lattice without actuation, per-voxel moduli or phases,
-// external forces or recorded bond sums, whose material-pair constants come
-// from the table (at most 16 materials); LEAN - 1 has bit 0 set for voxel
-// contacts and bit 1 for several bodies.  Those features are then
+// LEAN > 0: a lattice without per-voxel moduli, external forces or recorded
+// bond sums, whose material-pair constants come from the table (at most 16
+// materials), either without actuation and per-voxel phases or with both;
+// LEAN - 1 has bit 0 set for voxel contacts, bit 1 for several bodies and
+// bit 2 for actuation with per-voxel phases.  Those features are then
 // compile-time constants, which takes their tests and the registers they
 // hold out of the per-voxel path; the arithmetic and its bits are the
 // generic kernel's.
@@ -358,9 +359,9 @@ template <int TMAX, int LEAN>
 __device__ __forceinline__ StepArgs lean_args(const StepArgs& A_in) {
   StepArgs A = A_in;
   if (LEAN) {
-    A.act_on = 0;
+    A.act_on = ((LEAN - 1) & 4) ? 1 : 0;
     A.logE = nullptr;
-    A.phase = nullptr;
+    if (!((LEAN - 1) & 4)) A.phase = nullptr;
     A.fext = nullptr;
     A.fm_out = nullptr;
     if (!((LEAN - 1) & 2)) A.body = nullptr;
@@ -373,6 +374,7 @@ template <int TMAX, int LEAN = 0>
 __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) fused_pipe(StepArgs A_in) {
   const StepArgs A = lean_args<TMAX, LEAN>(A_in);
   if (LEAN) __builtin_assume(A.lut != nullptr);  // lean launches carry the material-pair table
+  if (LEAN && ((LEAN - 1) & 4)) __builtin_assume(A.phase != nullptr);
   extern __shared__ __align__(16) float smem[];
   const PipeLayout<TMAX> L(smem, A);
   if ((int)blockIdx.x < A.n_tiles) {  // uniform over the CTA
@@ -499,7 +501,9 @@ template <int TMAX, class K> int resident_ctas(K* kernel, size_t smem, int* n) {
 template <int TMAX> int prepare_pipe_t(size_t smem, int* grid) {
   if (TMAX == 256)  // the lean variants share the generic kernel's shared memory and grid
     if (allow_smem(fused_pipe<256, 1>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 2>, smem) != cudaSuccess ||
-        allow_smem(fused_pipe<256, 3>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 4>, smem) != cudaSuccess)
+        allow_smem(fused_pipe<256, 3>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 4>, smem) != cudaSuccess ||
+        allow_smem(fused_pipe<256, 5>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 6>, smem) != cudaSuccess ||
+        allow_smem(fused_pipe<256, 7>, smem) != cudaSuccess || allow_smem(fused_pipe<256, 8>, smem) != cudaSuccess)
       return -1;
   return resident_ctas<TMAX>(fused_pipe<TMAX>, smem, grid);
 }
@@ -552,8 +556,8 @@ cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, si
 // The lean variant of the 256-voxel kernel where the lattice's features
 // allow it (0: the generic kernel).
 static int lean_mode(const StepArgs& A) {
-  if (A.act_on || A.logE || A.phase || A.fext || A.fm_out || !A.lut) return 0;
-  return 1 + (A.collide_on ? 1 : 0) + (A.body ? 2 : 0);
+  if (A.logE || A.fext || A.fm_out || !A.lut || (A.act_on != 0) != (A.phase != nullptr)) return 0;
+  return 1 + (A.collide_on ? 1 : 0) + (A.body ? 2 : 0) + (A.act_on ? 4 : 0);
 }
 
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {
@@ -565,6 +569,10 @@ void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStr
     case 2: fused_pipe<256, 2><<<g, 256, smem, s>>>(A); break;
     case 3: fused_pipe<256, 3><<<g, 256, smem, s>>>(A); break;
     case 4: fused_pipe<256, 4><<<g, 256, smem, s>>>(A); break;
+    case 5: fused_pipe<256, 5><<<g, 256, smem, s>>>(A); break;
+    case 6: fused_pipe<256, 6><<<g, 256, smem, s>>>(A); break;
+    case 7: fused_pipe<256, 7><<<g, 256, smem, s>>>(A); break;
+    case 8: fused_pipe<256, 8><<<g, 256, smem, s>>>(A); break;
     default: fused_pipe<256><<<g, 256, smem, s>>>(A);
   }
 }
