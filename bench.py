@@ -333,7 +333,7 @@ def batched_form(stream, peak, n_bodies=4096, steps=200, warmup=5):
            "steps": steps, "l2": "inputs larger than L2", "bytes_per_voxel_step": b_alg,
            "per_step": {"value": N * steps / t_plain, "unit": METRIC, "ms_per_step": 1e3 * t_plain / steps,
                         "bond_steps_per_s": sim.n_bonds * steps / t_plain,
-                        "frac": b_alg * N * steps / t_plain / 1e9 / peak, "kernel": "fused_pipe<256, 0> (generic: actuated)"},
+                        "frac": b_alg * N * steps / t_plain / 1e9 / peak, "kernel": "fused_pipe<256, 5-8> (lean: actuated, per-voxel phase)"},
            "batched": {"value": N * steps / t_graph, "unit": METRIC, "ms_per_step": 1e3 * t_graph / steps,
                        "bond_steps_per_s": sim.n_bonds * steps / t_graph,
                        "frac": b_alg * N * steps / t_graph / 1e9 / peak, "kernel": f"batched_pipe<{sim.tiling()['tile_max']}>",
@@ -523,7 +523,7 @@ def hetero_block_line(stream, peak, flush, steps=2000, warmup=10):
            "bond_steps_per_s": sim.n_bonds / avg, "l2": "flushed between steps",
            "roofline": {"bound": "hbm", "achieved": b_alg * sim.N / avg / 1e9, "peak": peak, "unit": "GB/s",
                         "frac": b_alg * sim.N / avg / 1e9 / peak, "bytes_per_voxel_step": b_alg,
-                        "kernel": "fused_pipe<256, 0> (generic: actuated)", "traffic": measured_traffic("hetero_block_64x64x32")},
+                        "kernel": "fused_pipe<256, 5-8> (lean: actuated, per-voxel phase)", "traffic": measured_traffic("hetero_block_64x64x32")},
            "multi_step_call": multi_step_line(sim, stream, flush)}
     sim.close()
     return out
