@@ -98,6 +98,7 @@ struct vx_sim {
   int floor_on = 0, collide_on = 0;
   float actA = 0.f, actT0 = 0.f;
   int64_t actP = 0;
+  float actC = 0.f;       // fl(2 pi / actP): the actuation angle's step
   // per-material temperature signals (amplitude, offset, phase shift); an
   // empty vector means the global value (phase shift 0)
   std::vector<float> mactA, mactT0, mactPh;
@@ -755,6 +756,7 @@ ResArgs res_args(vx_sim* s, int64_t n) {
   R.n_steps = (int)n;
   R.step0 = s->step;
   R.act_P = s->actP;
+  R.act_c = s->actC;
   R.ctr = nullptr;
   R.cap = s->res_cap;
   return R;
@@ -853,14 +855,13 @@ BatchArgs batch_args(vx_sim* s, int64_t n) {
   Bt.n_steps = (int)n;
   Bt.step0 = s->step;
   Bt.act_P = s->actP;
+  Bt.act_c = s->actC;
   Bt.ctr = nullptr;
   return Bt;
 }
 
 // ---- adjoint form ----------------------------------------------------------
-float act_phase(const vx_sim* s, int64_t step) {
-  return s->actP > 0 ? (float)(2.0 * M_PI * (double)(step % s->actP) / (double)s->actP) : 0.f;
-}
+float act_phase(const vx_sim* s, int64_t step) { return act_angle(step, s->actP, s->actC); }
 
 // One step from A.st_in to A.st_out with the simulator's per-step form.
 int launch_form_step(vx_sim* s, const StepArgs& A, cudaStream_t st) {
@@ -1256,6 +1257,7 @@ int vx_set_actuation(vx_sim* s, float amplitude, int64_t period, float offset) {
   if (period < 0 || !std::isfinite(amplitude) || !std::isfinite(offset)) return fail(VX_ERR_ARG, "bad actuation");
   if (period == 0) amplitude = 0.f;
   s->actA = amplitude; s->actP = period; s->actT0 = offset;
+  s->actC = period > 0 ? (float)(2.0 * M_PI / (double)period) : 0.f;
   update_threshold(s);
   return upload_materials(s);
 }
@@ -1492,6 +1494,7 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
     M.n_steps = (int)n;
     M.step0 = s->step;
     M.act_P = s->actP;
+    M.act_c = s->actC;
     M.ctr = nullptr;
     M.bar = s->bar;
     M.spins = s->bar_spins;
@@ -1526,7 +1529,7 @@ int vx_step_async(vx_sim* s, int64_t n, void* stream) {
   const bool tail = s->collide_on && !s->coll_every && s->form == VX_FORM_PIPELINED;
   for (int64_t i = 0; i < n; ++i) {
     StepArgs A = step_args(s);
-    if (s->actP > 0) A.act_w = (float)(2.0 * M_PI * (double)(s->step % s->actP) / (double)s->actP);
+    if (s->actP > 0) A.act_w = act_phase(s, s->step);
     if (tail) {
       A.h_done = s->hdone;
       A.h_acc = s->acc;

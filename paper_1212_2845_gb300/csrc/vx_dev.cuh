@@ -65,6 +65,19 @@ __device__ __forceinline__ bool vx_in_bounds(int* status, long long i, long long
 #define VX_IN_BOUNDS(status, i, n, site) true
 #endif
 
+// Phase angle of the actuation signal at step n (Sec 2.3), 2 pi (n mod P) / P,
+// formed in FP32 as (n mod P) times c = fl(2 pi / P) with one rounding: the
+// host (per-step launches) and the device (multi-step, batched and resident
+// launches) get the same bits, and no FP64 runs on the GPU.
+__host__ __device__ __forceinline__ float act_angle(int64_t step, int64_t P, float c) {
+  if (P <= 0) return 0.f;
+#ifdef __CUDA_ARCH__
+  return __fmul_rn((float)(step % P), c);
+#else
+  return (float)(step % P) * c;
+#endif
+}
+
 struct StepArgs {
   int N;
   int64_t pitch;
@@ -86,7 +99,7 @@ struct StepArgs {
   float zb, zg, zc, gz;
   int floor_on, collide_on;
   int act_on;              // temperature offset is non-zero somewhere
-  float actA, actT0, act_w;  // global signal (materials carry their own copy); act_w = 2 pi (n mod P) / P
+  float actA, actT0, act_w;  // global signal (materials carry their own copy); act_w = act_angle(n, P, c)
   int64_t step;
   // two-pass form
   const int32_t* nbr;      // 6 planes (-x,+x,-y,+y,-z,+z), internal indices

@@ -95,6 +95,7 @@ struct BatchArgs {
   int n_steps;
   int64_t step0;
   int64_t act_P;
+  float act_c;                 // fl(2 pi / act_P)
   const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
 };
 int prepare_batched(int tile_max, size_t smem);
@@ -109,6 +110,7 @@ struct MultiArgs {
   int n_steps;
   int64_t step0;
   int64_t act_P;
+  float act_c;                 // fl(2 pi / act_P)
   const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
   unsigned* bar;               // barrier count and generation
   long long spins;             // wait budget of one barrier (units of 128 SM cycles)
@@ -135,6 +137,7 @@ struct ResArgs {
   int n_steps;
   int64_t step0;
   int64_t act_P;
+  float act_c;                 // fl(2 pi / act_P)
   const int64_t* ctr;          // device (step0, cur0) read at launch instead, or nullptr
   int cap;                     // voxels per CTA slice (shared memory layout)
 };

@@ -403,7 +403,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1))
     A.st_out = p ? M.buf0 : M.buf1;
     A.step = step0 + k;
     if (A.act_on && M.act_P > 0)
-      A.act_w = (float)(6.283185307179586 * (double)(A.step % M.act_P) / (double)M.act_P);
+      A.act_w = act_angle(A.step, M.act_P, M.act_c);
     pipe_tiles<TMAX>(A, blockIdx.x, gridDim.x, A.n_tiles, smem, L.sf, L.props, L.F4, L.F2, L.mats, L.lut);
     if (M.collide) {
       // every CTA's speeds and new state are in: horizon (or a forced
@@ -440,8 +440,11 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1))
 // Within a step the tiles of the group are pipelined as in fused_pipe; the
 // pipeline restarts after each barrier because the next step reads what this
 // one wrote.
-template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) batched_pipe(StepArgs A0, BatchArgs Bt) {
+template <int TMAX, int LEAN = 0>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) batched_pipe(StepArgs A0_in, BatchArgs Bt) {
+  const StepArgs A0 = lean_args<TMAX, LEAN>(A0_in);  // LEAN as for fused_pipe
+  if (LEAN) __builtin_assume(A0.lut != nullptr);
+  if (LEAN && ((LEAN - 1) & 4)) __builtin_assume(A0.phase != nullptr);
   constexpr int ML = 2 * TMAX;
   extern __shared__ __align__(16) float smem[];
   const bool hph = A0.phase != nullptr, hle = A0.logE != nullptr, hbody = A0.body != nullptr,
@@ -471,7 +474,7 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1))
       A.st_out = p ? Bt.buf0 : Bt.buf1;
       A.step = step0 + k;
       if (A.act_on && Bt.act_P > 0)
-        A.act_w = (float)(6.283185307179586 * (double)(A.step % Bt.act_P) / (double)Bt.act_P);
+        A.act_w = act_angle(A.step, Bt.act_P, Bt.act_c);
       pipe_tiles<TMAX>(A, t0, 1, t1, smem, sf, props, F4, F2, mats, lut);
       __syncthreads();  // the buffers are reused; the next step reads what this one wrote
     }
@@ -496,6 +499,13 @@ template <int TMAX, class K> int resident_ctas(K* kernel, size_t smem, int* n) {
     return -1;
   *n = per_sm * n_sm;
   return 0;
+}
+
+// The lean variant of the 256-voxel kernel where the lattice's features
+// allow it (0: the generic kernel).
+static int lean_mode(const StepArgs& A) {
+  if (A.logE || A.fext || A.fm_out || !A.lut || (A.act_on != 0) != (A.phase != nullptr)) return 0;
+  return 1 + (A.collide_on ? 1 : 0) + (A.body ? 2 : 0) + (A.act_on ? 4 : 0);
 }
 
 template <int TMAX> int prepare_pipe_t(size_t smem, int* grid) {
@@ -528,14 +538,24 @@ int prepare_batched(int tile_max, size_t smem) {
   cudaError_t e;
   if (tile_max == 128) e = allow_smem(batched_pipe<128>, smem);
   else if (tile_max == 512) e = allow_smem(batched_pipe<512>, smem);
-  else e = allow_smem(batched_pipe<256>, smem);
+  else {
+    e = allow_smem(batched_pipe<256>, smem);
+    if (e == cudaSuccess) e = allow_smem(batched_pipe<256, 3>, smem);
+    if (e == cudaSuccess) e = allow_smem(batched_pipe<256, 7>, smem);
+  }
   return e == cudaSuccess ? 0 : -1;
 }
 
+// Batched groups are several bodies without voxel contacts: the lean
+// instantiations for bodies without, and with actuation and phases.
 void launch_batched(const StepArgs& A, const BatchArgs& B, int tile_max, size_t smem, int grid, cudaStream_t s) {
   if (tile_max == 128) batched_pipe<128><<<grid, 128, smem, s>>>(A, B);
   else if (tile_max == 512) batched_pipe<512><<<grid, 512, smem, s>>>(A, B);
-  else batched_pipe<256><<<grid, 256, smem, s>>>(A, B);
+  else switch (lean_mode(A)) {
+    case 3: batched_pipe<256, 3><<<grid, 256, smem, s>>>(A, B); break;
+    case 7: batched_pipe<256, 7><<<grid, 256, smem, s>>>(A, B); break;
+    default: batched_pipe<256><<<grid, 256, smem, s>>>(A, B);
+  }
 }
 
 int prepare_multi(int tile_max, size_t smem, int n_tiles, int* grid, int* co_resident) {
@@ -553,12 +573,6 @@ cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, si
   return cudaLaunchCooperativeKernel((const void*)multi_pipe<256>, dim3(grid), dim3(256), args, smem, s);
 }
 
-// The lean variant of the 256-voxel kernel where the lattice's features
-// allow it (0: the generic kernel).
-static int lean_mode(const StepArgs& A) {
-  if (A.logE || A.fext || A.fm_out || !A.lut || (A.act_on != 0) != (A.phase != nullptr)) return 0;
-  return 1 + (A.collide_on ? 1 : 0) + (A.body ? 2 : 0) + (A.act_on ? 4 : 0);
-}
 
 void launch_pipe(const StepArgs& A, int tile_max, size_t smem, int grid, cudaStream_t s) {
   int g = grid < A.n_tiles ? grid : A.n_tiles;

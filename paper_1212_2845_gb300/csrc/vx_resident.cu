@@ -97,9 +97,6 @@ struct ResSmem {
   }
 };
 
-__device__ __forceinline__ float act_phase_of(int64_t step, int64_t P) {
-  return P > 0 ? (float)(6.283185307179586 * (double)(step % P) / (double)P) : 0.f;
-}
 
 // State and properties of slot k2 of cluster rank r2 through distributed
 // shared memory; with LOCAL, plain shared-memory loads when it is this CTA
@@ -170,7 +167,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
     // ---- load the slice: state at step0, properties at step0, neighbours
     {
       StepArgs A = A0;
-      A.act_w = act_phase_of(step0, R.act_P);
+      A.act_w = act_angle(step0, R.act_P, R.act_c);
       const StPtr G(const_cast<float*>(st_in), P);
       for (int u = tid; u < ns; u += T) {
         const int v = u0 + u;
@@ -267,7 +264,7 @@ __global__ void __launch_bounds__(kResThreads, 1) res_pipe(StepArgs A0, ResArgs 
       cl.sync();
       // ---- voxels: the per-step kernels' summation order (+x, +y, +z own
       // bonds, then the -x, -y, -z bonds of the neighbours), then the update
-      const float w_next = act_phase_of(step0 + k + 1, R.act_P);
+      const float w_next = act_angle(step0 + k + 1, R.act_P, R.act_c);
       for (int u = tid; u < ns; u += T) {
         V3f F, M;
         if (!PER_VOXEL) {
