@@ -388,8 +388,11 @@ __global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1))
 // every CTA walks its tiles of a step (as fused_pipe), then all CTAs meet at
 // a grid barrier before the next step reads what this one wrote.  The
 // lattice stays in L2 between steps and no launch separates them.
-template <int TMAX>
-__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) multi_pipe(StepArgs A0, MultiArgs M) {
+template <int TMAX, int LEAN = 0>
+__global__ void __launch_bounds__(TMAX, TMAX == 128 ? 4 : (TMAX == 256 ? 2 : 1)) multi_pipe(StepArgs A0_in, MultiArgs M) {
+  const StepArgs A0 = lean_args<TMAX, LEAN>(A0_in);  // LEAN as for fused_pipe
+  if (LEAN) __builtin_assume(A0.lut != nullptr);
+  if (LEAN && ((LEAN - 1) & 4)) __builtin_assume(A0.phase != nullptr);
   extern __shared__ __align__(16) float smem[];
   const PipeLayout<TMAX> L(smem, A0);
   L.load_tables(A0);
@@ -520,6 +523,12 @@ template <int TMAX> int prepare_pipe_t(size_t smem, int* grid) {
 
 template <int TMAX> int prepare_multi_t(size_t smem, int n_tiles, int* grid, int* co_resident) {
   int co = 0;
+  if (TMAX == 256)  // the lean variants: the generic kernel's shared memory and grid (they fit it)
+    if (allow_smem(multi_pipe<256, 1>, smem) != cudaSuccess || allow_smem(multi_pipe<256, 2>, smem) != cudaSuccess ||
+        allow_smem(multi_pipe<256, 3>, smem) != cudaSuccess || allow_smem(multi_pipe<256, 4>, smem) != cudaSuccess ||
+        allow_smem(multi_pipe<256, 5>, smem) != cudaSuccess || allow_smem(multi_pipe<256, 6>, smem) != cudaSuccess ||
+        allow_smem(multi_pipe<256, 7>, smem) != cudaSuccess || allow_smem(multi_pipe<256, 8>, smem) != cudaSuccess)
+      return -1;
   if (resident_ctas<TMAX>(multi_pipe<TMAX>, smem, &co) != 0) return -1;
   *grid = n_tiles < co ? n_tiles : co;
   *co_resident = co;
@@ -570,7 +579,19 @@ cudaError_t launch_multi(const StepArgs& A, const MultiArgs& M, int tile_max, si
     return cudaLaunchCooperativeKernel((const void*)multi_pipe<128>, dim3(grid), dim3(128), args, smem, s);
   if (tile_max == 512)
     return cudaLaunchCooperativeKernel((const void*)multi_pipe<512>, dim3(grid), dim3(512), args, smem, s);
-  return cudaLaunchCooperativeKernel((const void*)multi_pipe<256>, dim3(grid), dim3(256), args, smem, s);
+  const void* k = (const void*)multi_pipe<256>;
+  switch (lean_mode(A)) {
+    case 1: k = (const void*)multi_pipe<256, 1>; break;
+    case 2: k = (const void*)multi_pipe<256, 2>; break;
+    case 3: k = (const void*)multi_pipe<256, 3>; break;
+    case 4: k = (const void*)multi_pipe<256, 4>; break;
+    case 5: k = (const void*)multi_pipe<256, 5>; break;
+    case 6: k = (const void*)multi_pipe<256, 6>; break;
+    case 7: k = (const void*)multi_pipe<256, 7>; break;
+    case 8: k = (const void*)multi_pipe<256, 8>; break;
+    default: break;
+  }
+  return cudaLaunchCooperativeKernel(k, dim3(grid), dim3(256), args, smem, s);
 }
 
 
