@@ -470,6 +470,48 @@ def test_fused_tile_sizes_bitwise_and_two_pass_close(vx, which):
             assert np.array_equal(other[k].view(np.uint8), ref[k].view(np.uint8)), (form, tm, k)
 
 
+def _lean_scene(mode):
+    """A lattice of each lean step kernel's feature set: voxel contacts (bit
+    0), several bodies (bit 1), actuation with per-voxel phases (bit 2); and
+    two that take the generic kernel (actuation without phases, per-voxel
+    moduli)."""
+    if mode == "generic_act_no_phase":
+        sc = scenes.cantilever(n=(8, 5, 4))
+        sc.update(act_amplitude=10.0, act_period=300)
+        sc["palette"][:, 3] = 0.01
+        return sc
+    if mode == "generic_log_E":
+        return scenes.design_population(n_bodies=3, n=5, seed=2)
+    bits = mode - 1
+    if bits & 2:
+        sc = scenes.population(n_bodies=6, seed=5, lo=3, hi=8)
+    else:
+        sc = scenes.hollow_ball(R=8, t=3, drop=1)
+    sc["collide"] = bool(bits & 1)
+    if not bits & 4:
+        sc.update(act_amplitude=0.0, act_period=0)
+        sc["phase"] = None
+    elif sc.get("phase") is None:
+        sc.update(act_amplitude=15.0, act_period=400)
+        sc["palette"][:, 3] = 0.01
+        rng = np.random.default_rng(mode)
+        sc["phase"] = scenes.f32(rng.uniform(0.0, 6.28, scenes.n_occupied(sc)))
+    return sc
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6, 7, 8, "generic_act_no_phase", "generic_log_E"])
+def test_lean_step_kernels_bitwise_equal_generic(vx, mode):
+    """The 256-voxel pipelined step launches a lean instantiation with the
+    lattice's absent features fixed at compile time; every one gives the
+    bits of the generic kernel (the 128-voxel tiles always take it)."""
+    sc = _lean_scene(mode)
+    ref = run_form(vx, sc, 250, vx.FORM_PIPELINED, 128)
+    out = run_form(vx, sc, 250, vx.FORM_PIPELINED, 256)
+    assert np.abs(ref["vel"]).max() > 0
+    for k in ("offset", "quat", "vel", "angvel", "flags"):
+        assert np.array_equal(out[k].view(np.uint8), ref[k].view(np.uint8)), k
+
+
 # ---------------------------------------------------------------------------
 # batched form: many bodies, all steps in one launch
 # ---------------------------------------------------------------------------
