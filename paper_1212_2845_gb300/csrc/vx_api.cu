@@ -115,6 +115,7 @@ struct vx_sim {
   float* st = nullptr;     // two state buffers of NPLANE * pitch floats
   float* bf = nullptr;     // two-pass bond results (allocated on first use)
   int32_t* iperm = nullptr;
+  int32_t* perm = nullptr;  // internal -> canonical (state writes)
   int4* tile_a = nullptr;
   int4* tile_b = nullptr;
   int32_t* halo = nullptr;
@@ -999,7 +1000,7 @@ int vx_create(const vx_desc* desc, vx_sim** out) {
   int64_t N = L.N;
   s->pitch = (N + 31) / 32 * 32;
   if ((rc = dalloc(&s->st, 2 * NPLANE * s->pitch)) || (rc = dalloc(&s->flags, N)) || (rc = dalloc(&s->mat, N)) ||
-      (rc = dalloc(&s->lat, N)) || (rc = dalloc(&s->iperm, N)) || (rc = dalloc(&s->mask, N)) ||
+      (rc = dalloc(&s->lat, N)) || (rc = dalloc(&s->iperm, N)) || (rc = dalloc(&s->perm, N)) || (rc = dalloc(&s->mask, N)) ||
       (rc = dalloc(&s->mats, L.palette.size())) || (rc = dalloc(&s->dtb, L.n_bodies)) ||
       (rc = dalloc(&s->origin, 3 * L.n_bodies)) || (rc = dalloc(&s->status, 8)) ||
       (rc = dalloc(&s->vmax, L.n_bodies)) || (L.n_bodies > 1 && (rc = dalloc(&s->body, N)))) {
@@ -1015,6 +1016,7 @@ int vx_create(const vx_desc* desc, vx_sim** out) {
   }
   auto up = [&](void* d, const void* h, size_t n) { return cudaMemcpy(d, h, n, cudaMemcpyHostToDevice); };
   if (up(s->mat, mat.data(), N) || up(s->lat, lat.data(), N * 4) || up(s->iperm, s->T.iperm.data(), N * 4) ||
+      up(s->perm, s->T.perm.data(), N * 4) ||
       up(s->mask, s->T.mask.data(), N) || up(s->origin, L.origin.data(), 3 * L.n_bodies * 4) ||
       (s->body && up(s->body, body.data(), N * 4)) || cudaMemset(s->flags, 0, N) ||
       cudaMemset(s->status, 0, 32) || cudaMemset(s->vmax, 0, 4 * L.n_bodies) ||
@@ -1036,7 +1038,7 @@ void vx_destroy(vx_sim* s) {
   if (!s) return;
   cudaSetDevice(s->device);
   dfree(s->st); dfree(s->bf); dfree(s->flags); dfree(s->mat); dfree(s->lat); dfree(s->body); dfree(s->nbr);
-  dfree(s->iperm); dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds); dfree(s->mask);
+  dfree(s->iperm); dfree(s->perm); dfree(s->tile_a); dfree(s->tile_b); dfree(s->halo); dfree(s->plus); dfree(s->hbonds); dfree(s->mask);
   dfree(s->tdesc); dfree(s->hfix); dfree(s->vw); dfree(s->plus2);
   dfree(s->phase); dfree(s->logE); dfree(s->fext); dfree(s->mats); dfree(s->lut); dfree(s->dtb); dfree(s->origin);
   dfree(s->status); dfree(s->stage); dfree(s->surf); dfree(s->sidx); dfree(s->xq); dfree(s->cell); dfree(s->bucket);
@@ -1398,7 +1400,7 @@ int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_devi
   if (s->collide_on && (rc = alloc_collisions(s))) return rc;
   unsigned* dmax = s->collide_on ? s->dmax : nullptr;
   if (src_on_device) {
-    launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset, in->quat, in->vel, in->angvel,
+    launch_unpack_state(cur_state(s), s->pitch, N, s->perm, s->flags, in->offset, in->quat, in->vel, in->angvel,
                         in->flags, st, s->body, dmax);
     VX_CUDA(cudaGetLastError());
     return s->collide_on ? write_collisions(s, st) : VX_OK;
@@ -1414,7 +1416,7 @@ int vx_write_state_async(vx_sim* s, const vx_state_view* in, int32_t src_on_devi
   if (in->vel) VX_CUDA(cudaMemcpyAsync(vel, in->vel, 12 * (size_t)N, cudaMemcpyHostToDevice, st));
   if (in->angvel) VX_CUDA(cudaMemcpyAsync(w, in->angvel, 12 * (size_t)N, cudaMemcpyHostToDevice, st));
   if (in->flags) VX_CUDA(cudaMemcpyAsync(fl, in->flags, (size_t)N, cudaMemcpyHostToDevice, st));
-  launch_unpack_state(cur_state(s), s->pitch, N, s->iperm, s->flags, in->offset ? off : nullptr,
+  launch_unpack_state(cur_state(s), s->pitch, N, s->perm, s->flags, in->offset ? off : nullptr,
                       in->quat ? quat : nullptr, in->vel ? vel : nullptr, in->angvel ? w : nullptr,
                       in->flags ? fl : nullptr, st, s->body, dmax);
   VX_CUDA(cudaGetLastError());

@@ -17,39 +17,42 @@ __global__ void pack_state(const float* __restrict__ st, int64_t P, int N, const
   if (fl) fl[c] = flags[v];
 }
 
-// With dmax set (collisions on), the largest distance between a voxel's
-// written and current offsets is recorded per body (float bits, atomicMax:
-// the maximum does not depend on the order): one atomic per CTA when all its
-// voxels belong to one body, else per warp or per voxel.
+// Runs over the internal order (perm: internal -> canonical), so that the
+// state planes are written in runs and the caller's arrays are the ones read
+// out of order.  With dmax set (collisions on), the largest distance between
+// a voxel's written and current offsets is recorded per body (float bits,
+// atomicMax: the maximum does not depend on the order): one atomic per CTA
+// when all its voxels belong to one body (bodies are contiguous in the
+// internal order), else per voxel.
 __global__ void __launch_bounds__(256) unpack_state(float* __restrict__ st, int64_t P, int N,
-                                                    const int32_t* __restrict__ iperm, uint8_t* __restrict__ flags,
+                                                    const int32_t* __restrict__ perm, uint8_t* __restrict__ flags,
                                                     const float* off, const float* quat, const float* vel,
                                                     const float* angvel, const uint8_t* fl, const int32_t* body,
                                                     unsigned* dmax) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool active = c < N;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = v < N;
   float d2 = 0.f;
   int b = 0;
   if (active) {
-    const int64_t v = iperm[c];
+    const int64_t c = perm[v];
     if (off)
       for (int a = 0; a < 3; ++a) {
-        const float o1 = off[3 * (int64_t)c + a];
+        const float o1 = off[3 * c + a];
         if (dmax) {
           const float dd = __fsub_rn(o1, st[state_index(OX + a, v, P)]);
           d2 = __fmaf_rn(dd, dd, d2);
         }
         st[state_index(OX + a, v, P)] = o1;
       }
-    if (quat) for (int a = 0; a < 4; ++a) st[state_index(QW + a, v, P)] = quat[4 * (int64_t)c + a];
-    if (vel) for (int a = 0; a < 3; ++a) st[state_index(VX + a, v, P)] = vel[3 * (int64_t)c + a];
-    if (angvel) for (int a = 0; a < 3; ++a) st[state_index(WX + a, v, P)] = angvel[3 * (int64_t)c + a];
+    if (quat) for (int a = 0; a < 4; ++a) st[state_index(QW + a, v, P)] = quat[4 * c + a];
+    if (vel) for (int a = 0; a < 3; ++a) st[state_index(VX + a, v, P)] = vel[3 * c + a];
+    if (angvel) for (int a = 0; a < 3; ++a) st[state_index(WX + a, v, P)] = angvel[3 * c + a];
     if (fl) flags[v] = fl[c];
     if (body) b = body[v];
   }
   if (!dmax || !off) return;  // uniform over the grid
   const float d = sqrtf(d2);
-  const int b_first = body ? body[iperm[blockIdx.x * blockDim.x]] : 0;  // the CTA's first voxel exists
+  const int b_first = body ? body[blockIdx.x * blockDim.x] : 0;  // the CTA's first voxel exists
   float m = d;
   if (__syncthreads_and(!active || b == b_first)) {
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
@@ -112,11 +115,11 @@ void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* ipe
   pack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, iperm, flags, off, quat, vel, angvel, fl);
 }
 
-void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, uint8_t* flags, const float* off,
+void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* perm, uint8_t* flags, const float* off,
                          const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
                          cudaStream_t s, const int32_t* body, unsigned* dmax) {
   if (N > 0)
-    unpack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, iperm, flags, off, quat, vel, angvel, fl, body, dmax);
+    unpack_state<<<(N + 255) / 256, 256, 0, s>>>(st, pitch, N, perm, flags, off, quat, vel, angvel, fl, body, dmax);
 }
 
 void launch_set_velocity(float* st, int64_t pitch, int N, const uint8_t* flags, float vx, float vy, float vz,

@@ -229,10 +229,11 @@ void launch_flag_all(const CollideArgs& C, cudaStream_t s);
 // canonical to internal indices; any destination/source pointer may be null
 void launch_pack_state(const float* st, int64_t pitch, int N, const int32_t* iperm, const uint8_t* flags,
                        float* off, float* quat, float* vel, float* angvel, uint8_t* fl, cudaStream_t s);
-// With dmax (per body, float bits, zero at launch) the largest distance
-// between written and current offsets is recorded per body (body: per voxel,
+// The unpacking takes perm (internal -> canonical) instead of iperm.  With
+// dmax (per body, float bits, zero at launch) the largest distance between
+// written and current offsets is recorded per body (body: per voxel,
 // internal order, or nullptr for one body).
-void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* iperm, uint8_t* flags, const float* off,
+void launch_unpack_state(float* st, int64_t pitch, int N, const int32_t* perm, uint8_t* flags, const float* off,
                          const float* quat, const float* vel, const float* angvel, const uint8_t* fl,
                          cudaStream_t s, const int32_t* body = nullptr, unsigned* dmax = nullptr);
 // atomic max of |v| over the voxels into *out (float bits; zero it first)
